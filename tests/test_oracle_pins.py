@@ -1,0 +1,498 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix:
+closed-form spectra, hand-computed small cases, invariants (Arnoldi
+relation, orthogonality, GMRES monotonicity), textbook special cases (s = 1
+is CGS2-GMRES, m >= N terminates, dense LU agreement) and the values the
+paper prints for its worked examples (tests/golden/paper_pins.json).
+
+The last group plants mistakes in the oracle (on the CPU) and checks that
+some pin catches each of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import sgmres_oracle as O
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                   "paper_pins.json")))
+
+
+# ------------------------------------------------------------ generators
+def test_generator_nnz_closed_forms():
+    A = W.stencil2d(64, 64)
+    assert A.n == 4096 and A.nnz == 5 * 4096 - 4 * 64 == 20224
+    B = W.stencil3d_convdiff(16)
+    assert B.nnz == 7 * 16 ** 3 - 6 * 16 ** 2
+    C, _ = W.vardiff3d(12)
+    assert C.nnz == 7 * 12 ** 3 - 6 * 12 ** 2
+    D, _ = W.aniso2d(20)
+    assert D.nnz == 5 * 400 - 4 * 20
+    E, _ = W.random_band(50000, k=24, band=4096)
+    assert E.nnz == 25 * 50000
+
+
+def test_generator_row_sums_and_structure():
+    A = W.stencil3d_convdiff(8).to_scipy()
+    # interior row: 6 - 3*1.2 - 3*0.8 = 0; a corner row (0,0,0) has only
+    # the three downwind neighbours: 6 - 3*0.8
+    rs = np.asarray(A.sum(axis=1)).ravel()
+    i_int = 3 + 8 * 3 + 64 * 3
+    assert rs[i_int] == pytest.approx(0.0, abs=1e-14)
+    assert rs[0] == pytest.approx(6 - 2.4)
+    S = W.stencil2d(5, 4).to_scipy().toarray()
+    assert S[6, 5] == -1.1 and S[6, 7] == -0.9      # west / east
+    assert S[6, 1] == -1.1 and S[6, 11] == -0.9     # south / north
+    D, _ = W.aniso2d(16)
+    Ds = D.to_scipy()
+    assert abs(Ds - Ds.T).max() == 0.0
+    # diagonal = sum of 4 edge conductivities >= |off-diagonal row sum|
+    d = Ds.diagonal()
+    off = np.asarray(abs(Ds).sum(axis=1)).ravel() - d
+    assert np.all(d >= off - 1e-12)
+    E, _ = W.random_band(20000, k=24, band=4096)
+    Es = E.to_scipy()
+    d = Es.diagonal()
+    off = np.asarray(abs(Es).sum(axis=1)).ravel() - np.abs(d)
+    assert np.allclose(d, 1.1 * off)
+    rows = np.repeat(np.arange(E.n), 25)
+    assert np.all(np.abs(E.colind.astype(np.int64) - rows) <= 4096)
+    assert np.all(np.diff(E.colind.reshape(-1, 25), axis=1) > 0)
+    C, _ = W.vardiff3d(6, skew=0.1)
+    Cs = C.to_scipy()
+    K = (Cs - Cs.T) * 0.5
+    nz = K.data[np.abs(K.data) > 0]
+    assert np.allclose(np.abs(nz), 0.1)
+
+
+def _stencil2d_eigs(nx, ny, d, w, e, s, n_):
+    kx = np.arange(1, nx + 1)
+    ky = np.arange(1, ny + 1)
+    ex = 2 * math.sqrt(w * e) * np.cos(kx * np.pi / (nx + 1))
+    ey = 2 * math.sqrt(s * n_) * np.cos(ky * np.pi / (ny + 1))
+    return np.sort((d + ex[:, None] + ey[None, :]).ravel())
+
+
+def test_stencil_spectrum_closed_form():
+    """Separable nonsymmetric stencil with positive off-diagonal products:
+    eigenvalues d + 2 sqrt(ac) cos(k pi/(n+1)) summed over the axes."""
+    A = W.stencil2d(7, 5)
+    ev = np.sort(np.linalg.eigvals(A.to_scipy().toarray()).real)
+    assert np.allclose(ev, _stencil2d_eigs(7, 5, 4.0, -1.1, -0.9, -1.1, -0.9),
+                       atol=1e-12)
+
+
+def test_arnoldi_ritz_values_full_space():
+    """k = N Arnoldi steps: the Ritz values are the eigenvalues."""
+    A = W.stencil2d(4, 3)
+    op = O.as_operator(A)
+    q = np.random.default_rng(5).uniform(-1, 1, A.n)
+    H, steps = O.arnoldi_mgs(op, q / np.linalg.norm(q), A.n)
+    assert steps == A.n
+    rv = np.sort(O.ritz_values(H, steps).real)
+    ex = _stencil2d_eigs(4, 3, 4.0, -1.1, -0.9, -1.1, -0.9)
+    assert np.allclose(rv, ex, atol=1e-10)
+
+
+def test_ritz_values_inside_field_of_values():
+    """Ritz values lie in the field of values of A: their real parts are
+    bounded by the extreme eigenvalues of the symmetric part (A + A^T)/2
+    (for a non-normal A they may leave the spectral interval)."""
+    A = W.stencil2d(16, 16)
+    op = O.as_operator(A)
+    q = np.ones(A.n) / 16.0
+    H, steps = O.arnoldi_mgs(op, q, 10)
+    Ad = op.toarray()
+    fov = np.linalg.eigvalsh(0.5 * (Ad + Ad.T))
+    rv = O.ritz_values(H, steps)
+    assert np.all(rv.real >= fov[0] - 1e-10)
+    assert np.all(rv.real <= fov[-1] + 1e-10)
+
+
+# ------------------------------------------------------- Leja / gamma / E
+def test_leja_real_hand_example():
+    # |.| max -> 4; farthest from 4 -> 1; |x-4||x-1| ties (2 vs 3) -> larger
+    # real part first -> 3; then 2.
+    out = O.leja_order(np.array([2.0, 4.0, 1.0, 3.0]))
+    assert np.array_equal(out.real, [4.0, 1.0, 3.0, 2.0])
+
+
+def test_leja_complex_pair_adjacent():
+    th = np.array([1 - 2j, 3.0, -2.0, 1 + 2j])
+    out = O.leja_order(th)
+    # start 3 (|3| largest); |-2-3| = 5 > |1+2i-3| = 2.83 -> -2; then pair
+    assert np.allclose(out, [3.0, -2.0, 1 + 2j, 1 - 2j])
+
+
+def test_scaling_coefficients_closed_form():
+    th = np.array([4.0, 1.0, 1 + 2j, 1 - 2j])
+    tbar = (4 + 1 + 1 + 1) / 4.0
+    g = O.scaling_coefficients(th)
+    assert np.allclose(g, [abs(tbar - 4), abs(tbar - 1), abs(tbar - 1 - 2j),
+                           abs(tbar - 1 + 2j)])
+    # degenerate: one Ritz value -> gamma = 0 -> replaced by 1
+    assert O.scaling_coefficients(np.array([2.5]))[0] == 1.0
+    # symmetric triple: the middle one has gamma 0 -> mean of the others
+    g3 = O.scaling_coefficients(np.array([1.0, 2.0, 3.0]))
+    assert np.allclose(g3, [1.0, 1.0, 1.0])
+
+
+def test_estimator_two_values_by_hand():
+    eps = 2.0 ** -53
+    t1, t2 = 3.0, 1.0
+    tbar = 2.0
+    rho21 = abs(t2 - t1) / abs(tbar - t1)
+    E = np.array([[eps, eps], [1.0, eps * rho21]])
+    lg = O.estimator_log2_E(np.array([t1, t2]), eps)
+    assert np.allclose(np.exp2(lg), E, rtol=1e-14, atol=0)
+    nrm = O.estimator_column_norms(np.array([t1, t2]), eps)
+    assert np.allclose(nrm, np.linalg.norm(E, axis=0), rtol=1e-14)
+
+
+def test_estimator_three_values_by_hand():
+    eps = 1e-3
+    th = np.array([5.0, -1.0, 2.0])
+    tbar = 2.0
+    rho = lambda i, k: abs(th[i] - th[k]) / abs(tbar - th[k])
+    E = np.empty((3, 3))
+    for i in range(3):
+        for j in range(3):
+            ks = [k for k in range(j) if not (j > i and k == i)]
+            pr = np.prod([rho(i, k) for k in ks]) if ks else 1.0
+            E[i, j] = pr * (eps if j >= i else 1.0)
+    assert np.allclose(np.exp2(O.estimator_log2_E(th, eps)), E, rtol=1e-13)
+
+
+@pytest.mark.parametrize("key", ["test8_estimator_uniform",
+                                 "test8_estimator_lmax2000"])
+def test_estimator_paper_test8(key):
+    """Soft pin (paper's Test 8): the estimator's s0* and the column where
+    kappa(V_1:j) passes 1e8, with Ritz values from a 200-step Arnoldi
+    pre-pass from a ones start vector."""
+    gd = GOLD[key]
+    lam = np.linspace(1.0, 200.0, gd["n"])
+    lam[-1] = gd["lam_max"]
+    op = O.as_operator(W.diagonal(lam))
+    q = np.ones(gd["n"]) / math.sqrt(gd["n"])
+    H, steps = O.arnoldi_mgs(op, q, gd["n"])
+    ritz = O.leja_order(O.ritz_values(H, steps))
+    s0, _ = O.estimate_step_size(ritz, GOLD["omega"]["omega_est"])
+    assert abs(s0 - gd["s0_star"]) <= gd["s0_star_tol"]
+    th, gm = O.basis_shifts(O.BASIS_SCALED_NEWTON, ritz,
+                            O.scaling_coefficients(ritz))
+    kmax = min(gd["kappa_cross"] + gd["kappa_cross_tol"] + 2, gd["n"] - 1)
+    V, _ = O.mpk(op, q, kmax, th, gm)
+    cross = next(j for j in range(1, kmax + 2)
+                 if np.linalg.cond(V[:, :j]) > 1e8)
+    assert abs(cross - gd["kappa_cross"]) <= gd["kappa_cross_tol"]
+
+
+# ------------------------------------------------------- partial Cholesky
+def test_partial_cholesky_matches_cholesky_when_well_conditioned():
+    X = np.random.default_rng(1).standard_normal((200, 12))
+    G = X.T @ X
+    p, R, kap = O.partial_cholesky(G)
+    assert p == 12
+    assert np.allclose(R, np.linalg.cholesky(G).T, rtol=1e-12, atol=1e-12)
+    assert kap[0] == 1.0
+
+
+def test_partial_cholesky_stops_at_nonpositive_pivot():
+    G = np.diag([4.0, 1.0, -1.0, 1.0])
+    p, R, _ = O.partial_cholesky(G)
+    assert p == 2 and np.allclose(R, np.diag([2.0, 1.0]))
+    # a singular Gram: column 3 equals column 1 -> pivot 0
+    X = np.random.default_rng(2).standard_normal((50, 3))
+    X[:, 2] = X[:, 0]
+    p, _, _ = O.partial_cholesky(X.T @ X)
+    assert p == 2
+    # first pivot <= 0: nothing kept (happy breakdown)
+    p, _, _ = O.partial_cholesky(np.zeros((3, 3)))
+    assert p == 0
+
+
+def test_partial_cholesky_kappa_ramp():
+    """R = diag(10^0 .. 10^9): ICE is exact on a diagonal factor, kappa_j =
+    10^(j-1), and the first column with kappa > 1e7 is excluded."""
+    R = np.diag(10.0 ** np.arange(10))
+    p, Rp, kap = O.partial_cholesky(R.T @ R, omega=1e7)
+    assert p == 8
+    assert np.allclose(kap, 10.0 ** np.arange(9), rtol=1e-12)
+    p, _, _ = O.partial_cholesky(R.T @ R, omega=1e7, cond="svd")
+    assert p == 8
+
+
+def test_ice_bounds_svd():
+    """ICE never overestimates (its Delta is a lower bound of sigma_max and
+    its delta an upper bound of sigma_min) and stays within 10x of the SVD
+    value "generally" (Sec. 3.2): here at the 95th percentile of random
+    triangular factors, with a median near 1."""
+    rng = np.random.default_rng(3)
+    ratios = []
+    for trial in range(30):
+        n = 25
+        R = np.triu(rng.standard_normal((n, n))) + np.diag(
+            np.exp(rng.uniform(-4, 4, n)))
+        est = O.ICE(R[0, 0])
+        for j in range(1, n):
+            k = est.update(R[:j, j], R[j, j])
+            sv = np.linalg.svd(R[:j + 1, :j + 1], compute_uv=False)
+            ktrue = sv[0] / sv[-1]
+            assert k <= ktrue * (1 + 1e-10)
+            ratios.append(ktrue / k)
+    assert np.percentile(ratios, 95) < 10.0
+    assert np.median(ratios) < 1.5
+
+
+# --------------------------------------------------------------- MPK
+def test_mpk_diagonal_closed_form_with_pair():
+    """On a diagonal A, V_{j+1} is a polynomial in the eigenvalues; a
+    conjugate pair (a +- ib) contributes ((lam - a)^2 + b^2)/(g1 g2)."""
+    lam = np.linspace(0.5, 3.0, 40)
+    op = O.as_operator(W.diagonal(lam))
+    q = np.random.default_rng(4).uniform(-1, 1, 40)
+    th = np.array([2.0, 1 + 0.5j, 1 - 0.5j, 0.7])
+    gm = np.array([1.3, 0.9, 0.9, 1.7])
+    V, B = O.mpk(op, q, 4, th, gm)
+    assert np.allclose(V[:, 1], (lam - 2.0) * q / 1.3)
+    assert np.allclose(V[:, 2], (lam - 2.0) * (lam - 1.0) * q / (1.3 * 0.9))
+    assert np.allclose(V[:, 3], (lam - 2.0) * ((lam - 1.0) ** 2 + 0.25) * q
+                       / (1.3 * 0.9 * 0.9))
+    assert np.allclose(V[:, 4], (lam - 2.0) * ((lam - 1.0) ** 2 + 0.25)
+                       * (lam - 0.7) * q / (1.3 * 0.9 * 0.9 * 1.7))
+    assert np.allclose(op @ V[:, :4], V @ B, atol=1e-13)
+
+
+def test_mpk_change_of_basis_general_matrix():
+    A = W.stencil2d(10, 10)
+    op = O.as_operator(A)
+    q = np.ones(A.n) / 10.0
+    H, st = O.arnoldi_mgs(op, q, 12)
+    rz = O.leja_order(O.ritz_values(H, st))
+    th, gm = O.basis_shifts(O.BASIS_SCALED_NEWTON, rz,
+                            O.scaling_coefficients(rz))
+    V, B = O.mpk(op, q, 12, th, gm)
+    assert np.linalg.norm(op @ V[:, :12] - V @ B) < 1e-13 * np.linalg.norm(V)
+
+
+# ----------------------------------------------------------- block QR
+def test_block_qr_reproduces_block_and_is_orthonormal():
+    rng = np.random.default_rng(6)
+    Q, _ = np.linalg.qr(rng.standard_normal((300, 7)))
+    X = rng.standard_normal((300, 9))
+    bq = O.block_qr(Q, X)
+    assert bq.p1 == 9 and bq.p2 == 9
+    Qall = np.hstack([Q, bq.Qk])
+    assert O.loss_of_orthogonality(Qall) < 1e-13
+    recon = Q @ bq.R_top + bq.Qk @ bq.R_kk
+    assert np.allclose(recon, X, atol=1e-12)
+    assert np.allclose(np.tril(bq.R_kk, -1), 0.0)
+    assert np.all(np.diag(bq.R_kk) > 0)
+
+
+def test_block_qr_truncates_rank_deficient_block():
+    rng = np.random.default_rng(7)
+    Q, _ = np.linalg.qr(rng.standard_normal((300, 3)))
+    X = rng.standard_normal((300, 6))
+    X[:, 4] = X[:, 1] + 1e-12 * rng.standard_normal(300)
+    bq = O.block_qr(Q, X)
+    assert bq.p2 == 4
+    assert O.loss_of_orthogonality(np.hstack([Q, bq.Qk])) < 1e-13
+
+
+# ------------------------------------------------------------- solver
+def test_s1_is_mgs_gmres_on_stencil():
+    """s = 1: partial CholQR is a norm and the block QR is CGS2, so the
+    residual history equals MGS-GMRES to rounding (Sec. 3.3)."""
+    c = W.config_c1(32)
+    g = O.mgs_gmres(c["A"], c["b"], m=40, tol=1e-10)
+    r = O.adaptive_sgmres(c["A"], c["b"], m=40, s=1, tol=1e-10)
+    assert r.iters == g.iters and r.restarts == g.restarts
+    a, b = np.array(r.relres_hist), np.array(g.relres_hist)
+    assert np.max(np.abs(a - b)) <= 1e-12
+    assert np.max(np.abs(a[:40] - b[:40]) / b[:40]) <= 1e-10
+
+
+def test_s1_is_mgs_gmres_on_diagonal():
+    lam = np.linspace(0.1, 10, 2000)
+    b = np.random.default_rng(0).uniform(-1, 1, 2000)
+    g = O.mgs_gmres(W.diagonal(lam), b, m=50, tol=1e-10)
+    r = O.adaptive_sgmres(W.diagonal(lam), b, m=50, s=1, tol=1e-10)
+    a, bb = np.array(r.relres_hist), np.array(g.relres_hist)
+    assert a.size == bb.size and np.max(np.abs(a - bb)) <= 1e-12
+
+
+def test_c1_converges_with_invariants():
+    c = W.config_c1()
+    r = O.adaptive_sgmres(c["A"], c["b"], m=c["m"], s=c["s"], tol=c["tol"],
+                          diagnostics=True)
+    assert r.converged and r.final_relres <= 1e-10
+    assert max(r.loo) <= 1e-12            # LOO O(eps) at stable s
+    assert max(r.arnoldi_res) <= 1e-12    # A Q_j = Q_{j+1} H_j
+    # residual norms never increase inside a cycle (GMRES optimality)
+    h = np.array(r.relres_hist)
+    k = 0
+    for n_c in r.cycle_iters:
+        seg = h[k:k + n_c]
+        assert np.all(np.diff(seg) <= 1e-13 * seg[:-1])
+        k += n_c
+    assert k == h.size
+    # the implicit estimate at the end of the last cycle equals the true one
+    op = O.as_operator(c["A"])
+    assert np.linalg.norm(c["b"] - op @ r.x) / np.linalg.norm(c["b"]) \
+        == pytest.approx(r.final_relres, rel=1e-10)
+    assert h[-1] == pytest.approx(r.final_relres, rel=1e-3)
+
+
+def test_residuals_monotone_within_cycle():
+    c = W.config_c1(24)
+    r = O.adaptive_sgmres(c["A"], c["b"], m=200, s=8, tol=1e-10)
+    assert r.restarts == 0
+    h = np.array(r.relres_hist)
+    assert np.all(np.diff(h) <= 1e-13 * h[:-1])
+
+
+def test_tiny_system_matches_dense_lu_and_terminates():
+    """m >= N: GMRES reaches the exact solution within N columns."""
+    rng = np.random.default_rng(8)
+    n = 30
+    Ad = rng.standard_normal((n, n)) + 8 * np.eye(n)
+    import scipy.sparse as sp
+    A = sp.csr_matrix(Ad)
+    b = rng.standard_normal(n)
+    xs = O.dense_solve(A, b)
+    r = O.adaptive_sgmres(A, b, m=n, s=5, tol=1e-13)
+    assert r.converged and r.iters <= n
+    kappa = np.linalg.cond(Ad)
+    assert np.linalg.norm(r.x - xs) <= kappa * 1e-14 * np.linalg.norm(xs)
+
+
+def test_complex_spectrum_system():
+    """2x2 rotation blocks: eigenvalues a +- ib, so the Ritz values come in
+    conjugate pairs and the pair recurrence is exercised."""
+    rng = np.random.default_rng(9)
+    nb = 200
+    a = rng.uniform(1.0, 4.0, nb)
+    bb = rng.uniform(0.2, 1.5, nb)
+    import scipy.sparse as sp
+    blocks = [np.array([[a[k], bb[k]], [-bb[k], a[k]]]) for k in range(nb)]
+    A = sp.csr_matrix(sp.block_diag(blocks, format="csr"))
+    b = rng.uniform(-1, 1, 2 * nb)
+    r = O.adaptive_sgmres(A, b, m=80, s=12, tol=1e-10, diagnostics=True)
+    assert np.any(np.abs(r.ritz.imag) > 1e-3)
+    assert r.converged and max(r.loo) < 1e-12 and max(r.arnoldi_res) < 1e-12
+    assert np.linalg.norm(r.x - O.dense_solve(A, b)) < 1e-8 * np.linalg.norm(r.x)
+
+
+def test_zero_rhs():
+    c = W.config_c1(8)
+    r = O.adaptive_sgmres(c["A"], np.zeros(64), m=10, s=3)
+    assert r.converged and np.all(r.x == 0) and r.iters == 0
+
+
+def test_paper_test1_monomial_adapts_to_6():
+    """Paper Test 1: monomial basis with s0 = 10 adapts to s = 6."""
+    gd = GOLD["test1_diag_monomial"]
+    lam = np.linspace(gd["lam_lo"], gd["lam_hi"], gd["n"])
+    b = np.ones(gd["n"]) / math.sqrt(gd["n"])
+    r = O.adaptive_sgmres(W.diagonal(lam), b, m=100, s=gd["s0"], tol=1e-10,
+                          basis=O.BASIS_MONOMIAL, diagnostics=True)
+    full = [q for q, se in zip(r.s_hist, r.s_eff_hist)]
+    assert full[0] == gd["adapted_s"]
+    assert all(q == gd["adapted_s"] for q, se in zip(r.s_hist, r.s_eff_hist)
+               if se >= gd["adapted_s"])
+    assert max(r.loo) < 1e-12
+
+
+def test_paper_test3_scaled_newton_keeps_100():
+    """Paper Test 3: scaled Newton with s0 = 100 keeps s = 100."""
+    gd = GOLD["test3_diag_scaled_newton"]
+    lam = np.linspace(gd["lam_lo"], gd["lam_hi"], gd["n"])
+    b = np.ones(gd["n"]) / math.sqrt(gd["n"])
+    r = O.adaptive_sgmres(W.diagonal(lam), b, m=100, s=gd["s0"], tol=1e-10)
+    assert r.s_hist[0] == gd["adapted_s"] and r.p1_hist[0] == gd["adapted_s"]
+
+
+def test_estimator_drives_first_block():
+    c = W.config_c2(12)
+    r = O.adaptive_sgmres(c["A"], c["b"], m=60, s=0, tol=1e-10, s_min=4,
+                          s_max=30, diagnostics=True)
+    assert 4 <= r.s0 <= 30 and r.converged
+    assert max(r.loo) < 1e-12
+
+
+# ----------------------------------------------- planted-mistake checks
+def _pair_pin_fails():
+    try:
+        test_mpk_diagonal_closed_form_with_pair()
+    except AssertionError:
+        return True
+    return False
+
+
+def test_planted_pair_sign_is_caught(monkeypatch):
+    orig = O.mpk
+
+    def bad(A, q, s, theta, gamma):
+        # plant: drop the b^2 term of the second step of a pair
+        V, B = orig(A, q, s, theta, gamma)
+        for j in range(s):
+            if theta[j].imag < 0:
+                V[:, j + 1] = (A @ V[:, j] - theta[j].real * V[:, j]) \
+                    / gamma[j]
+        return V, B
+    monkeypatch.setattr(O, "mpk", bad)
+    assert _pair_pin_fails()
+
+
+def test_planted_hessenberg_term_is_caught(monkeypatch):
+    orig = O.assemble_hessenberg
+
+    def bad(H, i, R_top, R_kk, B):
+        # plant: forget the previous-columns correction
+        q = R_kk.shape[0]
+        Rbar = np.zeros((i + q, q + 1))
+        Rbar[i - 1, 0] = 1.0
+        Rbar[:i, 1:] = R_top
+        Rbar[i:, 1:] = R_kk
+        M = Rbar @ B[:q + 1, :q]
+        T = Rbar[i - 1:i + q - 1, :q]
+        import scipy.linalg as sla
+        H[:i + q, i - 1:i - 1 + q] = sla.solve_triangular(
+            T, M.T, trans="T", lower=False).T
+    monkeypatch.setattr(O, "assemble_hessenberg", bad)
+    c = W.config_c1(16)
+    r = O.adaptive_sgmres(c["A"], c["b"], m=40, s=6, tol=1e-10,
+                          diagnostics=True, max_iters=200)
+    assert (not r.converged) or max(r.arnoldi_res) > 1e-10
+
+
+def test_planted_ice_sign_is_caught(monkeypatch):
+    orig = O.ICE.update
+
+    def bad(self, v, gam):
+        return orig(self, -v, gam) if len(v) > 1 else orig(self, v, gam)
+    monkeypatch.setattr(O.ICE, "update", bad)
+    failed = False
+    try:
+        test_ice_bounds_svd()
+    except AssertionError:
+        failed = True
+    assert failed
+
+
+def test_planted_transposed_gram_is_caught(monkeypatch):
+    orig = O.block_qr
+
+    def bad(Q, X, omega=O.OMEGA, cond="ice"):
+        out = orig(Q, X, omega, cond)
+        out.R_top = out.R_top[:, ::-1].copy()   # plant: columns swapped
+        return out
+    monkeypatch.setattr(O, "block_qr", bad)
+    c = W.config_c1(16)
+    r = O.adaptive_sgmres(c["A"], c["b"], m=40, s=6, tol=1e-10,
+                          diagnostics=True, max_iters=200)
+    assert (not r.converged) or max(r.arnoldi_res) > 1e-10
