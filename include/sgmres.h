@@ -1,0 +1,248 @@
+/*
+ * sgmres.h -- C ABI of a single-GPU (sm_103a) adaptive s-step GMRES
+ * after Xu, Alonso and Darve, "A numerically stable communication-avoiding
+ * s-step GMRES algorithm" (arXiv 2303.08953).
+ *
+ * Problem statement (Alg. 4, REQUIRE/ENSURE): given a square sparse A
+ * (CSR), a right-hand side b, an initial guess x0, a restart length m, an
+ * initial step size s0 (or the estimator of Sec. 3.5), a polynomial basis
+ * (Sec. 3.4) and the condition bound Omega (Sec. 3.2), return x with
+ * ||b - A x||_2 / ||b - A x0||_2 <= tol.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an sg_status; no exception crosses the ABI.
+ *    On failure sg_last_error(h) gives a one-line message.
+ *  - Dense vectors are FP64 arrays of length n.  Dense matrices are
+ *    column-major with an explicit leading dimension (in elements).
+ *  - The caller owns every array it passes; the library copies what it
+ *    keeps (the matrix, on sg_analyze) and owns its own device workspace,
+ *    sized on first use and kept until sg_destroy.
+ *  - "stream" arguments are cudaStream_t values passed as void*; NULL
+ *    selects the handle's own stream.  Solver calls are stream-ordered and
+ *    return only after their results are complete (the small dense algebra
+ *    runs on the host between kernels, as in the paper).
+ *  - Indices are int32 (CSR requires nnz < 2^31).
+ */
+#ifndef SGMRES_H
+#define SGMRES_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SG_OK = 0,
+  SG_EINVAL = 1,    /* bad argument (null pointer, size, unsorted CSR ...) */
+  SG_ENOMEM = 2,    /* device or pinned-host allocation failed            */
+  SG_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed         */
+  SG_ENOCONV = 4,   /* iteration cap reached; x and the result are filled */
+  SG_ENUMERIC = 5,  /* NaN/Inf met in the data or the small algebra        */
+  SG_ESTATE = 6     /* call order violated (e.g. solve before analyze)     */
+} sg_status;
+
+/* Polynomial basis of the matrix powers kernel (Sec. 2 and Sec. 3.4):
+ * scaled Newton, Eq. (scalednewton) with gamma from Eq. (scalingcoeff);
+ * Newton, Eq. (newton) (gamma = 1); monomial, Eq. (monomial). */
+typedef enum {
+  SG_BASIS_SCALED_NEWTON = 0,
+  SG_BASIS_NEWTON = 1,
+  SG_BASIS_MONOMIAL = 2
+} sg_basis;
+
+/* Arithmetic of the Krylov basis.  FP64: everything in FP64.  FP32_IR:
+ * FP32 matrix powers and block orthogonalisation inside an FP64
+ * iterative-refinement loop (residual, Cholesky factors, Hessenberg least
+ * squares and the estimator stay FP64).  Not in the paper. */
+typedef enum { SG_PREC_FP64 = 0, SG_PREC_FP32_IR = 1 } sg_precision;
+
+typedef struct sg_handle sg_handle;
+
+/* Square CSR matrix, 0-based, columns sorted within each row. */
+typedef struct {
+  int32_t n;               /* rows = columns, >= 1                       */
+  int64_t nnz;             /* rowptr[n]; < 2^31                          */
+  const int32_t* rowptr;   /* n+1                                        */
+  const int32_t* colind;   /* nnz                                        */
+  const double* val;       /* nnz                                        */
+  int32_t on_device;       /* 1: the three arrays are device pointers    */
+} sg_csr;
+
+/* Inputs of Alg. 4. */
+typedef struct {
+  int32_t m;           /* restart length: Krylov columns per cycle (>= 1)  */
+  int32_t s;           /* > 0: initial step size s0; 0: estimator (Sec 3.5) */
+  int32_t s_min;       /* clamp of the estimated s0 (estimator only)       */
+  int32_t s_max;       /* Ritz values computed = s_max when s == 0         */
+  double tol;          /* target ||b-Ax||/||b-Ax0||                        */
+  int32_t max_iters;   /* cap on Krylov columns over all cycles (0: 50 m) */
+  double omega;        /* partial CholQR bound Omega (Sec. 3.2), 1e7       */
+  double omega_est;    /* estimator threshold (Sec. 3.5), 1e7              */
+  int32_t basis;       /* sg_basis                                         */
+  int32_t precision;   /* sg_precision                                     */
+  double inner_tol;    /* FP32_IR: relative tolerance of each inner solve  */
+  int32_t max_refine;  /* FP32_IR: cap on refinement steps                 */
+  int32_t vectors_on_device; /* 1: b/x/g/lam of sg_solve* are device ptrs */
+  void* stream;        /* cudaStream_t or NULL                             */
+} sg_opts;
+
+/* Outputs.  The array members are caller-owned buffers that may be NULL;
+ * each is filled up to its capacity, and the n_* counters give the true
+ * number of entries (which may exceed the capacity). */
+typedef struct {
+  int32_t converged;       /* 1 when the true relres <= tol                */
+  int32_t s0;              /* initial step size used (given or estimated)  */
+  int32_t iters;           /* Krylov columns over all cycles               */
+  int32_t restarts;        /* cycles - 1                                   */
+  int32_t refinements;     /* FP32_IR outer steps (0 for FP64)             */
+  double final_relres;     /* true ||b - A x|| / ||b - A x0||              */
+  /* per Krylov column: implicit relative residual |g_{j+1}| / beta0     */
+  int32_t hist_cap; double* relres_hist; int32_t n_hist;
+  /* per block: columns generated, kept by CholQR #1, kept by CholQR #2   */
+  int32_t blocks_cap; int32_t* s_eff_hist; int32_t* p1_hist;
+  int32_t* s_hist; int32_t n_blocks;
+  /* per cycle: true relative residual and columns used                   */
+  int32_t cycles_cap; double* cycle_relres; int32_t* cycle_iters;
+  int32_t n_cycles;
+  /* Leja-ordered Ritz values and the scaling coefficients gamma          */
+  int32_t ritz_cap; double* ritz_re; double* ritz_im; double* gamma;
+  int32_t n_ritz;
+  /* time spent per phase (ms, host wall clock around stream syncs)       */
+  double t_prepass_ms, t_mpk_ms, t_ortho_ms, t_host_ms, t_total_ms;
+} sg_result;
+
+/* ----------------------------------------------------------- lifecycle */
+/* Fill *o with the defaults (m=60, s=10, Omega=Omega_est=1e7, tol=1e-10,
+ * scaled Newton, FP64). */
+void sg_default_opts(sg_opts* o);
+
+/* Create a handle on CUDA device `device`.  Errors: SG_EINVAL (null out),
+ * SG_ECUDA (no such device / no driver). */
+sg_status sg_create(int device, sg_handle** out);
+
+/* Release the handle and all device memory it owns. NULL is a no-op. */
+void sg_destroy(sg_handle* h);
+
+/* Last error message of this handle ("" if none).  Valid until the next
+ * call on the handle. */
+const char* sg_last_error(const sg_handle* h);
+
+/* Ingest A (Sec. 2 input; CSR as in the paper's implementation): checks
+ * sizes, sorted in-range columns and int32 range, copies A to the device
+ * (FP64 values, plus FP32 values for SG_PREC_FP32_IR) and picks the SpMV
+ * variant from the row-length statistics.  Replaces any previous matrix.
+ * Errors: SG_EINVAL, SG_ENOMEM, SG_ECUDA. */
+sg_status sg_analyze(sg_handle* h, const sg_csr* A);
+
+/* ------------------------------------------------------------- solvers */
+/* Adaptive s-step GMRES(m) (Alg. 4 with restarts): solves A x = b.
+ * x holds x0 on entry and the solution on exit.  res may be NULL.
+ * Returns SG_OK when converged, SG_ENOCONV when max_iters was reached
+ * (x and res are still filled), SG_ENUMERIC on NaN/Inf. */
+sg_status sg_solve(sg_handle* h, const double* b, double* x,
+                   const sg_opts* opts, sg_result* res);
+
+/* Adjoint solve A^T lam = g with the same method on the transposed CSR,
+ * built on first use (not in the paper; gradient of a loss through
+ * x = A^-1 b).  lam holds the initial guess on entry. */
+sg_status sg_solve_adjoint(sg_handle* h, const double* g, double* lam,
+                           const sg_opts* opts, sg_result* res);
+
+/* Sampled outer product on A's pattern: dval[k] = -lam[row(k)] * x[col(k)]
+ * for every stored entry k, i.e. dL/dA_ij when x = A^-1 b and
+ * lam = A^-T dL/dx.  All three are device arrays (dval has nnz entries).
+ * Not in the paper. */
+sg_status sg_grad_values(sg_handle* h, const double* lam, const double* x,
+                         double* dval, void* stream);
+
+/* -------------------------------------------------- kernel-level calls
+ * Device-pointer entry points of the individual steps, with the layouts
+ * the solver uses.  They run on `stream` and return after enqueueing
+ * (no synchronisation) unless stated. */
+
+/* One Newton step of the matrix powers kernel (Eq. newtonrecurrence,
+ * plus the conjugate-pair form): y = (A x - theta x + c z) / gamma.
+ * z may be NULL when c == 0.  x, y, z: length-n device vectors; y must not
+ * alias x or z. */
+sg_status sg_spmv_newton(sg_handle* h, const double* x, const double* z,
+                         double* y, double theta, double c, double gamma,
+                         void* stream);
+
+/* r = b - A x (Alg. 4, first line). */
+sg_status sg_residual(sg_handle* h, const double* b, const double* x,
+                      double* r, void* stream);
+
+/* Matrix powers kernel (Sec. 2): V[:,0] = q, then s steps of the basis
+ * given by theta (Leja-ordered shifts; a conjugate pair appears as
+ * (a+ib, a-ib) in consecutive entries) and gamma.  V is n x (s+1),
+ * column-major with leading dimension ldv >= n. */
+sg_status sg_mpk(sg_handle* h, const double* q, double* V, int64_t ldv,
+                 int32_t s, const double* theta_re, const double* theta_im,
+                 const double* gamma, void* stream);
+
+/* Block dot product of BCGS (Alg. 4 'First BCGS'): W = Q^T X, with Q
+ * n x i (ldq), X n x s (ldx) and W i x s (ldw), all device memory.
+ * Deterministic split-n reduction through the handle's workspace.
+ * sym != 0 requires Q == X and fills W from its upper triangle. */
+sg_status sg_block_dot(sg_handle* h, int64_t n, const double* Q, int64_t ldq,
+                       int32_t i, const double* X, int64_t ldx, int32_t s,
+                       double* W, int32_t ldw, int32_t sym, void* stream);
+
+/* Block update of BCGS (Alg. 4): X <- beta X + alpha Q W, Q n x i,
+ * W i x s (device), X n x s.  X must not alias Q.  With upper != 0, W is
+ * upper triangular (i == s) and only its upper triangle is read: this is
+ * the triangular product Q_k = V Z^-1 of CholQR with W = Z^-1. */
+sg_status sg_block_update(sg_handle* h, int64_t n, const double* Q,
+                          int64_t ldq, int32_t i, const double* W,
+                          int32_t ldw, double* X, int64_t ldx, int32_t s,
+                          double alpha, double beta, int32_t upper,
+                          void* stream);
+
+/* Two-norm of a device vector, returned on the host (synchronises). */
+sg_status sg_nrm2(sg_handle* h, int64_t n, const double* x, double* out,
+                  void* stream);
+
+/* Number of kernels this library has launched in the process so far (a
+ * diagnostic for benchmarks: every launch goes through one counter). */
+int64_t sg_kernel_launches(void);
+
+/* ------------------------------------------- host small dense algebra
+ * Pure host functions (no handle, no GPU) used between kernels; exposed
+ * so they can be checked on their own. */
+
+/* Partial Cholesky with the ICE condition stop (Alg. 3, Sec. 3.2): G is
+ * s x s (ldg), R receives the p x p factor (column-major, ld = s), kappa
+ * the estimates kappa_1..kappa_p (and the rejected one, if any).  Returns
+ * p (0 when the first pivot is not positive). */
+int32_t sg_host_partial_cholesky(const double* G, int32_t ldg, int32_t s,
+                                 double omega, double* R, double* kappa);
+
+/* Eigenvalues of an upper Hessenberg k x k matrix (ldh) by the implicit
+ * double-shift QR iteration: the Ritz values of the Arnoldi pre-pass
+ * (Sec. 3.4).  Complex pairs are returned as exact conjugates.  Returns 0,
+ * or -1 when the iteration does not converge. */
+int32_t sg_host_hessenberg_eigvals(const double* H, int32_t ldh, int32_t k,
+                                   double* re, double* im);
+
+/* Leja order of k values with conjugate pairs adjacent (Sec. 3.4). */
+void sg_host_leja_order(int32_t k, const double* re, const double* im,
+                        double* out_re, double* out_im);
+
+/* gamma_i = |mean(theta) - theta_i| (Eq. scalingcoeff), degenerate
+ * values replaced by the mean of the others (1 if none). */
+void sg_host_scaling_coefficients(int32_t k, const double* re,
+                                  const double* im, double* gamma);
+
+/* Initial step size estimator (Sec. 3.5, Eq. auxiliarymatrix): column
+ * norms of E into norms (length k, may be NULL) and s0* = number of
+ * leading columns with ||E_j|| < omega_est, clamped to [s_min, s_max]. */
+int32_t sg_host_estimate_step(int32_t k, const double* re, const double* im,
+                              double eps, double omega_est, int32_t s_min,
+                              int32_t s_max, double* norms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SGMRES_H */

@@ -1,0 +1,441 @@
+"""Python binding of the sm_103a adaptive s-step GMRES library.
+
+Thin ctypes marshalling over the C ABI in include/sgmres.h (same names,
+without the ``sg_`` prefix).  Every step of the solver runs in the CUDA
+library; this module only passes pointers, sizes and the current torch
+stream.  Device memory comes from torch.  There is no CPU fallback: if the
+library is missing, importing the library raises.
+
+Dense matrices follow the library's column-major layout: an n x k matrix
+with leading dimension ld is held as a torch tensor of shape (k, ld) (its
+transpose, row-major), so column j is ``T[j]``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsgmres.so")
+
+SG_OK, SG_EINVAL, SG_ENOMEM, SG_ECUDA, SG_ENOCONV, SG_ENUMERIC, SG_ESTATE = range(7)
+STATUS_NAMES = {0: "SG_OK", 1: "SG_EINVAL", 2: "SG_ENOMEM", 3: "SG_ECUDA",
+                4: "SG_ENOCONV", 5: "SG_ENUMERIC", 6: "SG_ESTATE"}
+BASES = {"scaled_newton": 0, "newton": 1, "monomial": 2}
+PRECISIONS = {"fp64": 0, "fp32_ir": 1}
+
+EXPORTED = (
+    "sg_default_opts", "sg_create", "sg_destroy", "sg_last_error",
+    "sg_analyze", "sg_solve", "sg_solve_adjoint", "sg_grad_values",
+    "sg_spmv_newton", "sg_residual", "sg_mpk", "sg_block_dot",
+    "sg_block_update", "sg_nrm2", "sg_host_partial_cholesky",
+    "sg_host_hessenberg_eigvals", "sg_host_leja_order",
+    "sg_host_scaling_coefficients", "sg_host_estimate_step",
+    "sg_kernel_launches",
+)
+
+
+class SgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class sg_csr(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int64),
+                ("rowptr", C.c_void_p), ("colind", C.c_void_p),
+                ("val", C.c_void_p), ("on_device", C.c_int32)]
+
+
+class sg_opts(C.Structure):
+    _fields_ = [("m", C.c_int32), ("s", C.c_int32), ("s_min", C.c_int32),
+                ("s_max", C.c_int32), ("tol", C.c_double),
+                ("max_iters", C.c_int32), ("omega", C.c_double),
+                ("omega_est", C.c_double), ("basis", C.c_int32),
+                ("precision", C.c_int32), ("inner_tol", C.c_double),
+                ("max_refine", C.c_int32), ("vectors_on_device", C.c_int32),
+                ("stream", C.c_void_p)]
+
+
+_D = C.POINTER(C.c_double)
+_I = C.POINTER(C.c_int32)
+
+
+class sg_result(C.Structure):
+    _fields_ = [("converged", C.c_int32), ("s0", C.c_int32),
+                ("iters", C.c_int32), ("restarts", C.c_int32),
+                ("refinements", C.c_int32), ("final_relres", C.c_double),
+                ("hist_cap", C.c_int32), ("relres_hist", _D),
+                ("n_hist", C.c_int32),
+                ("blocks_cap", C.c_int32), ("s_eff_hist", _I),
+                ("p1_hist", _I), ("s_hist", _I), ("n_blocks", C.c_int32),
+                ("cycles_cap", C.c_int32), ("cycle_relres", _D),
+                ("cycle_iters", _I), ("n_cycles", C.c_int32),
+                ("ritz_cap", C.c_int32), ("ritz_re", _D), ("ritz_im", _D),
+                ("gamma", _D), ("n_ritz", C.c_int32),
+                ("t_prepass_ms", C.c_double), ("t_mpk_ms", C.c_double),
+                ("t_ortho_ms", C.c_double), ("t_host_ms", C.c_double),
+                ("t_total_ms", C.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is not built; run `python -c \"import "
+            "__graft_entry__ as g; g.build()\"` (needs nvcc)")
+    lib = C.CDLL(LIB_PATH)
+    vp, i32, i64, f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "sg_default_opts": (None, [C.POINTER(sg_opts)]),
+        "sg_create": (i32, [C.c_int, C.POINTER(vp)]),
+        "sg_destroy": (None, [vp]),
+        "sg_last_error": (C.c_char_p, [vp]),
+        "sg_analyze": (i32, [vp, C.POINTER(sg_csr)]),
+        "sg_solve": (i32, [vp, vp, vp, C.POINTER(sg_opts), C.POINTER(sg_result)]),
+        "sg_solve_adjoint": (i32, [vp, vp, vp, C.POINTER(sg_opts), C.POINTER(sg_result)]),
+        "sg_grad_values": (i32, [vp, vp, vp, vp, vp]),
+        "sg_spmv_newton": (i32, [vp, vp, vp, vp, f64, f64, f64, vp]),
+        "sg_residual": (i32, [vp, vp, vp, vp, vp]),
+        "sg_mpk": (i32, [vp, vp, vp, i64, i32, _D, _D, _D, vp]),
+        "sg_block_dot": (i32, [vp, i64, vp, i64, i32, vp, i64, i32, vp, i32, i32, vp]),
+        "sg_block_update": (i32, [vp, i64, vp, i64, i32, vp, i32, vp, i64, i32,
+                                  f64, f64, i32, vp]),
+        "sg_nrm2": (i32, [vp, i64, vp, _D, vp]),
+        "sg_host_partial_cholesky": (i32, [_D, i32, i32, f64, _D, _D]),
+        "sg_host_hessenberg_eigvals": (i32, [_D, i32, i32, _D, _D]),
+        "sg_host_leja_order": (None, [i32, _D, _D, _D, _D]),
+        "sg_host_scaling_coefficients": (None, [i32, _D, _D, _D]),
+        "sg_host_estimate_step": (i32, [i32, _D, _D, f64, f64, i32, i32, _D]),
+        "sg_kernel_launches": (i64, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def _ip(a: np.ndarray):
+    return a.ctypes.data_as(_I)
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(lib.sg_kernel_launches())
+
+
+# ------------------------------------------------------- host algebra
+def partial_cholesky(G, omega=1e7):
+    """Alg. 3 with the ICE stop: returns (p, R_p, kappas)."""
+    G = np.asfortranarray(G, dtype=np.float64)
+    s = G.shape[0]
+    R = np.zeros((s, s), order="F")
+    kap = np.zeros(max(s, 1))
+    p = lib.sg_host_partial_cholesky(_dp(G), s, s, omega, _dp(R), _dp(kap))
+    if p < 0:
+        raise SgError(SG_EINVAL, "partial_cholesky: bad arguments")
+    kk = min(s, p + 1)
+    return p, np.array(R[:p, :p]), kap[:kk].copy()
+
+
+def hessenberg_eigvals(H):
+    H = np.asfortranarray(H, dtype=np.float64)
+    k = H.shape[1]
+    re = np.zeros(k)
+    im = np.zeros(k)
+    rc = lib.sg_host_hessenberg_eigvals(_dp(H), H.shape[0], k, _dp(re), _dp(im))
+    if rc != 0:
+        raise SgError(SG_ENUMERIC, "Hessenberg QR did not converge")
+    return re + 1j * im
+
+
+def leja_order(theta):
+    th = np.asarray(theta, dtype=np.complex128)
+    re, im = np.ascontiguousarray(th.real), np.ascontiguousarray(th.imag)
+    ore, oim = np.zeros_like(re), np.zeros_like(im)
+    lib.sg_host_leja_order(th.size, _dp(re), _dp(im), _dp(ore), _dp(oim))
+    return ore + 1j * oim
+
+
+def scaling_coefficients(theta):
+    th = np.asarray(theta, dtype=np.complex128)
+    re, im = np.ascontiguousarray(th.real), np.ascontiguousarray(th.imag)
+    g = np.zeros_like(re)
+    lib.sg_host_scaling_coefficients(th.size, _dp(re), _dp(im), _dp(g))
+    return g
+
+
+def estimate_step(theta, eps=2.0 ** -53, omega_est=1e7, s_min=1, s_max=0):
+    th = np.asarray(theta, dtype=np.complex128)
+    re, im = np.ascontiguousarray(th.real), np.ascontiguousarray(th.imag)
+    norms = np.zeros(max(th.size, 1))
+    s0 = lib.sg_host_estimate_step(th.size, _dp(re), _dp(im), eps, omega_est,
+                                   s_min, s_max, _dp(norms))
+    return int(s0), norms[:th.size].copy()
+
+
+# ------------------------------------------------------------ solver
+@dataclass
+class SolveInfo:
+    status: int
+    converged: bool
+    s0: int
+    iters: int
+    restarts: int
+    refinements: int
+    final_relres: float
+    relres_hist: np.ndarray
+    s_eff_hist: np.ndarray
+    p1_hist: np.ndarray
+    s_hist: np.ndarray
+    cycle_relres: np.ndarray
+    cycle_iters: np.ndarray
+    ritz: np.ndarray
+    gamma: np.ndarray
+    times_ms: dict = field(default_factory=dict)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy: the legacy default stream
+
+
+def _stream_ptr(stream=None):
+    """cudaStream_t of a torch stream.  torch's default stream has handle
+    0, which the C ABI reads as "the handle's own stream"; it is passed as
+    cudaStreamLegacy instead so the work stays ordered with torch's."""
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream or CUDA_STREAM_LEGACY)
+
+
+class Solver:
+    """One handle of the C library bound to a CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self._h = C.c_void_p()
+        rc = lib.sg_create(device, C.byref(self._h))
+        if rc != SG_OK:
+            raise SgError(rc, f"sg_create(device={device}) failed")
+        self.device = device
+        self.n = None
+        self.nnz = None
+
+    def close(self):
+        if self._h:
+            lib.sg_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, allow=()):
+        if rc != SG_OK and rc not in allow:
+            raise SgError(rc, lib.sg_last_error(self._h).decode())
+        return rc
+
+    # -------------------------------------------------- ingest
+    def analyze(self, rowptr, colind, val, n=None):
+        """Ingest a CSR matrix.  Arrays may be numpy (host) or torch
+        tensors on this device (int32, int32, float64)."""
+        torch = _torch()
+        on_dev = isinstance(val, torch.Tensor) and val.is_cuda
+        keep = []
+        if on_dev:
+            rp, ci, v = (t.contiguous() for t in (rowptr, colind, val))
+            assert rp.dtype == torch.int32 and ci.dtype == torch.int32
+            assert v.dtype == torch.float64
+            keep = [rp, ci, v]
+            ptrs = [t.data_ptr() for t in keep]
+            nn = rp.numel() - 1
+            nnz = ci.numel()
+        else:
+            rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+            ci = np.ascontiguousarray(colind, dtype=np.int32)
+            v = np.ascontiguousarray(val, dtype=np.float64)
+            keep = [rp, ci, v]
+            ptrs = [a.ctypes.data for a in keep]
+            nn = rp.size - 1
+            nnz = ci.size
+        if n is not None:
+            assert n == nn
+        A = sg_csr(nn, nnz, ptrs[0], ptrs[1], ptrs[2], 1 if on_dev else 0)
+        self._check(lib.sg_analyze(self._h, C.byref(A)))
+        self.n, self.nnz = nn, nnz
+        return self
+
+    def analyze_csr(self, A):
+        """Ingest a workloads.CSR (host numpy arrays)."""
+        return self.analyze(A.rowptr, A.colind, A.val)
+
+    # -------------------------------------------------- solve
+    @staticmethod
+    def make_opts(m=60, s=10, s_min=1, s_max=0, tol=1e-10, max_iters=0,
+                  omega=1e7, omega_est=1e7, basis="scaled_newton",
+                  precision="fp64", inner_tol=1e-4, max_refine=20):
+        o = sg_opts()
+        lib.sg_default_opts(C.byref(o))
+        o.m, o.s, o.s_min, o.s_max = m, s, s_min, s_max
+        o.tol, o.max_iters = tol, max_iters
+        o.omega, o.omega_est = omega, omega_est
+        o.basis = BASES[basis] if isinstance(basis, str) else basis
+        o.precision = (PRECISIONS[precision] if isinstance(precision, str)
+                       else precision)
+        o.inner_tol, o.max_refine = inner_tol, max_refine
+        return o
+
+    def _solve(self, fn, b, x0, opts, stream, hist_cap):
+        torch = _torch()
+        on_dev = isinstance(b, torch.Tensor) and b.is_cuda
+        if on_dev:
+            assert b.dtype == torch.float64 and b.numel() == self.n
+            bb = b.contiguous()
+            x = (torch.zeros_like(bb) if x0 is None
+                 else x0.to(torch.float64).contiguous().clone())
+            opts.vectors_on_device = 1
+            opts.stream = _stream_ptr(stream)
+            bp, xp = bb.data_ptr(), x.data_ptr()
+        else:
+            bb = np.ascontiguousarray(b, dtype=np.float64)
+            x = (np.zeros(self.n) if x0 is None
+                 else np.array(x0, dtype=np.float64, copy=True))
+            opts.vectors_on_device = 0
+            opts.stream = (_stream_ptr(stream) if stream is not None else None)
+            bp, xp = bb.ctypes.data, x.ctypes.data
+        res = sg_result()
+        hist = np.zeros(hist_cap)
+        nb = hist_cap
+        s_eff = np.zeros(nb, np.int32)
+        p1 = np.zeros(nb, np.int32)
+        sh = np.zeros(nb, np.int32)
+        cyc = np.zeros(nb)
+        cyi = np.zeros(nb, np.int32)
+        rcap = max(opts.s_max, opts.s, opts.m) + 1
+        rre, rim, gam = np.zeros(rcap), np.zeros(rcap), np.zeros(rcap)
+        res.hist_cap, res.relres_hist = hist_cap, _dp(hist)
+        res.blocks_cap, res.s_eff_hist, res.p1_hist, res.s_hist = nb, _ip(s_eff), _ip(p1), _ip(sh)
+        res.cycles_cap, res.cycle_relres, res.cycle_iters = nb, _dp(cyc), _ip(cyi)
+        res.ritz_cap, res.ritz_re, res.ritz_im, res.gamma = rcap, _dp(rre), _dp(rim), _dp(gam)
+        rc = fn(self._h, C.c_void_p(bp), C.c_void_p(xp), C.byref(opts),
+                C.byref(res))
+        self._check(rc, allow=(SG_ENOCONV,))
+        nh = min(res.n_hist, hist_cap)
+        nbk = min(res.n_blocks, nb)
+        nc = min(res.n_cycles, nb)
+        nr = min(res.n_ritz, rcap)
+        info = SolveInfo(
+            status=rc, converged=bool(res.converged), s0=res.s0,
+            iters=res.iters, restarts=res.restarts,
+            refinements=res.refinements, final_relres=res.final_relres,
+            relres_hist=hist[:nh].copy(), s_eff_hist=s_eff[:nbk].copy(),
+            p1_hist=p1[:nbk].copy(), s_hist=sh[:nbk].copy(),
+            cycle_relres=cyc[:nc].copy(), cycle_iters=cyi[:nc].copy(),
+            ritz=rre[:nr] + 1j * rim[:nr], gamma=gam[:nr].copy(),
+            times_ms=dict(prepass=res.t_prepass_ms, mpk=res.t_mpk_ms,
+                          ortho=res.t_ortho_ms, host=res.t_host_ms,
+                          total=res.t_total_ms))
+        return x, info
+
+    def solve(self, b, x0=None, stream=None, hist_cap=1 << 16, **kw):
+        """Solve A x = b (Alg. 4 with restarts).  b: numpy (host) or a
+        float64 CUDA tensor.  Returns (x, SolveInfo)."""
+        return self._solve(lib.sg_solve, b, x0, self.make_opts(**kw), stream,
+                           hist_cap)
+
+    def solve_adjoint(self, g, lam0=None, stream=None, hist_cap=1 << 16, **kw):
+        """Solve A^T lam = g with the same method (transposed CSR)."""
+        return self._solve(lib.sg_solve_adjoint, g, lam0, self.make_opts(**kw),
+                           stream, hist_cap)
+
+    def grad_values(self, lam, x, out=None, stream=None):
+        """dval[k] = -lam[row(k)] x[col(k)] on A's pattern (device)."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty(self.nnz, dtype=torch.float64, device=lam.device)
+        self._check(lib.sg_grad_values(self._h, C.c_void_p(lam.data_ptr()),
+                                       C.c_void_p(x.data_ptr()),
+                                       C.c_void_p(out.data_ptr()),
+                                       _stream_ptr(stream)))
+        return out
+
+    # ------------------------------------------------ kernel-level calls
+    def spmv_newton(self, x, theta=0.0, gamma=1.0, z=None, c=0.0, out=None,
+                    stream=None):
+        torch = _torch()
+        y = torch.empty_like(x) if out is None else out
+        self._check(lib.sg_spmv_newton(
+            self._h, C.c_void_p(x.data_ptr()),
+            C.c_void_p(z.data_ptr() if z is not None else 0),
+            C.c_void_p(y.data_ptr()), theta, c, gamma, _stream_ptr(stream)))
+        return y
+
+    def residual(self, b, x, out=None, stream=None):
+        torch = _torch()
+        r = torch.empty_like(b) if out is None else out
+        self._check(lib.sg_residual(self._h, C.c_void_p(b.data_ptr()),
+                                    C.c_void_p(x.data_ptr()),
+                                    C.c_void_p(r.data_ptr()),
+                                    _stream_ptr(stream)))
+        return r
+
+    def mpk(self, q, s, theta, gamma, stream=None):
+        """V (as a (s+1, n) tensor, row j = column j) of Sec. 2's MPK."""
+        torch = _torch()
+        th = np.asarray(theta, dtype=np.complex128)
+        re = np.ascontiguousarray(th.real[:s])
+        im = np.ascontiguousarray(th.imag[:s])
+        gm = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64)[:s])
+        V = torch.empty((s + 1, self.n), dtype=torch.float64, device=q.device)
+        self._check(lib.sg_mpk(self._h, C.c_void_p(q.data_ptr()),
+                               C.c_void_p(V.data_ptr()), self.n, s, _dp(re),
+                               _dp(im), _dp(gm), _stream_ptr(stream)))
+        return V
+
+    def block_dot(self, Qt, Xt, sym=False, stream=None):
+        """W = Q^T X for column-major Q (tensor (i, ld)) and X ((s, ld));
+        returns W as an (s, i) tensor (column-major i x s)."""
+        torch = _torch()
+        i, ldq = Qt.shape
+        s, ldx = Xt.shape
+        n = min(ldq, ldx) if self.n is None else self.n
+        W = torch.empty((s, i), dtype=torch.float64, device=Qt.device)
+        self._check(lib.sg_block_dot(
+            self._h, n, C.c_void_p(Qt.data_ptr()), ldq, i,
+            C.c_void_p(Xt.data_ptr()), ldx, s, C.c_void_p(W.data_ptr()), i,
+            1 if sym else 0, _stream_ptr(stream)))
+        return W
+
+    def block_update(self, Qt, Wt, Xt, alpha=-1.0, beta=1.0, upper=False,
+                     n=None, stream=None):
+        """X = beta X + alpha Q W in place (X as an (s, ld) tensor, W as
+        (s, i) = column-major i x s)."""
+        i, ldq = Qt.shape
+        s, ldx = Xt.shape
+        n = n if n is not None else (self.n if self.n is not None else ldq)
+        self._check(lib.sg_block_update(
+            self._h, n, C.c_void_p(Qt.data_ptr()), ldq, i,
+            C.c_void_p(Wt.data_ptr()), i, C.c_void_p(Xt.data_ptr()), ldx, s,
+            alpha, beta, 1 if upper else 0, _stream_ptr(stream)))
+        return Xt
+
+    def nrm2(self, x, stream=None):
+        out = C.c_double()
+        self._check(lib.sg_nrm2(self._h, x.numel(), C.c_void_p(x.data_ptr()),
+                                C.byref(out), _stream_ptr(stream)))
+        return out.value

@@ -1,0 +1,370 @@
+// Tall-skinny dense kernels of the block orthogonalisation (Alg. 4):
+//   block_dot:    W = Q^T X   (BCGS projections and the CholQR Gram
+//                 matrices), a reduction over the n rows split across
+//                 CTAs with per-split partial tiles summed in fixed order;
+//   block_update: X = beta X + alpha Q W (BCGS update; with an upper
+//                 triangular W = Z^-1 it is the CholQR product V Z^-1).
+//
+// FP64 on this chip is bound by the FP64 pipe, not by HBM (the arithmetic
+// intensity of W = Q^T X is ~i s / (4 (i+s)) flop/B), so the tiles are
+// small (32 x 32 outputs per CTA, 2 x 2 per thread): the FP64 pipe stays
+// saturated while padding waste and the Gram matrices' redundant lower
+// tiles stay small.  Narrow shapes get their own tiles: for i <= 8 a
+// warp-per-row layout lets whole warps skip padded rows, and for s <= 8 a
+// 64 x 8 tile reads Q once without padding the columns.
+//
+// FP32 data: projections accumulate in FP32 per 32-row stage and fold the
+// stage sums into a compensated total; Gram matrices (EXACT) form every
+// product exactly (p = a b rounded plus its FMA remainder) and add it with
+// a two-sum, so the Gram of FP32 vectors is accurate to about eps_32^2
+// relative to the sum of |products| -- the accuracy the partial Cholesky
+// bound of the FP32 basis relies on.
+#include "sg_internal.h"
+
+namespace sg {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int BK = 32;  // rows of Q/X per shared-memory stage
+
+// two-sum: s + e == a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// C_part[z] (M x N, column-major) = A(k0:k1, :)^T B(k0:k1, :)
+// Tile BM x BN, thread tile TM x TN; MW: thread rows vary across warps
+// (whole warps idle on padded rows).
+template <int BM, int BN, int TM, int TN, bool MW, bool EXACT, typename T>
+__global__ void __launch_bounds__(kThreads)
+dot_tile_kernel(int64_t K, int M, int N, const T* __restrict__ A,
+                int64_t lda, const T* __restrict__ B, int64_t ldb,
+                double* __restrict__ part, int64_t rows_per_split, int sym) {
+  constexpr bool kF32 = sizeof(T) == 4;
+  constexpr int TMN = BM / TM, TNN = BN / TN;
+  static_assert(TMN * TNN == kThreads, "thread layout");
+  if (sym && blockIdx.x > blockIdx.y) return;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int64_t k0 = blockIdx.z * rows_per_split;
+  const int64_t k1 = (k0 + rows_per_split < K) ? k0 + rows_per_split : K;
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN + 1];
+  const int tid = threadIdx.x;
+  const int tx = MW ? tid / TNN : tid % TMN;
+  const int ty = MW ? tid % TNN : tid / TMN;
+  const bool active = (m0 + tx * TM) < M;
+  T acc[TM][TN], comp[TM][TN];
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TN; ++b) { acc[a][b] = T(0); comp[a][b] = T(0); }
+  for (int64_t kb = k0; kb < k1; kb += BK) {
+    for (int e = tid; e < BK * BM; e += kThreads) {
+      const int kk = e % BK, mm = e / BK;
+      const int64_t k = kb + kk;
+      const int m = m0 + mm;
+      As[kk][mm] = (k < k1 && m < M) ? A[k + m * lda] : T(0);
+    }
+    for (int e = tid; e < BK * BN; e += kThreads) {
+      const int kk = e % BK, nn = e / BK;
+      const int64_t k = kb + kk;
+      const int nc = n0 + nn;
+      Bs[kk][nn] = (k < k1 && nc < N) ? B[k + nc * ldb] : T(0);
+    }
+    __syncthreads();
+    if (active) {
+      if (EXACT) {
+#pragma unroll 4
+        for (int kk = 0; kk < BK; ++kk) {
+          T av[TM], bv[TN];
+#pragma unroll
+          for (int a = 0; a < TM; ++a) av[a] = As[kk][tx * TM + a];
+#pragma unroll
+          for (int b = 0; b < TN; ++b) bv[b] = Bs[kk][ty * TN + b];
+#pragma unroll
+          for (int a = 0; a < TM; ++a)
+#pragma unroll
+            for (int b = 0; b < TN; ++b) {
+              const float p = av[a] * bv[b];
+              const float pe = fmaf(av[a], bv[b], -p);  // exact remainder
+              float s, e;
+              two_sum(acc[a][b], p, s, e);
+              acc[a][b] = s;
+              comp[a][b] += e + pe;
+            }
+        }
+      } else {
+        T st[TM][TN];
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+          for (int b = 0; b < TN; ++b) st[a][b] = kF32 ? T(0) : acc[a][b];
+#pragma unroll 8
+        for (int kk = 0; kk < BK; ++kk) {
+          T av[TM], bv[TN];
+#pragma unroll
+          for (int a = 0; a < TM; ++a) av[a] = As[kk][tx * TM + a];
+#pragma unroll
+          for (int b = 0; b < TN; ++b) bv[b] = Bs[kk][ty * TN + b];
+#pragma unroll
+          for (int a = 0; a < TM; ++a)
+#pragma unroll
+            for (int b = 0; b < TN; ++b) st[a][b] = fma(av[a], bv[b], st[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+          for (int b = 0; b < TN; ++b) {
+            if (kF32) {  // compensated fold of the stage sum: acc - comp
+              const T y = st[a][b] - comp[a][b];
+              const T t = acc[a][b] + y;
+              comp[a][b] = (t - acc[a][b]) - y;
+              acc[a][b] = t;
+            } else {
+              acc[a][b] = st[a][b];
+            }
+          }
+      }
+    }
+    __syncthreads();
+  }
+  double* P = part + static_cast<int64_t>(blockIdx.z) * M * N;
+#pragma unroll
+  for (int a = 0; a < TM; ++a)
+#pragma unroll
+    for (int b = 0; b < TN; ++b) {
+      const int m = m0 + tx * TM + a, nc = n0 + ty * TN + b;
+      if (m < M && nc < N) {
+        double v;
+        if (EXACT) v = static_cast<double>(acc[a][b]) + static_cast<double>(comp[a][b]);
+        else v = static_cast<double>(acc[a][b]) - static_cast<double>(comp[a][b]);
+        P[m + static_cast<int64_t>(nc) * M] = v;
+      }
+    }
+}
+
+// W(m, n) = sum_z part[z](m, n) in split order; sym reads the upper
+// element for both (m, n) and (n, m).
+__global__ void reduce_parts_kernel(int M, int N, int S,
+                                    const double* __restrict__ part,
+                                    double* __restrict__ W, int ldw, int sym) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= M * N) return;
+  const int m = idx % M, n = idx / M;
+  int sm = m, sn = n;
+  if (sym && m > n) { sm = n; sn = m; }
+  double acc = 0.0;
+  const int64_t MN = static_cast<int64_t>(M) * N;
+  for (int z = 0; z < S; ++z) acc += part[z * MN + sm + static_cast<int64_t>(sn) * M];
+  W[m + static_cast<int64_t>(n) * ldw] = acc;
+}
+
+enum Cfg { CFG_SQ = 0, CFG_NARROW_M = 1, CFG_NARROW_N = 2 };
+
+struct DotPlan {
+  int cfg, BM, BN, tm, tn, S;
+  int64_t rows;
+};
+
+DotPlan plan_dot(int64_t n, int i, int s) {
+  DotPlan p;
+  if (i <= 8) { p.cfg = CFG_NARROW_M; p.BM = 8; p.BN = 32; }
+  else if (s <= 8) { p.cfg = CFG_NARROW_N; p.BM = 64; p.BN = 8; }
+  else { p.cfg = CFG_SQ; p.BM = 32; p.BN = 32; }
+  p.tm = (i + p.BM - 1) / p.BM;
+  p.tn = (s + p.BN - 1) / p.BN;
+  const int64_t tiles = static_cast<int64_t>(p.tm) * p.tn;
+  const int64_t target = static_cast<int64_t>(device_sm_count()) * 6;
+  int64_t S = (target + tiles - 1) / tiles;
+  const int64_t maxS = (n + 4 * BK - 1) / (4 * BK);  // >= 4 stages per split
+  if (S > maxS) S = maxS;
+  if (S < 1) S = 1;
+  if (S > 4096) S = 4096;
+  int64_t rows = (n + S - 1) / S;
+  rows = (rows + BK - 1) / BK * BK;
+  S = (n + rows - 1) / rows;
+  if (S < 1) S = 1;
+  p.S = static_cast<int>(S);
+  p.rows = rows;
+  return p;
+}
+
+template <bool EXACT, typename T>
+void launch_dot(const DotPlan& p, cudaStream_t st, int64_t n, int i, int s,
+                const T* Q, int64_t ldq, const T* X, int64_t ldx, double* part,
+                bool sym) {
+  dim3 grid(p.tm, p.tn, p.S);
+  const int sy = sym ? 1 : 0;
+  switch (p.cfg) {
+    case CFG_NARROW_M:
+      dot_tile_kernel<8, 32, 1, 1, true, EXACT, T><<<grid, kThreads, 0, st>>>(
+          n, i, s, Q, ldq, X, ldx, part, p.rows, 0);
+      break;
+    case CFG_NARROW_N:
+      dot_tile_kernel<64, 8, 2, 1, false, EXACT, T><<<grid, kThreads, 0, st>>>(
+          n, i, s, Q, ldq, X, ldx, part, p.rows, 0);
+      break;
+    default:
+      dot_tile_kernel<32, 32, 2, 2, false, EXACT, T><<<grid, kThreads, 0, st>>>(
+          n, i, s, Q, ldq, X, ldx, part, p.rows, sy);
+  }
+  SG_LAUNCH_CHECK();
+}
+
+template <typename T>
+void block_dot_impl(int64_t n, const T* Q, int64_t ldq, int i, const T* X,
+                    int64_t ldx, int s, double* W, int ldw, bool sym,
+                    double* part, int64_t part_cap, cudaStream_t st) {
+  if (i <= 0 || s <= 0) return;
+  if (n <= 0) {
+    for (int c = 0; c < s; ++c)
+      SG_CUDA(cudaMemsetAsync(W + static_cast<int64_t>(c) * ldw, 0,
+                              sizeof(double) * i, st));
+    return;
+  }
+  DotPlan p = plan_dot(n, i, s);
+  const bool exact = sym && sizeof(T) == 4;   // Gram of FP32 vectors
+  if (sym && (p.cfg != CFG_SQ || i != s)) sym = false;
+  SG_REQUIRE(static_cast<int64_t>(p.S) * i * s <= part_cap, SG_EINVAL,
+             "block_dot: workspace too small");
+  if (exact) launch_dot<true, float>(p, st, n, i, s, reinterpret_cast<const float*>(Q), ldq,
+                                     reinterpret_cast<const float*>(X), ldx, part, sym);
+  else launch_dot<false, T>(p, st, n, i, s, Q, ldq, X, ldx, part, sym);
+  const int tot = i * s;
+  reduce_parts_kernel<<<(tot + 255) / 256, 256, 0, st>>>(i, s, p.S, part, W,
+                                                         ldw, sym ? 1 : 0);
+  SG_LAUNCH_CHECK();
+}
+
+// --------------------------------------------------------- block_update
+// C(r0:r0+UR, n0:n0+UN) = beta C + alpha A(rows, :) B(:, cols); thread
+// tile TR rows x TN cols; the inner dimension M (= i) is staged UK at a
+// time.
+constexpr int UK = 16;
+
+template <int UR, int UN, int TR, int TN, typename T>
+__global__ void __launch_bounds__(kThreads)
+update_kernel(int64_t K, int M, int N, const T* __restrict__ A, int64_t lda,
+              const double* __restrict__ B, int ldb, T* __restrict__ C,
+              int64_t ldc, double alpha, double beta, int upper) {
+  constexpr int TRN = UR / TR, TNN = UN / TN;
+  static_assert(TRN * TNN == kThreads, "thread layout");
+  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * UR;
+  const int n0 = blockIdx.y * UN;
+  __shared__ T As[UK][UR + 2];
+  __shared__ T Bs[UK][UN + 1];
+  const int tid = threadIdx.x;
+  const int tx = tid % TRN, ty = tid / TRN;
+  T acc[TR][TN];
+#pragma unroll
+  for (int a = 0; a < TR; ++a)
+#pragma unroll
+    for (int b = 0; b < TN; ++b) acc[a][b] = T(0);
+  const int mend = upper ? ((n0 + UN < M) ? n0 + UN : M) : M;
+  for (int mb = 0; mb < mend; mb += UK) {
+    for (int e = tid; e < UK * UR; e += kThreads) {
+      const int rr = e % UR, mm = e / UR;
+      const int64_t r = r0 + rr;
+      const int m = mb + mm;
+      As[mm][rr] = (r < K && m < mend) ? A[r + m * lda] : T(0);
+    }
+    for (int e = tid; e < UK * UN; e += kThreads) {
+      const int mm = e % UK, nn = e / UK;
+      const int m = mb + mm, nc = n0 + nn;
+      T v = T(0);
+      if (m < mend && nc < N && !(upper && m > nc)) v = static_cast<T>(B[m + nc * ldb]);
+      Bs[mm][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int mm = 0; mm < UK; ++mm) {
+      T av[TR], bv[TN];
+#pragma unroll
+      for (int a = 0; a < TR; ++a) av[a] = As[mm][tx * TR + a];
+#pragma unroll
+      for (int b = 0; b < TN; ++b) bv[b] = Bs[mm][ty * TN + b];
+#pragma unroll
+      for (int a = 0; a < TR; ++a)
+#pragma unroll
+        for (int b = 0; b < TN; ++b) acc[a][b] = fma(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int b = 0; b < TN; ++b) {
+    const int nc = n0 + ty * TN + b;
+    if (nc >= N) continue;
+#pragma unroll
+    for (int a = 0; a < TR; ++a) {
+      const int64_t r = r0 + tx * TR + a;
+      if (r >= K) continue;
+      T* cp = C + r + nc * ldc;
+      T v = static_cast<T>(alpha) * acc[a][b];
+      if (beta != 0.0) v = fma(static_cast<T>(beta), *cp, v);
+      *cp = v;
+    }
+  }
+}
+
+template <typename T>
+void block_update_impl(int64_t n, const T* Q, int64_t ldq, int i,
+                       const double* W, int ldw, T* X, int64_t ldx, int s,
+                       double alpha, double beta, bool upper,
+                       cudaStream_t st) {
+  if (n <= 0 || s <= 0) return;
+  if (i <= 0) {
+    if (beta == 1.0) return;
+    alpha = 0.0;  // X = beta X
+  }
+  const int ii = i > 0 ? i : 0;
+  if (s <= 8) {
+    dim3 grid(static_cast<unsigned>((n + 127) / 128), 1);
+    update_kernel<128, 8, 4, 1, T><<<grid, kThreads, 0, st>>>(
+        n, ii, s, Q, ldq, W, ldw, X, ldx, alpha, beta, upper ? 1 : 0);
+  } else {
+    dim3 grid(static_cast<unsigned>((n + 63) / 64), (s + 31) / 32);
+    update_kernel<64, 32, 4, 2, T><<<grid, kThreads, 0, st>>>(
+        n, ii, s, Q, ldq, W, ldw, X, ldx, alpha, beta, upper ? 1 : 0);
+  }
+  SG_LAUNCH_CHECK();
+}
+
+}  // namespace
+
+int64_t block_dot_part_size(int64_t n, int i, int s) {
+  DotPlan p = plan_dot(n, i, s);
+  return static_cast<int64_t>(p.S) * i * s;
+}
+
+void block_dot(int64_t n, const double* Q, int64_t ldq, int i,
+               const double* X, int64_t ldx, int s, double* W, int ldw,
+               bool sym, double* part, int64_t part_cap, cudaStream_t st) {
+  block_dot_impl<double>(n, Q, ldq, i, X, ldx, s, W, ldw, sym, part, part_cap,
+                         st);
+}
+
+void block_dot32(int64_t n, const float* Q, int64_t ldq, int i,
+                 const float* X, int64_t ldx, int s, double* W, int ldw,
+                 bool sym, double* part, int64_t part_cap, cudaStream_t st) {
+  block_dot_impl<float>(n, Q, ldq, i, X, ldx, s, W, ldw, sym, part, part_cap,
+                        st);
+}
+
+void block_update(int64_t n, const double* Q, int64_t ldq, int i,
+                  const double* W, int ldw, double* X, int64_t ldx, int s,
+                  double alpha, double beta, bool upper, cudaStream_t st) {
+  block_update_impl<double>(n, Q, ldq, i, W, ldw, X, ldx, s, alpha, beta,
+                            upper, st);
+}
+
+void block_update32(int64_t n, const float* Q, int64_t ldq, int i,
+                    const double* W, int ldw, float* X, int64_t ldx, int s,
+                    double alpha, double beta, bool upper, cudaStream_t st) {
+  block_update_impl<float>(n, Q, ldq, i, W, ldw, X, ldx, s, alpha, beta,
+                           upper, st);
+}
+
+}  // namespace sg

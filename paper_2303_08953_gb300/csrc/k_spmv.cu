@@ -1,0 +1,235 @@
+// CSR sparse kernels: the Newton-step SpMV of the matrix powers kernel
+// (Sec. 2, Eq. newtonrecurrence), the residual, the sampled outer product
+// of the adjoint gradient and the CSR transpose.
+//
+// SpMV layout: one thread per row.  A CTA owns a contiguous block of rows
+// and first stages that block's values and column indices in shared
+// memory with coalesced streaming loads (they do not fit in L2 and are
+// not reused within one product), then each thread walks its own row from
+// shared memory and gathers x through the read-only path (stencil
+// locality gives cache hits).  One thread per row matters on this chip:
+// FP64 warp instructions are expensive (the FP64 pipe is ~1/64 of the FP32
+// rate), so the per-row reduction must not spend shuffles and adds on idle
+// lanes; the epilogue multiplies by 1/gamma instead of dividing.
+#include "sg_internal.h"
+
+namespace sg {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kStage = 2048;   // staged nonzeros per CTA
+
+__device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
+__device__ __forceinline__ int ld_stream(const int* p) { return __ldcs(p); }
+
+// MODE 0: y = (A x - theta x + c z) * inv_gamma   (HAS_Z: c z present)
+// MODE 1: y = z - A x                              (residual, z = b)
+template <int MODE, bool HAS_Z, typename T>
+__global__ void __launch_bounds__(kThreads)
+spmv_kernel(int n, int rows_per_cta, const int* __restrict__ rowptr,
+            const int* __restrict__ colind, const T* __restrict__ val,
+            const T* __restrict__ x, const T* __restrict__ z,
+            T* __restrict__ y, T theta, T c, T inv_gamma) {
+  __shared__ T sval[kStage];
+  __shared__ int scol[kStage];
+  const int t = threadIdx.x;
+  for (int64_t r0 = static_cast<int64_t>(blockIdx.x) * rows_per_cta; r0 < n;
+       r0 += static_cast<int64_t>(gridDim.x) * rows_per_cta) {
+    const int64_t r1 = (r0 + rows_per_cta < n) ? r0 + rows_per_cta : n;
+    const int k0 = rowptr[r0];
+    const int len = rowptr[r1] - k0;
+    const bool staged = len <= kStage;
+    if (staged) {
+      for (int e = t; e < len; e += kThreads) {
+        sval[e] = ld_stream(val + k0 + e);
+        scol[e] = ld_stream(colind + k0 + e);
+      }
+    }
+    __syncthreads();
+    for (int64_t row = r0 + t; row < r1; row += kThreads) {
+      const int a = rowptr[row], b = rowptr[row + 1];
+      T sum = T(0);
+      if (staged) {
+        for (int k = a - k0; k < b - k0; ++k) sum = fma(sval[k], __ldg(x + scol[k]), sum);
+      } else {
+        for (int k = a; k < b; ++k) sum = fma(ld_stream(val + k), __ldg(x + ld_stream(colind + k)), sum);
+      }
+      if (MODE == 1) {
+        y[row] = z[row] - sum;
+      } else {
+        T v = fma(-theta, x[row], sum);
+        if (HAS_Z) v = fma(c, z[row], v);
+        y[row] = v * inv_gamma;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+int rows_per_cta(const DevCsr& A) {
+  // as many rows as keep the CTA's nonzeros within the staging buffer,
+  // with 25% slack for row-length variation; at most one row per thread
+  const double per = A.mean_row > 0 ? A.mean_row * 1.25 : 1.0;
+  int r = static_cast<int>(kStage / per);
+  if (r > kThreads) r = kThreads;
+  if (r < 32) r = 32;
+  return r;
+}
+
+int grid_for(const DevCsr& A, int rpc) {
+  int64_t blocks = (static_cast<int64_t>(A.n) + rpc - 1) / rpc;
+  const int64_t cap = static_cast<int64_t>(device_sm_count()) * 16;
+  if (blocks > cap) blocks = cap;
+  return static_cast<int>(blocks < 1 ? 1 : blocks);
+}
+
+template <int MODE, bool HAS_Z, typename T>
+void dispatch(const DevCsr& A, const T* val, const T* x, const T* z, T* y,
+              T theta, T c, T gamma, cudaStream_t st) {
+  const int rpc = rows_per_cta(A);
+  spmv_kernel<MODE, HAS_Z, T><<<grid_for(A, rpc), kThreads, 0, st>>>(
+      A.n, rpc, A.rowptr, A.colind, val, x, z, y, theta, c, T(1) / gamma);
+  SG_LAUNCH_CHECK();
+}
+
+__global__ void sampled_outer_kernel(int n, const int* __restrict__ rowptr,
+                                     const int* __restrict__ colind,
+                                     const double* __restrict__ lam,
+                                     const double* __restrict__ x,
+                                     double* __restrict__ dval) {
+  // one warp per 32/8 rows, 8 lanes per row, like the SpMV
+  constexpr int VEC = 8, RPW = 32 / VEC;
+  const int lane = threadIdx.x & 31;
+  const int sub = lane / VEC, l = lane % VEC;
+  const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t base = warp * RPW; base < n; base += nwarps * RPW) {
+    const int64_t row = base + sub;
+    if (row >= n) continue;
+    const double li = -lam[row];
+    const int s = rowptr[row], e = rowptr[row + 1];
+    for (int k = s + l; k < e; k += VEC) dval[k] = li * __ldg(x + colind[k]);
+  }
+}
+
+// --- transpose: count entries per column, scan, scatter, sort rows ---
+__global__ void count_cols_kernel(int64_t nnz, const int* __restrict__ colind,
+                                  int* __restrict__ counts) {
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+       k < nnz; k += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    atomicAdd(counts + colind[k], 1);
+}
+
+// single-block exclusive scan of n+1 counters (n up to a few million;
+// each thread scans a contiguous chunk, then the chunk totals)
+__global__ void scan_kernel(int n, const int* __restrict__ counts,
+                            int* __restrict__ rowptr) {
+  __shared__ long long tot[1024];
+  const int t = threadIdx.x, T = blockDim.x;
+  const int64_t chunk = (static_cast<int64_t>(n) + T - 1) / T;
+  const int64_t a = t * chunk, b = (a + chunk < n) ? a + chunk : n;
+  long long s = 0;
+  for (int64_t i = a; i < b; ++i) s += counts[i];
+  tot[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    long long run = 0;
+    for (int i = 0; i < T; ++i) { long long v = tot[i]; tot[i] = run; run += v; }
+  }
+  __syncthreads();
+  long long run = tot[t];
+  for (int64_t i = a; i < b; ++i) { rowptr[i] = static_cast<int>(run); run += counts[i]; }
+  if (b == n && a < b) rowptr[n] = static_cast<int>(run);
+  if (n == 0 && t == 0) rowptr[0] = 0;
+}
+
+__global__ void scatter_kernel(int n, const int* __restrict__ rowptr,
+                               const int* __restrict__ colind,
+                               const double* __restrict__ val,
+                               const int* __restrict__ trowptr,
+                               int* __restrict__ fill, int* __restrict__ tcol,
+                               double* __restrict__ tval) {
+  for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+       r < n; r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    for (int k = rowptr[r]; k < rowptr[r + 1]; ++k) {
+      const int c = colind[k];
+      const int pos = trowptr[c] + atomicAdd(fill + c, 1);
+      tcol[pos] = static_cast<int>(r);
+      tval[pos] = val[k];
+    }
+  }
+}
+
+// insertion sort of each (short) row by column index: makes the transpose
+// independent of the atomic scatter order
+__global__ void sort_rows_kernel(int n, const int* __restrict__ rowptr,
+                                 int* __restrict__ col,
+                                 double* __restrict__ val) {
+  for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+       r < n; r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int a = rowptr[r], b = rowptr[r + 1];
+    for (int i = a + 1; i < b; ++i) {
+      const int ci = col[i];
+      const double vi = val[i];
+      int j = i - 1;
+      while (j >= a && col[j] > ci) { col[j + 1] = col[j]; val[j + 1] = val[j]; --j; }
+      col[j + 1] = ci;
+      val[j + 1] = vi;
+    }
+  }
+}
+
+}  // namespace
+
+void spmv_newton(const DevCsr& A, const double* x, const double* z,
+                 double* y, double theta, double c, double gamma,
+                 cudaStream_t st) {
+  if (c != 0.0 && z)
+    dispatch<0, true, double>(A, A.val, x, z, y, theta, c, gamma, st);
+  else
+    dispatch<0, false, double>(A, A.val, x, nullptr, y, theta, 0.0, gamma, st);
+}
+
+void spmv_newton32(const DevCsr& A, const float* x, const float* z, float* y,
+                   float theta, float c, float gamma, cudaStream_t st) {
+  if (c != 0.0f && z)
+    dispatch<0, true, float>(A, A.val32, x, z, y, theta, c, gamma, st);
+  else
+    dispatch<0, false, float>(A, A.val32, x, nullptr, y, theta, 0.0f, gamma, st);
+}
+
+void residual(const DevCsr& A, const double* b, const double* x, double* r,
+              cudaStream_t st) {
+  dispatch<1, false, double>(A, A.val, x, b, r, 0.0, 0.0, 1.0, st);
+}
+
+void sampled_outer(const DevCsr& A, const double* lam, const double* x,
+                   double* dval, cudaStream_t st) {
+  int64_t gb = (static_cast<int64_t>(A.n) + 31) / 32;
+  const int64_t cap = static_cast<int64_t>(device_sm_count()) * 16;
+  const int g = static_cast<int>(gb > cap ? cap : (gb < 1 ? 1 : gb));
+  sampled_outer_kernel<<<g, kThreads, 0, st>>>(A.n, A.rowptr, A.colind, lam, x,
+                                               dval);
+  SG_LAUNCH_CHECK();
+}
+
+void csr_transpose(const DevCsr& A, DevCsr& T, int32_t* counts,
+                   cudaStream_t st) {
+  // counts: n+1 ints of scratch; T's arrays are allocated by the caller
+  SG_CUDA(cudaMemsetAsync(counts, 0, sizeof(int32_t) * (A.n + 1), st));
+  const int g = device_sm_count() * 8;
+  count_cols_kernel<<<g, kThreads, 0, st>>>(A.nnz, A.colind, counts);
+  SG_LAUNCH_CHECK();
+  scan_kernel<<<1, 1024, 0, st>>>(A.n, counts, T.rowptr);
+  SG_LAUNCH_CHECK();
+  SG_CUDA(cudaMemsetAsync(counts, 0, sizeof(int32_t) * (A.n + 1), st));
+  scatter_kernel<<<g, kThreads, 0, st>>>(A.n, A.rowptr, A.colind, A.val,
+                                         T.rowptr, counts, T.colind, T.val);
+  SG_LAUNCH_CHECK();
+  sort_rows_kernel<<<g, kThreads, 0, st>>>(A.n, T.rowptr, T.colind, T.val);
+  SG_LAUNCH_CHECK();
+}
+
+}  // namespace sg

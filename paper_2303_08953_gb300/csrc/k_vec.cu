@@ -1,0 +1,247 @@
+// Vector kernels: deterministic dot products and norms (warp shuffles,
+// then a fixed-order sum of per-block partials), the fused modified
+// Gram-Schmidt step of the Arnoldi pre-pass that supplies the Ritz values
+// (Sec. 3.4), normalisation, the solution update x += Q y (Alg. 4, last
+// line) and precision conversions.
+#include "sg_internal.h"
+
+namespace sg {
+
+namespace {
+
+constexpr int kThreads = 256;
+int g_red_blocks = 0;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// Sum over the block; every thread receives the result.
+__device__ double block_sum(double v) {
+  __shared__ double sh[kThreads / 32];
+  __shared__ double total;
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    double t = (l < kThreads / 32) ? sh[l] : 0.0;
+    t = warp_sum(t);
+    if (l == 0) total = t;
+  }
+  __syncthreads();
+  return total;
+}
+
+// Fixed-order sum of the G partials of a previous reduction.
+__device__ double sum_partials(const double* __restrict__ p, int G) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < G; i += kThreads) v += p[i];
+  return block_sum(v);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+dot_kernel(int64_t n, const T* __restrict__ x, const T* __restrict__ y,
+           double* __restrict__ part) {
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * kThreads)
+    acc += static_cast<double>(x[i]) * static_cast<double>(y[i]);
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+__global__ void finish_kernel(const double* __restrict__ part, int G,
+                              double* out, int sqrt_out) {
+  const double s = sum_partials(part, G);
+  if (threadIdx.x == 0) out[0] = sqrt_out ? sqrt(s) : s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+mgs_kernel(int64_t n, T* __restrict__ w, const T* __restrict__ v,
+           const T* __restrict__ vnext, const double* __restrict__ pin,
+           int G, double* hout, double* __restrict__ pout) {
+  const double h = sum_partials(pin, G);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *hout = h;
+  const T ht = static_cast<T>(h);
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * kThreads) {
+    const T wi = w[i] - ht * v[i];
+    w[i] = wi;
+    acc += static_cast<double>(vnext ? vnext[i] : wi) * static_cast<double>(wi);
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) pout[blockIdx.x] = acc;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+normalize_kernel(int64_t n, const double* __restrict__ pin, int G,
+                 const T* x, T* y, double* nout) {
+  const double nrm = sqrt(sum_partials(pin, G));
+  if (blockIdx.x == 0 && threadIdx.x == 0) *nout = nrm;
+  const double inv = 1.0 / nrm;
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * kThreads)
+    y[i] = static_cast<T>(static_cast<double>(x[i]) * inv);
+}
+
+__global__ void scale_kernel(int64_t n, const double* __restrict__ x,
+                             double* __restrict__ y, double a) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * kThreads)
+    y[i] = x[i] * a;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+gemv_kernel(int64_t n, int k, const T* __restrict__ Q, int64_t ldq,
+            const double* __restrict__ y, double* __restrict__ x) {
+  extern __shared__ double ys[];
+  for (int j = threadIdx.x; j < k; j += kThreads) ys[j] = y[j];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * kThreads) {
+    double acc = 0.0;
+    for (int j = 0; j < k; ++j) acc += static_cast<double>(Q[i + j * ldq]) * ys[j];
+    x[i] += acc;
+  }
+}
+
+__global__ void to_f32_kernel(int64_t n, const double* __restrict__ x,
+                              float* __restrict__ y, float s) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * kThreads)
+    y[i] = static_cast<float>(x[i]) * s;
+}
+
+__global__ void axpy_f32_kernel(int64_t n, double a, const float* __restrict__ d,
+                                double* __restrict__ x) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * kThreads)
+    x[i] += a * static_cast<double>(d[i]);
+}
+
+int stream_grid(int64_t n) {
+  int64_t b = (n + kThreads - 1) / kThreads;
+  const int64_t cap = static_cast<int64_t>(device_sm_count()) * 16;
+  if (b > cap) b = cap;
+  return static_cast<int>(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+int device_sm_count() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev) !=
+            cudaSuccess || cached <= 0)
+      cached = 1;
+  }
+  return cached;
+}
+
+int reduction_blocks() {
+  if (!g_red_blocks) {
+    g_red_blocks = device_sm_count() * 4;
+    if (g_red_blocks > 1024) g_red_blocks = 1024;
+  }
+  return g_red_blocks;
+}
+
+void dot_partials(int64_t n, const double* x, const double* y,
+                  double* partials, cudaStream_t st) {
+  dot_kernel<double><<<reduction_blocks(), kThreads, 0, st>>>(n, x, y, partials);
+  SG_LAUNCH_CHECK();
+}
+
+void dot_partials32(int64_t n, const float* x, const float* y,
+                    double* partials, cudaStream_t st) {
+  dot_kernel<float><<<reduction_blocks(), kThreads, 0, st>>>(n, x, y, partials);
+  SG_LAUNCH_CHECK();
+}
+
+void finish_sum(const double* partials, double* out, bool sqrt_out,
+                cudaStream_t st) {
+  finish_kernel<<<1, kThreads, 0, st>>>(partials, reduction_blocks(), out,
+                                        sqrt_out ? 1 : 0);
+  SG_LAUNCH_CHECK();
+}
+
+void mgs_step(int64_t n, double* w, const double* v, const double* vnext,
+              const double* pin, double* hout, double* pout,
+              cudaStream_t st) {
+  mgs_kernel<double><<<reduction_blocks(), kThreads, 0, st>>>(
+      n, w, v, vnext, pin, reduction_blocks(), hout, pout);
+  SG_LAUNCH_CHECK();
+}
+
+void mgs_step32(int64_t n, float* w, const float* v, const float* vnext,
+                const double* pin, double* hout, double* pout,
+                cudaStream_t st) {
+  mgs_kernel<float><<<reduction_blocks(), kThreads, 0, st>>>(
+      n, w, v, vnext, pin, reduction_blocks(), hout, pout);
+  SG_LAUNCH_CHECK();
+}
+
+void normalize(int64_t n, const double* pin, const double* x, double* y,
+               double* nout, cudaStream_t st) {
+  normalize_kernel<double><<<stream_grid(n), kThreads, 0, st>>>(
+      n, pin, reduction_blocks(), x, y, nout);
+  SG_LAUNCH_CHECK();
+}
+
+void normalize32(int64_t n, const double* pin, const float* x, float* y,
+                 double* nout, cudaStream_t st) {
+  normalize_kernel<float><<<stream_grid(n), kThreads, 0, st>>>(
+      n, pin, reduction_blocks(), x, y, nout);
+  SG_LAUNCH_CHECK();
+}
+
+void scale_copy(int64_t n, const double* x, double* y, double alpha,
+                cudaStream_t st) {
+  scale_kernel<<<stream_grid(n), kThreads, 0, st>>>(n, x, y, alpha);
+  SG_LAUNCH_CHECK();
+}
+
+void gemv_n_add(int64_t n, int k, const double* Q, int64_t ldq,
+                const double* y, double* x, cudaStream_t st) {
+  if (k <= 0) return;
+  gemv_kernel<double><<<stream_grid(n), kThreads, sizeof(double) * k, st>>>(
+      n, k, Q, ldq, y, x);
+  SG_LAUNCH_CHECK();
+}
+
+void gemv_n_add32(int64_t n, int k, const float* Q, int64_t ldq,
+                  const double* y, double* x, cudaStream_t st) {
+  if (k <= 0) return;
+  gemv_kernel<float><<<stream_grid(n), kThreads, sizeof(double) * k, st>>>(
+      n, k, Q, ldq, y, x);
+  SG_LAUNCH_CHECK();
+}
+
+void to_f32(int64_t n, const double* x, float* y, float scale,
+            cudaStream_t st) {
+  to_f32_kernel<<<stream_grid(n), kThreads, 0, st>>>(n, x, y, scale);
+  SG_LAUNCH_CHECK();
+}
+
+void axpy_f32_to_f64(int64_t n, double alpha, const float* d, double* x,
+                     cudaStream_t st) {
+  axpy_f32_kernel<<<stream_grid(n), kThreads, 0, st>>>(n, alpha, d, x);
+  SG_LAUNCH_CHECK();
+}
+
+void fill_zero(int64_t n, double* x, cudaStream_t st) {
+  SG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+}
+
+}  // namespace sg

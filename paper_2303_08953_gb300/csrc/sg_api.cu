@@ -1,0 +1,470 @@
+// extern "C" boundary of the library (declared in include/sgmres.h).
+// Every entry point catches the internal sg::Error / CUDA failures and
+// returns a status; the message is kept in the handle.
+#include <algorithm>
+#include <atomic>
+#include <cstdlib>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sg_solver.h"
+
+using sg::Error;
+
+namespace sg {
+namespace {
+std::atomic<long long> g_launches{0};
+}
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace sg
+
+namespace {
+
+sg_status fail(sg_handle* h, sg_status code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+template <typename F>
+sg_status guarded(sg_handle* h, F&& f) {
+  try {
+    if (h) h->err.clear();
+    f();
+    return SG_OK;
+  } catch (const Error& e) {
+    return fail(h, e.code, e.what());
+  } catch (const std::bad_alloc&) {
+    return fail(h, SG_ENOMEM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(h, SG_EINVAL, e.what());
+  }
+}
+
+cudaStream_t pick(sg_handle* h, void* s) {
+  return s ? static_cast<cudaStream_t>(s) : h->own;
+}
+
+void free_csr(sg::DevCsr& A) {
+  if (A.rowptr) cudaFree(A.rowptr);
+  if (A.colind) cudaFree(A.colind);
+  if (A.val) cudaFree(A.val);
+  if (A.val32) cudaFree(A.val32);
+  A = sg::DevCsr();
+}
+
+__global__ void f64_to_f32_kernel(int64_t n, const double* x, float* y) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    y[i] = static_cast<float>(x[i]);
+}
+
+void make_val32(sg::DevCsr& A, cudaStream_t st) {
+  if (A.val32) cudaFree(A.val32);
+  A.val32 = nullptr;
+  SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&A.val32), sizeof(float) * std::max<int64_t>(A.nnz, 1)));
+  f64_to_f32_kernel<<<sg::device_sm_count() * 8, 256, 0, st>>>(A.nnz, A.val, A.val32);
+  SG_LAUNCH_CHECK();
+}
+
+sg::SolveOpts to_internal(const sg_opts* o) {
+  sg::SolveOpts s;
+  s.m = o->m;
+  s.s = o->s;
+  s.s_min = std::max(1, o->s_min);
+  s.s_max = o->s_max > 0 ? o->s_max : o->m;
+  s.max_iters = o->max_iters;
+  s.basis = o->basis;
+  s.tol = o->tol;
+  s.omega = o->omega;
+  s.omega_est = o->omega_est;
+  s.eps = std::ldexp(1.0, -53);
+  return s;
+}
+
+void check_opts(const sg_opts* o) {
+  SG_REQUIRE(o, SG_EINVAL, "opts is NULL");
+  SG_REQUIRE(o->m >= 1, SG_EINVAL, "m must be >= 1");
+  SG_REQUIRE(o->s >= 0, SG_EINVAL, "s must be >= 0");
+  SG_REQUIRE(o->s > 0 || o->s_max >= 1 || o->m >= 1, SG_EINVAL, "bad s_max");
+  SG_REQUIRE(o->tol >= 0.0, SG_EINVAL, "tol must be >= 0");
+  SG_REQUIRE(o->omega > 1.0 && o->omega_est > 0.0, SG_EINVAL, "bad omega");
+  SG_REQUIRE(o->basis >= 0 && o->basis <= 2, SG_EINVAL, "bad basis");
+  SG_REQUIRE(o->precision == SG_PREC_FP64 || o->precision == SG_PREC_FP32_IR,
+             SG_EINVAL, "bad precision");
+}
+
+template <typename T>
+void copy_in(T* dst, const T* src, int64_t n, bool on_device, cudaStream_t st) {
+  SG_CUDA(cudaMemcpyAsync(dst, src, sizeof(T) * n,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+}
+
+void fill_result(const sg::SolveLog& L, sg_result* r) {
+  if (!r) return;
+  r->converged = L.converged ? 1 : 0;
+  r->s0 = L.s0;
+  r->iters = L.iters;
+  r->restarts = L.restarts;
+  r->refinements = L.refinements;
+  r->final_relres = L.final_relres;
+  auto put = [](auto* dst, int cap, const auto& v) {
+    if (!dst) return;
+    const int k = std::min<int>(cap, static_cast<int>(v.size()));
+    for (int t = 0; t < k; ++t) dst[t] = v[t];
+  };
+  r->n_hist = static_cast<int32_t>(L.relres_hist.size());
+  put(r->relres_hist, r->hist_cap, L.relres_hist);
+  r->n_blocks = static_cast<int32_t>(L.s_hist.size());
+  put(r->s_eff_hist, r->blocks_cap, L.s_eff_hist);
+  put(r->p1_hist, r->blocks_cap, L.p1_hist);
+  put(r->s_hist, r->blocks_cap, L.s_hist);
+  r->n_cycles = static_cast<int32_t>(L.cycle_relres.size());
+  put(r->cycle_relres, r->cycles_cap, L.cycle_relres);
+  put(r->cycle_iters, r->cycles_cap, L.cycle_iters);
+  r->n_ritz = static_cast<int32_t>(L.ritz_re.size());
+  put(r->ritz_re, r->ritz_cap, L.ritz_re);
+  put(r->ritz_im, r->ritz_cap, L.ritz_im);
+  put(r->gamma, r->ritz_cap, L.gamma);
+  r->t_prepass_ms = L.t_prepass;
+  r->t_mpk_ms = L.t_mpk;
+  r->t_ortho_ms = L.t_ortho;
+  r->t_host_ms = L.t_host;
+  r->t_total_ms = L.t_total;
+}
+
+sg_status run_solve(sg_handle* h, bool adjoint, const double* b, double* x,
+                    const sg_opts* opts, sg_result* res) {
+  sg_status st_code = SG_OK;
+  sg::SolveLog log;
+  sg_status rc = guarded(h, [&] {
+    SG_REQUIRE(h->have_A, SG_ESTATE, "no matrix: call sg_analyze first");
+    check_opts(opts);
+    SG_REQUIRE(b && x, SG_EINVAL, "b/x is NULL");
+    SG_CUDA(cudaSetDevice(h->device));
+    cudaStream_t st = pick(h, opts->stream);
+    const sg::DevCsr* M = &h->A;
+    if (adjoint) {
+      if (!h->have_AT) {
+        h->AT.n = h->A.n;
+        h->AT.nnz = h->A.nnz;
+        SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&h->AT.rowptr), sizeof(int32_t) * (h->A.n + 1)));
+        SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&h->AT.colind), sizeof(int32_t) * std::max<int64_t>(h->A.nnz, 1)));
+        SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&h->AT.val), sizeof(double) * std::max<int64_t>(h->A.nnz, 1)));
+        int32_t* counts = nullptr;
+        SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&counts), sizeof(int32_t) * (h->A.n + 1)));
+        try {
+          sg::csr_transpose(h->A, h->AT, counts, st);
+          SG_CUDA(cudaStreamSynchronize(st));
+        } catch (...) {
+          cudaFree(counts);
+          throw;
+        }
+        cudaFree(counts);
+        h->AT.mean_row = h->A.mean_row;
+        if (h->A.val32) make_val32(h->AT, st);
+        h->have_AT = true;
+      }
+      M = &h->AT;
+    }
+    const int64_t n = M->n;
+    sg::SolveOpts o = to_internal(opts);
+    const int kritz = std::min(o.s > 0 ? o.s : o.s_max, o.m);
+    sg::ensure_workspace(h, n, o.m, std::max(kritz, 1));
+    const bool dev = opts->vectors_on_device != 0;
+    copy_in(h->bvec, b, n, dev, st);
+    copy_in(h->xvec, static_cast<const double*>(x), n, dev, st);
+    if (opts->precision == SG_PREC_FP32_IR) {
+      if (!M->val32) make_val32(*const_cast<sg::DevCsr*>(M), st);
+      sg::solve_fp32_ir(h, *M, o, opts->inner_tol > 0 ? opts->inner_tol : 1e-4,
+                        opts->max_refine > 0 ? opts->max_refine : 20, st, log);
+    } else {
+      sg::solve_fp64(h, *M, o, st, log);
+    }
+    SG_CUDA(cudaMemcpyAsync(x, h->xvec, sizeof(double) * n,
+                            dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    SG_CUDA(cudaStreamSynchronize(st));
+    fill_result(log, res);
+    if (!log.converged) st_code = SG_ENOCONV;
+  });
+  if (rc != SG_OK) return rc;
+  if (st_code == SG_ENOCONV)
+    return fail(h, SG_ENOCONV, "iteration cap reached before tol");
+  return SG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t sg_kernel_launches(void) { return sg::g_launches.load(); }
+
+void sg_default_opts(sg_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->m = 60;
+  o->s = 10;
+  o->s_min = 1;
+  o->s_max = 0;
+  o->tol = 1e-10;
+  o->max_iters = 0;
+  o->omega = 1e7;
+  o->omega_est = 1e7;
+  o->basis = SG_BASIS_SCALED_NEWTON;
+  o->precision = SG_PREC_FP64;
+  o->inner_tol = 1e-4;
+  o->max_refine = 20;
+  o->vectors_on_device = 0;
+  o->stream = nullptr;
+}
+
+sg_status sg_create(int device, sg_handle** out) {
+  if (!out) return SG_EINVAL;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count)
+    return SG_ECUDA;
+  sg_handle* h = new (std::nothrow) sg_handle();
+  if (!h) return SG_ENOMEM;
+  h->device = device;
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess) {
+    delete h;
+    return SG_ECUDA;
+  }
+  *out = h;
+  return SG_OK;
+}
+
+void sg_destroy(sg_handle* h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->own) cudaStreamSynchronize(h->own);
+  free_csr(h->A);
+  free_csr(h->AT);
+  double* d[] = {h->Q, h->V, h->Y, h->bvec, h->xvec, h->rvec, h->part, h->red, h->small, h->dvec};
+  for (double* p : d) if (p) cudaFree(p);
+  float* f[] = {h->Q32, h->V32, h->Y32, h->r32};
+  for (float* p : f) if (p) cudaFree(p);
+  if (h->hbuf) cudaFreeHost(h->hbuf);
+  for (auto e : h->ev) if (e) cudaEventDestroy(e);
+  if (h->own) cudaStreamDestroy(h->own);
+  delete h;
+}
+
+const char* sg_last_error(const sg_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+sg_status sg_analyze(sg_handle* h, const sg_csr* A) {
+  if (!h) return SG_EINVAL;
+  return guarded(h, [&] {
+    SG_REQUIRE(A && A->rowptr && A->colind && A->val, SG_EINVAL, "null CSR array");
+    SG_REQUIRE(A->n >= 1, SG_EINVAL, "n must be >= 1");
+    SG_REQUIRE(A->nnz >= 0 && A->nnz < (int64_t(1) << 31), SG_EINVAL, "nnz out of int32 range");
+    SG_CUDA(cudaSetDevice(h->device));
+    cudaStream_t st = h->own;
+    const int64_t n = A->n, nnz = A->nnz;
+    // validation on the host (from a host copy when A is on the device)
+    std::vector<int32_t> rp(n + 1), ci(nnz);
+    const cudaMemcpyKind kind = A->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    SG_CUDA(cudaMemcpy(rp.data(), A->rowptr, sizeof(int32_t) * (n + 1), kind));
+    if (nnz) SG_CUDA(cudaMemcpy(ci.data(), A->colind, sizeof(int32_t) * nnz, kind));
+    SG_REQUIRE(rp[0] == 0 && rp[n] == nnz, SG_EINVAL, "rowptr must start at 0 and end at nnz");
+    int32_t maxrow = 0;
+    for (int64_t r = 0; r < n; ++r) {
+      SG_REQUIRE(rp[r + 1] >= rp[r], SG_EINVAL, "rowptr not non-decreasing");
+      maxrow = std::max(maxrow, rp[r + 1] - rp[r]);
+      for (int32_t k = rp[r]; k < rp[r + 1]; ++k) {
+        SG_REQUIRE(ci[k] >= 0 && ci[k] < n, SG_EINVAL, "column index out of range");
+        SG_REQUIRE(k == rp[r] || ci[k] > ci[k - 1], SG_EINVAL, "columns not sorted/unique in a row");
+      }
+    }
+    free_csr(h->A);
+    free_csr(h->AT);
+    h->have_A = h->have_AT = false;
+    sg::DevCsr& D = h->A;
+    D.n = A->n;
+    D.nnz = nnz;
+    SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&D.rowptr), sizeof(int32_t) * (n + 1)));
+    SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&D.colind), sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+    SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&D.val), sizeof(double) * std::max<int64_t>(nnz, 1)));
+    const bool dev = A->on_device != 0;
+    copy_in(D.rowptr, A->rowptr, n + 1, dev, st);
+    if (nnz) {
+      copy_in(D.colind, A->colind, nnz, dev, st);
+      copy_in(D.val, A->val, nnz, dev, st);
+    }
+    D.mean_row = static_cast<double>(nnz) / static_cast<double>(n);
+    D.max_row = maxrow;
+    SG_CUDA(cudaStreamSynchronize(st));
+    h->have_A = true;
+  });
+}
+
+sg_status sg_solve(sg_handle* h, const double* b, double* x,
+                   const sg_opts* opts, sg_result* res) {
+  if (!h) return SG_EINVAL;
+  return run_solve(h, false, b, x, opts, res);
+}
+
+sg_status sg_solve_adjoint(sg_handle* h, const double* g, double* lam,
+                           const sg_opts* opts, sg_result* res) {
+  if (!h) return SG_EINVAL;
+  return run_solve(h, true, g, lam, opts, res);
+}
+
+sg_status sg_grad_values(sg_handle* h, const double* lam, const double* x,
+                         double* dval, void* stream) {
+  if (!h) return SG_EINVAL;
+  return guarded(h, [&] {
+    SG_REQUIRE(h->have_A, SG_ESTATE, "no matrix");
+    SG_REQUIRE(lam && x && dval, SG_EINVAL, "null pointer");
+    SG_CUDA(cudaSetDevice(h->device));
+    sg::sampled_outer(h->A, lam, x, dval, pick(h, stream));
+  });
+}
+
+sg_status sg_spmv_newton(sg_handle* h, const double* x, const double* z,
+                         double* y, double theta, double c, double gamma,
+                         void* stream) {
+  if (!h) return SG_EINVAL;
+  return guarded(h, [&] {
+    SG_REQUIRE(h->have_A, SG_ESTATE, "no matrix");
+    SG_REQUIRE(x && y && (c == 0.0 || z), SG_EINVAL, "null pointer");
+    SG_REQUIRE(gamma != 0.0, SG_EINVAL, "gamma must be nonzero");
+    SG_CUDA(cudaSetDevice(h->device));
+    sg::spmv_newton(h->A, x, z, y, theta, c, gamma, pick(h, stream));
+  });
+}
+
+sg_status sg_residual(sg_handle* h, const double* b, const double* x,
+                      double* r, void* stream) {
+  if (!h) return SG_EINVAL;
+  return guarded(h, [&] {
+    SG_REQUIRE(h->have_A, SG_ESTATE, "no matrix");
+    SG_REQUIRE(b && x && r, SG_EINVAL, "null pointer");
+    SG_CUDA(cudaSetDevice(h->device));
+    sg::residual(h->A, b, x, r, pick(h, stream));
+  });
+}
+
+sg_status sg_mpk(sg_handle* h, const double* q, double* V, int64_t ldv,
+                 int32_t s, const double* theta_re, const double* theta_im,
+                 const double* gamma, void* stream) {
+  if (!h) return SG_EINVAL;
+  return guarded(h, [&] {
+    SG_REQUIRE(h->have_A, SG_ESTATE, "no matrix");
+    SG_REQUIRE(q && V && ldv >= h->A.n && s >= 0, SG_EINVAL, "bad MPK arguments");
+    SG_REQUIRE(s == 0 || (theta_re && theta_im && gamma), SG_EINVAL, "null shifts");
+    SG_CUDA(cudaSetDevice(h->device));
+    cudaStream_t st = pick(h, stream);
+    std::vector<sg::BasisStep> steps;
+    sg::basis_steps(s, theta_re, theta_im, gamma, steps);
+    SG_CUDA(cudaMemcpyAsync(V, q, sizeof(double) * h->A.n, cudaMemcpyDeviceToDevice, st));
+    for (int j = 0; j < s; ++j) {
+      SG_REQUIRE(steps[j].gamma != 0.0, SG_EINVAL, "gamma must be nonzero");
+      const double* z = steps[j].c != 0.0 ? V + static_cast<int64_t>(j - 1) * ldv : nullptr;
+      sg::spmv_newton(h->A, V + static_cast<int64_t>(j) * ldv, z,
+                      V + static_cast<int64_t>(j + 1) * ldv, steps[j].theta, steps[j].c,
+                      steps[j].gamma, st);
+    }
+  });
+}
+
+sg_status sg_block_dot(sg_handle* h, int64_t n, const double* Q, int64_t ldq,
+                       int32_t i, const double* X, int64_t ldx, int32_t s,
+                       double* W, int32_t ldw, int32_t sym, void* stream) {
+  if (!h) return SG_EINVAL;
+  return guarded(h, [&] {
+    SG_REQUIRE(n >= 0 && i >= 0 && s >= 0 && ldq >= n && ldx >= n && ldw >= i,
+               SG_EINVAL, "bad sizes");
+    SG_REQUIRE((Q && X && W) || i == 0 || s == 0, SG_EINVAL, "null pointer");
+    SG_REQUIRE(!sym || (Q == X && i == s), SG_EINVAL, "sym needs Q == X");
+    SG_CUDA(cudaSetDevice(h->device));
+    cudaStream_t st = pick(h, stream);
+    const int64_t need = sg::block_dot_part_size(n, i, s);
+    if (need > h->part_cap) {
+      SG_CUDA(cudaStreamSynchronize(st));
+      if (h->part) cudaFree(h->part);
+      h->part = nullptr;
+      h->part_cap = 0;
+      SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&h->part), sizeof(double) * need));
+      h->part_cap = need;
+    }
+    sg::block_dot(n, Q, ldq, i, X, ldx, s, W, ldw, sym != 0, h->part, h->part_cap, st);
+  });
+}
+
+sg_status sg_block_update(sg_handle* h, int64_t n, const double* Q,
+                          int64_t ldq, int32_t i, const double* W,
+                          int32_t ldw, double* X, int64_t ldx, int32_t s,
+                          double alpha, double beta, int32_t upper,
+                          void* stream) {
+  if (!h) return SG_EINVAL;
+  return guarded(h, [&] {
+    SG_REQUIRE(n >= 0 && i >= 0 && s >= 0 && ldq >= n && ldx >= n && ldw >= i,
+               SG_EINVAL, "bad sizes");
+    SG_REQUIRE(X || s == 0 || n == 0, SG_EINVAL, "null X");
+    SG_REQUIRE((Q && W) || i == 0, SG_EINVAL, "null Q/W");
+    SG_REQUIRE(!upper || i == s, SG_EINVAL, "upper needs i == s");
+    SG_CUDA(cudaSetDevice(h->device));
+    sg::block_update(n, Q, ldq, i, W, ldw, X, ldx, s, alpha, beta, upper != 0,
+                     pick(h, stream));
+  });
+}
+
+sg_status sg_nrm2(sg_handle* h, int64_t n, const double* x, double* out,
+                  void* stream) {
+  if (!h) return SG_EINVAL;
+  return guarded(h, [&] {
+    SG_REQUIRE(x && out && n >= 0, SG_EINVAL, "bad arguments");
+    SG_CUDA(cudaSetDevice(h->device));
+    cudaStream_t st = pick(h, stream);
+    if (!h->red) {
+      SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&h->red),
+                         sizeof(double) * sg::reduction_blocks() * 3));
+    }
+    double* slot = nullptr;
+    SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&slot), sizeof(double)));
+    sg::dot_partials(n, x, x, h->red, st);
+    sg::finish_sum(h->red, slot, true, st);
+    cudaError_t e1 = cudaMemcpyAsync(out, slot, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaError_t e2 = cudaStreamSynchronize(st);
+    cudaFree(slot);
+    SG_CUDA(e1);
+    SG_CUDA(e2);
+  });
+}
+
+int32_t sg_host_partial_cholesky(const double* G, int32_t ldg, int32_t s,
+                                 double omega, double* R, double* kappa) {
+  if (!G || !R || s < 0 || ldg < s) return -1;
+  return sg::partial_cholesky(G, ldg, s, omega, R, s, kappa);
+}
+
+int32_t sg_host_hessenberg_eigvals(const double* H, int32_t ldh, int32_t k,
+                                   double* re, double* im) {
+  if (!H || !re || !im || k < 0 || ldh < k) return -1;
+  return sg::hessenberg_eigvals(H, ldh, k, re, im);
+}
+
+void sg_host_leja_order(int32_t k, const double* re, const double* im,
+                        double* out_re, double* out_im) {
+  if (k <= 0 || !re || !im || !out_re || !out_im) return;
+  sg::leja_order(k, re, im, out_re, out_im);
+}
+
+void sg_host_scaling_coefficients(int32_t k, const double* re,
+                                  const double* im, double* gamma) {
+  if (k <= 0 || !re || !im || !gamma) return;
+  sg::scaling_coefficients(k, re, im, gamma);
+}
+
+int32_t sg_host_estimate_step(int32_t k, const double* re, const double* im,
+                              double eps, double omega_est, int32_t s_min,
+                              int32_t s_max, double* norms) {
+  if (k < 0 || (k > 0 && (!re || !im))) return -1;
+  return sg::estimate_step(k, re, im, eps, omega_est, s_min, s_max, norms);
+}
+
+}  // extern "C"

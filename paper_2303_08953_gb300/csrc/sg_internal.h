@@ -1,0 +1,128 @@
+// Internal declarations of the sm_103a s-step GMRES library: device
+// matrix, workspace, error handling and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <stdexcept>
+#include <string>
+
+#include "sgmres.h"
+
+namespace sg {
+
+struct Error : std::runtime_error {
+  sg_status code;
+  Error(sg_status c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define SG_CUDA(call)                                                      \
+  do {                                                                     \
+    cudaError_t e_ = (call);                                               \
+    if (e_ != cudaSuccess)                                                 \
+      throw ::sg::Error(SG_ECUDA, std::string(#call) + ": " +              \
+                                      cudaGetErrorString(e_));             \
+  } while (0)
+// every kernel launch of the library goes through this check, which also
+// counts it (sg_kernel_launches)
+void count_launch();
+#define SG_LAUNCH_CHECK()                                                  \
+  do {                                                                     \
+    ::sg::count_launch();                                                  \
+    SG_CUDA(cudaGetLastError());                                           \
+  } while (0)
+#define SG_REQUIRE(cond, code, msg)                                        \
+  do {                                                                     \
+    if (!(cond)) throw ::sg::Error(code, msg);                             \
+  } while (0)
+
+// CSR on the device (int32 indices, FP64 values, optional FP32 copy).
+struct DevCsr {
+  int32_t n = 0;
+  int64_t nnz = 0;
+  int32_t* rowptr = nullptr;
+  int32_t* colind = nullptr;
+  double* val = nullptr;
+  float* val32 = nullptr;
+  double mean_row = 0;  // row-length statistics recorded at ingest
+  int32_t max_row = 0;
+};
+
+// ---------------------------------------------------------------- SpMV
+// y = (A x - theta x + c z) / gamma      (z may be null when c == 0)
+void spmv_newton(const DevCsr& A, const double* x, const double* z,
+                 double* y, double theta, double c, double gamma,
+                 cudaStream_t st);
+void spmv_newton32(const DevCsr& A, const float* x, const float* z, float* y,
+                   float theta, float c, float gamma, cudaStream_t st);
+// r = b - A x
+void residual(const DevCsr& A, const double* b, const double* x, double* r,
+              cudaStream_t st);
+// dval[k] = -lam[row(k)] * x[col(k)]
+void sampled_outer(const DevCsr& A, const double* lam, const double* x,
+                   double* dval, cudaStream_t st);
+// CSR transpose (device to device), sorted columns.
+void csr_transpose(const DevCsr& A, DevCsr& T, int32_t* work_counts,
+                   cudaStream_t st);
+
+// ------------------------------------------------------- vector kernels
+// Deterministic two-stage reductions: stage 1 writes `nred` per-block
+// partial sums, consumers add them in a fixed order.
+int reduction_blocks();
+void dot_partials(int64_t n, const double* x, const double* y,
+                  double* partials, cudaStream_t st);
+void dot_partials32(int64_t n, const float* x, const float* y,
+                    double* partials, cudaStream_t st);
+// out[0] = sum(partials) (or its square root when sqrt_out)
+void finish_sum(const double* partials, double* out, bool sqrt_out,
+                cudaStream_t st);
+// One modified Gram-Schmidt step of Arnoldi: h = sum(pin) (written to
+// *hout), w -= h v, pout = partials of dot(vnext ? vnext : w, w).
+void mgs_step(int64_t n, double* w, const double* v, const double* vnext,
+              const double* pin, double* hout, double* pout,
+              cudaStream_t st);
+void mgs_step32(int64_t n, float* w, const float* v, const float* vnext,
+                const double* pin, double* hout, double* pout,
+                cudaStream_t st);
+// nrm = sqrt(sum(pin)); *nout = nrm; y = x / nrm (y may alias x)
+void normalize(int64_t n, const double* pin, const double* x, double* y,
+               double* nout, cudaStream_t st);
+void normalize32(int64_t n, const double* pin, const float* x, float* y,
+                 double* nout, cudaStream_t st);
+// y = x * (alpha_host)
+void scale_copy(int64_t n, const double* x, double* y, double alpha,
+                cudaStream_t st);
+// x += Q(:, 0:k-1) y   (y: device, length k)
+void gemv_n_add(int64_t n, int k, const double* Q, int64_t ldq,
+                const double* y, double* x, cudaStream_t st);
+void gemv_n_add32(int64_t n, int k, const float* Q, int64_t ldq,
+                  const double* y, double* x, cudaStream_t st);
+// precision conversions
+void to_f32(int64_t n, const double* x, float* y, float scale,
+            cudaStream_t st);
+void axpy_f32_to_f64(int64_t n, double alpha, const float* d, double* x,
+                     cudaStream_t st);
+void fill_zero(int64_t n, double* x, cudaStream_t st);
+
+// ------------------------------------------------------ dense kernels
+// W = Q^T X through split-n partials (workspace `part`, `part_cap`
+// doubles); sym: Q == X, only the upper tile triangle is computed.
+void block_dot(int64_t n, const double* Q, int64_t ldq, int i,
+               const double* X, int64_t ldx, int s, double* W, int ldw,
+               bool sym, double* part, int64_t part_cap, cudaStream_t st);
+void block_dot32(int64_t n, const float* Q, int64_t ldq, int i,
+                 const float* X, int64_t ldx, int s, double* W, int ldw,
+                 bool sym, double* part, int64_t part_cap, cudaStream_t st);
+int64_t block_dot_part_size(int64_t n, int i, int s);
+// X = beta X + alpha Q W (W on the device, i x s, upper-triangular if
+// `upper`, i == s)
+void block_update(int64_t n, const double* Q, int64_t ldq, int i,
+                  const double* W, int ldw, double* X, int64_t ldx, int s,
+                  double alpha, double beta, bool upper, cudaStream_t st);
+void block_update32(int64_t n, const float* Q, int64_t ldq, int i,
+                    const double* W, int ldw, float* X, int64_t ldx, int s,
+                    double alpha, double beta, bool upper, cudaStream_t st);
+
+int device_sm_count();
+
+}  // namespace sg

@@ -1,0 +1,590 @@
+// Host driver of the adaptive s-step GMRES (Alg. 4 with restarts): the
+// kernels run on one stream; the s x s Cholesky factors, the Hessenberg
+// matrix and the Givens rotations live on the host, as in the paper where
+// they are "local to each processor" (Sec. 2).  Control crosses to the
+// host twice per block (after each Gram matrix), carrying (i+s) x s
+// values.
+#include "sg_solver.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+namespace sg {
+
+namespace {
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+template <typename T>
+void dev_alloc(T** p, size_t count) {
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  if (count == 0) return;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * count);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    throw Error(SG_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+}
+
+// Small-matrix slots inside h->small / h->hbuf (offsets in doubles).
+struct Slots {
+  int64_t W, G, Z, Y, scal, H, wn, total;
+};
+Slots slots_for(int m, int k) {
+  Slots s{};
+  const int64_t mm = m + 1, kk = k + 1;
+  int64_t o = 0;
+  s.W = o;    o += mm * kk;   // i x s block products (W, R')
+  s.G = o;    o += kk * kk;   // Gram matrices
+  s.Z = o;    o += kk * kk;   // inverse Cholesky factors
+  s.Y = o;    o += mm;        // least-squares solution
+  s.scal = o; o += 16;        // scalars (norms)
+  s.H = o;    o += kk * kk;   // Arnoldi pre-pass Hessenberg ((k+1) x k)
+  s.wn = o;   o += kk;        // pre-pass norms before projection
+  s.total = o;
+  return s;
+}
+
+// Largest split-partials buffer over every block shape the solver uses
+// (i <= imax rows of Q^T, s <= smax columns).
+int64_t max_part_size(int64_t n, int imax, int smax) {
+  int64_t best = 1;
+  for (int i = 1; i <= std::max(imax, smax); ++i)
+    for (int s = 1; s <= smax; ++s)
+      best = std::max(best, block_dot_part_size(n, i, s));
+  return best;
+}
+
+}  // namespace
+
+void ensure_workspace(sg_handle* h, int64_t n, int m, int k) {
+  if (h->ws_n == n && h->ws_m >= m && h->ws_k >= k && h->Q) return;
+  m = std::max(m, h->ws_n == n ? h->ws_m : 0);
+  k = std::max(k, h->ws_n == n ? h->ws_k : 0);
+  const int64_t ld = (n + 31) / 32 * 32;  // 256-byte aligned columns
+  dev_alloc(&h->Q, static_cast<size_t>(ld) * (m + 1));
+  dev_alloc(&h->V, static_cast<size_t>(ld) * (k + 1));
+  dev_alloc(&h->Y, static_cast<size_t>(ld) * k);
+  dev_alloc(&h->bvec, n);
+  dev_alloc(&h->xvec, n);
+  dev_alloc(&h->rvec, n);
+  const int64_t part = max_part_size(n, m + 1, k);
+  dev_alloc(&h->part, part);
+  h->part_cap = part;
+  dev_alloc(&h->red, static_cast<size_t>(reduction_blocks()) * 3);
+  Slots sl = slots_for(m, k);
+  dev_alloc(&h->small, sl.total);
+  h->small_cap = sl.total;
+  if (h->hbuf) cudaFreeHost(h->hbuf);
+  h->hbuf = nullptr;
+  SG_CUDA(cudaMallocHost(reinterpret_cast<void**>(&h->hbuf), sizeof(double) * sl.total));
+  for (auto& e : h->ev)
+    if (!e) SG_CUDA(cudaEventCreate(&e));
+  h->ws_n = n;
+  h->ld = ld;
+  h->ws_m = m;
+  h->ws_k = k;
+}
+
+void ensure_workspace32(sg_handle* h, int64_t n, int m, int k) {
+  // FP64 vectors, partials and small slots come from the FP64 workspace
+  // with empty basis blocks; the FP32 basis is allocated here.
+  if (!(h->ws_n == n && h->ws_m >= m && h->ws_k >= k)) {
+    if (h->Q) cudaFree(h->Q);
+    if (h->V) cudaFree(h->V);
+    if (h->Y) cudaFree(h->Y);
+    h->Q = h->V = h->Y = nullptr;
+    const int mm = std::max(m, h->ws_n == n ? h->ws_m : 0);
+    const int kk = std::max(k, h->ws_n == n ? h->ws_k : 0);
+    const int64_t ld = (n + 31) / 32 * 32;
+    dev_alloc(&h->bvec, n);
+    dev_alloc(&h->xvec, n);
+    dev_alloc(&h->rvec, n);
+    const int64_t part = max_part_size(n, mm + 1, kk);
+    dev_alloc(&h->part, part);
+    h->part_cap = part;
+    dev_alloc(&h->red, static_cast<size_t>(reduction_blocks()) * 3);
+    Slots sl = slots_for(mm, kk);
+    dev_alloc(&h->small, sl.total);
+    h->small_cap = sl.total;
+    if (h->hbuf) cudaFreeHost(h->hbuf);
+    h->hbuf = nullptr;
+    SG_CUDA(cudaMallocHost(reinterpret_cast<void**>(&h->hbuf), sizeof(double) * sl.total));
+    for (auto& e : h->ev)
+      if (!e) SG_CUDA(cudaEventCreate(&e));
+    h->ws_n = n;
+    h->ld = ld;
+    h->ws_m = mm;
+    h->ws_k = kk;
+  }
+  if (h->ws32_n == n && h->ws32_m >= m && h->ws32_k >= k) return;
+  const int64_t ld = h->ld;
+  const int mm = std::max(m, h->ws_m), kk = std::max(k, h->ws_k);
+  dev_alloc(&h->Q32, static_cast<size_t>(ld) * (mm + 1));
+  dev_alloc(&h->V32, static_cast<size_t>(ld) * (kk + 1));
+  dev_alloc(&h->Y32, static_cast<size_t>(ld) * kk);
+  h->ws32_n = n;
+  h->ws32_m = mm;
+  h->ws32_k = kk;
+}
+
+namespace {
+
+// Kernel set of one basis precision: FP64 (T = double) or FP32 (float).
+template <typename T> struct Basis;
+
+template <> struct Basis<double> {
+  static double* Q(sg_handle* h) { return h->Q; }
+  static double* V(sg_handle* h) { return h->V; }
+  static double* Y(sg_handle* h) { return h->Y; }
+  static void spmv(const DevCsr& M, const double* x, const double* z, double* y,
+                   double th, double c, double g, cudaStream_t st) {
+    spmv_newton(M, x, z, y, th, c, g, st);
+  }
+  static void dot(int64_t n, const double* x, const double* y, double* p, cudaStream_t st) {
+    dot_partials(n, x, y, p, st);
+  }
+  static void mgs(int64_t n, double* w, const double* v, const double* vn,
+                  const double* pin, double* hout, double* pout, cudaStream_t st) {
+    mgs_step(n, w, v, vn, pin, hout, pout, st);
+  }
+  static void norml(int64_t n, const double* pin, const double* x, double* y,
+                    double* nout, cudaStream_t st) {
+    normalize(n, pin, x, y, nout, st);
+  }
+  static void from_f64(int64_t n, const double* r, double* q, double a, cudaStream_t st) {
+    scale_copy(n, r, q, a, st);
+  }
+  static void bdot(int64_t n, const double* Q, int64_t ldq, int i, const double* X,
+                   int64_t ldx, int s, double* W, int ldw, bool sym, double* part,
+                   int64_t cap, cudaStream_t st) {
+    block_dot(n, Q, ldq, i, X, ldx, s, W, ldw, sym, part, cap, st);
+  }
+  static void bupd(int64_t n, const double* Q, int64_t ldq, int i, const double* W,
+                   int ldw, double* X, int64_t ldx, int s, double al, double be,
+                   bool up, cudaStream_t st) {
+    block_update(n, Q, ldq, i, W, ldw, X, ldx, s, al, be, up, st);
+  }
+  static void gemv(int64_t n, int k, const double* Q, int64_t ldq, const double* y,
+                   double* x, cudaStream_t st) {
+    gemv_n_add(n, k, Q, ldq, y, x, st);
+  }
+};
+
+template <> struct Basis<float> {
+  static float* Q(sg_handle* h) { return h->Q32; }
+  static float* V(sg_handle* h) { return h->V32; }
+  static float* Y(sg_handle* h) { return h->Y32; }
+  static void spmv(const DevCsr& M, const float* x, const float* z, float* y,
+                   double th, double c, double g, cudaStream_t st) {
+    spmv_newton32(M, x, z, y, static_cast<float>(th), static_cast<float>(c),
+                  static_cast<float>(g), st);
+  }
+  static void dot(int64_t n, const float* x, const float* y, double* p, cudaStream_t st) {
+    dot_partials32(n, x, y, p, st);
+  }
+  static void mgs(int64_t n, float* w, const float* v, const float* vn,
+                  const double* pin, double* hout, double* pout, cudaStream_t st) {
+    mgs_step32(n, w, v, vn, pin, hout, pout, st);
+  }
+  static void norml(int64_t n, const double* pin, const float* x, float* y,
+                    double* nout, cudaStream_t st) {
+    normalize32(n, pin, x, y, nout, st);
+  }
+  static void from_f64(int64_t n, const double* r, float* q, double a, cudaStream_t st) {
+    to_f32(n, r, q, static_cast<float>(a), st);
+  }
+  static void bdot(int64_t n, const float* Q, int64_t ldq, int i, const float* X,
+                   int64_t ldx, int s, double* W, int ldw, bool sym, double* part,
+                   int64_t cap, cudaStream_t st) {
+    block_dot32(n, Q, ldq, i, X, ldx, s, W, ldw, sym, part, cap, st);
+  }
+  static void bupd(int64_t n, const float* Q, int64_t ldq, int i, const double* W,
+                   int ldw, float* X, int64_t ldx, int s, double al, double be,
+                   bool up, cudaStream_t st) {
+    block_update32(n, Q, ldq, i, W, ldw, X, ldx, s, al, be, up, st);
+  }
+  static void gemv(int64_t n, int k, const float* Q, int64_t ldq, const double* y,
+                   double* x, cudaStream_t st) {
+    gemv_n_add32(n, k, Q, ldq, y, x, st);
+  }
+};
+
+// ---------------------------------------------------------------------
+// Ritz pre-pass: k steps of MGS-Arnoldi from q (device, unit norm) with
+// the basis in V's columns (Sec. 3.4).  Returns the steps completed and
+// fills Hh ((k+1) x k, host, ld k+1).
+template <typename T>
+int arnoldi_prepass(sg_handle* h, const DevCsr& M, const T* q, int k,
+                    cudaStream_t st, std::vector<double>& Hh) {
+  using B = Basis<T>;
+  const int64_t n = M.n, ld = h->ld;
+  T* V = B::V(h);
+  Slots sl = slots_for(h->ws_m, h->ws_k);
+  double* Hd = h->small + sl.H;
+  double* wn = h->small + sl.wn;
+  const int ldh = k + 1;
+  SG_CUDA(cudaMemsetAsync(Hd, 0, sizeof(double) * ldh * k, st));
+  SG_CUDA(cudaMemcpyAsync(V, q, sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
+  const int G = reduction_blocks();
+  double* redA = h->red;
+  double* redB = h->red + G;
+  double* redC = h->red + 2 * G;
+  for (int j = 0; j < k; ++j) {
+    T* w = V + static_cast<int64_t>(j + 1) * ld;
+    B::spmv(M, V + static_cast<int64_t>(j) * ld, nullptr, w, 0.0, 0.0, 1.0, st);
+    B::dot(n, w, w, redC, st);
+    finish_sum(redC, wn + j, true, st);
+    B::dot(n, V, w, redA, st);
+    double* pin = redA;
+    double* pout = redB;
+    for (int l = 0; l <= j; ++l) {
+      const T* vnext = (l < j) ? V + static_cast<int64_t>(l + 1) * ld : nullptr;
+      B::mgs(n, w, V + static_cast<int64_t>(l) * ld, vnext, pin,
+             Hd + l + static_cast<int64_t>(j) * ldh, pout, st);
+      std::swap(pin, pout);
+    }
+    B::norml(n, pin, w, w, Hd + (j + 1) + static_cast<int64_t>(j) * ldh, st);
+  }
+  Hh.assign(static_cast<size_t>(ldh) * k, 0.0);
+  std::vector<double> wnh(k);
+  SG_CUDA(cudaMemcpyAsync(h->hbuf, Hd, sizeof(double) * ldh * k, cudaMemcpyDeviceToHost, st));
+  SG_CUDA(cudaMemcpyAsync(h->hbuf + ldh * k, wn, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+  SG_CUDA(cudaStreamSynchronize(st));
+  std::memcpy(Hh.data(), h->hbuf, sizeof(double) * ldh * k);
+  std::memcpy(wnh.data(), h->hbuf + ldh * k, sizeof(double) * k);
+  for (int j = 0; j < k; ++j) {
+    const double sub = Hh[(j + 1) + static_cast<size_t>(j) * ldh];
+    if (!(sub > 1e-12 * wnh[j]) || !std::isfinite(sub)) return j + 1;
+  }
+  return k;
+}
+
+struct Shifts {
+  std::vector<double> re, im, gamma;
+  std::vector<BasisStep> steps;
+};
+
+Shifts make_shifts(const std::vector<double>& Hh, int ldh, int steps,
+                   int basis) {
+  Shifts sh;
+  std::vector<double> re(steps), im(steps);
+  if (hessenberg_eigvals(Hh.data(), ldh, steps, re.data(), im.data()) != 0)
+    throw Error(SG_ENUMERIC, "Ritz values: QR iteration did not converge");
+  for (int t = 0; t < steps; ++t)
+    if (!std::isfinite(re[t]) || !std::isfinite(im[t]))
+      throw Error(SG_ENUMERIC, "Ritz values: non-finite");
+  sh.re.resize(steps);
+  sh.im.resize(steps);
+  leja_order(steps, re.data(), im.data(), sh.re.data(), sh.im.data());
+  sh.gamma.resize(steps);
+  scaling_coefficients(steps, sh.re.data(), sh.im.data(), sh.gamma.data());
+  std::vector<double> th_re(sh.re), th_im(sh.im), gm(sh.gamma);
+  if (basis == SG_BASIS_MONOMIAL) {
+    std::fill(th_re.begin(), th_re.end(), 0.0);
+    std::fill(th_im.begin(), th_im.end(), 0.0);
+    std::fill(gm.begin(), gm.end(), 1.0);
+  } else if (basis == SG_BASIS_NEWTON) {
+    std::fill(gm.begin(), gm.end(), 1.0);
+  }
+  basis_steps(steps, th_re.data(), th_im.data(), gm.data(), sh.steps);
+  return sh;
+}
+
+// -------------------------------------------------------------------------
+// Alg. 4 with restarts.  T is the storage/arithmetic of the Krylov basis;
+// x, r and b are always FP64 (xvec, rvec, bvec), so with T = float every
+// cycle restarts from an FP64 residual: one iterative-refinement step per
+// cycle.  cycle_tol > 0 ends a cycle once the implicit residual has
+// dropped by that factor relative to the cycle's own start.
+template <typename T>
+void solve_impl(sg_handle* h, const DevCsr& M, const SolveOpts& o,
+                double cycle_tol, cudaStream_t st, SolveLog& log) {
+  using B = Basis<T>;
+  const double t0 = now_ms();
+  const int64_t n = M.n;
+  const int m = o.m;
+  const int kritz = std::min(o.s > 0 ? o.s : o.s_max, m);
+  const int64_t ld = h->ld;
+  T* Qb = B::Q(h);
+  T* Vb = B::V(h);
+  T* Yb = B::Y(h);
+  Slots sl = slots_for(h->ws_m, h->ws_k);
+  double* Wd = h->small + sl.W;
+  double* Gd = h->small + sl.G;
+  double* Zd = h->small + sl.Z;
+  double* yd = h->small + sl.Y;
+  double* sc = h->small + sl.scal;
+  double* hb = h->hbuf;
+  const int max_iters = o.max_iters > 0 ? o.max_iters : 50 * m;
+
+  auto device_norm = [&](const double* v, double* slot) {
+    dot_partials(n, v, v, h->red, st);
+    finish_sum(h->red, slot, true, st);
+  };
+  auto fetch = [&](const double* src, int64_t count, double* dst) {
+    SG_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * count, cudaMemcpyDeviceToHost, st));
+  };
+
+  // r = b - A x0, beta0 (Alg. 4, first line)
+  residual(M, h->bvec, h->xvec, h->rvec, st);
+  device_norm(h->rvec, sc);
+  fetch(sc, 1, hb);
+  SG_CUDA(cudaStreamSynchronize(st));
+  const double beta0 = hb[0];
+  log = SolveLog();
+  if (!std::isfinite(beta0)) throw Error(SG_ENUMERIC, "non-finite initial residual");
+  if (beta0 == 0.0) {
+    log.converged = true;
+    log.t_total = now_ms() - t0;
+    return;
+  }
+  double beta = beta0;
+  Shifts sh;
+  bool have_shifts = false;
+  int cur_s = 0;
+  int total = 0;
+  std::vector<double> Hh(static_cast<size_t>(m + 1) * m);
+  const int ldH = m + 1;
+  Givens gv;
+  const size_t kk2 = static_cast<size_t>(h->ws_k + 1) * (h->ws_k + 1);
+  std::vector<double> Wh, Gh, Zinv(kk2), Z1(kk2), Rph, R2(kk2), Rtop, Rkk, Bm, yv;
+
+  for (;;) {
+    // Q_1 = r / beta
+    B::from_f64(n, h->rvec, Qb, 1.0 / beta, st);
+    if (!have_shifts) {
+      const double tp = now_ms();
+      std::vector<double> Hp;
+      const int steps = arnoldi_prepass<T>(h, M, Qb, kritz, st, Hp);
+      sh = make_shifts(Hp, kritz + 1, steps, o.basis);
+      if (o.s > 0) {
+        cur_s = std::min(o.s, steps);
+      } else {
+        cur_s = estimate_step(steps, sh.re.data(), sh.im.data(), o.eps,
+                              o.omega_est, o.s_min, std::min(o.s_max, steps),
+                              nullptr);
+        cur_s = std::min(cur_s, steps);
+      }
+      cur_s = std::max(cur_s, 1);
+      log.s0 = cur_s;
+      log.ritz_re = sh.re;
+      log.ritz_im = sh.im;
+      log.gamma = sh.gamma;
+      have_shifts = true;
+      log.t_prepass += now_ms() - tp;
+    }
+    std::fill(Hh.begin(), Hh.end(), 0.0);
+    gv.reset(m, beta);
+    int i = 1, jdone = 0;
+    bool stop_cycle = false;
+    while (i <= m && !stop_cycle) {
+      const int s_eff = std::min(cur_s, m + 1 - i);
+      const T* qi = Qb + static_cast<int64_t>(i - 1) * ld;
+      SG_CUDA(cudaEventRecord(h->ev[0], st));
+      // matrix powers kernel (Sec. 2): V[:, j+1] from V[:, j] (V[:,0] = Q_i)
+      for (int j = 0; j < s_eff; ++j) {
+        const T* src = (j == 0) ? qi : Vb + static_cast<int64_t>(j) * ld;
+        const T* zsrc = nullptr;
+        if (sh.steps[j].c != 0.0)
+          zsrc = (j == 1) ? qi : Vb + static_cast<int64_t>(j - 1) * ld;
+        B::spmv(M, src, zsrc, Vb + static_cast<int64_t>(j + 1) * ld,
+                sh.steps[j].theta, sh.steps[j].c, sh.steps[j].gamma, st);
+      }
+      SG_CUDA(cudaEventRecord(h->ev[1], st));
+      T* X = Vb + ld;
+      // first BCGS: W = Q^T X; X -= Q W; G = X^T X
+      B::bdot(n, Qb, ld, i, X, ld, s_eff, Wd, i, false, h->part, h->part_cap, st);
+      B::bupd(n, Qb, ld, i, Wd, i, X, ld, s_eff, -1.0, 1.0, false, st);
+      B::bdot(n, X, ld, s_eff, X, ld, s_eff, Gd, s_eff, true, h->part, h->part_cap, st);
+      fetch(Wd, static_cast<int64_t>(i) * s_eff, hb);
+      fetch(Gd, static_cast<int64_t>(s_eff) * s_eff, hb + static_cast<int64_t>(i) * s_eff);
+      SG_CUDA(cudaEventRecord(h->ev[2], st));
+      SG_CUDA(cudaStreamSynchronize(st));
+      {
+        float a = 0, b = 0;
+        cudaEventElapsedTime(&a, h->ev[0], h->ev[1]);
+        cudaEventElapsedTime(&b, h->ev[1], h->ev[2]);
+        log.t_mpk += a;
+        log.t_ortho += b;
+      }
+      const double th0 = now_ms();
+      Wh.assign(hb, hb + static_cast<int64_t>(i) * s_eff);
+      Gh.assign(hb + static_cast<int64_t>(i) * s_eff,
+                hb + static_cast<int64_t>(i) * s_eff + static_cast<int64_t>(s_eff) * s_eff);
+      for (double v : Gh)
+        if (!std::isfinite(v)) throw Error(SG_ENUMERIC, "non-finite Gram matrix");
+      // first partial CholQR (Alg. 3)
+      const int ldr = s_eff;
+      Z1.assign(static_cast<size_t>(s_eff) * s_eff, 0.0);
+      const int p1 = partial_cholesky(Gh.data(), s_eff, s_eff, o.omega, Z1.data(), ldr, nullptr);
+      int q = 0;
+      bool breakdown = false;
+      Rtop.clear();
+      Rkk.clear();
+      log.s_eff_hist.push_back(s_eff);
+      log.p1_hist.push_back(p1);
+      log.t_host += now_ms() - th0;
+      if (p1 == 0) {
+        breakdown = true;
+        q = 1;
+        Rtop.assign(Wh.begin(), Wh.begin() + i);
+        Rkk.assign(1, 0.0);
+      } else {
+        upper_inverse(Z1.data(), ldr, p1, Zinv.data(), p1);
+        // H2D staging uses its own pinned slot: the D2H slots may be
+        // refilled before this copy has run
+        std::memcpy(hb + sl.Z, Zinv.data(), sizeof(double) * p1 * p1);
+        SG_CUDA(cudaMemcpyAsync(Zd, hb + sl.Z, sizeof(double) * p1 * p1, cudaMemcpyHostToDevice, st));
+        SG_CUDA(cudaEventRecord(h->ev[1], st));
+        // Q_k = X(:, 1:p) Z^-1, then second BCGS and the second Gram
+        B::bupd(n, X, ld, p1, Zd, p1, Yb, ld, p1, 1.0, 0.0, true, st);
+        B::bdot(n, Qb, ld, i, Yb, ld, p1, Wd, i, false, h->part, h->part_cap, st);
+        B::bupd(n, Qb, ld, i, Wd, i, Yb, ld, p1, -1.0, 1.0, false, st);
+        B::bdot(n, Yb, ld, p1, Yb, ld, p1, Gd, p1, true, h->part, h->part_cap, st);
+        fetch(Wd, static_cast<int64_t>(i) * p1, hb);
+        fetch(Gd, static_cast<int64_t>(p1) * p1, hb + static_cast<int64_t>(i) * p1);
+        SG_CUDA(cudaEventRecord(h->ev[2], st));
+        SG_CUDA(cudaStreamSynchronize(st));
+        {
+          float b = 0;
+          cudaEventElapsedTime(&b, h->ev[1], h->ev[2]);
+          log.t_ortho += b;
+        }
+        const double th1 = now_ms();
+        Rph.assign(hb, hb + static_cast<int64_t>(i) * p1);
+        Gh.assign(hb + static_cast<int64_t>(i) * p1,
+                  hb + static_cast<int64_t>(i) * p1 + static_cast<int64_t>(p1) * p1);
+        for (double v : Gh)
+          if (!std::isfinite(v)) throw Error(SG_ENUMERIC, "non-finite Gram matrix");
+        R2.assign(static_cast<size_t>(p1) * p1, 0.0);
+        const int p2 = partial_cholesky(Gh.data(), p1, p1, o.omega, R2.data(), p1, nullptr);
+        if (p2 == 0) {
+          breakdown = true;
+          q = 1;
+          Rtop.resize(i);
+          for (int r = 0; r < i; ++r) Rtop[r] = Wh[r] + Rph[r] * Z1[0];
+          Rkk.assign(1, 0.0);
+          log.t_host += now_ms() - th1;
+        } else {
+          q = p2;
+          // R_top = W(:, 1:q) + R'(:, 1:q) Z(1:q, 1:q); R_kk = Z~ Z(1:q, 1:q)
+          Rtop.assign(static_cast<size_t>(i) * q, 0.0);
+          Rkk.assign(static_cast<size_t>(q) * q, 0.0);
+          for (int c = 0; c < q; ++c) {
+            for (int r = 0; r < i; ++r) {
+              double acc = Wh[r + static_cast<int64_t>(c) * i];
+              for (int t = 0; t <= c; ++t)
+                acc += Rph[r + static_cast<int64_t>(t) * i] * Z1[t + static_cast<int64_t>(c) * ldr];
+              Rtop[r + static_cast<int64_t>(c) * i] = acc;
+            }
+            for (int r = 0; r <= c; ++r) {
+              double acc = 0.0;
+              for (int t = r; t <= c; ++t)
+                acc += R2[r + static_cast<int64_t>(t) * p1] * Z1[t + static_cast<int64_t>(c) * ldr];
+              Rkk[r + static_cast<int64_t>(c) * q] = acc;
+            }
+          }
+          upper_inverse(R2.data(), p1, q, Zinv.data(), q);
+          std::memcpy(hb + sl.Z, Zinv.data(), sizeof(double) * q * q);
+          log.t_host += now_ms() - th1;
+          SG_CUDA(cudaMemcpyAsync(Zd, hb + sl.Z, sizeof(double) * q * q, cudaMemcpyHostToDevice, st));
+          // Q_k = Q_k(:, 1:q) Z~^-1 into Q's next columns
+          B::bupd(n, Yb, ld, q, Zd, q, Qb + static_cast<int64_t>(i) * ld, ld, q,
+                  1.0, 0.0, true, st);
+        }
+      }
+      const double th2 = now_ms();
+      // Hessenberg columns, Givens rotations, convergence check
+      Bm.assign(static_cast<size_t>(q + 1) * q, 0.0);
+      {
+        std::vector<BasisStep> stq(sh.steps.begin(), sh.steps.begin() + q);
+        change_of_basis(stq, q, Bm.data(), q + 1);
+      }
+      assemble_hessenberg(Hh.data(), ldH, i, q, Rtop.data(), i, Rkk.data(), q, Bm.data(), q + 1);
+      log.s_hist.push_back(breakdown ? 0 : q);
+      for (int c = 0; c < q; ++c) {
+        const int j = i - 1 + c;
+        const double gj = gv.add_column(Hh.data(), ldH, j);
+        const double rel = gj / beta0;
+        if (!std::isfinite(rel)) throw Error(SG_ENUMERIC, "non-finite residual estimate");
+        log.relres_hist.push_back(rel);
+        jdone = j + 1;
+        if (rel <= o.tol || breakdown || (cycle_tol > 0.0 && gj <= cycle_tol * beta)) {
+          stop_cycle = true;
+          break;
+        }
+      }
+      if (!breakdown && q < s_eff) cur_s = q;  // Alg. 4: s = p
+      i += q;
+      if (total + jdone >= max_iters) stop_cycle = true;
+      log.t_host += now_ms() - th2;
+    }
+    // end of cycle: y from the triangular least-squares problem, x += Q y
+    yv.assign(jdone, 0.0);
+    gv.solve(jdone, yv.data());
+    std::memcpy(hb + sl.Y, yv.data(), sizeof(double) * jdone);
+    SG_CUDA(cudaMemcpyAsync(yd, hb + sl.Y, sizeof(double) * jdone, cudaMemcpyHostToDevice, st));
+    B::gemv(n, jdone, Qb, ld, yd, h->xvec, st);
+    residual(M, h->bvec, h->xvec, h->rvec, st);
+    device_norm(h->rvec, sc);
+    fetch(sc, 1, hb);
+    SG_CUDA(cudaStreamSynchronize(st));
+    beta = hb[0];
+    total += jdone;
+    const double rel_true = beta / beta0;
+    log.cycle_relres.push_back(rel_true);
+    log.cycle_iters.push_back(jdone);
+    if (!std::isfinite(rel_true)) throw Error(SG_ENUMERIC, "non-finite residual");
+    if (rel_true <= o.tol) {
+      log.converged = true;
+      break;
+    }
+    if (total >= max_iters) break;
+    if (beta == 0.0) { log.converged = true; break; }
+  }
+  log.iters = total;
+  log.restarts = static_cast<int>(log.cycle_relres.size()) - 1;
+  log.final_relres = log.cycle_relres.back();
+  log.t_total = now_ms() - t0;
+}
+
+}  // namespace
+
+void solve_fp64(sg_handle* h, const DevCsr& M, const SolveOpts& o,
+                cudaStream_t st, SolveLog& log) {
+  const int kritz = std::min(o.s > 0 ? o.s : o.s_max, o.m);
+  ensure_workspace(h, M.n, o.m, std::max(kritz, 1));
+  solve_impl<double>(h, M, o, 0.0, st, log);
+}
+
+void solve_fp32_ir(sg_handle* h, const DevCsr& M, const SolveOpts& o,
+                   double inner_tol, int max_refine, cudaStream_t st,
+                   SolveLog& log) {
+  const int kritz = std::min(o.s > 0 ? o.s : o.s_max, o.m);
+  ensure_workspace32(h, M.n, o.m, std::max(kritz, 1));
+  SolveOpts o32 = o;
+  // Bounds of the FP32 basis.  The paper's rule Omega ~ 0.1 eps^-1/2
+  // (Sec. 3.2) is set by the accuracy of the Gram matrix the Cholesky
+  // factor comes from; the FP32 Gram matrices here are formed from exact
+  // products with compensated sums (relative accuracy ~2^-40 after the
+  // split reduction), so Omega_32 = 0.1 (2^-40)^-1/2 = 0.1 2^20.  That also
+  // keeps the FP32 triangular product's orthogonality loss eps_32 Omega
+  // below 1e-2, which the second CholQR pass removes.  The estimator uses
+  // the basis round-off eps_32 = 2^-24 and the same threshold.
+  const double omega32 = 0.1 * std::ldexp(1.0, 20);
+  o32.eps = std::ldexp(1.0, -24);
+  o32.omega = std::min(o.omega, omega32);
+  o32.omega_est = std::min(o.omega_est, omega32);
+  o32.max_iters = o.max_iters > 0 ? o.max_iters : max_refine * o.m;
+  solve_impl<float>(h, M, o32, inner_tol, st, log);
+  log.refinements = static_cast<int>(log.cycle_relres.size());
+}
+
+}  // namespace sg

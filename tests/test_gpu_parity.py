@@ -1,0 +1,398 @@
+"""GPU parity: the CUDA library (through its C ABI) against the CPU oracle
+on the same seeded inputs.
+
+Per-step kernels are compared element by element; whole solves must give
+identical step-size decisions and iteration counts, per-cycle true
+residual norms within 1e-8 relative and the final x within 1e-9 relative
+(the FP64 parity bar).  Sizes span several tiles and a ragged tail.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import sgmres_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2303_08953_gb300 as sg  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=DEV)
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+@pytest.fixture(scope="module")
+def solver():
+    s = sg.Solver(0)
+    yield s
+    s.close()
+
+
+def _analyze(solver, A):
+    solver.analyze_csr(A)
+    return O.as_operator(A)
+
+
+SMALL_MATRICES = {
+    "stencil2d_37x29": lambda: W.stencil2d(37, 29),
+    "convdiff3d_11": lambda: W.stencil3d_convdiff(11),
+    "randband_5003": lambda: W.random_band(5003, k=24, band=300)[0],
+    "vardiff3d_9": lambda: W.vardiff3d(9)[0],
+    "aniso2d_41": lambda: W.aniso2d(41)[0],
+}
+
+
+# ------------------------------------------------------------- SpMV / MPK
+@pytest.mark.parametrize("name", list(SMALL_MATRICES))
+def test_spmv_newton_matches_oracle(solver, name):
+    A = SMALL_MATRICES[name]()
+    op = _analyze(solver, A)
+    rng = np.random.default_rng(21)
+    x = rng.uniform(-1, 1, A.n)
+    z = rng.uniform(-1, 1, A.n)
+    for theta, c, gamma in [(0.0, 0.0, 1.0), (1.7, 0.0, 2.5), (-0.3, 0.8, 0.9)]:
+        y = host(solver.spmv_newton(dev(x), theta, gamma, dev(z) if c else None, c))
+        ref = (O.spmv(op, x) - theta * x + c * z) / gamma
+        scale = (np.abs(op) @ np.abs(x) + abs(theta) * np.abs(x) + abs(c) * np.abs(z)) / abs(gamma)
+        assert np.all(np.abs(y - ref) <= 1e-14 * scale + 1e-300)
+
+
+def test_residual_matches_oracle(solver):
+    A = W.stencil3d_convdiff(13)
+    op = _analyze(solver, A)
+    rng = np.random.default_rng(22)
+    x, b = rng.uniform(-1, 1, A.n), rng.uniform(-1, 1, A.n)
+    r = host(solver.residual(dev(b), dev(x)))
+    assert np.allclose(r, b - op @ x, rtol=0, atol=1e-14 * (np.abs(b).max() + 10))
+
+
+def test_mpk_matches_oracle_with_pair(solver):
+    A = W.stencil2d(33, 21)
+    op = _analyze(solver, A)
+    q = np.random.default_rng(23).uniform(-1, 1, A.n)
+    q /= np.linalg.norm(q)
+    theta = np.array([7.1, 0.4, 3.0 + 1.2j, 3.0 - 1.2j, 5.5, 1.9 + 0.4j, 1.9 - 0.4j])
+    gamma = np.array([3.0, 3.6, 1.3, 1.3, 1.9, 2.2, 2.2])
+    V_o, _ = O.mpk(op, q, 7, theta, gamma)
+    V_g = host(solver.mpk(dev(q), 7, theta, gamma)).T
+    assert np.allclose(V_g, V_o, rtol=1e-12, atol=1e-13 * np.abs(V_o).max())
+
+
+def test_spmv_empty_rows(solver):
+    # rows with no entries produce zero (times 1/gamma) plus the shift part
+    rowptr = np.array([0, 1, 1, 3, 3], np.int32)
+    colind = np.array([0, 0, 3], np.int32)
+    val = np.array([2.0, -1.0, 4.0])
+    solver.analyze(rowptr, colind, val)
+    x = np.array([1.0, 2.0, 3.0, 4.0])
+    y = host(solver.spmv_newton(dev(x), 0.5, 2.0))
+    Ax = np.array([2.0, 0.0, -1.0 + 16.0, 0.0])
+    assert np.allclose(y, (Ax - 0.5 * x) / 2.0, rtol=0, atol=1e-15)
+
+
+# ------------------------------------------------------ dense block kernels
+@pytest.mark.parametrize("n", [1, 97, 4133, 70001])
+@pytest.mark.parametrize("i,s", [(1, 1), (1, 120), (5, 7), (8, 33), (9, 32),
+                                 (33, 65), (121, 120), (241, 17)])
+def test_block_dot_matches_definition(solver, n, i, s):
+    rng = np.random.default_rng(100 * i + s)
+    ld = n + (7 if n > 1 else 0)
+    Q = rng.standard_normal((i, ld))
+    X = rng.standard_normal((s, ld))
+    Wt = host(_block_dot(solver, Q, X, n))
+    ref = Q[:, :n] @ X[:, :n].T        # (i, s): Q^T X in column-major terms
+    scale = np.abs(Q[:, :n]) @ np.abs(X[:, :n]).T
+    assert np.all(np.abs(Wt.T - ref) <= 1e-14 * scale + 1e-300)
+
+
+def _block_dot(solver, Q, X, n, sym=False):
+    i, ld = Q.shape
+    s = X.shape[0]
+    Qd = dev(Q)
+    Xd = Qd if sym else dev(X)
+    W = torch.empty((s, i), dtype=torch.float64, device=DEV)
+    import ctypes as C
+    rc = sg.lib.sg_block_dot(solver._h, n, C.c_void_p(Qd.data_ptr()), ld, i,
+                             C.c_void_p(Xd.data_ptr()), ld, s,
+                             C.c_void_p(W.data_ptr()), i, 1 if sym else 0,
+                             sg._stream_ptr())
+    assert rc == 0, sg.lib.sg_last_error(solver._h)
+    return W
+
+
+@pytest.mark.parametrize("n,s", [(4133, 1), (4133, 31), (70001, 64), (3001, 120)])
+def test_block_dot_symmetric_gram(solver, n, s):
+    rng = np.random.default_rng(s)
+    X = rng.standard_normal((s, n))
+    G = host(_block_dot(solver, X, X, n, sym=True))
+    ref = X @ X.T
+    assert np.array_equal(G, G.T)
+    assert np.allclose(G, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("n", [1, 63, 64, 65, 5000, 70001])
+@pytest.mark.parametrize("i,s,upper", [(1, 1, False), (3, 120, False),
+                                       (121, 40, False), (33, 33, True),
+                                       (120, 120, True), (7, 7, True)])
+def test_block_update_matches_definition(solver, n, i, s, upper):
+    rng = np.random.default_rng(n + i + s)
+    Q = rng.standard_normal((i, n))
+    Wm = rng.standard_normal((i, s))          # i x s
+    if upper:
+        Wm = np.triu(Wm) + np.tril(np.full((i, s), np.nan), -1)
+    X = rng.standard_normal((s, n))
+    Wt = dev(np.ascontiguousarray(Wm.T))      # (s, i) = column-major i x s
+    Xd = dev(X)
+    solver.block_update(dev(Q), Wt, Xd, alpha=-0.7, beta=1.3 if not upper else 0.0,
+                        upper=upper, n=n)
+    Wz = np.nan_to_num(Wm, nan=0.0)
+    ref = (1.3 if not upper else 0.0) * X + (-0.7) * (Q.T @ Wz).T
+    scale = np.abs(X) + 0.7 * (np.abs(Q).T @ np.abs(Wz)).T
+    got = host(Xd)
+    assert np.all(np.abs(got - ref) <= 1e-14 * scale + 1e-300)
+
+
+def test_nrm2(solver):
+    x = np.random.default_rng(5).standard_normal(123457)
+    assert solver.nrm2(dev(x)) == pytest.approx(np.linalg.norm(x), rel=1e-14)
+
+
+# ------------------------------------------------------------ whole solves
+def residual_floor(A, b, x, x0=None):
+    """Rounding floor of evaluating ||b - A x|| / ||b - A x0|| in FP64:
+    each side's computed residual is within (k+1) u (|b| + |A||x|) of the
+    exact one componentwise (k = longest row), so two correct evaluations
+    of the same relres can differ by twice that, relative to beta0."""
+    op = O.as_operator(A)
+    k = int(np.max(np.diff(op.indptr)))
+    u = 2.0 ** -53
+    x0 = np.zeros_like(b) if x0 is None else x0
+    beta0 = np.linalg.norm(b - op @ x0)
+    return 2 * (k + 1) * u * np.linalg.norm(np.abs(b) + abs(op) @ np.abs(x)) / beta0
+
+
+def _compare(res_o, x_g, info, A, b, x0=None, xrel=1e-9, crel=1e-8, hrel=1e-6):
+    """Decisions identical; per-cycle true residuals within 1e-8 relative
+    (or the FP64 evaluation floor); x within 1e-9 relative."""
+    assert info.s0 == res_o.s0
+    assert list(info.s_hist) == list(res_o.s_hist)
+    assert list(info.p1_hist) == list(res_o.p1_hist)
+    assert list(info.s_eff_hist) == list(res_o.s_eff_hist)
+    assert info.iters == res_o.iters and info.restarts == res_o.restarts
+    assert list(info.cycle_iters) == list(res_o.cycle_iters)
+    assert info.converged == res_o.converged
+    floor = residual_floor(A, b, res_o.x, x0)
+    co = np.array(res_o.cycle_relres)
+    dc = np.abs(info.cycle_relres - co)
+    assert np.all(dc <= np.maximum(crel * co, floor)), (dc, co, floor)
+    ho = np.array(res_o.relres_hist)
+    assert info.relres_hist.size == ho.size
+    dh = np.abs(info.relres_hist - ho)
+    assert np.all(dh <= np.maximum(hrel * ho, floor)), (dh.max(), floor)
+    err = np.linalg.norm(x_g - res_o.x) / np.linalg.norm(res_o.x)
+    assert err <= xrel, err
+
+
+def test_solve_c1_matches_oracle(solver):
+    c = W.config_c1()
+    _analyze(solver, c["A"])
+    ro = O.adaptive_sgmres(c["A"], c["b"], m=c["m"], s=c["s"], tol=c["tol"])
+    x, info = solver.solve(c["b"], m=c["m"], s=c["s"], tol=c["tol"])
+    assert info.converged and info.final_relres <= 1e-10
+    _compare(ro, x, info, c["A"], c["b"])
+    # Ritz values and scaling coefficients agree too
+    assert np.allclose(info.ritz, ro.ritz, rtol=1e-9)
+    assert np.allclose(info.gamma, ro.gamma, rtol=1e-9)
+
+
+def test_solve_device_vectors_and_x0(solver):
+    c = W.config_c1(40)
+    _analyze(solver, c["A"])
+    x0 = np.random.default_rng(3).uniform(-1, 1, c["A"].n)
+    ro = O.adaptive_sgmres(c["A"], c["b"], x0=x0, m=50, s=8, tol=1e-10)
+    xd, info = solver.solve(dev(c["b"]), x0=dev(x0), m=50, s=8, tol=1e-10)
+    _compare(ro, host(xd), info, c["A"], c["b"], x0)
+
+
+def test_solve_estimator_c2_small(solver):
+    c = W.config_c2(16)
+    _analyze(solver, c["A"])
+    ro = O.adaptive_sgmres(c["A"], c["b"], m=80, s=0, s_min=4, s_max=40, tol=1e-10)
+    x, info = solver.solve(c["b"], m=80, s=0, s_min=4, s_max=40, tol=1e-10)
+    _compare(ro, x, info, c["A"], c["b"])
+
+
+@pytest.mark.parametrize("basis", ["newton", "monomial"])
+def test_solve_other_bases(solver, basis):
+    c = W.config_c1(24)
+    _analyze(solver, c["A"])
+    ro = O.adaptive_sgmres(c["A"], c["b"], m=40, s=6, tol=1e-10, basis=basis)
+    x, info = solver.solve(c["b"], m=40, s=6, tol=1e-10, basis=basis)
+    _compare(ro, x, info, c["A"], c["b"])
+
+
+def test_solve_paper_test1_monomial_s6(solver):
+    lam = np.linspace(0.1, 10.0, 10000)
+    A = W.diagonal(lam)
+    b = np.ones(10000) / 100.0
+    _analyze(solver, A)
+    ro = O.adaptive_sgmres(A, b, m=100, s=10, tol=1e-10, basis="monomial")
+    x, info = solver.solve(b, m=100, s=10, tol=1e-10, basis="monomial")
+    assert info.s_hist[0] == 6
+    _compare(ro, x, info, A, b)
+
+
+def test_solve_paper_test3_scaled_newton_s100(solver):
+    lam = np.linspace(0.1, 10.0, 10000)
+    A = W.diagonal(lam)
+    b = np.ones(10000) / 100.0
+    _analyze(solver, A)
+    ro = O.adaptive_sgmres(A, b, m=100, s=100, tol=1e-10)
+    x, info = solver.solve(b, m=100, s=100, tol=1e-10)
+    assert info.s_hist[0] == 100
+    _compare(ro, x, info, A, b)
+
+
+def test_solve_s1_matches_mgs_gmres(solver):
+    c = W.config_c1(20)
+    _analyze(solver, c["A"])
+    g = O.mgs_gmres(c["A"], c["b"], m=30, tol=1e-10)
+    x, info = solver.solve(c["b"], m=30, s=1, tol=1e-10)
+    assert info.iters == g.iters
+    assert np.max(np.abs(info.relres_hist - np.array(g.relres_hist))) <= 1e-12
+
+
+def test_solve_complex_spectrum(solver):
+    import scipy.sparse as sp
+    rng = np.random.default_rng(9)
+    nb = 300
+    a, bb = rng.uniform(1.0, 4.0, nb), rng.uniform(0.2, 1.5, nb)
+    blocks = [sp.csr_matrix(np.array([[a[k], bb[k]], [-bb[k], a[k]]]))
+              for k in range(nb)]
+    S = sp.csr_matrix(sp.block_diag(blocks, format="csr"))
+    S.sort_indices()
+    A = W.CSR(S.shape[0], S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data)
+    b = rng.uniform(-1, 1, A.n)
+    _analyze(solver, A)
+    ro = O.adaptive_sgmres(A, b, m=80, s=12, tol=1e-10)
+    x, info = solver.solve(b, m=80, s=12, tol=1e-10)
+    assert np.any(np.abs(info.ritz.imag) > 1e-3)
+    _compare(ro, x, info, A, b)
+
+
+def test_solve_random_band_small(solver):
+    A, rng = W.random_band(20000, k=24, band=4096)
+    xs = W.uniform_vector(A.n, rng)
+    b = W.rhs_from_solution(A, xs)
+    _analyze(solver, A)
+    ro = O.adaptive_sgmres(A, b, m=60, s=0, s_max=40, tol=1e-10)
+    x, info = solver.solve(b, m=60, s=0, s_max=40, tol=1e-10)
+    _compare(ro, x, info, A, b)
+
+
+def test_solve_zero_rhs_and_tiny(solver):
+    c = W.config_c1(6)
+    _analyze(solver, c["A"])
+    x, info = solver.solve(np.zeros(36), m=10, s=3)
+    assert info.converged and np.all(x == 0) and info.iters == 0
+    rng = np.random.default_rng(8)
+    import scipy.sparse as sp
+    Ad = rng.standard_normal((25, 25)) + 8 * np.eye(25)
+    S = sp.csr_matrix(Ad)
+    A = W.CSR(25, S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data)
+    b = rng.standard_normal(25)
+    _analyze(solver, A)
+    x, info = solver.solve(b, m=25, s=5, tol=1e-13)
+    xs = O.dense_solve(A, b)
+    assert info.iters <= 25
+    assert np.linalg.norm(x - xs) <= np.linalg.cond(Ad) * 1e-14 * np.linalg.norm(xs)
+
+
+def test_solve_max_iters_reports_noconv(solver):
+    c = W.config_c1(32)
+    _analyze(solver, c["A"])
+    x, info = solver.solve(c["b"], m=20, s=5, tol=1e-14, max_iters=40)
+    assert info.status == sg.SG_ENOCONV and not info.converged
+    assert info.iters == 40
+
+
+def test_analyze_rejects_bad_csr(solver):
+    with pytest.raises(sg.SgError):
+        solver.analyze(np.array([0, 2, 1], np.int32), np.array([0, 1], np.int32),
+                       np.array([1.0, 2.0]))
+    with pytest.raises(sg.SgError):
+        solver.analyze(np.array([0, 2, 3], np.int32), np.array([1, 0, 5], np.int32),
+                       np.array([1.0, 2.0, 3.0]))
+
+
+# ------------------------------------------------------------ adjoint path
+def test_adjoint_solve_and_grad_values(solver):
+    c = W.config_c1(30)
+    A = c["A"]
+    op = _analyze(solver, A)
+    g = np.random.default_rng(4).uniform(-1, 1, A.n)
+    AT = op.T.tocsr()
+    AT.sort_indices()
+    ro = O.adaptive_sgmres(AT, g, m=60, s=8, tol=1e-10)
+    lam, info = solver.solve_adjoint(g, m=60, s=8, tol=1e-10)
+    _compare(ro, lam, info, AT, g)
+    x = np.random.default_rng(5).uniform(-1, 1, A.n)
+    dval = host(solver.grad_values(dev(lam), dev(x)))
+    rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    assert np.allclose(dval, -lam[rows] * x[A.colind], rtol=0, atol=0)
+
+
+# ------------------------------------------------------- FP32 basis + IR
+def test_fp32_ir_reaches_fp64_accuracy(solver):
+    c = W.config_c2(20)
+    _analyze(solver, c["A"])
+    x, info = solver.solve(c["b"], m=60, s=0, s_min=2, s_max=40, tol=1e-10,
+                           precision="fp32_ir")
+    assert info.converged and info.final_relres <= 1e-10
+    op = O.as_operator(c["A"])
+    rel = np.linalg.norm(c["b"] - op @ x) / np.linalg.norm(c["b"])
+    assert rel <= 1e-10
+    ro = O.adaptive_sgmres(c["A"], c["b"], m=60, s=0, s_min=2, s_max=40, tol=1e-10)
+    err = np.linalg.norm(x - ro.x) / np.linalg.norm(ro.x)
+    assert err <= 1e-8, err
+    assert info.refinements >= 2
+
+
+# ------------------------------------------------------ full-size workload
+@pytest.mark.slow
+def test_full_size_c2_sampled_and_converged(solver):
+    c = W.config_c2()
+    A = c["A"]
+    op = _analyze(solver, A)
+    rng = np.random.default_rng(31)
+    x = rng.uniform(-1, 1, A.n)
+    y = host(solver.spmv_newton(dev(x), 1.3, 2.1))
+    rows = rng.choice(A.n, 2000, replace=False)
+    for r in rows:
+        a, e = A.rowptr[r], A.rowptr[r + 1]
+        ref = (np.dot(A.val[a:e], x[A.colind[a:e]]) - 1.3 * x[r]) / 2.1
+        assert abs(y[r] - ref) <= 1e-14 * (np.abs(A.val[a:e]) @ np.abs(x[A.colind[a:e]]) + 2)
+    xs, info = solver.solve(c["b"], m=c["m"], s=0, s_min=c["s_min"],
+                            s_max=c["s_max"], tol=c["tol"])
+    assert info.converged
+    rel = np.linalg.norm(c["b"] - op @ xs) / np.linalg.norm(c["b"])
+    assert rel <= 1e-10
+    assert c["s_min"] <= info.s0 <= c["s_max"]
+    h = info.relres_hist
+    k = 0
+    for n_c in info.cycle_iters:
+        seg = h[k:k + n_c]
+        assert np.all(np.diff(seg) <= 1e-12 * seg[:-1])
+        k += n_c
