@@ -203,6 +203,32 @@ sg_status sg_block_update(sg_handle* h, int64_t n, const double* Q,
 sg_status sg_nrm2(sg_handle* h, int64_t n, const double* x, double* out,
                   void* stream);
 
+/* Allocation-free block dot product W = Q^T X (same layouts and result as
+ * sg_block_dot without `sym`).  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc -- frameworks and
+ * services that give out all device memory through their own pool
+ * allocator, programs with a device-memory budget fixed at start-up, and
+ * code that must not add the device-wide synchronisation of cudaFree.
+ *  - No handle and no allocation: the split partial sums live in a
+ *    file-scope device array of SG_NOALLOC_SCRATCH_DOUBLES doubles (4 MiB)
+ *    that every GPU loading the library holds until the process exits.
+ *  - Runs on the calling thread's current device and on `stream` (NULL is
+ *    the legacy default stream).  The first call on a device looks up the
+ *    array's device address (cudaGetSymbolAddress); make that first call
+ *    before any stream capture.
+ *  - Requires i*s <= SG_NOALLOC_SCRATCH_DOUBLES; larger shapes return
+ *    SG_EINVAL with the limit in the message.  Q, X, W: device memory.
+ *  - Every call shares the one array, so calls that overlap on the GPU
+ *    (other streams, other host threads) race and corrupt each other;
+ *    serialise them.  Each call overwrites the partials it reads, so
+ *    nothing needs clearing between calls.
+ *  - err (may be NULL) receives a message of at most err_cap bytes. */
+#define SG_NOALLOC_SCRATCH_DOUBLES (1 << 19)
+sg_status sg_block_dot_noalloc(int64_t n, const double* Q, int64_t ldq,
+                               int32_t i, const double* X, int64_t ldx,
+                               int32_t s, double* W, int32_t ldw,
+                               void* stream, char* err, int32_t err_cap);
+
 /* Number of kernels this library has launched in the process so far (a
  * diagnostic for benchmarks: every launch goes through one counter). */
 int64_t sg_kernel_launches(void);

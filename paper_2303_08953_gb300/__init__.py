@@ -34,7 +34,7 @@ EXPORTED = (
     "sg_block_update", "sg_nrm2", "sg_host_partial_cholesky",
     "sg_host_hessenberg_eigvals", "sg_host_leja_order",
     "sg_host_scaling_coefficients", "sg_host_estimate_step",
-    "sg_kernel_launches",
+    "sg_kernel_launches", "sg_block_dot_noalloc",
 )
 
 
@@ -110,6 +110,8 @@ def _load():
         "sg_host_scaling_coefficients": (None, [i32, _D, _D, _D]),
         "sg_host_estimate_step": (i32, [i32, _D, _D, f64, f64, i32, i32, _D]),
         "sg_kernel_launches": (i64, []),
+        "sg_block_dot_noalloc": (i32, [i64, vp, i64, i32, vp, i64, i32, vp, i32,
+                                       vp, C.c_char_p, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

@@ -334,6 +334,35 @@ void block_update_impl(int64_t n, const T* Q, int64_t ldq, int i,
 
 }  // namespace
 
+void block_dot_capped(int64_t n, const double* Q, int64_t ldq, int i,
+                      const double* X, int64_t ldx, int s, double* W, int ldw,
+                      double* part, int64_t part_cap, cudaStream_t st) {
+  // same kernels as block_dot, with the number of splits reduced so that
+  // the split partials fit in `part_cap` doubles
+  if (i <= 0 || s <= 0) return;
+  SG_REQUIRE(static_cast<int64_t>(i) * s <= part_cap, SG_EINVAL,
+             "block_dot_capped: i*s exceeds the scratch");
+  if (n <= 0) {
+    for (int c = 0; c < s; ++c)
+      SG_CUDA(cudaMemsetAsync(W + static_cast<int64_t>(c) * ldw, 0,
+                              sizeof(double) * i, st));
+    return;
+  }
+  DotPlan p = plan_dot(n, i, s);
+  const int64_t maxS = part_cap / (static_cast<int64_t>(i) * s);
+  if (p.S > maxS) {
+    int64_t rows = (n + maxS - 1) / maxS;
+    rows = (rows + BK - 1) / BK * BK;
+    p.rows = rows;
+    p.S = static_cast<int>((n + rows - 1) / rows);
+  }
+  launch_dot<false, double>(p, st, n, i, s, Q, ldq, X, ldx, part, false);
+  const int tot = i * s;
+  reduce_parts_kernel<<<(tot + 255) / 256, 256, 0, st>>>(i, s, p.S, part, W,
+                                                         ldw, 0);
+  SG_LAUNCH_CHECK();
+}
+
 int64_t block_dot_part_size(int64_t n, int i, int s) {
   DotPlan p = plan_dot(n, i, s);
   return static_cast<int64_t>(p.S) * i * s;

@@ -114,6 +114,11 @@ void block_dot32(int64_t n, const float* Q, int64_t ldq, int i,
                  const float* X, int64_t ldx, int s, double* W, int ldw,
                  bool sym, double* part, int64_t part_cap, cudaStream_t st);
 int64_t block_dot_part_size(int64_t n, int i, int s);
+// block_dot without the symmetric option, splitting n into as many parts
+// as fit in part_cap doubles (which must hold at least i*s)
+void block_dot_capped(int64_t n, const double* Q, int64_t ldq, int i,
+                      const double* X, int64_t ldx, int s, double* W, int ldw,
+                      double* part, int64_t part_cap, cudaStream_t st);
 // X = beta X + alpha Q W (W on the device, i x s, upper-triangular if
 // `upper`, i == s)
 void block_update(int64_t n, const double* Q, int64_t ldq, int i,
