@@ -199,6 +199,26 @@ sg_status sg_block_update(sg_handle* h, int64_t n, const double* Q,
                           double alpha, double beta, int32_t upper,
                           void* stream);
 
+/* FP32 forms of the two block kernels, as used by the FP32 basis of
+ * SG_PREC_FP32_IR: Q and X are FP32 (column-major), W is FP64.  With sym,
+ * sg_block_dot_f32 forms the Gram matrix X^T X from exact FP32 products
+ * accumulated with compensated sums (accurate to ~eps_32^2 relative to
+ * sum |x_k y_k|).  Otherwise, when the leading dimensions are multiples of
+ * 4, the pointers 16-byte aligned, n >= 256 and s <= 128, it runs on the
+ * tensor cores (TMA + tcgen05, TF32 hi/lo split: hi*hi + lo*hi + hi*lo,
+ * FP32 accumulation), else in FP32 FFMA.  sg_block_dot_f32 synchronises
+ * the stream before returning (it reports a tensor-core wait timeout as
+ * SG_ECUDA). */
+sg_status sg_block_dot_f32(sg_handle* h, int64_t n, const float* Q,
+                           int64_t ldq, int32_t i, const float* X,
+                           int64_t ldx, int32_t s, double* W, int32_t ldw,
+                           int32_t sym, void* stream);
+sg_status sg_block_update_f32(sg_handle* h, int64_t n, const float* Q,
+                              int64_t ldq, int32_t i, const double* W,
+                              int32_t ldw, float* X, int64_t ldx, int32_t s,
+                              double alpha, double beta, int32_t upper,
+                              void* stream);
+
 /* Two-norm of a device vector, returned on the host (synchronises). */
 sg_status sg_nrm2(sg_handle* h, int64_t n, const double* x, double* out,
                   void* stream);

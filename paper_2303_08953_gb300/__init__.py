@@ -34,7 +34,8 @@ EXPORTED = (
     "sg_block_update", "sg_nrm2", "sg_host_partial_cholesky",
     "sg_host_hessenberg_eigvals", "sg_host_leja_order",
     "sg_host_scaling_coefficients", "sg_host_estimate_step",
-    "sg_kernel_launches", "sg_block_dot_noalloc",
+    "sg_kernel_launches", "sg_block_dot_noalloc", "sg_block_dot_f32",
+    "sg_block_update_f32",
 )
 
 
@@ -104,6 +105,9 @@ def _load():
         "sg_block_update": (i32, [vp, i64, vp, i64, i32, vp, i32, vp, i64, i32,
                                   f64, f64, i32, vp]),
         "sg_nrm2": (i32, [vp, i64, vp, _D, vp]),
+        "sg_block_dot_f32": (i32, [vp, i64, vp, i64, i32, vp, i64, i32, vp, i32, i32, vp]),
+        "sg_block_update_f32": (i32, [vp, i64, vp, i64, i32, vp, i32, vp, i64, i32,
+                                      f64, f64, i32, vp]),
         "sg_host_partial_cholesky": (i32, [_D, i32, i32, f64, _D, _D]),
         "sg_host_hessenberg_eigvals": (i32, [_D, i32, i32, _D, _D]),
         "sg_host_leja_order": (None, [i32, _D, _D, _D, _D]),
@@ -431,6 +435,31 @@ class Solver:
         s, ldx = Xt.shape
         n = n if n is not None else (self.n if self.n is not None else ldq)
         self._check(lib.sg_block_update(
+            self._h, n, C.c_void_p(Qt.data_ptr()), ldq, i,
+            C.c_void_p(Wt.data_ptr()), i, C.c_void_p(Xt.data_ptr()), ldx, s,
+            alpha, beta, 1 if upper else 0, _stream_ptr(stream)))
+        return Xt
+
+    def block_dot32(self, Qt, Xt, sym=False, stream=None):
+        """FP32 form of block_dot (Q, X float32; W returned float64)."""
+        torch = _torch()
+        i, ldq = Qt.shape
+        s, ldx = Xt.shape
+        n = min(ldq, ldx) if self.n is None else self.n
+        W = torch.empty((s, i), dtype=torch.float64, device=Qt.device)
+        self._check(lib.sg_block_dot_f32(
+            self._h, n, C.c_void_p(Qt.data_ptr()), ldq, i,
+            C.c_void_p(Xt.data_ptr()), ldx, s, C.c_void_p(W.data_ptr()), i,
+            1 if sym else 0, _stream_ptr(stream)))
+        return W
+
+    def block_update32(self, Qt, Wt, Xt, alpha=-1.0, beta=1.0, upper=False,
+                       n=None, stream=None):
+        """FP32 form of block_update (Q, X float32; W float64)."""
+        i, ldq = Qt.shape
+        s, ldx = Xt.shape
+        n = n if n is not None else (self.n if self.n is not None else ldq)
+        self._check(lib.sg_block_update_f32(
             self._h, n, C.c_void_p(Qt.data_ptr()), ldq, i,
             C.c_void_p(Wt.data_ptr()), i, C.c_void_p(Xt.data_ptr()), ldx, s,
             alpha, beta, 1 if upper else 0, _stream_ptr(stream)))

@@ -19,6 +19,8 @@
 // a two-sum, so the Gram of FP32 vectors is accurate to about eps_32^2
 // relative to the sum of |products| -- the accuracy the partial Cholesky
 // bound of the FP32 basis relies on.
+#include <cstdlib>
+
 #include "sg_internal.h"
 
 namespace sg {
@@ -146,33 +148,51 @@ dot_tile_kernel(int64_t K, int M, int N, const T* __restrict__ A,
     }
 }
 
-// W(m, n) = sum_z part[z](m, n) in split order; sym reads the upper
-// element for both (m, n) and (n, m).
+// W(m, n) = sum_z part[z](m, n); sym reads the upper element for both
+// (m, n) and (n, m).  One warp per output: lane l adds splits l, l+32, ...
+// in order, then a fixed xor-shuffle tree combines the lanes, so the
+// result is deterministic and the S loads are issued 32 at a time.
 __global__ void reduce_parts_kernel(int M, int N, int S,
                                     const double* __restrict__ part,
                                     double* __restrict__ W, int ldw, int sym) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= M * N) return;
-  const int m = idx % M, n = idx / M;
+  const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gw >= static_cast<int64_t>(M) * N) return;
+  const int m = static_cast<int>(gw % M), n = static_cast<int>(gw / M);
   int sm = m, sn = n;
   if (sym && m > n) { sm = n; sn = m; }
   double acc = 0.0;
   const int64_t MN = static_cast<int64_t>(M) * N;
-  for (int z = 0; z < S; ++z) acc += part[z * MN + sm + static_cast<int64_t>(sn) * M];
-  W[m + static_cast<int64_t>(n) * ldw] = acc;
+  const double* p = part + sm + static_cast<int64_t>(sn) * M;
+  for (int z = lane; z < S; z += 32) acc += p[z * MN];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (lane == 0) W[m + static_cast<int64_t>(n) * ldw] = acc;
 }
 
-enum Cfg { CFG_SQ = 0, CFG_NARROW_M = 1, CFG_NARROW_N = 2 };
+void launch_reduce(int M, int N, int S, const double* part, double* W, int ldw,
+                   bool sym, cudaStream_t st) {
+  const int64_t threads = static_cast<int64_t>(M) * N * 32;
+  reduce_parts_kernel<<<static_cast<unsigned>((threads + 255) / 256), 256, 0, st>>>(
+      M, N, S, part, W, ldw, sym ? 1 : 0);
+  SG_LAUNCH_CHECK();
+}
+
+enum Cfg { CFG_SQ = 0, CFG_NARROW_M = 1, CFG_NARROW_N = 2, CFG_SQ16 = 3 };
 
 struct DotPlan {
   int cfg, BM, BN, tm, tn, S;
   int64_t rows;
 };
 
-DotPlan plan_dot(int64_t n, int i, int s) {
+// FP64 (wide = false): 16 x 16 tiles, one output per thread -- the FP64
+// pipe, not shared memory, is the limit, and 16-wide tiles pad i and s
+// less.  FP32: 32 x 32 tiles with 2 x 2 outputs per thread.
+DotPlan plan_dot(int64_t n, int i, int s, bool wide) {
   DotPlan p;
   if (i <= 8) { p.cfg = CFG_NARROW_M; p.BM = 8; p.BN = 32; }
   else if (s <= 8) { p.cfg = CFG_NARROW_N; p.BM = 64; p.BN = 8; }
+  else if (!wide) { p.cfg = CFG_SQ16; p.BM = 16; p.BN = 16; }
   else { p.cfg = CFG_SQ; p.BM = 32; p.BN = 32; }
   p.tm = (i + p.BM - 1) / p.BM;
   p.tn = (s + p.BN - 1) / p.BN;
@@ -207,11 +227,24 @@ void launch_dot(const DotPlan& p, cudaStream_t st, int64_t n, int i, int s,
       dot_tile_kernel<64, 8, 2, 1, false, EXACT, T><<<grid, kThreads, 0, st>>>(
           n, i, s, Q, ldq, X, ldx, part, p.rows, 0);
       break;
+    case CFG_SQ16:
+      dot_tile_kernel<16, 16, 1, 1, false, EXACT, T><<<grid, kThreads, 0, st>>>(
+          n, i, s, Q, ldq, X, ldx, part, p.rows, sy);
+      break;
     default:
       dot_tile_kernel<32, 32, 2, 2, false, EXACT, T><<<grid, kThreads, 0, st>>>(
           n, i, s, Q, ldq, X, ldx, part, p.rows, sy);
   }
   SG_LAUNCH_CHECK();
+}
+
+bool tc_disabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("SGMRES_NO_TC");
+    v = (e && e[0] == '1') ? 1 : 0;
+  }
+  return v == 1;
 }
 
 template <typename T>
@@ -225,18 +258,25 @@ void block_dot_impl(int64_t n, const T* Q, int64_t ldq, int i, const T* X,
                               sizeof(double) * i, st));
     return;
   }
-  DotPlan p = plan_dot(n, i, s);
+  if (sizeof(T) == 4 && !sym && !tc_disabled() &&
+      tc_dot_supported(n, reinterpret_cast<const float*>(Q), ldq, i,
+                       reinterpret_cast<const float*>(X), ldx, s)) {
+    // projections of the FP32 basis on the tensor cores
+    int S = 0;
+    tc_dot(n, reinterpret_cast<const float*>(Q), ldq, i,
+           reinterpret_cast<const float*>(X), ldx, s, part, part_cap, &S, st);
+    launch_reduce(i, s, S, part, W, ldw, false, st);
+    return;
+  }
+  DotPlan p = plan_dot(n, i, s, sizeof(T) == 4);
   const bool exact = sym && sizeof(T) == 4;   // Gram of FP32 vectors
-  if (sym && (p.cfg != CFG_SQ || i != s)) sym = false;
+  if (sym && ((p.cfg != CFG_SQ && p.cfg != CFG_SQ16) || i != s)) sym = false;
   SG_REQUIRE(static_cast<int64_t>(p.S) * i * s <= part_cap, SG_EINVAL,
              "block_dot: workspace too small");
   if (exact) launch_dot<true, float>(p, st, n, i, s, reinterpret_cast<const float*>(Q), ldq,
                                      reinterpret_cast<const float*>(X), ldx, part, sym);
   else launch_dot<false, T>(p, st, n, i, s, Q, ldq, X, ldx, part, sym);
-  const int tot = i * s;
-  reduce_parts_kernel<<<(tot + 255) / 256, 256, 0, st>>>(i, s, p.S, part, W,
-                                                         ldw, sym ? 1 : 0);
-  SG_LAUNCH_CHECK();
+  launch_reduce(i, s, p.S, part, W, ldw, sym, st);
 }
 
 // --------------------------------------------------------- block_update
@@ -324,6 +364,10 @@ void block_update_impl(int64_t n, const T* Q, int64_t ldq, int i,
     dim3 grid(static_cast<unsigned>((n + 127) / 128), 1);
     update_kernel<128, 8, 4, 1, T><<<grid, kThreads, 0, st>>>(
         n, ii, s, Q, ldq, W, ldw, X, ldx, alpha, beta, upper ? 1 : 0);
+  } else if (sizeof(T) == 8) {
+    dim3 grid(static_cast<unsigned>((n + 63) / 64), (s + 15) / 16);
+    update_kernel<64, 16, 4, 1, T><<<grid, kThreads, 0, st>>>(
+        n, ii, s, Q, ldq, W, ldw, X, ldx, alpha, beta, upper ? 1 : 0);
   } else {
     dim3 grid(static_cast<unsigned>((n + 63) / 64), (s + 31) / 32);
     update_kernel<64, 32, 4, 2, T><<<grid, kThreads, 0, st>>>(
@@ -348,7 +392,7 @@ void block_dot_capped(int64_t n, const double* Q, int64_t ldq, int i,
                               sizeof(double) * i, st));
     return;
   }
-  DotPlan p = plan_dot(n, i, s);
+  DotPlan p = plan_dot(n, i, s, false);
   const int64_t maxS = part_cap / (static_cast<int64_t>(i) * s);
   if (p.S > maxS) {
     int64_t rows = (n + maxS - 1) / maxS;
@@ -357,15 +401,14 @@ void block_dot_capped(int64_t n, const double* Q, int64_t ldq, int i,
     p.S = static_cast<int>((n + rows - 1) / rows);
   }
   launch_dot<false, double>(p, st, n, i, s, Q, ldq, X, ldx, part, false);
-  const int tot = i * s;
-  reduce_parts_kernel<<<(tot + 255) / 256, 256, 0, st>>>(i, s, p.S, part, W,
-                                                         ldw, 0);
-  SG_LAUNCH_CHECK();
+  launch_reduce(i, s, p.S, part, W, ldw, false, st);
 }
 
 int64_t block_dot_part_size(int64_t n, int i, int s) {
-  DotPlan p = plan_dot(n, i, s);
-  return static_cast<int64_t>(p.S) * i * s;
+  const DotPlan a = plan_dot(n, i, s, false), b = plan_dot(n, i, s, true);
+  int64_t need = static_cast<int64_t>(a.S > b.S ? a.S : b.S) * i * s;
+  const int64_t tc = tc_dot_part_size(n, i, s);
+  return need > tc ? need : tc;
 }
 
 void block_dot(int64_t n, const double* Q, int64_t ldq, int i,

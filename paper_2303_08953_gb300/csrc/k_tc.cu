@@ -1,0 +1,397 @@
+// Tensor-core block dot product for the FP32 basis: W = Q^T X (the BCGS
+// projections of Alg. 4) on the 5th-generation tensor cores.
+//
+// Q (n x i) and X (n x s) are FP32 column-major, so Q^T and X^T are
+// K-major operands (K = the n rows) of a tcgen05 MMA with M = 128 columns
+// of Q per tile and N = s (rounded up to 16).  Each CTA reduces one range
+// of rows for one 128-column tile:
+//   * one thread issues TMA loads of 32-row x 128 B tiles (128-byte
+//     swizzle) into a 3-stage ring guarded by mbarriers;
+//   * all four warps split every tile in place into a TF32 "hi" part
+//     (low 13 mantissa bits cleared) and an exact FP32 remainder "lo";
+//   * the same elected thread issues tcgen05.mma.kind::tf32 for
+//     hi*hi + lo*hi + hi*lo (the low*low term is below FP32 rounding), with
+//     the FP32 accumulator in tensor memory, and commits each stage's MMAs
+//     to an mbarrier that frees the stage;
+//   * the accumulator is read back with tcgen05.ld and written as one
+//     split partial; the fixed-order split reduction is the SIMT path's.
+// Every wait is bounded: on timeout the kernel records an error code,
+// drains its own copies, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "sg_internal.h"
+
+namespace sg {
+
+namespace {
+
+constexpr int kBM = 128;          // MMA M: columns of Q per tile
+constexpr int kBK = 32;           // rows per stage: 32 FP32 = one 128 B row
+constexpr int kStages = 3;
+constexpr int kThreads = 128;
+constexpr uint32_t kSpinLimit = 1u << 26;
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
+constexpr int kMaxN = 128;        // s <= 128 per launch
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// bounded wait for the phase with the given parity to complete: gives up
+// after kWaitNs nanoseconds (or kSpinLimit attempts) and returns false
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 255) == 255 && global_ns() - t0 > kWaitNs) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
+// 8-row groups 1024 bytes apart (tile base aligned to 1024 bytes).
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= static_cast<uint64_t>(1) << 16;                 // leading byte offset (unused)
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;         // stride byte offset
+  d |= static_cast<uint64_t>(1) << 46;                 // descriptor version
+  d |= static_cast<uint64_t>(2) << 61;                 // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: kind::tf32, FP32 accumulator, K-major A and B.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) |
+         (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void split_tf32(float4* hi, float4* lo, int count4, int tid) {
+  for (int e = tid; e < count4; e += kThreads) {
+    float4 v = hi[e];
+    float4 h, l;
+    h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u); l.x = v.x - h.x;
+    h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u); l.y = v.y - h.y;
+    h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u); l.z = v.z - h.z;
+    h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u); l.w = v.w - h.w;
+    hi[e] = h;
+    lo[e] = l;
+  }
+}
+
+struct __align__(8) TcShared {
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+  uint64_t done;
+  uint32_t tmem_base;
+  int fail;
+};
+
+// grid: (tiles of 128 Q columns, 1, splits); block: 128 threads
+__global__ void __launch_bounds__(kThreads, 1)
+tc_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
+              const __grid_constant__ CUtensorMap mapX, int64_t n, int M, int N,
+              int BN, int64_t rows_per_split, double* __restrict__ part,
+              int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char dsmem[];
+  // 1024-byte aligned tiles: per stage A, A_lo (128 x 128 B), B, B_lo (BN x 128 B)
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int a_bytes = kBM * kBK * 4;
+  const int b_bytes = BN * kBK * 4;
+  const int stage_bytes = 2 * a_bytes + 2 * b_bytes;
+  __shared__ TcShared sh;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int m0 = blockIdx.x * kBM;
+  const int64_t k0 = static_cast<int64_t>(blockIdx.z) * rows_per_split;
+  const int64_t k1 = (k0 + rows_per_split < n) ? k0 + rows_per_split : n;
+  const int nk = static_cast<int>((k1 - k0 + kBK - 1) / kBK);
+  const uint32_t ncols = BN <= 32 ? 32 : (BN <= 64 ? 64 : 128);
+  const uint32_t idesc = idesc_tf32(kBM, BN);
+
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&sh.full[s], 1);
+      mbar_init(&sh.empty[s], 1);
+    }
+    mbar_init(&sh.done, 1);
+    sh.fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&sh.tmem_base)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = sh.tmem_base;
+
+  auto stA = [&](int s) { return base + s * stage_bytes; };
+  auto stAlo = [&](int s) { return base + s * stage_bytes + a_bytes; };
+  auto stB = [&](int s) { return base + s * stage_bytes + 2 * a_bytes; };
+  auto stBlo = [&](int s) { return base + s * stage_bytes + 2 * a_bytes + b_bytes; };
+  auto issue = [&](int kb) {  // thread 0 only
+    const int s = kb % kStages;
+    mbar_expect_tx(&sh.full[s], static_cast<uint32_t>(a_bytes + b_bytes));
+    const int x = static_cast<int>(k0 + static_cast<int64_t>(kb) * kBK);
+    tma_load_2d(stA(s), &mapQ, &sh.full[s], x, m0);
+    tma_load_2d(stB(s), &mapX, &sh.full[s], x, 0);
+  };
+
+  int issued = 0;    // k-blocks whose loads were issued (thread 0's count)
+  int consumed = 0;  // k-blocks whose loads this thread saw land
+  if (tid == 0) {
+    for (; issued < kStages - 1 && issued < nk; ++issued) issue(issued);
+  }
+  bool ok = true;
+  for (int kb = 0; kb < nk; ++kb) {
+    const int s = kb % kStages;
+    const uint32_t ph = static_cast<uint32_t>((kb / kStages) & 1);
+    if (!mbar_wait(&sh.full[s], ph)) sh.fail = 1;
+    else consumed = kb + 1;
+    split_tf32(reinterpret_cast<float4*>(stA(s)), reinterpret_cast<float4*>(stAlo(s)),
+               a_bytes / 16, tid);
+    split_tf32(reinterpret_cast<float4*>(stB(s)), reinterpret_cast<float4*>(stBlo(s)),
+               b_bytes / 16, tid);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (sh.fail) { ok = false; break; }
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint64_t a = sdesc(smem_u32(stA(s))), al = sdesc(smem_u32(stAlo(s)));
+      const uint64_t b = sdesc(smem_u32(stB(s))), bl = sdesc(smem_u32(stBlo(s)));
+#pragma unroll
+      for (int k8 = 0; k8 < kBK / 8; ++k8) {  // K = 8 TF32 = 32 bytes per MMA
+        const uint64_t adv = static_cast<uint64_t>((k8 * 32) >> 4);
+        mma_tf32(tmem, a + adv, b + adv, idesc, (kb > 0 || k8 > 0) ? 1u : 0u);
+        mma_tf32(tmem, al + adv, b + adv, idesc, 1u);
+        mma_tf32(tmem, a + adv, bl + adv, idesc, 1u);
+      }
+      mma_commit(&sh.empty[s]);
+      // refill the stage used one iteration ago once its MMAs are done
+      if (issued < nk) {
+        const int rs = issued % kStages;
+        if (issued >= kStages) {
+          const uint32_t rph = static_cast<uint32_t>(((issued - kStages) / kStages) & 1);
+          if (!mbar_wait(&sh.empty[rs], rph)) sh.fail = 1;
+        }
+        if (!sh.fail) { issue(issued); ++issued; }
+      }
+    }
+  }
+  // every MMA this CTA issued must complete before the accumulator is read
+  // (or the tensor memory freed, on the failure path)
+  if (tid == 0) mma_commit(&sh.done);
+  __syncthreads();
+  if (!mbar_wait(&sh.done, 0)) sh.fail = 1;
+  __syncthreads();
+  const bool good = ok && !sh.fail;
+  if (!good) {
+    if (tid == 0) {
+      atomicExch(err, 1);
+      // drain this CTA's loads that are still in flight (each is the
+      // latest use of its stage, so its parity identifies it)
+      for (int kb = consumed; kb < issued; ++kb)
+        mbar_wait(&sh.full[kb % kStages], static_cast<uint32_t>((kb / kStages) & 1));
+    }
+  } else {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // TMEM lane = accumulator row m (warp w owns lanes 32w..32w+31)
+    const int row = warp * 32 + (tid & 31);
+    const int m = m0 + row;
+    double* P = part + static_cast<int64_t>(blockIdx.z) * M * N;
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      uint32_t v[16];
+      const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+            "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+            "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (m < M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int nc = c0 + j;
+          if (nc < N) P[m + static_cast<int64_t>(nc) * M] = static_cast<double>(__uint_as_float(v[j]));
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols)
+                 : "memory");
+  }
+}
+
+__device__ int g_tc_err;  // set to 1 by a CTA whose wait ran out
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap* map, const float* base, int64_t rows, int64_t cols,
+              int64_t ld, int box_cols) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(rows), static_cast<cuuint64_t>(cols)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * sizeof(float)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(kBK), static_cast<cuuint32_t>(box_cols)};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims,
+            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool tc_dot_supported(int64_t n, const float* Q, int64_t ldq, int i, const float* X,
+                      int64_t ldx, int s) {
+  if (n < 8 * kBK || i < 1 || s < 1 || s > kMaxN) return false;
+  if ((reinterpret_cast<uintptr_t>(Q) | reinterpret_cast<uintptr_t>(X)) & 15) return false;
+  if (((ldq * 4) & 15) || ((ldx * 4) & 15)) return false;
+  if (n > (int64_t(1) << 31) - 1) return false;
+  return encode_fn() != nullptr;
+}
+
+int64_t tc_dot_part_size(int64_t n, int i, int s) {
+  const int tiles = (i + kBM - 1) / kBM;
+  int64_t S = (static_cast<int64_t>(device_sm_count()) * 2 + tiles - 1) / tiles;
+  const int64_t maxS = n / (8 * kBK);
+  if (S > maxS) S = maxS;
+  if (S < 1) S = 1;
+  return S * i * s;
+}
+
+int* tc_err_flag() {
+  static int* ptr[64] = {};
+  static std::mutex mu;
+  int dev = 0;
+  SG_CUDA(cudaGetDevice(&dev));
+  SG_REQUIRE(dev >= 0 && dev < 64, SG_ECUDA, "device index out of range");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!ptr[dev]) {
+    void* p = nullptr;
+    SG_CUDA(cudaGetSymbolAddress(&p, g_tc_err));
+    ptr[dev] = static_cast<int*>(p);
+  }
+  return ptr[dev];
+}
+
+void tc_check_error(cudaStream_t st) {
+  int* f = tc_err_flag();
+  int host = 0;
+  SG_CUDA(cudaMemcpyAsync(&host, f, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SG_CUDA(cudaStreamSynchronize(st));
+  if (host) {
+    SG_CUDA(cudaMemsetAsync(f, 0, sizeof(int), st));
+    throw Error(SG_ECUDA, "tensor-core block dot: a bounded wait ran out");
+  }
+}
+
+void tc_dot(int64_t n, const float* Q, int64_t ldq, int i, const float* X, int64_t ldx,
+            int s, double* part, int64_t part_cap, int* nsplit, cudaStream_t st) {
+  int* err = tc_err_flag();
+  const int BN = (s + 15) / 16 * 16;
+  const int tiles = (i + kBM - 1) / kBM;
+  int64_t S = (static_cast<int64_t>(device_sm_count()) * 2 + tiles - 1) / tiles;
+  const int64_t maxS = n / (8 * kBK);
+  if (S > maxS) S = maxS;
+  if (S < 1) S = 1;
+  int64_t rows = (n + S - 1) / S;
+  rows = (rows + kBK - 1) / kBK * kBK;
+  S = (n + rows - 1) / rows;
+  SG_REQUIRE(S * i * s <= part_cap, SG_EINVAL, "tc_dot: workspace too small");
+  CUtensorMap mq, mx;
+  SG_REQUIRE(make_map(&mq, Q, n, i, ldq, kBM) && make_map(&mx, X, n, s, ldx, BN), SG_ECUDA,
+             "cuTensorMapEncodeTiled failed");
+  const int smem = kStages * (2 * kBM * kBK * 4 + 2 * BN * kBK * 4) + 1024;
+  static int configured = 0;
+  if (configured < smem) {
+    SG_CUDA(cudaFuncSetAttribute(tc_dot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kStages * (2 * kBM * kBK * 4 + 2 * kMaxN * kBK * 4) + 1024));
+    configured = smem;
+  }
+  dim3 grid(tiles, 1, static_cast<unsigned>(S));
+  tc_dot_kernel<<<grid, kThreads, smem, st>>>(mq, mx, n, i, s, BN, rows, part, err);
+  SG_LAUNCH_CHECK();
+  *nsplit = static_cast<int>(S);
+}
+
+}  // namespace sg

@@ -43,16 +43,19 @@ __device__ double sum_partials(const double* __restrict__ p, int G) {
   return block_sum(v);
 }
 
+// Per-thread partial sums run in the vectors' own precision (T): FP64
+// vectors in FP64, FP32 vectors in FP32 (each thread adds ~n/155k terms);
+// the block and cross-block stages are FP64.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 dot_kernel(int64_t n, const T* __restrict__ x, const T* __restrict__ y,
            double* __restrict__ part) {
-  double acc = 0.0;
+  T acc = T(0);
   for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * kThreads)
-    acc += static_cast<double>(x[i]) * static_cast<double>(y[i]);
-  acc = block_sum(acc);
-  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    acc = fma(x[i], y[i], acc);
+  const double tot = block_sum(static_cast<double>(acc));
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
 __global__ void finish_kernel(const double* __restrict__ part, int G,
@@ -69,15 +72,15 @@ mgs_kernel(int64_t n, T* __restrict__ w, const T* __restrict__ v,
   const double h = sum_partials(pin, G);
   if (blockIdx.x == 0 && threadIdx.x == 0) *hout = h;
   const T ht = static_cast<T>(h);
-  double acc = 0.0;
+  T acc = T(0);
   for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < n;
        i += static_cast<int64_t>(gridDim.x) * kThreads) {
-    const T wi = w[i] - ht * v[i];
+    const T wi = fma(-ht, v[i], w[i]);
     w[i] = wi;
-    acc += static_cast<double>(vnext ? vnext[i] : wi) * static_cast<double>(wi);
+    acc = fma(vnext ? vnext[i] : wi, wi, acc);
   }
-  acc = block_sum(acc);
-  if (threadIdx.x == 0) pout[blockIdx.x] = acc;
+  const double tot = block_sum(static_cast<double>(acc));
+  if (threadIdx.x == 0) pout[blockIdx.x] = tot;
 }
 
 template <typename T>

@@ -18,6 +18,8 @@ namespace {
 std::atomic<long long> g_launches{0};
 }
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(); }
 }  // namespace sg
 
 namespace {
@@ -241,6 +243,7 @@ void sg_destroy(sg_handle* h) {
   if (!h) return;
   cudaSetDevice(h->device);
   if (h->own) cudaStreamSynchronize(h->own);
+  h->drop_graphs();
   free_csr(h->A);
   free_csr(h->AT);
   double* d[] = {h->Q, h->V, h->Y, h->bvec, h->xvec, h->rvec, h->part, h->red, h->small, h->dvec};
@@ -279,6 +282,7 @@ sg_status sg_analyze(sg_handle* h, const sg_csr* A) {
         SG_REQUIRE(k == rp[r] || ci[k] > ci[k - 1], SG_EINVAL, "columns not sorted/unique in a row");
       }
     }
+    h->drop_graphs();
     free_csr(h->A);
     free_csr(h->AT);
     h->have_A = h->have_AT = false;
@@ -410,6 +414,54 @@ sg_status sg_block_update(sg_handle* h, int64_t n, const double* Q,
     SG_CUDA(cudaSetDevice(h->device));
     sg::block_update(n, Q, ldq, i, W, ldw, X, ldx, s, alpha, beta, upper != 0,
                      pick(h, stream));
+  });
+}
+
+namespace {
+void ensure_part(sg_handle* h, int64_t need, cudaStream_t st) {
+  if (need <= h->part_cap) return;
+  SG_CUDA(cudaStreamSynchronize(st));
+  if (h->part) cudaFree(h->part);
+  h->part = nullptr;
+  h->part_cap = 0;
+  SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&h->part), sizeof(double) * need));
+  h->part_cap = need;
+}
+}  // namespace
+
+sg_status sg_block_dot_f32(sg_handle* h, int64_t n, const float* Q,
+                           int64_t ldq, int32_t i, const float* X,
+                           int64_t ldx, int32_t s, double* W, int32_t ldw,
+                           int32_t sym, void* stream) {
+  if (!h) return SG_EINVAL;
+  return guarded(h, [&] {
+    SG_REQUIRE(n >= 0 && i >= 0 && s >= 0 && ldq >= n && ldx >= n && ldw >= i,
+               SG_EINVAL, "bad sizes");
+    SG_REQUIRE((Q && X && W) || i == 0 || s == 0, SG_EINVAL, "null pointer");
+    SG_REQUIRE(!sym || (Q == X && i == s), SG_EINVAL, "sym needs Q == X");
+    SG_CUDA(cudaSetDevice(h->device));
+    cudaStream_t st = pick(h, stream);
+    ensure_part(h, sg::block_dot_part_size(n, i, s), st);
+    sg::block_dot32(n, Q, ldq, i, X, ldx, s, W, ldw, sym != 0, h->part, h->part_cap, st);
+    sg::tc_check_error(st);  // synchronises: reports a tensor-core timeout
+  });
+}
+
+sg_status sg_block_update_f32(sg_handle* h, int64_t n, const float* Q,
+                              int64_t ldq, int32_t i, const double* W,
+                              int32_t ldw, float* X, int64_t ldx, int32_t s,
+                              double alpha, double beta, int32_t upper,
+                              void* stream) {
+  if (!h) return SG_EINVAL;
+  return guarded(h, [&] {
+    SG_REQUIRE(n >= 0 && i >= 0 && s >= 0 && ldq >= n && ldx >= n && ldw >= i,
+               SG_EINVAL, "bad sizes");
+    SG_REQUIRE(X || s == 0 || n == 0, SG_EINVAL, "null X");
+    SG_REQUIRE((Q && W) || i == 0, SG_EINVAL, "null Q/W");
+    SG_REQUIRE(!upper || i == s, SG_EINVAL, "upper needs i == s");
+    SG_CUDA(cudaSetDevice(h->device));
+    sg::block_update32(n, Q, ldq, i, W, ldw, X, ldx, s, alpha, beta, upper != 0,
+                       pick(h, stream));
   });
 }
 

@@ -128,6 +128,17 @@ void block_update32(int64_t n, const float* Q, int64_t ldq, int i,
                     const double* W, int ldw, float* X, int64_t ldx, int s,
                     double alpha, double beta, bool upper, cudaStream_t st);
 
+// Tensor-core (tcgen05, TMA) FP32 block dot W = Q^T X: split partials
+// into `part`, number of splits in *nsplit; bounded waits record failure
+// in a device flag that tc_check_error reads (and clears, then throws).
+bool tc_dot_supported(int64_t n, const float* Q, int64_t ldq, int i,
+                      const float* X, int64_t ldx, int s);
+int64_t tc_dot_part_size(int64_t n, int i, int s);
+void tc_dot(int64_t n, const float* Q, int64_t ldq, int i, const float* X,
+            int64_t ldx, int s, double* part, int64_t part_cap, int* nsplit,
+            cudaStream_t st);
+void tc_check_error(cudaStream_t st);
+
 int device_sm_count();
 
 }  // namespace sg

@@ -68,6 +68,7 @@ void ensure_workspace(sg_handle* h, int64_t n, int m, int k) {
   m = std::max(m, h->ws_n == n ? h->ws_m : 0);
   k = std::max(k, h->ws_n == n ? h->ws_k : 0);
   const int64_t ld = (n + 31) / 32 * 32;  // 256-byte aligned columns
+  h->drop_graphs();
   dev_alloc(&h->Q, static_cast<size_t>(ld) * (m + 1));
   dev_alloc(&h->V, static_cast<size_t>(ld) * (k + 1));
   dev_alloc(&h->Y, static_cast<size_t>(ld) * k);
@@ -96,6 +97,7 @@ void ensure_workspace32(sg_handle* h, int64_t n, int m, int k) {
   // FP64 vectors, partials and small slots come from the FP64 workspace
   // with empty basis blocks; the FP32 basis is allocated here.
   if (!(h->ws_n == n && h->ws_m >= m && h->ws_k >= k)) {
+    h->drop_graphs();
     if (h->Q) cudaFree(h->Q);
     if (h->V) cudaFree(h->V);
     if (h->Y) cudaFree(h->Y);
@@ -126,6 +128,7 @@ void ensure_workspace32(sg_handle* h, int64_t n, int m, int k) {
   if (h->ws32_n == n && h->ws32_m >= m && h->ws32_k >= k) return;
   const int64_t ld = h->ld;
   const int mm = std::max(m, h->ws_m), kk = std::max(k, h->ws_k);
+  h->drop_graphs();
   dev_alloc(&h->Q32, static_cast<size_t>(ld) * (mm + 1));
   dev_alloc(&h->V32, static_cast<size_t>(ld) * (kk + 1));
   dev_alloc(&h->Y32, static_cast<size_t>(ld) * kk);
@@ -221,8 +224,8 @@ template <> struct Basis<float> {
 // the basis in V's columns (Sec. 3.4).  Returns the steps completed and
 // fills Hh ((k+1) x k, host, ld k+1).
 template <typename T>
-int arnoldi_prepass(sg_handle* h, const DevCsr& M, const T* q, int k,
-                    cudaStream_t st, std::vector<double>& Hh) {
+void enqueue_prepass(sg_handle* h, const DevCsr& M, const T* q, int k,
+                     cudaStream_t st) {
   using B = Basis<T>;
   const int64_t n = M.n, ld = h->ld;
   T* V = B::V(h);
@@ -252,10 +255,68 @@ int arnoldi_prepass(sg_handle* h, const DevCsr& M, const T* q, int k,
     }
     B::norml(n, pin, w, w, Hd + (j + 1) + static_cast<int64_t>(j) * ldh, st);
   }
+}
+
+// Ritz pre-pass: k steps of MGS-Arnoldi from q (device, unit norm) with
+// the basis in V's columns (Sec. 3.4).  The ~k^2/2 small kernels are
+// captured once into a CUDA graph on the handle's own stream and replayed
+// (ordered after/before `st` with events); if capture is not possible the
+// kernels are launched directly.  Returns the steps completed and fills
+// Hh ((k+1) x k, host, ld k+1).
+template <typename T>
+int arnoldi_prepass(sg_handle* h, const DevCsr& M, const T* q, int k,
+                    cudaStream_t st, std::vector<double>& Hh) {
+  using B = Basis<T>;
+  const void* key[6] = {M.rowptr, sizeof(T) == 8 ? static_cast<const void*>(M.val)
+                                                 : static_cast<const void*>(M.val32),
+                        q, B::V(h), h->small, h->red};
+  sg_handle::PrepassGraph* g = nullptr;
+  for (auto& c : h->graphs)
+    if (c.k == k && c.n == M.n && std::equal(key, key + 6, c.key)) g = &c;
+  if (!g) {
+    sg_handle::PrepassGraph ng;
+    std::copy(key, key + 6, ng.key);
+    ng.k = k;
+    ng.n = M.n;
+    cudaGraph_t graph = nullptr;
+    const long long before = launches_so_far();
+    bool ok = cudaStreamBeginCapture(h->own, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      try {
+        enqueue_prepass<T>(h, M, q, k, h->own);
+      } catch (...) {
+        ok = false;
+      }
+      ok = (cudaStreamEndCapture(h->own, &graph) == cudaSuccess) && ok && graph;
+    }
+    ng.kernels = launches_so_far() - before;
+    count_launches(-ng.kernels);  // captured, not launched
+    if (ok && cudaGraphInstantiate(&ng.exec, graph, 0) != cudaSuccess) ok = false;
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();  // clear the error a failed capture leaves behind
+    if (ok) {
+      h->graphs.push_back(ng);
+      g = &h->graphs.back();
+    }
+  }
+  if (g) {
+    SG_CUDA(cudaEventRecord(h->ev[3], st));
+    SG_CUDA(cudaStreamWaitEvent(h->own, h->ev[3], 0));
+    SG_CUDA(cudaGraphLaunch(g->exec, h->own));
+    count_launches(g->kernels);
+    SG_CUDA(cudaEventRecord(h->ev[3], h->own));
+    SG_CUDA(cudaStreamWaitEvent(st, h->ev[3], 0));
+  } else {
+    enqueue_prepass<T>(h, M, q, k, st);
+  }
+  Slots sl = slots_for(h->ws_m, h->ws_k);
+  const int ldh = k + 1;
   Hh.assign(static_cast<size_t>(ldh) * k, 0.0);
   std::vector<double> wnh(k);
-  SG_CUDA(cudaMemcpyAsync(h->hbuf, Hd, sizeof(double) * ldh * k, cudaMemcpyDeviceToHost, st));
-  SG_CUDA(cudaMemcpyAsync(h->hbuf + ldh * k, wn, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+  SG_CUDA(cudaMemcpyAsync(h->hbuf, h->small + sl.H, sizeof(double) * ldh * k,
+                          cudaMemcpyDeviceToHost, st));
+  SG_CUDA(cudaMemcpyAsync(h->hbuf + ldh * k, h->small + sl.wn, sizeof(double) * k,
+                          cudaMemcpyDeviceToHost, st));
   SG_CUDA(cudaStreamSynchronize(st));
   std::memcpy(Hh.data(), h->hbuf, sizeof(double) * ldh * k);
   std::memcpy(wnh.data(), h->hbuf + ldh * k, sizeof(double) * k);
@@ -407,6 +468,7 @@ void solve_impl(sg_handle* h, const DevCsr& M, const SolveOpts& o,
       fetch(Gd, static_cast<int64_t>(s_eff) * s_eff, hb + static_cast<int64_t>(i) * s_eff);
       SG_CUDA(cudaEventRecord(h->ev[2], st));
       SG_CUDA(cudaStreamSynchronize(st));
+      if (sizeof(T) == 4) tc_check_error(st);
       {
         float a = 0, b = 0;
         cudaEventElapsedTime(&a, h->ev[0], h->ev[1]);
@@ -452,6 +514,7 @@ void solve_impl(sg_handle* h, const DevCsr& M, const SolveOpts& o,
         fetch(Gd, static_cast<int64_t>(p1) * p1, hb + static_cast<int64_t>(i) * p1);
         SG_CUDA(cudaEventRecord(h->ev[2], st));
         SG_CUDA(cudaStreamSynchronize(st));
+        if (sizeof(T) == 4) tc_check_error(st);
         {
           float b = 0;
           cudaEventElapsedTime(&b, h->ev[1], h->ev[2]);

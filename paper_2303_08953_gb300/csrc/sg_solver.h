@@ -38,6 +38,20 @@ struct sg_handle {
   int ws32_m = 0, ws32_k = 0;
   double* dvec = nullptr;   // n, FP64 correction accumulator
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // captured Ritz pre-pass graphs, keyed by everything their kernels read
+  struct PrepassGraph {
+    const void* key[6];
+    int k = 0;
+    int64_t n = 0;
+    long long kernels = 0;
+    cudaGraphExec_t exec = nullptr;
+  };
+  std::vector<PrepassGraph> graphs;
+  void drop_graphs() {
+    for (auto& g : graphs)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+    graphs.clear();
+  }
 };
 
 namespace sg {
@@ -58,6 +72,8 @@ struct SolveLog {
 };
 
 void ensure_workspace(sg_handle* h, int64_t n, int m, int k);
+void count_launches(long long k);
+long long launches_so_far();
 void ensure_workspace32(sg_handle* h, int64_t n, int m, int k);
 
 // FP64 adaptive s-step GMRES on matrix M (A or A^T): b, x device vectors
