@@ -135,6 +135,13 @@ const char* sg_last_error(const sg_handle* h);
  * Errors: SG_EINVAL, SG_ENOMEM, SG_ECUDA. */
 sg_status sg_analyze(sg_handle* h, const sg_csr* A);
 
+/* Replace the values of the analysed matrix, keeping its pattern: val
+ * has nnz entries (device pointer when on_device, else host).  The FP32
+ * copy is refreshed and the transpose is rebuilt on the next adjoint
+ * call.  Errors: SG_ESTATE (no matrix), SG_EINVAL, SG_ECUDA. */
+sg_status sg_update_values(sg_handle* h, const double* val,
+                           int32_t on_device);
+
 /* ------------------------------------------------------------- solvers */
 /* Adaptive s-step GMRES(m) (Alg. 4 with restarts): solves A x = b.
  * x holds x0 on entry and the solution on exit.  res may be NULL.

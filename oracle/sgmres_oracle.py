@@ -639,3 +639,20 @@ def dense_solve(A, b):
 def loss_of_orthogonality(Q):
     """||I - Q^T Q||_F (Sec. 2.2, Eq. LOO)."""
     return float(np.linalg.norm(np.eye(Q.shape[1]) - Q.T @ Q))
+
+
+def loss_gradients(A, b, x_target):
+    """Dense reference for the adjoint gradient of L = 0.5 ||x - x_t||^2
+    with x = A^-1 b (the differentiation workload): lam = A^-T (x - x_t),
+    dL/db = lam, dL/dA_ij = -lam_i x_j on A's stored pattern.  Returns
+    (L, dL/dvalues, dL/db, x)."""
+    op = as_operator(A)
+    Ad = op.toarray()
+    lu = sla.lu_factor(Ad)
+    x = sla.lu_solve(lu, b)
+    r = x - x_target
+    lam = sla.lu_solve(lu, r, trans=1)
+    rows = np.repeat(np.arange(op.shape[0]), np.diff(op.indptr))
+    dvals = -lam[rows] * x[op.indices]
+    return 0.5 * float(r @ r), dvals, lam, x
+

@@ -35,7 +35,7 @@ EXPORTED = (
     "sg_host_hessenberg_eigvals", "sg_host_leja_order",
     "sg_host_scaling_coefficients", "sg_host_estimate_step",
     "sg_kernel_launches", "sg_block_dot_noalloc", "sg_block_dot_f32",
-    "sg_block_update_f32",
+    "sg_block_update_f32", "sg_update_values",
 )
 
 
@@ -95,6 +95,7 @@ def _load():
         "sg_destroy": (None, [vp]),
         "sg_last_error": (C.c_char_p, [vp]),
         "sg_analyze": (i32, [vp, C.POINTER(sg_csr)]),
+        "sg_update_values": (i32, [vp, vp, i32]),
         "sg_solve": (i32, [vp, vp, vp, C.POINTER(sg_opts), C.POINTER(sg_result)]),
         "sg_solve_adjoint": (i32, [vp, vp, vp, C.POINTER(sg_opts), C.POINTER(sg_result)]),
         "sg_grad_values": (i32, [vp, vp, vp, vp, vp]),
@@ -284,6 +285,18 @@ class Solver:
         A = sg_csr(nn, nnz, ptrs[0], ptrs[1], ptrs[2], 1 if on_dev else 0)
         self._check(lib.sg_analyze(self._h, C.byref(A)))
         self.n, self.nnz = nn, nnz
+        return self
+
+    def update_values(self, val):
+        """New values for the analysed pattern (numpy or a CUDA tensor)."""
+        torch = _torch()
+        if isinstance(val, torch.Tensor) and val.is_cuda:
+            v = val.to(torch.float64).contiguous()
+            torch.cuda.current_stream().synchronize()
+            self._check(lib.sg_update_values(self._h, C.c_void_p(v.data_ptr()), 1))
+        else:
+            v = np.ascontiguousarray(val, dtype=np.float64)
+            self._check(lib.sg_update_values(self._h, C.c_void_p(v.ctypes.data), 0))
         return self
 
     def analyze_csr(self, A):

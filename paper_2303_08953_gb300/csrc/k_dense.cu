@@ -369,8 +369,10 @@ void block_update_impl(int64_t n, const T* Q, int64_t ldq, int i,
     update_kernel<64, 16, 4, 1, T><<<grid, kThreads, 0, st>>>(
         n, ii, s, Q, ldq, W, ldw, X, ldx, alpha, beta, upper ? 1 : 0);
   } else {
-    dim3 grid(static_cast<unsigned>((n + 63) / 64), (s + 31) / 32);
-    update_kernel<64, 32, 4, 2, T><<<grid, kThreads, 0, st>>>(
+    // FP32: 128 x 32 tiles, 4 x 4 outputs per thread (FFMA-bound rather
+    // than shared-memory-bound)
+    dim3 grid(static_cast<unsigned>((n + 127) / 128), (s + 31) / 32);
+    update_kernel<128, 32, 4, 4, T><<<grid, kThreads, 0, st>>>(
         n, ii, s, Q, ldq, W, ldw, X, ldx, alpha, beta, upper ? 1 : 0);
   }
   SG_LAUNCH_CHECK();

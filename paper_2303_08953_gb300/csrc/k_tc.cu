@@ -31,7 +31,7 @@ namespace {
 constexpr int kBM = 128;          // MMA M: columns of Q per tile
 constexpr int kBK = 32;           // rows per stage: 32 FP32 = one 128 B row
 constexpr int kStages = 3;
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;     // 8 warps split tiles; warps 0-3 own TMEM lanes
 constexpr uint32_t kSpinLimit = 1u << 26;
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
 constexpr int kMaxN = 128;        // s <= 128 per launch
@@ -122,6 +122,7 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 }
 
 __device__ __forceinline__ void split_tf32(float4* hi, float4* lo, int count4, int tid) {
+#pragma unroll 4
   for (int e = tid; e < count4; e += kThreads) {
     float4 v = hi[e];
     float4 h, l;
@@ -142,7 +143,7 @@ struct __align__(8) TcShared {
   int fail;
 };
 
-// grid: (tiles of 128 Q columns, 1, splits); block: 128 threads
+// grid: (tiles of 128 Q columns, 1, splits); block: 256 threads
 __global__ void __launch_bounds__(kThreads, 1)
 tc_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
               const __grid_constant__ CUtensorMap mapX, int64_t n, int M, int N,
@@ -255,7 +256,7 @@ tc_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
       for (int kb = consumed; kb < issued; ++kb)
         mbar_wait(&sh.full[kb % kStages], static_cast<uint32_t>((kb / kStages) & 1));
     }
-  } else {
+  } else if (warp < 4) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // TMEM lane = accumulator row m (warp w owns lanes 32w..32w+31)
     const int row = warp * 32 + (tid & 31);

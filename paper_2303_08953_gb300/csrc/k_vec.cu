@@ -51,9 +51,16 @@ __global__ void __launch_bounds__(kThreads)
 dot_kernel(int64_t n, const T* __restrict__ x, const T* __restrict__ y,
            double* __restrict__ part) {
   T acc = T(0);
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * kThreads)
-    acc = fma(x[i], y[i], acc);
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * kThreads;
+  int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x;
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    T xv[4], yv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) { xv[u] = x[i + u * stride]; yv[u] = y[i + u * stride]; }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc = fma(xv[u], yv[u], acc);
+  }
+  for (; i < n; i += stride) acc = fma(x[i], y[i], acc);
   const double tot = block_sum(static_cast<double>(acc));
   if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
@@ -73,8 +80,24 @@ mgs_kernel(int64_t n, T* __restrict__ w, const T* __restrict__ v,
   if (blockIdx.x == 0 && threadIdx.x == 0) *hout = h;
   const T ht = static_cast<T>(h);
   T acc = T(0);
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * kThreads) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * kThreads;
+  int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x;
+  for (; i + 3 * stride < n; i += 4 * stride) {  // four independent streams
+    T wv[4], vv[4], nv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) { wv[u] = w[i + u * stride]; vv[u] = v[i + u * stride]; }
+    if (vnext) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) nv[u] = vnext[i + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const T wi = fma(-ht, vv[u], wv[u]);
+      w[i + u * stride] = wi;
+      acc = fma(vnext ? nv[u] : wi, wi, acc);
+    }
+  }
+  for (; i < n; i += stride) {
     const T wi = fma(-ht, v[i], w[i]);
     w[i] = wi;
     acc = fma(vnext ? vnext[i] : wi, wi, acc);
@@ -153,8 +176,10 @@ int device_sm_count() {
 }
 
 int reduction_blocks() {
+  // two 256-thread CTAs per SM: enough loads in flight for a streaming
+  // pass, and few partials for every consumer CTA to re-add
   if (!g_red_blocks) {
-    g_red_blocks = device_sm_count() * 4;
+    g_red_blocks = device_sm_count() * 2;
     if (g_red_blocks > 1024) g_red_blocks = 1024;
   }
   return g_red_blocks;

@@ -305,6 +305,24 @@ sg_status sg_analyze(sg_handle* h, const sg_csr* A) {
   });
 }
 
+sg_status sg_update_values(sg_handle* h, const double* val, int32_t on_device) {
+  if (!h) return SG_EINVAL;
+  return guarded(h, [&] {
+    SG_REQUIRE(h->have_A, SG_ESTATE, "no matrix: call sg_analyze first");
+    SG_REQUIRE(val || h->A.nnz == 0, SG_EINVAL, "val is NULL");
+    SG_CUDA(cudaSetDevice(h->device));
+    cudaStream_t st = h->own;
+    if (h->A.nnz) copy_in(h->A.val, val, h->A.nnz, on_device != 0, st);
+    if (h->A.val32) make_val32(h->A, st);
+    if (h->have_AT) {  // values of the transpose are stale: rebuild lazily
+      h->drop_graphs();
+      free_csr(h->AT);
+      h->have_AT = false;
+    }
+    SG_CUDA(cudaStreamSynchronize(st));
+  });
+}
+
 sg_status sg_solve(sg_handle* h, const double* b, double* x,
                    const sg_opts* opts, sg_result* res) {
   if (!h) return SG_EINVAL;

@@ -472,3 +472,37 @@ def test_full_size_c2_sampled_and_converged(solver):
         seg = h[k:k + n_c]
         assert np.all(np.diff(seg) <= 1e-12 * seg[:-1])
         k += n_c
+
+
+# ------------------------------------------------------------ gradients
+def test_autograd_matches_dense_gradient_and_fd(solver):
+    """Autograd through the solver (forward solve, adjoint solve, sampled
+    outer product) against the oracle's dense gradient (1e-6 relative) and
+    against central differences of the exact loss (dense LU) along 16 seeded
+    directions with h = 1e-6."""
+    from paper_2303_08953_gb300.autograd import sparse_solve
+    A, rng = W.aniso2d(24)
+    b = rng.uniform(-1, 1, A.n)
+    xt = rng.uniform(-1, 1, A.n)
+    solver.analyze_csr(A)
+    opts = dict(m=600, s=8, tol=1e-13)
+    vals = dev(A.val).requires_grad_(True)
+    bt = dev(b).requires_grad_(True)
+    x = sparse_solve(vals, bt, solver, **opts)
+    L = 0.5 * ((x - dev(xt)) ** 2).sum()
+    L.backward()
+    L0, dv, db, _ = O.loss_gradients(A, b, xt)
+    assert abs(L.item() - L0) <= 1e-9 * abs(L0)
+    gv, gb = host(vals.grad), host(bt.grad)
+    assert np.linalg.norm(gv - dv) <= 1e-6 * np.linalg.norm(dv)
+    assert np.linalg.norm(gb - db) <= 1e-6 * np.linalg.norm(db)
+    h = 1e-6
+    for k in range(16):
+        d = np.random.default_rng(100 + k).standard_normal(A.nnz)
+        e = np.random.default_rng(200 + k).standard_normal(A.n)
+        Ap = W.CSR(A.n, A.rowptr, A.colind, A.val + h * d)
+        Am = W.CSR(A.n, A.rowptr, A.colind, A.val - h * d)
+        fd = (O.loss_gradients(Ap, b + h * e, xt)[0]
+              - O.loss_gradients(Am, b - h * e, xt)[0]) / (2 * h)
+        an = gv @ d + gb @ e
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3), (k, fd, an)

@@ -424,6 +424,26 @@ def test_estimator_drives_first_block():
     assert max(r.loo) < 1e-12
 
 
+# ------------------------------------------------------ adjoint gradient
+def test_loss_gradients_match_central_differences():
+    """dL/dvalues and dL/db of L = 0.5||A^-1 b - x_t||^2 against central
+    differences along 16 seeded random directions (h = 1e-6)."""
+    A, rng = W.aniso2d(8)
+    b = rng.uniform(-1, 1, A.n)
+    xt = rng.uniform(-1, 1, A.n)
+    L0, dv, db, _ = O.loss_gradients(A, b, xt)
+    h = 1e-6
+    for k in range(16):
+        d = np.random.default_rng(100 + k).standard_normal(A.nnz)
+        e = np.random.default_rng(200 + k).standard_normal(A.n)
+        Ap = W.CSR(A.n, A.rowptr, A.colind, A.val + h * d)
+        Am = W.CSR(A.n, A.rowptr, A.colind, A.val - h * d)
+        fd = (O.loss_gradients(Ap, b + h * e, xt)[0]
+              - O.loss_gradients(Am, b - h * e, xt)[0]) / (2 * h)
+        an = dv @ d + db @ e
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3)
+
+
 # ----------------------------------------------- planted-mistake checks
 def _pair_pin_fails():
     try:
