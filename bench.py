@@ -46,7 +46,7 @@ def parse():
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--case", default=None,
                    choices=["solve-fp64", "solve-fp32ir", "spmv", "dot64",
-                            "upd64", "dot32", "gram32"],
+                            "upd64", "dot32", "gram32", "upd32"],
                    help="run one small workload for a profiler and exit")
     return p.parse_args()
 
@@ -442,9 +442,12 @@ def run_case(args):
                 solver.block_update(Q, Wt, X)
         else:
             Q32, X32 = Q.to(fp), X.to(fp)
+            Wt = torch.randn(s, i, dtype=torch.float64, device=dev)
             for _ in range(3):
                 if name == "dot32":
                     solver.block_dot32(Q32, X32)
+                elif name == "upd32":
+                    solver.block_update32(Q32, Wt, X32)
                 else:
                     solver.block_dot32(X32, X32, sym=True)
     torch.cuda.synchronize()

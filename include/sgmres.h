@@ -213,9 +213,12 @@ sg_status sg_block_update(sg_handle* h, int64_t n, const double* Q,
  * sum |x_k y_k|).  Otherwise, when the leading dimensions are multiples of
  * 4, the pointers 16-byte aligned, n >= 256 and s <= 128, it runs on the
  * tensor cores (TMA + tcgen05, TF32 hi/lo split: hi*hi + lo*hi + hi*lo,
- * FP32 accumulation), else in FP32 FFMA.  sg_block_dot_f32 synchronises
- * the stream before returning (it reports a tensor-core wait timeout as
- * SG_ECUDA). */
+ * FP32 accumulation), else in FP32 FFMA.  sg_block_update_f32 likewise
+ * runs on the tensor cores when Q is 16-byte aligned with a leading
+ * dimension that is a multiple of 4, n >= 128 and s <= 128 (Q tile as an
+ * MN-major operand, W split into TF32 hi + FP32 remainder).  Both calls
+ * synchronise the stream before returning (a tensor-core wait timeout is
+ * reported as SG_ECUDA). */
 sg_status sg_block_dot_f32(sg_handle* h, int64_t n, const float* Q,
                            int64_t ldq, int32_t i, const float* X,
                            int64_t ldx, int32_t s, double* W, int32_t ldw,

@@ -285,6 +285,73 @@ void block_dot_impl(int64_t n, const T* Q, int64_t ldq, int i, const T* X,
 // time.
 constexpr int UK = 16;
 
+// FP32 wide form: one CTA owns 64 rows x 128 columns (Q is read once for
+// s <= 128), 4 x 8 outputs per thread, shared rows padded to 16-byte
+// multiples and read as float4.
+constexpr int WR = 64, WN = 128, WK = 16;
+
+__global__ void __launch_bounds__(kThreads)
+update_wide_kernel(int64_t K, int M, int N, const float* __restrict__ A, int64_t lda,
+                   const double* __restrict__ B, int ldb, float* __restrict__ C,
+                   int64_t ldc, float alpha, float beta, int upper) {
+  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * WR;
+  const int n0 = blockIdx.y * WN;
+  __shared__ __align__(16) float As[WK][WR + 4];
+  __shared__ __align__(16) float Bs[WK][WN + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid % 16;  // rows tx*4 .. +3
+  const int ty = tid / 16;  // cols ty*8 .. +7
+  float acc[4][8];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[a][b] = 0.0f;
+  const int mend = upper ? ((n0 + WN < M) ? n0 + WN : M) : M;
+  for (int mb = 0; mb < mend; mb += WK) {
+    for (int e = tid; e < WK * WR; e += kThreads) {
+      const int rr = e % WR, mm = e / WR;
+      const int64_t r = r0 + rr;
+      const int m = mb + mm;
+      As[mm][rr] = (r < K && m < mend) ? A[r + m * lda] : 0.0f;
+    }
+    for (int e = tid; e < WK * WN; e += kThreads) {
+      const int mm = e % WK, nn = e / WK;
+      const int m = mb + mm, nc = n0 + nn;
+      float v = 0.0f;
+      if (m < mend && nc < N && !(upper && m > nc)) v = static_cast<float>(B[m + nc * ldb]);
+      Bs[mm][nn] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int mm = 0; mm < WK; ++mm) {
+      const float4 av = *reinterpret_cast<const float4*>(&As[mm][tx * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[mm][ty * 8]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[mm][ty * 8 + 4]);
+      const float a4[4] = {av.x, av.y, av.z, av.w};
+      const float b8[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(a4[a], b8[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const int nc = n0 + ty * 8 + b;
+    if (nc >= N) continue;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int64_t r = r0 + tx * 4 + a;
+      if (r >= K) continue;
+      float* cp = C + r + nc * ldc;
+      float v = alpha * acc[a][b];
+      if (beta != 0.0f) v = fmaf(beta, *cp, v);
+      *cp = v;
+    }
+  }
+}
+
 template <int UR, int UN, int TR, int TN, typename T>
 __global__ void __launch_bounds__(kThreads)
 update_kernel(int64_t K, int M, int N, const T* __restrict__ A, int64_t lda,
@@ -368,12 +435,17 @@ void block_update_impl(int64_t n, const T* Q, int64_t ldq, int i,
     dim3 grid(static_cast<unsigned>((n + 63) / 64), (s + 15) / 16);
     update_kernel<64, 16, 4, 1, T><<<grid, kThreads, 0, st>>>(
         n, ii, s, Q, ldq, W, ldw, X, ldx, alpha, beta, upper ? 1 : 0);
-  } else {
-    // FP32: 128 x 32 tiles, 4 x 4 outputs per thread (FFMA-bound rather
-    // than shared-memory-bound)
-    dim3 grid(static_cast<unsigned>((n + 127) / 128), (s + 31) / 32);
+  } else if (s <= 32) {
+    // FP32, narrow blocks: 128 x 32 tiles, 4 x 4 outputs per thread
+    dim3 grid(static_cast<unsigned>((n + 127) / 128), 1);
     update_kernel<128, 32, 4, 4, T><<<grid, kThreads, 0, st>>>(
         n, ii, s, Q, ldq, W, ldw, X, ldx, alpha, beta, upper ? 1 : 0);
+  } else {
+    dim3 grid(static_cast<unsigned>((n + WR - 1) / WR), (s + WN - 1) / WN);
+    update_wide_kernel<<<grid, kThreads, 0, st>>>(
+        n, ii, s, reinterpret_cast<const float*>(Q), ldq, W, ldw,
+        reinterpret_cast<float*>(X), ldx, static_cast<float>(alpha),
+        static_cast<float>(beta), upper ? 1 : 0);
   }
   SG_LAUNCH_CHECK();
 }
@@ -436,7 +508,15 @@ void block_update(int64_t n, const double* Q, int64_t ldq, int i,
 
 void block_update32(int64_t n, const float* Q, int64_t ldq, int i,
                     const double* W, int ldw, float* X, int64_t ldx, int s,
-                    double alpha, double beta, bool upper, cudaStream_t st) {
+                    double alpha, double beta, bool upper, double* scratch,
+                    int64_t scratch_doubles, cudaStream_t st) {
+  if (i > 0 && s > 0 && scratch && !tc_disabled() &&
+      tc_update_scratch(i, s) <= 2 * scratch_doubles &&
+      tc_update_supported(n, Q, ldq, i, X, ldx, s)) {
+    tc_update(n, Q, ldq, i, W, ldw, X, ldx, s, alpha, beta, upper,
+              reinterpret_cast<float*>(scratch), 2 * scratch_doubles, st);
+    return;
+  }
   block_update_impl<float>(n, Q, ldq, i, W, ldw, X, ldx, s, alpha, beta,
                            upper, st);
 }

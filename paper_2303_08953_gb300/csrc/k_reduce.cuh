@@ -1,0 +1,43 @@
+// Block-level reductions shared by the streaming kernels: warp shuffles,
+// then one warp over the per-warp sums; the cross-block stage always adds
+// the per-block partials in index order, so every sum is deterministic.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace sg {
+
+template <int THREADS>
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// Sum over the block; every thread receives the result.
+template <int THREADS>
+__device__ double block_sum_d(double v) {
+  __shared__ double sh[THREADS / 32];
+  __shared__ double total;
+  v = warp_sum_d<THREADS>(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    double t = (l < THREADS / 32) ? sh[l] : 0.0;
+    t = warp_sum_d<THREADS>(t);
+    if (l == 0) total = t;
+  }
+  __syncthreads();
+  return total;
+}
+
+// Fixed-order sum of G per-block partials; every thread receives it.
+template <int THREADS>
+__device__ double sum_partials_d(const double* __restrict__ p, int G) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < G; i += THREADS) v += p[i];
+  return block_sum_d<THREADS>(v);
+}
+
+}  // namespace sg

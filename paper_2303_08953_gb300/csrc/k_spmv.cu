@@ -11,6 +11,7 @@
 // FP64 warp instructions are expensive (the FP64 pipe is ~1/64 of the FP32
 // rate), so the per-row reduction must not spend shuffles and adds on idle
 // lanes; the epilogue multiplies by 1/gamma instead of dividing.
+#include "k_reduce.cuh"
 #include "sg_internal.h"
 
 namespace sg {
@@ -92,6 +93,194 @@ void dispatch(const DevCsr& A, const T* val, const T* x, const T* z, T* y,
   spmv_kernel<MODE, HAS_Z, T><<<grid_for(A, rpc), kThreads, 0, st>>>(
       A.n, rpc, A.rowptr, A.colind, val, x, z, y, theta, c, T(1) / gamma);
   SG_LAUNCH_CHECK();
+}
+
+// ------------------------------------------------------------------------
+// One Arnoldi step of the Ritz pre-pass (Sec. 3.4) in a single cooperative
+// launch: w = A v_j with the partial sums of w.w and v_0.w fused into the
+// SpMV, then the j+1 modified Gram-Schmidt phases (h_l = v_l.w from the
+// previous phase's partials, w -= h_l v_l, partials of v_{l+1}.w), then
+// w /= ||w||.  Phases are separated by a grid barrier on a global arrival
+// counter and generation word; every block is resident (cooperative
+// launch), and each wait is time-bounded: on timeout the kernel records
+// an error and runs to completion with whatever it has.  bar: 64 zeroed
+// words (arrival counter and generation on separate 128-byte lines).
+constexpr uint64_t kBarrierNs = 2000000000ull;
+
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// bar[0]: arrivals; bar[32]: generation (a separate 128-byte line, so the
+// pollers do not contend with the arrivals)
+__device__ void grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 32;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == nblocks - 1) {
+      bar[0] = 0;
+      __threadfence();
+      atomicAdd(bar + 32, 1u);
+    } else if (*reinterpret_cast<volatile int*>(err) == 0) {
+      // (after an earlier timeout every barrier is skipped, so a broken
+      // barrier costs one time limit, not one per phase)
+      const uint64_t t0 = now_ns();
+      unsigned spins = 0;
+      while (*gen == g) {
+        __nanosleep(32);
+        if ((++spins & 255u) == 0 && now_ns() - t0 > kBarrierNs) {
+          atomicExch(err, 1);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+constexpr int kCoopThreads = 1024;  // one CTA per SM, 32 warps in flight
+constexpr int kCoopStage = 8192;    // staged nonzeros per CTA tile
+
+template <typename T>
+__global__ void __launch_bounds__(kCoopThreads, 1)
+arnoldi_step_kernel(int n, int rows_per_cta, const int* __restrict__ rowptr,
+                    const int* __restrict__ colind, const T* __restrict__ val,
+                    T* __restrict__ V, int64_t ld, int j, double* __restrict__ H,
+                    int ldh, double* __restrict__ wn, double* __restrict__ red,
+                    unsigned* bar, int* err) {
+  extern __shared__ __align__(16) unsigned char coop_smem[];
+  T* sval = reinterpret_cast<T*>(coop_smem);
+  int* scol = reinterpret_cast<int*>(coop_smem + sizeof(T) * kCoopStage);
+  const int G = gridDim.x;
+  const int t = threadIdx.x;
+  const T* vj = V + static_cast<int64_t>(j) * ld;
+  const T* v0 = V;
+  T* w = V + static_cast<int64_t>(j + 1) * ld;
+  double* pWW = red;
+  double* pA = red + G;
+  double* pB = red + 2 * G;
+  // phase 0: w = A v_j, partials of w.w and v_0.w
+  T accw = T(0), accv = T(0);
+  for (int64_t r0 = static_cast<int64_t>(blockIdx.x) * rows_per_cta; r0 < n;
+       r0 += static_cast<int64_t>(G) * rows_per_cta) {
+    const int64_t r1 = (r0 + rows_per_cta < n) ? r0 + rows_per_cta : n;
+    const int k0 = rowptr[r0];
+    const int len = rowptr[r1] - k0;
+    const bool staged = len <= kCoopStage;
+    if (staged) {
+      for (int e = t; e < len; e += kCoopThreads) {
+        sval[e] = ld_stream(val + k0 + e);
+        scol[e] = ld_stream(colind + k0 + e);
+      }
+    }
+    __syncthreads();
+    for (int64_t row = r0 + t; row < r1; row += kCoopThreads) {
+      const int a = rowptr[row], b = rowptr[row + 1];
+      T sum = T(0);
+      if (staged) {
+        for (int k = a - k0; k < b - k0; ++k) sum = fma(sval[k], __ldg(vj + scol[k]), sum);
+      } else {
+        for (int k = a; k < b; ++k) sum = fma(ld_stream(val + k), __ldg(vj + ld_stream(colind + k)), sum);
+      }
+      w[row] = sum;
+      accw = fma(sum, sum, accw);
+      accv = fma(v0[row], sum, accv);
+    }
+    __syncthreads();
+  }
+  {
+    const double sw = block_sum_d<kCoopThreads>(static_cast<double>(accw));
+    const double sv = block_sum_d<kCoopThreads>(static_cast<double>(accv));
+    if (t == 0) { pWW[blockIdx.x] = sw; pA[blockIdx.x] = sv; }
+  }
+  grid_barrier(bar, G, err);
+  if (blockIdx.x == 0) {
+    const double ww = sum_partials_d<kCoopThreads>(pWW, G);
+    if (t == 0) wn[j] = sqrt(ww);
+  }
+  // MGS phases l = 0..j (four independent element streams per thread)
+  const int64_t stride = static_cast<int64_t>(G) * kCoopThreads;
+  const int64_t i0 = blockIdx.x * static_cast<int64_t>(kCoopThreads) + t;
+  double* pin = pA;
+  double* pout = pB;
+  for (int l = 0; l <= j; ++l) {
+    const double h = sum_partials_d<kCoopThreads>(pin, G);
+    if (blockIdx.x == 0 && t == 0) H[l + static_cast<int64_t>(j) * ldh] = h;
+    const T ht = static_cast<T>(h);
+    const T* vl = V + static_cast<int64_t>(l) * ld;
+    const T* vn = (l < j) ? V + static_cast<int64_t>(l + 1) * ld : w;
+    T acc = T(0);
+    int64_t i = i0;
+    for (; i + 3 * stride < n; i += 4 * stride) {
+      T wv[4], vv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { wv[u] = w[i + u * stride]; vv[u] = vl[i + u * stride]; }
+      T nv[4];
+      if (l < j) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) nv[u] = vn[i + u * stride];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const T wi = fma(-ht, vv[u], wv[u]);
+        w[i + u * stride] = wi;
+        acc = fma(l < j ? nv[u] : wi, wi, acc);
+      }
+    }
+    for (; i < n; i += stride) {
+      const T wi = fma(-ht, vl[i], w[i]);
+      w[i] = wi;
+      acc = fma(l < j ? vn[i] : wi, wi, acc);
+    }
+    const double tot = block_sum_d<kCoopThreads>(static_cast<double>(acc));
+    if (t == 0) pout[blockIdx.x] = tot;
+    grid_barrier(bar, G, err);
+    double* tmp = pin; pin = pout; pout = tmp;
+  }
+  // normalise
+  const double nrm = sqrt(sum_partials_d<kCoopThreads>(pin, G));
+  if (blockIdx.x == 0 && t == 0) H[(j + 1) + static_cast<int64_t>(j) * ldh] = nrm;
+  const double inv = 1.0 / nrm;
+  for (int64_t i = i0; i < n; i += stride)
+    w[i] = static_cast<T>(static_cast<double>(w[i]) * inv);
+}
+
+template <typename T>
+void launch_arnoldi_step(const DevCsr& A, const T* val, T* V, int64_t ld, int j,
+                         double* H, int ldh, double* wn, double* red, int red_cap,
+                         unsigned* bar, int* err, cudaStream_t st) {
+  const int smem = kCoopStage * static_cast<int>(sizeof(T) + sizeof(int));
+  static int max_blocks[2] = {0, 0};
+  int& mb = max_blocks[sizeof(T) == 8 ? 0 : 1];
+  if (!mb) {
+    SG_CUDA(cudaFuncSetAttribute(arnoldi_step_kernel<T>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int per_sm = 0;
+    SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, arnoldi_step_kernel<T>,
+                                                          kCoopThreads, smem));
+    mb = per_sm * device_sm_count();
+    SG_REQUIRE(mb > 0, SG_ECUDA, "arnoldi step: no resident blocks");
+  }
+  int G = device_sm_count();  // one CTA per SM: fewer arrivals and partials
+  if (G > mb) G = mb;
+  SG_REQUIRE(3 * G <= red_cap, SG_EINVAL, "arnoldi step: partials buffer too small");
+  // rows per tile: the staged nonzeros fit with 25% slack, <= one per thread
+  const double per = A.mean_row > 0 ? A.mean_row * 1.25 : 1.0;
+  int rpc = static_cast<int>(kCoopStage / per);
+  if (rpc > kCoopThreads) rpc = kCoopThreads;
+  if (rpc < 32) rpc = 32;
+  int n = A.n;
+  void* args[] = {&n, &rpc, const_cast<int**>(&A.rowptr), const_cast<int**>(&A.colind),
+                  const_cast<T**>(&val), &V, &ld, &j, &H, const_cast<int*>(&ldh), &wn, &red,
+                  &bar, &err};
+  SG_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(arnoldi_step_kernel<T>),
+                                      dim3(G), dim3(kCoopThreads), args, smem, st));
+  count_launch();
 }
 
 __global__ void sampled_outer_kernel(int n, const int* __restrict__ rowptr,
@@ -230,6 +419,18 @@ void csr_transpose(const DevCsr& A, DevCsr& T, int32_t* counts,
   SG_LAUNCH_CHECK();
   sort_rows_kernel<<<g, kThreads, 0, st>>>(A.n, T.rowptr, T.colind, T.val);
   SG_LAUNCH_CHECK();
+}
+
+void arnoldi_step(const DevCsr& A, double* V, int64_t ld, int j, double* H,
+                  int ldh, double* wn, double* red, int red_cap, unsigned* bar,
+                  int* err, cudaStream_t st) {
+  launch_arnoldi_step<double>(A, A.val, V, ld, j, H, ldh, wn, red, red_cap, bar, err, st);
+}
+
+void arnoldi_step32(const DevCsr& A, float* V, int64_t ld, int j, double* H,
+                    int ldh, double* wn, double* red, int red_cap, unsigned* bar,
+                    int* err, cudaStream_t st) {
+  launch_arnoldi_step<float>(A, A.val32, V, ld, j, H, ldh, wn, red, red_cap, bar, err, st);
 }
 
 }  // namespace sg

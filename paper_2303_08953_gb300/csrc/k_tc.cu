@@ -22,118 +22,20 @@
 
 #include <mutex>
 
+#include "k_tc_common.cuh"
 #include "sg_internal.h"
 
 namespace sg {
 
 namespace {
 
+using namespace tc;
+
 constexpr int kBM = 128;          // MMA M: columns of Q per tile
 constexpr int kBK = 32;           // rows per stage: 32 FP32 = one 128 B row
 constexpr int kStages = 3;
 constexpr int kThreads = 256;     // 8 warps split tiles; warps 0-3 own TMEM lanes
-constexpr uint32_t kSpinLimit = 1u << 26;
-constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
 constexpr int kMaxN = 128;        // s <= 128 per launch
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// bounded wait for the phase with the given parity to complete: gives up
-// after kWaitNs nanoseconds (or kSpinLimit attempts) and returns false
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  const uint32_t addr = smem_u32(bar);
-  const uint64_t t0 = global_ns();
-  for (uint32_t it = 0; it < kSpinLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if ((it & 255) == 255 && global_ns() - t0 > kWaitNs) return false;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
-                                            int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
-      : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
-// 8-row groups 1024 bytes apart (tile base aligned to 1024 bytes).
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);  // start address
-  d |= static_cast<uint64_t>(1) << 16;                 // leading byte offset (unused)
-  d |= static_cast<uint64_t>(1024 >> 4) << 32;         // stride byte offset
-  d |= static_cast<uint64_t>(1) << 46;                 // descriptor version
-  d |= static_cast<uint64_t>(2) << 61;                 // 128-byte swizzle
-  return d;
-}
-
-// Instruction descriptor: kind::tf32, FP32 accumulator, K-major A and B.
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) |
-         (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b,
-                                         uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void split_tf32(float4* hi, float4* lo, int count4, int tid) {
-#pragma unroll 4
-  for (int e = tid; e < count4; e += kThreads) {
-    float4 v = hi[e];
-    float4 h, l;
-    h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u); l.x = v.x - h.x;
-    h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u); l.y = v.y - h.y;
-    h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u); l.z = v.z - h.z;
-    h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u); l.w = v.w - h.w;
-    hi[e] = h;
-    lo[e] = l;
-  }
-}
 
 struct __align__(8) TcShared {
   uint64_t full[kStages];
@@ -211,9 +113,9 @@ tc_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
     const uint32_t ph = static_cast<uint32_t>((kb / kStages) & 1);
     if (!mbar_wait(&sh.full[s], ph)) sh.fail = 1;
     else consumed = kb + 1;
-    split_tf32(reinterpret_cast<float4*>(stA(s)), reinterpret_cast<float4*>(stAlo(s)),
+    split_tf32<kThreads>(reinterpret_cast<float4*>(stA(s)), reinterpret_cast<float4*>(stAlo(s)),
                a_bytes / 16, tid);
-    split_tf32(reinterpret_cast<float4*>(stB(s)), reinterpret_cast<float4*>(stBlo(s)),
+    split_tf32<kThreads>(reinterpret_cast<float4*>(stB(s)), reinterpret_cast<float4*>(stBlo(s)),
                b_bytes / 16, tid);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();

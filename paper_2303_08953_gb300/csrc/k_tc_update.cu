@@ -1,0 +1,379 @@
+// Tensor-core block update for the FP32 basis: X = beta X + alpha Q W
+// (the BCGS updates and the CholQR triangular products of Alg. 4).
+//
+// D (128 rows of X x s) = Q (128 rows x i) . W (i x s) on tcgen05 (kind::tf32,
+// FP32 accumulator in tensor memory).  Q is column-major, so TMA delivers
+// its tile row-contiguous: four 32-row x 32-column boxes per stage, each
+// 32 lines of 128 B (one line per column of Q, 128-byte swizzle).  The
+// split warps transpose each box into the K-major 128-byte-swizzled layout
+// the MMA reads (one 128 B row of 32 k-values per row of X) while they
+// split it into a TF32 hi part and its FP32 remainder; the lane mapping
+// (8 rows x 4 columns per warp instruction) keeps the stores free of bank
+// conflicts.  W is tiny: a prologue kernel writes its hi part and
+// remainder as FP32 arrays that TMA loads as K-major tiles.  hi*hi +
+// lo*hi + hi*lo is accumulated.
+//
+// Persistent and warp-specialised: one CTA per SM walks 128-row tiles;
+//   warp 8 (one lane) issues the TMA loads of a 2-stage ring,
+//   warps 4-7 split each Q tile into hi/lo,
+//   warp 9 (one lane) issues the MMAs into one of two TMEM accumulators,
+//   warps 0-3 (the TMEM lane owners) read an accumulator back and write X
+//   while the next tile accumulates into the other.
+// Every wait is time-bounded; a timeout records an error flag, the roles
+// stop, in-flight copies and MMAs are drained and the TMEM is freed.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "k_tc_common.cuh"
+#include "sg_internal.h"
+
+namespace sg {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kRows = 128;      // rows of X per tile (MMA M)
+constexpr int kKC = 32;         // columns of Q (K) per stage
+constexpr int kStages = 2;
+constexpr int kThreads = 320;   // 10 warps
+constexpr int kMaxN = 128;
+
+struct __align__(8) UpdShared {
+  uint64_t full[kStages];
+  uint64_t split[kStages];
+  uint64_t empty[kStages];
+  uint64_t accf[2];
+  uint64_t acce[2];
+  uint64_t done;
+  uint32_t tmem_base;
+  int fail;
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+tc_update_kernel(const __grid_constant__ CUtensorMap mapQ,
+                 const __grid_constant__ CUtensorMap mapWh,
+                 const __grid_constant__ CUtensorMap mapWl, int64_t n, int i, int s,
+                 int BN, float* __restrict__ X, int64_t ldx, float alpha, float beta,
+                 int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char dsmem[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~static_cast<uintptr_t>(1023));
+  constexpr int a_bytes = kRows * kKC * 4;  // 16 KB: four 4 KB boxes
+  const int b_bytes = BN * kKC * 4;
+  const int stage_bytes = 3 * a_bytes + 2 * b_bytes;  // raw, hi, lo, B hi, B lo
+  __shared__ UpdShared sh;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+  const int64_t tiles = (n + kRows - 1) / kRows;
+  const int KC = (i + kKC - 1) / kKC;
+  const int my_tiles = static_cast<int>((tiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
+  const int total = my_tiles * KC;  // (tile, k-chunk) pairs of this CTA
+  const uint32_t idesc = idesc_tf32(kRows, BN);
+
+  if (tid == 0) {
+    for (int q = 0; q < kStages; ++q) {
+      mbar_init(&sh.full[q], 1);
+      mbar_init(&sh.split[q], 128);
+      mbar_init(&sh.empty[q], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sh.accf[b], 1);
+      mbar_init(&sh.acce[b], 128);
+    }
+    mbar_init(&sh.done, 1);
+    sh.fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&sh.tmem_base)),
+                 "r"(256)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = sh.tmem_base;
+
+  auto stRaw = [&](int q) { return base + q * stage_bytes; };
+  auto stA = [&](int q) { return base + q * stage_bytes + a_bytes; };
+  auto stAlo = [&](int q) { return base + q * stage_bytes + 2 * a_bytes; };
+  auto stB = [&](int q) { return base + q * stage_bytes + 3 * a_bytes; };
+  auto stBlo = [&](int q) { return base + q * stage_bytes + 3 * a_bytes + b_bytes; };
+  auto fail_now = [&]() {
+    sh.fail = 1;
+    atomicExch(err, 1);
+  };
+
+  if (warp == 8) {
+    // ------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int c = 0; c < total; ++c) {
+        if (*reinterpret_cast<volatile int*>(&sh.fail)) break;
+        const int q = c % kStages;
+        if (c >= kStages &&
+            !mbar_wait(&sh.empty[q], static_cast<uint32_t>(((c / kStages) - 1) & 1))) {
+          fail_now();
+          break;
+        }
+        const int lt = c / KC, kc = c % KC;
+        const int64_t row0 = (static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(lt) * gridDim.x) * kRows;
+        mbar_expect_tx(&sh.full[q], static_cast<uint32_t>(a_bytes + 2 * b_bytes));
+        for (int g = 0; g < 4; ++g)
+          tma_load_2d(stRaw(q) + g * 4096, &mapQ, &sh.full[q], static_cast<int>(row0 + g * 32),
+                      kc * kKC);
+        tma_load_2d(stB(q), &mapWh, &sh.full[q], kc * kKC, 0);
+        tma_load_2d(stBlo(q), &mapWl, &sh.full[q], kc * kKC, 0);
+        ++issued;
+      }
+      if (*reinterpret_cast<volatile int*>(&sh.fail)) {
+        // drain the loads still in flight (the latest use of each stage)
+        for (int c = (issued > kStages ? issued - kStages : 0); c < issued; ++c)
+          mbar_wait(&sh.full[c % kStages], static_cast<uint32_t>((c / kStages) & 1));
+      }
+    }
+  } else if (warp >= 4 && warp < 8) {
+    // ------------------------------------------------ hi/lo split of Q
+    const int st = tid - 128;
+    for (int c = 0; c < total; ++c) {
+      if (*reinterpret_cast<volatile int*>(&sh.fail)) break;
+      const int q = c % kStages;
+      if (!mbar_wait(&sh.full[q], static_cast<uint32_t>((c / kStages) & 1))) {
+        fail_now();
+        break;
+      }
+      // slot sl covers rows rb*8 .. +7 and columns kg*4 .. +3 of box g;
+      // lane -> (row r8 = lane & 7, column kq = lane >> 3)
+      const float* raw = reinterpret_cast<const float*>(stRaw(q));
+      float* hi = reinterpret_cast<float*>(stA(q));
+      float* lo = reinterpret_cast<float*>(stAlo(q));
+      const int w4 = st >> 5, ln = st & 31, r8 = ln & 7, kq = ln >> 3;
+#pragma unroll 4
+      for (int it = 0; it < 32; ++it) {
+        const int sl = it * 4 + w4;
+        const int g = sl >> 5, rb = (sl >> 3) & 3, kg = sl & 7;
+        const int r = rb * 8 + r8, k = kg * 4 + kq;
+        const float v = raw[g * 1024 + k * 32 + ((((r >> 2) ^ (k & 7)) << 2) | (r & 3))];
+        const int m = g * 32 + r;
+        const int d = m * 32 + ((((k >> 2) ^ (m & 7)) << 2) | (k & 3));
+        const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+        hi[d] = h;
+        lo[d] = v - h;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&sh.split[q]);
+    }
+  } else if (warp == 9) {
+    // ------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      for (int lt = 0; lt < my_tiles && !*reinterpret_cast<volatile int*>(&sh.fail); ++lt) {
+        const int b = lt & 1;
+        if (lt >= 2 &&
+            !mbar_wait(&sh.acce[b], static_cast<uint32_t>(((lt / 2) - 1) & 1))) {
+          fail_now();
+          break;
+        }
+        const uint32_t dt = tmem + static_cast<uint32_t>(b * 128);
+        bool ok = true;
+        for (int kc = 0; kc < KC; ++kc) {
+          const int c = lt * KC + kc;
+          const int q = c % kStages;
+          if (!mbar_wait(&sh.split[q], static_cast<uint32_t>((c / kStages) & 1))) {
+            fail_now();
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t ah = sdesc(smem_u32(stA(q))), al = sdesc(smem_u32(stAlo(q)));
+          const uint64_t bh = sdesc(smem_u32(stB(q))), bl = sdesc(smem_u32(stBlo(q)));
+#pragma unroll
+          for (int k8 = 0; k8 < kKC / 8; ++k8) {  // K = 8 TF32 = 32 bytes per MMA
+            const uint64_t adv = static_cast<uint64_t>((k8 * 32) >> 4);
+            mma_tf32(dt, ah + adv, bh + adv, idesc, (kc > 0 || k8 > 0) ? 1u : 0u);
+            mma_tf32(dt, al + adv, bh + adv, idesc, 1u);
+            mma_tf32(dt, ah + adv, bl + adv, idesc, 1u);
+          }
+          mma_commit(&sh.empty[q]);
+        }
+        if (!ok) break;
+        mma_commit(&sh.accf[b]);
+      }
+      mma_commit(&sh.done);  // every MMA issued above has completed
+      if (!mbar_wait(&sh.done, 0)) fail_now();
+    }
+  } else {
+    // ------------------------------------------------ epilogue (warps 0-3)
+    for (int lt = 0; lt < my_tiles; ++lt) {
+      if (*reinterpret_cast<volatile int*>(&sh.fail)) break;
+      const int b = lt & 1;
+      if (!mbar_wait(&sh.accf[b], static_cast<uint32_t>((lt / 2) & 1))) {
+        fail_now();
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int64_t row = (static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(lt) * gridDim.x) * kRows +
+                          warp * 32 + lane;
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t v[16];
+        const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16) +
+                               static_cast<uint32_t>(b * 128 + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+              "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+              "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row < n) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int col = c0 + j;
+            if (col < s) {
+              float* p = X + row + static_cast<int64_t>(col) * ldx;
+              float y = alpha * __uint_as_float(v[j]);
+              if (beta != 0.0f) y = fmaf(beta, *p, y);
+              *p = y;
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&sh.acce[b]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256)
+                 : "memory");
+  }
+}
+
+// W (FP64, i x s, ld ldw) -> TF32 hi part and FP32 remainder, ld ldp >= i
+// (16-byte rows for TMA); padding and, for an upper-triangular W, the
+// entries below the diagonal are zero.
+__global__ void split_w_kernel(int i, int s, const double* __restrict__ W, int ldw,
+                               float* __restrict__ hi, float* __restrict__ lo, int ldp,
+                               int upper) {
+  const int64_t tot = static_cast<int64_t>(ldp) * s;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < tot;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int k = static_cast<int>(e % ldp), c = static_cast<int>(e / ldp);
+    double w = 0.0;
+    if (k < i && !(upper && k > c)) w = W[k + static_cast<int64_t>(c) * ldw];
+    const float h = __uint_as_float(__float_as_uint(static_cast<float>(w)) & 0xFFFFE000u);
+    hi[e] = h;
+    lo[e] = static_cast<float>(w - static_cast<double>(h));
+  }
+}
+
+__device__ int g_tcu_err;
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap* map, const float* base, int64_t inner, int64_t outer,
+              int64_t ld, int box_inner, int box_outer) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(outer)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * sizeof(float)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(box_inner), static_cast<cuuint32_t>(box_outer)};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims,
+            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+int* err_flag() {
+  static int* ptr[64] = {};
+  static std::mutex mu;
+  int dev = 0;
+  SG_CUDA(cudaGetDevice(&dev));
+  SG_REQUIRE(dev >= 0 && dev < 64, SG_ECUDA, "device index out of range");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!ptr[dev]) {
+    void* p = nullptr;
+    SG_CUDA(cudaGetSymbolAddress(&p, g_tcu_err));
+    ptr[dev] = static_cast<int*>(p);
+  }
+  return ptr[dev];
+}
+
+}  // namespace
+
+bool tc_update_supported(int64_t n, const float* Q, int64_t ldq, int i, const float* X,
+                         int64_t ldx, int s) {
+  if (n < kRows || i < 1 || s < 1 || s > kMaxN) return false;
+  if (reinterpret_cast<uintptr_t>(Q) & 15) return false;
+  if ((ldq * 4) & 15) return false;
+  (void)X; (void)ldx;
+  return encode_fn() != nullptr;
+}
+
+int64_t tc_update_scratch(int i, int s) {  // floats
+  const int ldp = (i + 3) / 4 * 4;
+  return 2 * static_cast<int64_t>(ldp) * s + 8;
+}
+
+void tc_update(int64_t n, const float* Q, int64_t ldq, int i, const double* W, int ldw,
+               float* X, int64_t ldx, int s, double alpha, double beta, bool upper,
+               float* scratch, int64_t scratch_floats, cudaStream_t st) {
+  const int ldp = (i + 3) / 4 * 4;
+  SG_REQUIRE(tc_update_scratch(i, s) <= scratch_floats, SG_EINVAL, "tc_update: scratch too small");
+  float* hi = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(scratch) + 15) & ~uintptr_t(15));
+  float* lo = hi + static_cast<int64_t>(ldp) * s;
+  split_w_kernel<<<64, 256, 0, st>>>(i, s, W, ldw, hi, lo, ldp, upper ? 1 : 0);
+  SG_LAUNCH_CHECK();
+  const int BN = (s + 15) / 16 * 16;
+  CUtensorMap mq, mh, ml;
+  SG_REQUIRE(make_map(&mq, Q, n, i, ldq, 32, kKC) && make_map(&mh, hi, ldp, s, ldp, kKC, BN) &&
+                 make_map(&ml, lo, ldp, s, ldp, kKC, BN),
+             SG_ECUDA, "cuTensorMapEncodeTiled failed");
+  const int smem = kStages * (3 * kRows * kKC * 4 + 2 * BN * kKC * 4) + 1024;
+  static bool configured = false;
+  if (!configured) {
+    SG_CUDA(cudaFuncSetAttribute(tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kStages * (3 * kRows * kKC * 4 + 2 * kMaxN * kKC * 4) + 1024));
+    configured = true;
+  }
+  const int64_t tiles = (n + kRows - 1) / kRows;
+  int grid = device_sm_count();
+  if (grid > tiles) grid = static_cast<int>(tiles);
+  tc_update_kernel<<<grid, kThreads, smem, st>>>(mq, mh, ml, n, i, s, BN, X, ldx,
+                                                  static_cast<float>(alpha),
+                                                  static_cast<float>(beta), err_flag());
+  SG_LAUNCH_CHECK();
+}
+
+void tc_update_check_error(cudaStream_t st) {
+  int* f = err_flag();
+  int host = 0;
+  SG_CUDA(cudaMemcpyAsync(&host, f, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SG_CUDA(cudaStreamSynchronize(st));
+  if (host) {
+    SG_CUDA(cudaMemsetAsync(f, 0, sizeof(int), st));
+    throw Error(SG_ECUDA, "tensor-core block update: a bounded wait ran out");
+  }
+}
+
+}  // namespace sg

@@ -1,8 +1,6 @@
 // Vector kernels: deterministic dot products and norms (warp shuffles,
-// then a fixed-order sum of per-block partials), the fused modified
-// Gram-Schmidt step of the Arnoldi pre-pass that supplies the Ritz values
-// (Sec. 3.4), normalisation, the solution update x += Q y (Alg. 4, last
-// line) and precision conversions.
+// then a fixed-order sum of per-block partials), the solution update
+// x += Q y (Alg. 4, last line) and precision conversions.
 #include "sg_internal.h"
 
 namespace sg {
@@ -69,53 +67,6 @@ __global__ void finish_kernel(const double* __restrict__ part, int G,
                               double* out, int sqrt_out) {
   const double s = sum_partials(part, G);
   if (threadIdx.x == 0) out[0] = sqrt_out ? sqrt(s) : s;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-mgs_kernel(int64_t n, T* __restrict__ w, const T* __restrict__ v,
-           const T* __restrict__ vnext, const double* __restrict__ pin,
-           int G, double* hout, double* __restrict__ pout) {
-  const double h = sum_partials(pin, G);
-  if (blockIdx.x == 0 && threadIdx.x == 0) *hout = h;
-  const T ht = static_cast<T>(h);
-  T acc = T(0);
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * kThreads;
-  int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x;
-  for (; i + 3 * stride < n; i += 4 * stride) {  // four independent streams
-    T wv[4], vv[4], nv[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) { wv[u] = w[i + u * stride]; vv[u] = v[i + u * stride]; }
-    if (vnext) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) nv[u] = vnext[i + u * stride];
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const T wi = fma(-ht, vv[u], wv[u]);
-      w[i + u * stride] = wi;
-      acc = fma(vnext ? nv[u] : wi, wi, acc);
-    }
-  }
-  for (; i < n; i += stride) {
-    const T wi = fma(-ht, v[i], w[i]);
-    w[i] = wi;
-    acc = fma(vnext ? vnext[i] : wi, wi, acc);
-  }
-  const double tot = block_sum(static_cast<double>(acc));
-  if (threadIdx.x == 0) pout[blockIdx.x] = tot;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-normalize_kernel(int64_t n, const double* __restrict__ pin, int G,
-                 const T* x, T* y, double* nout) {
-  const double nrm = sqrt(sum_partials(pin, G));
-  if (blockIdx.x == 0 && threadIdx.x == 0) *nout = nrm;
-  const double inv = 1.0 / nrm;
-  for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < n;
-       i += static_cast<int64_t>(gridDim.x) * kThreads)
-    y[i] = static_cast<T>(static_cast<double>(x[i]) * inv);
 }
 
 __global__ void scale_kernel(int64_t n, const double* __restrict__ x,
@@ -191,46 +142,10 @@ void dot_partials(int64_t n, const double* x, const double* y,
   SG_LAUNCH_CHECK();
 }
 
-void dot_partials32(int64_t n, const float* x, const float* y,
-                    double* partials, cudaStream_t st) {
-  dot_kernel<float><<<reduction_blocks(), kThreads, 0, st>>>(n, x, y, partials);
-  SG_LAUNCH_CHECK();
-}
-
 void finish_sum(const double* partials, double* out, bool sqrt_out,
                 cudaStream_t st) {
   finish_kernel<<<1, kThreads, 0, st>>>(partials, reduction_blocks(), out,
                                         sqrt_out ? 1 : 0);
-  SG_LAUNCH_CHECK();
-}
-
-void mgs_step(int64_t n, double* w, const double* v, const double* vnext,
-              const double* pin, double* hout, double* pout,
-              cudaStream_t st) {
-  mgs_kernel<double><<<reduction_blocks(), kThreads, 0, st>>>(
-      n, w, v, vnext, pin, reduction_blocks(), hout, pout);
-  SG_LAUNCH_CHECK();
-}
-
-void mgs_step32(int64_t n, float* w, const float* v, const float* vnext,
-                const double* pin, double* hout, double* pout,
-                cudaStream_t st) {
-  mgs_kernel<float><<<reduction_blocks(), kThreads, 0, st>>>(
-      n, w, v, vnext, pin, reduction_blocks(), hout, pout);
-  SG_LAUNCH_CHECK();
-}
-
-void normalize(int64_t n, const double* pin, const double* x, double* y,
-               double* nout, cudaStream_t st) {
-  normalize_kernel<double><<<stream_grid(n), kThreads, 0, st>>>(
-      n, pin, reduction_blocks(), x, y, nout);
-  SG_LAUNCH_CHECK();
-}
-
-void normalize32(int64_t n, const double* pin, const float* x, float* y,
-                 double* nout, cudaStream_t st) {
-  normalize_kernel<float><<<stream_grid(n), kThreads, 0, st>>>(
-      n, pin, reduction_blocks(), x, y, nout);
   SG_LAUNCH_CHECK();
 }
 

@@ -248,6 +248,7 @@ void sg_destroy(sg_handle* h) {
   free_csr(h->AT);
   double* d[] = {h->Q, h->V, h->Y, h->bvec, h->xvec, h->rvec, h->part, h->red, h->small, h->dvec};
   for (double* p : d) if (p) cudaFree(p);
+  if (h->sync) cudaFree(h->sync);
   float* f[] = {h->Q32, h->V32, h->Y32, h->r32};
   for (float* p : f) if (p) cudaFree(p);
   if (h->hbuf) cudaFreeHost(h->hbuf);
@@ -478,8 +479,11 @@ sg_status sg_block_update_f32(sg_handle* h, int64_t n, const float* Q,
     SG_REQUIRE((Q && W) || i == 0, SG_EINVAL, "null Q/W");
     SG_REQUIRE(!upper || i == s, SG_EINVAL, "upper needs i == s");
     SG_CUDA(cudaSetDevice(h->device));
+    cudaStream_t st = pick(h, stream);
+    if (i > 0 && s > 0) ensure_part(h, (sg::tc_update_scratch(i, s) + 1) / 2, st);
     sg::block_update32(n, Q, ldq, i, W, ldw, X, ldx, s, alpha, beta, upper != 0,
-                       pick(h, stream));
+                       h->part, h->part_cap, st);
+    sg::tc_update_check_error(st);  // synchronises: reports a tensor-core timeout
   });
 }
 

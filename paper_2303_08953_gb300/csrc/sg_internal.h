@@ -26,6 +26,7 @@ struct Error : std::runtime_error {
 // every kernel launch of the library goes through this check, which also
 // counts it (sg_kernel_launches)
 void count_launch();
+void count_launches(long long k);
 #define SG_LAUNCH_CHECK()                                                  \
   do {                                                                     \
     ::sg::count_launch();                                                  \
@@ -55,6 +56,16 @@ void spmv_newton(const DevCsr& A, const double* x, const double* z,
                  cudaStream_t st);
 void spmv_newton32(const DevCsr& A, const float* x, const float* z, float* y,
                    float theta, float c, float gamma, cudaStream_t st);
+// One Arnoldi step of the Ritz pre-pass (cooperative launch): V[:, j+1] =
+// normalised MGS projection of A V[:, j]; writes H(0..j+1, j) (ld ldh) and
+// wn[j] = ||A v_j||.  red: >= 3 x SMs doubles; bar: 64 zeroed unsigned
+// words (barrier state); err: set to 1 if a barrier wait ran out.
+void arnoldi_step(const DevCsr& A, double* V, int64_t ld, int j, double* H,
+                  int ldh, double* wn, double* red, int red_cap, unsigned* bar,
+                  int* err, cudaStream_t st);
+void arnoldi_step32(const DevCsr& A, float* V, int64_t ld, int j, double* H,
+                    int ldh, double* wn, double* red, int red_cap, unsigned* bar,
+                    int* err, cudaStream_t st);
 // r = b - A x
 void residual(const DevCsr& A, const double* b, const double* x, double* r,
               cudaStream_t st);
@@ -71,24 +82,9 @@ void csr_transpose(const DevCsr& A, DevCsr& T, int32_t* work_counts,
 int reduction_blocks();
 void dot_partials(int64_t n, const double* x, const double* y,
                   double* partials, cudaStream_t st);
-void dot_partials32(int64_t n, const float* x, const float* y,
-                    double* partials, cudaStream_t st);
 // out[0] = sum(partials) (or its square root when sqrt_out)
 void finish_sum(const double* partials, double* out, bool sqrt_out,
                 cudaStream_t st);
-// One modified Gram-Schmidt step of Arnoldi: h = sum(pin) (written to
-// *hout), w -= h v, pout = partials of dot(vnext ? vnext : w, w).
-void mgs_step(int64_t n, double* w, const double* v, const double* vnext,
-              const double* pin, double* hout, double* pout,
-              cudaStream_t st);
-void mgs_step32(int64_t n, float* w, const float* v, const float* vnext,
-                const double* pin, double* hout, double* pout,
-                cudaStream_t st);
-// nrm = sqrt(sum(pin)); *nout = nrm; y = x / nrm (y may alias x)
-void normalize(int64_t n, const double* pin, const double* x, double* y,
-               double* nout, cudaStream_t st);
-void normalize32(int64_t n, const double* pin, const float* x, float* y,
-                 double* nout, cudaStream_t st);
 // y = x * (alpha_host)
 void scale_copy(int64_t n, const double* x, double* y, double alpha,
                 cudaStream_t st);
@@ -124,9 +120,12 @@ void block_dot_capped(int64_t n, const double* Q, int64_t ldq, int i,
 void block_update(int64_t n, const double* Q, int64_t ldq, int i,
                   const double* W, int ldw, double* X, int64_t ldx, int s,
                   double alpha, double beta, bool upper, cudaStream_t st);
+// FP32: runs on the tensor cores when supported (scratch: >= the
+// tc_update_scratch floats, may be null to force the FFMA kernels)
 void block_update32(int64_t n, const float* Q, int64_t ldq, int i,
                     const double* W, int ldw, float* X, int64_t ldx, int s,
-                    double alpha, double beta, bool upper, cudaStream_t st);
+                    double alpha, double beta, bool upper, double* scratch,
+                    int64_t scratch_doubles, cudaStream_t st);
 
 // Tensor-core (tcgen05, TMA) FP32 block dot W = Q^T X: split partials
 // into `part`, number of splits in *nsplit; bounded waits record failure
@@ -138,6 +137,15 @@ void tc_dot(int64_t n, const float* Q, int64_t ldq, int i, const float* X,
             int64_t ldx, int s, double* part, int64_t part_cap, int* nsplit,
             cudaStream_t st);
 void tc_check_error(cudaStream_t st);
+// Tensor-core (tcgen05, TMA) FP32 block update X = beta X + alpha Q W.
+bool tc_update_supported(int64_t n, const float* Q, int64_t ldq, int i,
+                         const float* X, int64_t ldx, int s);
+int64_t tc_update_scratch(int i, int s);  // floats
+void tc_update(int64_t n, const float* Q, int64_t ldq, int i, const double* W,
+               int ldw, float* X, int64_t ldx, int s, double alpha, double beta,
+               bool upper, float* scratch, int64_t scratch_floats,
+               cudaStream_t st);
+void tc_update_check_error(cudaStream_t st);
 
 int device_sm_count();
 

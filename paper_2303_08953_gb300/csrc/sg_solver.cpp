@@ -150,17 +150,6 @@ template <> struct Basis<double> {
                    double th, double c, double g, cudaStream_t st) {
     spmv_newton(M, x, z, y, th, c, g, st);
   }
-  static void dot(int64_t n, const double* x, const double* y, double* p, cudaStream_t st) {
-    dot_partials(n, x, y, p, st);
-  }
-  static void mgs(int64_t n, double* w, const double* v, const double* vn,
-                  const double* pin, double* hout, double* pout, cudaStream_t st) {
-    mgs_step(n, w, v, vn, pin, hout, pout, st);
-  }
-  static void norml(int64_t n, const double* pin, const double* x, double* y,
-                    double* nout, cudaStream_t st) {
-    normalize(n, pin, x, y, nout, st);
-  }
   static void from_f64(int64_t n, const double* r, double* q, double a, cudaStream_t st) {
     scale_copy(n, r, q, a, st);
   }
@@ -169,9 +158,9 @@ template <> struct Basis<double> {
                    int64_t cap, cudaStream_t st) {
     block_dot(n, Q, ldq, i, X, ldx, s, W, ldw, sym, part, cap, st);
   }
-  static void bupd(int64_t n, const double* Q, int64_t ldq, int i, const double* W,
-                   int ldw, double* X, int64_t ldx, int s, double al, double be,
-                   bool up, cudaStream_t st) {
+  static void bupd(sg_handle*, int64_t n, const double* Q, int64_t ldq, int i,
+                   const double* W, int ldw, double* X, int64_t ldx, int s, double al,
+                   double be, bool up, cudaStream_t st) {
     block_update(n, Q, ldq, i, W, ldw, X, ldx, s, al, be, up, st);
   }
   static void gemv(int64_t n, int k, const double* Q, int64_t ldq, const double* y,
@@ -189,17 +178,6 @@ template <> struct Basis<float> {
     spmv_newton32(M, x, z, y, static_cast<float>(th), static_cast<float>(c),
                   static_cast<float>(g), st);
   }
-  static void dot(int64_t n, const float* x, const float* y, double* p, cudaStream_t st) {
-    dot_partials32(n, x, y, p, st);
-  }
-  static void mgs(int64_t n, float* w, const float* v, const float* vn,
-                  const double* pin, double* hout, double* pout, cudaStream_t st) {
-    mgs_step32(n, w, v, vn, pin, hout, pout, st);
-  }
-  static void norml(int64_t n, const double* pin, const float* x, float* y,
-                    double* nout, cudaStream_t st) {
-    normalize32(n, pin, x, y, nout, st);
-  }
   static void from_f64(int64_t n, const double* r, float* q, double a, cudaStream_t st) {
     to_f32(n, r, q, static_cast<float>(a), st);
   }
@@ -208,10 +186,12 @@ template <> struct Basis<float> {
                    int64_t cap, cudaStream_t st) {
     block_dot32(n, Q, ldq, i, X, ldx, s, W, ldw, sym, part, cap, st);
   }
-  static void bupd(int64_t n, const float* Q, int64_t ldq, int i, const double* W,
-                   int ldw, float* X, int64_t ldx, int s, double al, double be,
-                   bool up, cudaStream_t st) {
-    block_update32(n, Q, ldq, i, W, ldw, X, ldx, s, al, be, up, st);
+  // the tensor-core update stages W's TF32 split in the (then idle)
+  // split-partials buffer of the workspace
+  static void bupd(sg_handle* h, int64_t n, const float* Q, int64_t ldq, int i,
+                   const double* W, int ldw, float* X, int64_t ldx, int s, double al,
+                   double be, bool up, cudaStream_t st) {
+    block_update32(n, Q, ldq, i, W, ldw, X, ldx, s, al, be, up, h->part, h->part_cap, st);
   }
   static void gemv(int64_t n, int k, const float* Q, int64_t ldq, const double* y,
                    double* x, cudaStream_t st) {
@@ -224,6 +204,34 @@ template <> struct Basis<float> {
 // the basis in V's columns (Sec. 3.4).  Returns the steps completed and
 // fills Hh ((k+1) x k, host, ld k+1).
 template <typename T>
+void step_kernel(const DevCsr& M, T* V, int64_t ld, int j, double* H, int ldh,
+                 double* wn, double* red, int red_cap, unsigned* bar, int* err,
+                 cudaStream_t st);
+template <>
+void step_kernel<double>(const DevCsr& M, double* V, int64_t ld, int j, double* H,
+                         int ldh, double* wn, double* red, int red_cap, unsigned* bar,
+                         int* err, cudaStream_t st) {
+  arnoldi_step(M, V, ld, j, H, ldh, wn, red, red_cap, bar, err, st);
+}
+template <>
+void step_kernel<float>(const DevCsr& M, float* V, int64_t ld, int j, double* H,
+                        int ldh, double* wn, double* red, int red_cap, unsigned* bar,
+                        int* err, cudaStream_t st) {
+  arnoldi_step32(M, V, ld, j, H, ldh, wn, red, red_cap, bar, err, st);
+}
+
+// Barrier words (words 0 and 32) and error flag (word 48) of the
+// cooperative pre-pass kernels: a 256-byte device block of the handle.
+unsigned* prepass_barrier(sg_handle* h) {
+  if (!h->sync) {
+    SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&h->sync), 256));
+    SG_CUDA(cudaMemset(h->sync, 0, 256));
+  }
+  return h->sync;
+}
+int* prepass_error(sg_handle* h) { return reinterpret_cast<int*>(prepass_barrier(h) + 48); }
+
+template <typename T>
 void enqueue_prepass(sg_handle* h, const DevCsr& M, const T* q, int k,
                      cudaStream_t st) {
   using B = Basis<T>;
@@ -234,34 +242,18 @@ void enqueue_prepass(sg_handle* h, const DevCsr& M, const T* q, int k,
   double* wn = h->small + sl.wn;
   const int ldh = k + 1;
   SG_CUDA(cudaMemsetAsync(Hd, 0, sizeof(double) * ldh * k, st));
+  SG_CUDA(cudaMemsetAsync(prepass_barrier(h), 0, 256, st));
   SG_CUDA(cudaMemcpyAsync(V, q, sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
-  const int G = reduction_blocks();
-  double* redA = h->red;
-  double* redB = h->red + G;
-  double* redC = h->red + 2 * G;
-  for (int j = 0; j < k; ++j) {
-    T* w = V + static_cast<int64_t>(j + 1) * ld;
-    B::spmv(M, V + static_cast<int64_t>(j) * ld, nullptr, w, 0.0, 0.0, 1.0, st);
-    B::dot(n, w, w, redC, st);
-    finish_sum(redC, wn + j, true, st);
-    B::dot(n, V, w, redA, st);
-    double* pin = redA;
-    double* pout = redB;
-    for (int l = 0; l <= j; ++l) {
-      const T* vnext = (l < j) ? V + static_cast<int64_t>(l + 1) * ld : nullptr;
-      B::mgs(n, w, V + static_cast<int64_t>(l) * ld, vnext, pin,
-             Hd + l + static_cast<int64_t>(j) * ldh, pout, st);
-      std::swap(pin, pout);
-    }
-    B::norml(n, pin, w, w, Hd + (j + 1) + static_cast<int64_t>(j) * ldh, st);
-  }
+  for (int j = 0; j < k; ++j)
+    step_kernel<T>(M, V, ld, j, Hd, ldh, wn, h->red, 3 * reduction_blocks(),
+                   prepass_barrier(h), prepass_error(h), st);
 }
 
 // Ritz pre-pass: k steps of MGS-Arnoldi from q (device, unit norm) with
-// the basis in V's columns (Sec. 3.4).  The ~k^2/2 small kernels are
-// captured once into a CUDA graph on the handle's own stream and replayed
-// (ordered after/before `st` with events); if capture is not possible the
-// kernels are launched directly.  Returns the steps completed and fills
+// the basis in V's columns (Sec. 3.4), one cooperative kernel per step.
+// The k launches are captured once into a CUDA graph on the handle's own
+// stream and replayed (ordered after/before `st` with events); if capture
+// is not possible the kernels are launched directly.  Returns the steps completed and fills
 // Hh ((k+1) x k, host, ld k+1).
 template <typename T>
 int arnoldi_prepass(sg_handle* h, const DevCsr& M, const T* q, int k,
@@ -270,6 +262,7 @@ int arnoldi_prepass(sg_handle* h, const DevCsr& M, const T* q, int k,
   const void* key[6] = {M.rowptr, sizeof(T) == 8 ? static_cast<const void*>(M.val)
                                                  : static_cast<const void*>(M.val32),
                         q, B::V(h), h->small, h->red};
+  prepass_barrier(h);  // allocate the barrier block before any capture
   sg_handle::PrepassGraph* g = nullptr;
   for (auto& c : h->graphs)
     if (c.k == k && c.n == M.n && std::equal(key, key + 6, c.key)) g = &c;
@@ -317,7 +310,13 @@ int arnoldi_prepass(sg_handle* h, const DevCsr& M, const T* q, int k,
                           cudaMemcpyDeviceToHost, st));
   SG_CUDA(cudaMemcpyAsync(h->hbuf + ldh * k, h->small + sl.wn, sizeof(double) * k,
                           cudaMemcpyDeviceToHost, st));
+  SG_CUDA(cudaMemcpyAsync(h->hbuf + ldh * k + k, prepass_error(h), sizeof(int),
+                          cudaMemcpyDeviceToHost, st));
   SG_CUDA(cudaStreamSynchronize(st));
+  int flag = 0;
+  std::memcpy(&flag, h->hbuf + ldh * k + k, sizeof(int));
+  if (flag != 0)
+    throw Error(SG_ECUDA, "Ritz pre-pass: a grid barrier wait ran out");
   std::memcpy(Hh.data(), h->hbuf, sizeof(double) * ldh * k);
   std::memcpy(wnh.data(), h->hbuf + ldh * k, sizeof(double) * k);
   for (int j = 0; j < k; ++j) {
@@ -462,13 +461,13 @@ void solve_impl(sg_handle* h, const DevCsr& M, const SolveOpts& o,
       T* X = Vb + ld;
       // first BCGS: W = Q^T X; X -= Q W; G = X^T X
       B::bdot(n, Qb, ld, i, X, ld, s_eff, Wd, i, false, h->part, h->part_cap, st);
-      B::bupd(n, Qb, ld, i, Wd, i, X, ld, s_eff, -1.0, 1.0, false, st);
+      B::bupd(h, n, Qb, ld, i, Wd, i, X, ld, s_eff, -1.0, 1.0, false, st);
       B::bdot(n, X, ld, s_eff, X, ld, s_eff, Gd, s_eff, true, h->part, h->part_cap, st);
       fetch(Wd, static_cast<int64_t>(i) * s_eff, hb);
       fetch(Gd, static_cast<int64_t>(s_eff) * s_eff, hb + static_cast<int64_t>(i) * s_eff);
       SG_CUDA(cudaEventRecord(h->ev[2], st));
       SG_CUDA(cudaStreamSynchronize(st));
-      if (sizeof(T) == 4) tc_check_error(st);
+      if (sizeof(T) == 4) { tc_check_error(st); tc_update_check_error(st); }
       {
         float a = 0, b = 0;
         cudaEventElapsedTime(&a, h->ev[0], h->ev[1]);
@@ -506,15 +505,19 @@ void solve_impl(sg_handle* h, const DevCsr& M, const SolveOpts& o,
         SG_CUDA(cudaMemcpyAsync(Zd, hb + sl.Z, sizeof(double) * p1 * p1, cudaMemcpyHostToDevice, st));
         SG_CUDA(cudaEventRecord(h->ev[1], st));
         // Q_k = X(:, 1:p) Z^-1, then second BCGS and the second Gram
-        B::bupd(n, X, ld, p1, Zd, p1, Yb, ld, p1, 1.0, 0.0, true, st);
+        B::bupd(h, n, X, ld, p1, Zd, p1, Yb, ld, p1, 1.0, 0.0, true, st);
         B::bdot(n, Qb, ld, i, Yb, ld, p1, Wd, i, false, h->part, h->part_cap, st);
-        B::bupd(n, Qb, ld, i, Wd, i, Yb, ld, p1, -1.0, 1.0, false, st);
-        B::bdot(n, Yb, ld, p1, Yb, ld, p1, Gd, p1, true, h->part, h->part_cap, st);
+        B::bupd(h, n, Qb, ld, i, Wd, i, Yb, ld, p1, -1.0, 1.0, false, st);
+        // Gram of the block the first pass already orthonormalised: FP64
+        // uses the symmetric kernel; the FP32 basis needs only FP32-level
+        // accuracy here (its condition number is ~1), so it goes to the
+        // tensor-core kernel like the projections
+        B::bdot(n, Yb, ld, p1, Yb, ld, p1, Gd, p1, sizeof(T) == 8, h->part, h->part_cap, st);
         fetch(Wd, static_cast<int64_t>(i) * p1, hb);
         fetch(Gd, static_cast<int64_t>(p1) * p1, hb + static_cast<int64_t>(i) * p1);
         SG_CUDA(cudaEventRecord(h->ev[2], st));
         SG_CUDA(cudaStreamSynchronize(st));
-        if (sizeof(T) == 4) tc_check_error(st);
+        if (sizeof(T) == 4) { tc_check_error(st); tc_update_check_error(st); }
         {
           float b = 0;
           cudaEventElapsedTime(&b, h->ev[1], h->ev[2]);
@@ -559,7 +562,7 @@ void solve_impl(sg_handle* h, const DevCsr& M, const SolveOpts& o,
           log.t_host += now_ms() - th1;
           SG_CUDA(cudaMemcpyAsync(Zd, hb + sl.Z, sizeof(double) * q * q, cudaMemcpyHostToDevice, st));
           // Q_k = Q_k(:, 1:q) Z~^-1 into Q's next columns
-          B::bupd(n, Yb, ld, q, Zd, q, Qb + static_cast<int64_t>(i) * ld, ld, q,
+          B::bupd(h, n, Yb, ld, q, Zd, q, Qb + static_cast<int64_t>(i) * ld, ld, q,
                   1.0, 0.0, true, st);
         }
       }

@@ -27,6 +27,7 @@ struct sg_handle {
   int64_t part_cap = 0;
   double* red = nullptr;    // 3 x reduction_blocks partial sums
   double* small = nullptr;  // device small matrices
+  unsigned* sync = nullptr;  // 256 B: grid-barrier words + error flag
   int64_t small_cap = 0;
   double* hbuf = nullptr;   // pinned host mirror of `small`
   // FP32 basis workspace (precision FP32_IR)

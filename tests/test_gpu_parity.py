@@ -239,6 +239,45 @@ def test_block_update_f32_matches_definition(solver, n, i, s, upper):
     assert np.all(np.abs(host(Xd) - ref) <= 64 * 2.0 ** -24 * scale)
 
 
+@pytest.mark.parametrize("n", [128, 4133, 70001, 1 << 20])
+@pytest.mark.parametrize("i,s,upper", [(1, 1, False), (7, 16, False), (33, 120, False),
+                                       (107, 106, False), (128, 128, False),
+                                       (241, 17, False), (33, 33, True), (120, 120, True)])
+def test_block_update_f32_tensor_cores(solver, n, i, s, upper):
+    """Aligned leading dimensions take the TMA + tcgen05 update (Q tile as an
+    MN-major operand, TF32 hi/lo split); an unaligned copy of the same data
+    takes the FFMA path.  Both within a few FP32 roundings of the FP64
+    result."""
+    rng = np.random.default_rng(900 + i + s + n % 97)
+    ld = (n + 3) // 4 * 4
+    Q = np.zeros((i, ld), np.float32)
+    Q[:, :n] = rng.standard_normal((i, n))
+    Wm = rng.standard_normal((i, s))
+    if upper:
+        Wm = np.triu(Wm) + np.tril(np.full((i, s), np.nan), -1)
+    X = np.zeros((s, ld), np.float32)
+    X[:, :n] = rng.standard_normal((s, n))
+    beta = 0.0 if upper else 1.3
+    Wz = np.nan_to_num(Wm, nan=0.0)
+    Q64, X64 = Q[:, :n].astype(np.float64), X[:, :n].astype(np.float64)
+    ref = beta * X64 - 0.7 * (Q64.T @ Wz).T
+    scale = np.abs(X64) * abs(beta) + 0.7 * (np.abs(Q64).T @ np.abs(Wz)).T
+    Wt = dev(np.ascontiguousarray(Wm.T))
+    Xd = dev(X, torch.float32)
+    solver.block_update32(dev(Q, torch.float32), Wt, Xd, alpha=-0.7, beta=beta,
+                          upper=upper, n=n)
+    Xu = np.zeros((s, n + 1), np.float32)
+    Xu[:, :n] = X[:, :n]
+    Qu = np.zeros((i, n + 1), np.float32)
+    Qu[:, :n] = Q[:, :n]
+    Xud = dev(Xu, torch.float32)
+    solver.block_update32(dev(Qu, torch.float32), Wt, Xud, alpha=-0.7, beta=beta,
+                          upper=upper, n=n)
+    for got in (host(Xd)[:, :n], host(Xud)[:, :n]):
+        err = np.abs(got - ref)
+        assert np.all(err <= 2.0 ** -18 * scale + 1e-30), (err / (scale + 1e-30)).max()
+
+
 def test_nrm2(solver):
     x = np.random.default_rng(5).standard_normal(123457)
     assert solver.nrm2(dev(x)) == pytest.approx(np.linalg.norm(x), rel=1e-14)
