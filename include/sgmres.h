@@ -142,6 +142,15 @@ sg_status sg_analyze(sg_handle* h, const sg_csr* A);
 sg_status sg_update_values(sg_handle* h, const double* val,
                            int32_t on_device);
 
+/* Storage the SpMV kernels use for the analysed matrix: *sell = 1 when
+ * the SELL-32 copy (slices of 32 rows, column-major within a slice) was
+ * built at ingest, 0 when the CSR arrays are walked directly (the padding
+ * to each slice's longest row would exceed 20% of nnz); *stored = the
+ * entries the SpMV reads per product (padded count for SELL-32, nnz for
+ * CSR).  Either pointer may be NULL.  Not in the paper: a layout report.
+ * Errors: SG_EINVAL (NULL handle), SG_ESTATE (no matrix). */
+sg_status sg_matrix_info(const sg_handle* h, int32_t* sell, int64_t* stored);
+
 /* ------------------------------------------------------------- solvers */
 /* Adaptive s-step GMRES(m) (Alg. 4 with restarts): solves A x = b.
  * x holds x0 on entry and the solution on exit.  res may be NULL.

@@ -35,7 +35,7 @@ EXPORTED = (
     "sg_host_hessenberg_eigvals", "sg_host_leja_order",
     "sg_host_scaling_coefficients", "sg_host_estimate_step",
     "sg_kernel_launches", "sg_block_dot_noalloc", "sg_block_dot_f32",
-    "sg_block_update_f32", "sg_update_values",
+    "sg_block_update_f32", "sg_update_values", "sg_matrix_info",
 )
 
 
@@ -96,6 +96,7 @@ def _load():
         "sg_last_error": (C.c_char_p, [vp]),
         "sg_analyze": (i32, [vp, C.POINTER(sg_csr)]),
         "sg_update_values": (i32, [vp, vp, i32]),
+        "sg_matrix_info": (i32, [vp, C.POINTER(i32), C.POINTER(i64)]),
         "sg_solve": (i32, [vp, vp, vp, C.POINTER(sg_opts), C.POINTER(sg_result)]),
         "sg_solve_adjoint": (i32, [vp, vp, vp, C.POINTER(sg_opts), C.POINTER(sg_result)]),
         "sg_grad_values": (i32, [vp, vp, vp, vp, vp]),
@@ -286,6 +287,13 @@ class Solver:
         self._check(lib.sg_analyze(self._h, C.byref(A)))
         self.n, self.nnz = nn, nnz
         return self
+
+    def matrix_info(self):
+        """(sell, stored): whether the SpMV uses the SELL-32 copy, and the
+        entries it reads per product."""
+        sell, stored = C.c_int32(0), C.c_int64(0)
+        self._check(lib.sg_matrix_info(self._h, C.byref(sell), C.byref(stored)))
+        return bool(sell.value), int(stored.value)
 
     def update_values(self, val):
         """New values for the analysed pattern (numpy or a CUDA tensor)."""

@@ -2,15 +2,26 @@
 // (Sec. 2, Eq. newtonrecurrence), the residual, the sampled outer product
 // of the adjoint gradient and the CSR transpose.
 //
-// SpMV layout: one thread per row.  A CTA owns a contiguous block of rows
-// and first stages that block's values and column indices in shared
-// memory with coalesced streaming loads (they do not fit in L2 and are
-// not reused within one product), then each thread walks its own row from
-// shared memory and gathers x through the read-only path (stencil
-// locality gives cache hits).  One thread per row matters on this chip:
-// FP64 warp instructions are expensive (the FP64 pipe is ~1/64 of the FP32
-// rate), so the per-row reduction must not spend shuffles and adds on idle
-// lanes; the epilogue multiplies by 1/gamma instead of dividing.
+// SpMV layout: one thread per row.  One thread per row matters on this
+// chip: FP64 warp instructions are expensive (the FP64 pipe is ~1/64 of the
+// FP32 rate), so the per-row reduction must not spend shuffles and adds on
+// idle lanes; the epilogue multiplies by 1/gamma instead of dividing.
+//
+// Preferred storage is SELL-32, built at ingest: rows are cut into slices
+// of 32 (one warp), and slice q stores entry j of its row l at
+// sptr[q] + 32 j + l, padded to the slice's longest row with column -1.
+// Lane l of a warp then walks row 32q + l while the warp reads each entry
+// index j as one coalesced 256-byte (values) and 128-byte (indices) line,
+// with no staging and no barriers; x is gathered through the read-only
+// path (stencil locality gives cache hits).  Up to eight entries per row
+// are loaded before the FMAs, so their gathers are in flight together.
+//
+// When the padding would be large, CSR is used as is: a CTA owns a
+// contiguous block of rows and first stages that block's values and
+// column indices in shared memory with coalesced streaming loads, then
+// each thread walks its own row from shared memory.
+#include <vector>
+
 #include "k_reduce.cuh"
 #include "sg_internal.h"
 
@@ -69,6 +80,57 @@ spmv_kernel(int n, int rows_per_cta, const int* __restrict__ rowptr,
   }
 }
 
+// Sum over the SELL-32 row `row` (entries in column order, padding
+// skipped), the same FMA sequence as the CSR walk of that row.
+template <typename T>
+__device__ __forceinline__ T sell_row(const int* __restrict__ sptr,
+                                      const int* __restrict__ scol,
+                                      const T* __restrict__ sval,
+                                      const T* __restrict__ x, int64_t row) {
+  const int64_t q = row >> 5;
+  const int a = sptr[q], e = sptr[q + 1];
+  const int w = (e - a) >> 5;  // slice width: the same for every lane
+  const int k0 = a + static_cast<int>(row & 31);
+  T sum = T(0);
+  for (int j0 = 0; j0 < w; j0 += 8) {
+    int c[8];
+    T v[8], xv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const bool in = j0 + u < w;
+      c[u] = in ? ld_stream(scol + k0 + 32 * (j0 + u)) : -1;
+      v[u] = in ? ld_stream(sval + k0 + 32 * (j0 + u)) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) xv[u] = c[u] >= 0 ? __ldg(x + c[u]) : T(0);
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (c[u] >= 0) sum = fma(v[u], xv[u], sum);
+  }
+  return sum;
+}
+
+template <int MODE, bool HAS_Z, typename T>
+__global__ void __launch_bounds__(kThreads)
+sell_kernel(int n, int64_t rows32, const int* __restrict__ sptr,
+            const int* __restrict__ scol, const T* __restrict__ sval,
+            const T* __restrict__ x, const T* __restrict__ z,
+            T* __restrict__ y, T theta, T c, T inv_gamma) {
+  for (int64_t row = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; row < rows32;
+       row += static_cast<int64_t>(gridDim.x) * kThreads) {
+    const T sum = sell_row(sptr, scol, sval, x, row);
+    if (row < n) {
+      if (MODE == 1) {
+        y[row] = z[row] - sum;
+      } else {
+        T v = fma(-theta, x[row], sum);
+        if (HAS_Z) v = fma(c, z[row], v);
+        y[row] = v * inv_gamma;
+      }
+    }
+  }
+}
+
 int rows_per_cta(const DevCsr& A) {
   // as many rows as keep the CTA's nonzeros within the staging buffer,
   // with 25% slack for row-length variation; at most one row per thread
@@ -87,8 +149,18 @@ int grid_for(const DevCsr& A, int rpc) {
 }
 
 template <int MODE, bool HAS_Z, typename T>
-void dispatch(const DevCsr& A, const T* val, const T* x, const T* z, T* y,
+void dispatch(const DevCsr& A, const T* val, const T* sval, const T* x, const T* z, T* y,
               T theta, T c, T gamma, cudaStream_t st) {
+  if (A.sptr && sval) {
+    const int64_t rows32 = static_cast<int64_t>(A.nslices) * 32;
+    int64_t blocks = (rows32 + kThreads - 1) / kThreads;
+    const int64_t cap = static_cast<int64_t>(device_sm_count()) * 64;
+    if (blocks > cap) blocks = cap;
+    sell_kernel<MODE, HAS_Z, T><<<static_cast<int>(blocks < 1 ? 1 : blocks), kThreads, 0, st>>>(
+        A.n, rows32, A.sptr, A.scol, sval, x, z, y, theta, c, T(1) / gamma);
+    SG_LAUNCH_CHECK();
+    return;
+  }
   const int rpc = rows_per_cta(A);
   spmv_kernel<MODE, HAS_Z, T><<<grid_for(A, rpc), kThreads, 0, st>>>(
       A.n, rpc, A.rowptr, A.colind, val, x, z, y, theta, c, T(1) / gamma);
@@ -146,13 +218,15 @@ __device__ void grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
 constexpr int kCoopThreads = 1024;  // one CTA per SM, 32 warps in flight
 constexpr int kCoopStage = 8192;    // staged nonzeros per CTA tile
 
-template <typename T>
+// SELL: the SpMV phase walks the SELL-32 arrays (rowptr = sptr, colind =
+// scol, val = sval, rows_per_cta unused) instead of staging CSR tiles.
+template <typename T, bool SELL>
 __global__ void __launch_bounds__(kCoopThreads, 1)
 arnoldi_step_kernel(int n, int rows_per_cta, const int* __restrict__ rowptr,
                     const int* __restrict__ colind, const T* __restrict__ val,
                     T* __restrict__ V, int64_t ld, int j, double* __restrict__ H,
                     int ldh, double* __restrict__ wn, double* __restrict__ red,
-                    unsigned* bar, int* err) {
+                    unsigned* bar, int* err, int64_t rows32) {
   extern __shared__ __align__(16) unsigned char coop_smem[];
   T* sval = reinterpret_cast<T*>(coop_smem);
   int* scol = reinterpret_cast<int*>(coop_smem + sizeof(T) * kCoopStage);
@@ -166,6 +240,17 @@ arnoldi_step_kernel(int n, int rows_per_cta, const int* __restrict__ rowptr,
   double* pB = red + 2 * G;
   // phase 0: w = A v_j, partials of w.w and v_0.w
   T accw = T(0), accv = T(0);
+  if (SELL) {
+    for (int64_t row = blockIdx.x * static_cast<int64_t>(kCoopThreads) + t; row < rows32;
+         row += static_cast<int64_t>(G) * kCoopThreads) {
+      const T sum = sell_row(rowptr, colind, val, vj, row);
+      if (row < n) {
+        w[row] = sum;
+        accw = fma(sum, sum, accw);
+        accv = fma(v0[row], sum, accv);
+      }
+    }
+  } else
   for (int64_t r0 = static_cast<int64_t>(blockIdx.x) * rows_per_cta; r0 < n;
        r0 += static_cast<int64_t>(G) * rows_per_cta) {
     const int64_t r1 = (r0 + rows_per_cta < n) ? r0 + rows_per_cta : n;
@@ -250,18 +335,18 @@ arnoldi_step_kernel(int n, int rows_per_cta, const int* __restrict__ rowptr,
     w[i] = static_cast<T>(static_cast<double>(w[i]) * inv);
 }
 
-template <typename T>
+template <typename T, bool SELL>
 void launch_arnoldi_step(const DevCsr& A, const T* val, T* V, int64_t ld, int j,
                          double* H, int ldh, double* wn, double* red, int red_cap,
                          unsigned* bar, int* err, cudaStream_t st) {
-  const int smem = kCoopStage * static_cast<int>(sizeof(T) + sizeof(int));
+  const int smem = SELL ? 0 : kCoopStage * static_cast<int>(sizeof(T) + sizeof(int));
   static int max_blocks[2] = {0, 0};
   int& mb = max_blocks[sizeof(T) == 8 ? 0 : 1];
   if (!mb) {
-    SG_CUDA(cudaFuncSetAttribute(arnoldi_step_kernel<T>,
+    SG_CUDA(cudaFuncSetAttribute(arnoldi_step_kernel<T, SELL>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
-    SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, arnoldi_step_kernel<T>,
+    SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, arnoldi_step_kernel<T, SELL>,
                                                           kCoopThreads, smem));
     mb = per_sm * device_sm_count();
     SG_REQUIRE(mb > 0, SG_ECUDA, "arnoldi step: no resident blocks");
@@ -275,10 +360,13 @@ void launch_arnoldi_step(const DevCsr& A, const T* val, T* V, int64_t ld, int j,
   if (rpc > kCoopThreads) rpc = kCoopThreads;
   if (rpc < 32) rpc = 32;
   int n = A.n;
-  void* args[] = {&n, &rpc, const_cast<int**>(&A.rowptr), const_cast<int**>(&A.colind),
+  int64_t rows32 = static_cast<int64_t>(A.nslices) * 32;
+  const int* rp = SELL ? A.sptr : A.rowptr;
+  const int* ci = SELL ? A.scol : A.colind;
+  void* args[] = {&n, &rpc, const_cast<int**>(&rp), const_cast<int**>(&ci),
                   const_cast<T**>(&val), &V, &ld, &j, &H, const_cast<int*>(&ldh), &wn, &red,
-                  &bar, &err};
-  SG_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(arnoldi_step_kernel<T>),
+                  &bar, &err, &rows32};
+  SG_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(arnoldi_step_kernel<T, SELL>),
                                       dim3(G), dim3(kCoopThreads), args, smem, st));
   count_launch();
 }
@@ -376,22 +464,22 @@ void spmv_newton(const DevCsr& A, const double* x, const double* z,
                  double* y, double theta, double c, double gamma,
                  cudaStream_t st) {
   if (c != 0.0 && z)
-    dispatch<0, true, double>(A, A.val, x, z, y, theta, c, gamma, st);
+    dispatch<0, true, double>(A, A.val, A.sval, x, z, y, theta, c, gamma, st);
   else
-    dispatch<0, false, double>(A, A.val, x, nullptr, y, theta, 0.0, gamma, st);
+    dispatch<0, false, double>(A, A.val, A.sval, x, nullptr, y, theta, 0.0, gamma, st);
 }
 
 void spmv_newton32(const DevCsr& A, const float* x, const float* z, float* y,
                    float theta, float c, float gamma, cudaStream_t st) {
   if (c != 0.0f && z)
-    dispatch<0, true, float>(A, A.val32, x, z, y, theta, c, gamma, st);
+    dispatch<0, true, float>(A, A.val32, A.sval32, x, z, y, theta, c, gamma, st);
   else
-    dispatch<0, false, float>(A, A.val32, x, nullptr, y, theta, 0.0f, gamma, st);
+    dispatch<0, false, float>(A, A.val32, A.sval32, x, nullptr, y, theta, 0.0f, gamma, st);
 }
 
 void residual(const DevCsr& A, const double* b, const double* x, double* r,
               cudaStream_t st) {
-  dispatch<1, false, double>(A, A.val, x, b, r, 0.0, 0.0, 1.0, st);
+  dispatch<1, false, double>(A, A.val, A.sval, x, b, r, 0.0, 0.0, 1.0, st);
 }
 
 void sampled_outer(const DevCsr& A, const double* lam, const double* x,
@@ -421,16 +509,130 @@ void csr_transpose(const DevCsr& A, DevCsr& T, int32_t* counts,
   SG_LAUNCH_CHECK();
 }
 
+namespace {
+
+// slice widths: width[q] = 32 * (longest row of slice q)
+__global__ void sell_width_kernel(int n, int nslices, const int* __restrict__ rowptr,
+                                  int* __restrict__ width) {
+  for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < nslices;
+       q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r0 = q * 32, r1 = (r0 + 32 < n) ? r0 + 32 : n;
+    int w = 0;
+    for (int64_t r = r0; r < r1; ++r) w = max(w, rowptr[r + 1] - rowptr[r]);
+    width[q] = 32 * w;
+  }
+}
+
+// one thread per (padded) row: entry j of row 32q + l -> sptr[q] + 32 j + l
+template <bool COLS>
+__global__ void sell_fill_kernel(int n, int64_t rows32, const int* __restrict__ rowptr,
+                                 const int* __restrict__ colind,
+                                 const double* __restrict__ val,
+                                 const int* __restrict__ sptr, int* __restrict__ scol,
+                                 double* __restrict__ sval) {
+  for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < rows32;
+       r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t q = r >> 5;
+    const int base = sptr[q] + static_cast<int>(r & 31);
+    const int w = (sptr[q + 1] - sptr[q]) >> 5;
+    const int a = r < n ? rowptr[r] : 0;
+    const int len = r < n ? rowptr[r + 1] - a : 0;
+    for (int j = 0; j < w; ++j) {
+      const int k = base + 32 * j;
+      if (j < len) {
+        if (COLS) scol[k] = colind[a + j];
+        sval[k] = val[a + j];
+      } else {
+        if (COLS) scol[k] = -1;
+        sval[k] = 0.0;
+      }
+    }
+  }
+}
+
+void free_sell(DevCsr& A) {
+  if (A.sptr) cudaFree(A.sptr);
+  if (A.scol) cudaFree(A.scol);
+  if (A.sval) cudaFree(A.sval);
+  if (A.sval32) cudaFree(A.sval32);
+  A.sptr = A.scol = nullptr;
+  A.sval = nullptr;
+  A.sval32 = nullptr;
+  A.nslices = 0;
+  A.sell_nnz = 0;
+}
+
+}  // namespace
+
+void build_sell(DevCsr& A, cudaStream_t st) {
+  free_sell(A);
+  if (A.n <= 0 || A.nnz <= 0) return;
+  const int nsl = static_cast<int>((static_cast<int64_t>(A.n) + 31) / 32);
+  int* width = nullptr;
+  SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&width), sizeof(int) * nsl));
+  std::vector<int> hw(nsl);
+  try {
+    sell_width_kernel<<<device_sm_count() * 8, kThreads, 0, st>>>(A.n, nsl, A.rowptr, width);
+    SG_LAUNCH_CHECK();
+    SG_CUDA(cudaMemcpyAsync(hw.data(), width, sizeof(int) * nsl, cudaMemcpyDeviceToHost, st));
+    SG_CUDA(cudaStreamSynchronize(st));
+  } catch (...) {
+    cudaFree(width);
+    throw;
+  }
+  cudaFree(width);
+  std::vector<int> hp(static_cast<size_t>(nsl) + 1);
+  int64_t tot = 0;
+  for (int q = 0; q < nsl; ++q) {
+    hp[q] = static_cast<int>(tot < (int64_t(1) << 31) ? tot : 0);
+    tot += hw[q];
+  }
+  // keep SELL only when the padding is modest and the offsets fit int32
+  if (tot >= (int64_t(1) << 31) - 1 || tot > A.nnz + A.nnz / 5 + 32 * static_cast<int64_t>(nsl))
+    return;
+  hp[nsl] = static_cast<int>(tot);
+  try {
+    SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&A.sptr), sizeof(int) * (nsl + 1)));
+    SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&A.scol), sizeof(int) * tot));
+    SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&A.sval), sizeof(double) * tot));
+    SG_CUDA(cudaMemcpyAsync(A.sptr, hp.data(), sizeof(int) * (nsl + 1), cudaMemcpyHostToDevice, st));
+    A.nslices = nsl;
+    A.sell_nnz = tot;
+    const int64_t rows32 = static_cast<int64_t>(nsl) * 32;
+    sell_fill_kernel<true><<<device_sm_count() * 8, kThreads, 0, st>>>(
+        A.n, rows32, A.rowptr, A.colind, A.val, A.sptr, A.scol, A.sval);
+    SG_LAUNCH_CHECK();
+    SG_CUDA(cudaStreamSynchronize(st));  // the host offsets go out of scope
+  } catch (...) {
+    free_sell(A);
+    throw;
+  }
+}
+
+void sell_refill_values(const DevCsr& A, cudaStream_t st) {
+  if (!A.sptr) return;
+  const int64_t rows32 = static_cast<int64_t>(A.nslices) * 32;
+  sell_fill_kernel<false><<<device_sm_count() * 8, kThreads, 0, st>>>(
+      A.n, rows32, A.rowptr, A.colind, A.val, A.sptr, nullptr, A.sval);
+  SG_LAUNCH_CHECK();
+}
+
 void arnoldi_step(const DevCsr& A, double* V, int64_t ld, int j, double* H,
                   int ldh, double* wn, double* red, int red_cap, unsigned* bar,
                   int* err, cudaStream_t st) {
-  launch_arnoldi_step<double>(A, A.val, V, ld, j, H, ldh, wn, red, red_cap, bar, err, st);
+  if (A.sptr && A.sval)
+    launch_arnoldi_step<double, true>(A, A.sval, V, ld, j, H, ldh, wn, red, red_cap, bar, err, st);
+  else
+    launch_arnoldi_step<double, false>(A, A.val, V, ld, j, H, ldh, wn, red, red_cap, bar, err, st);
 }
 
 void arnoldi_step32(const DevCsr& A, float* V, int64_t ld, int j, double* H,
                     int ldh, double* wn, double* red, int red_cap, unsigned* bar,
                     int* err, cudaStream_t st) {
-  launch_arnoldi_step<float>(A, A.val32, V, ld, j, H, ldh, wn, red, red_cap, bar, err, st);
+  if (A.sptr && A.sval32)
+    launch_arnoldi_step<float, true>(A, A.sval32, V, ld, j, H, ldh, wn, red, red_cap, bar, err, st);
+  else
+    launch_arnoldi_step<float, false>(A, A.val32, V, ld, j, H, ldh, wn, red, red_cap, bar, err, st);
 }
 
 }  // namespace sg

@@ -53,6 +53,10 @@ void free_csr(sg::DevCsr& A) {
   if (A.colind) cudaFree(A.colind);
   if (A.val) cudaFree(A.val);
   if (A.val32) cudaFree(A.val32);
+  if (A.sptr) cudaFree(A.sptr);
+  if (A.scol) cudaFree(A.scol);
+  if (A.sval) cudaFree(A.sval);
+  if (A.sval32) cudaFree(A.sval32);
   A = sg::DevCsr();
 }
 
@@ -62,12 +66,20 @@ __global__ void f64_to_f32_kernel(int64_t n, const double* x, float* y) {
     y[i] = static_cast<float>(x[i]);
 }
 
+// FP32 copies of the values (CSR and, when present, SELL-32)
 void make_val32(sg::DevCsr& A, cudaStream_t st) {
   if (A.val32) cudaFree(A.val32);
   A.val32 = nullptr;
+  if (A.sval32) cudaFree(A.sval32);
+  A.sval32 = nullptr;
   SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&A.val32), sizeof(float) * std::max<int64_t>(A.nnz, 1)));
   f64_to_f32_kernel<<<sg::device_sm_count() * 8, 256, 0, st>>>(A.nnz, A.val, A.val32);
   SG_LAUNCH_CHECK();
+  if (A.sptr) {
+    SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&A.sval32), sizeof(float) * A.sell_nnz));
+    f64_to_f32_kernel<<<sg::device_sm_count() * 8, 256, 0, st>>>(A.sell_nnz, A.sval, A.sval32);
+    SG_LAUNCH_CHECK();
+  }
 }
 
 sg::SolveOpts to_internal(const sg_opts* o) {
@@ -165,6 +177,7 @@ sg_status run_solve(sg_handle* h, bool adjoint, const double* b, double* x,
         }
         cudaFree(counts);
         h->AT.mean_row = h->A.mean_row;
+        sg::build_sell(h->AT, st);
         if (h->A.val32) make_val32(h->AT, st);
         h->have_AT = true;
       }
@@ -301,6 +314,7 @@ sg_status sg_analyze(sg_handle* h, const sg_csr* A) {
     }
     D.mean_row = static_cast<double>(nnz) / static_cast<double>(n);
     D.max_row = maxrow;
+    sg::build_sell(D, st);
     SG_CUDA(cudaStreamSynchronize(st));
     h->have_A = true;
   });
@@ -314,6 +328,7 @@ sg_status sg_update_values(sg_handle* h, const double* val, int32_t on_device) {
     SG_CUDA(cudaSetDevice(h->device));
     cudaStream_t st = h->own;
     if (h->A.nnz) copy_in(h->A.val, val, h->A.nnz, on_device != 0, st);
+    sg::sell_refill_values(h->A, st);
     if (h->A.val32) make_val32(h->A, st);
     if (h->have_AT) {  // values of the transpose are stale: rebuild lazily
       h->drop_graphs();
@@ -322,6 +337,14 @@ sg_status sg_update_values(sg_handle* h, const double* val, int32_t on_device) {
     }
     SG_CUDA(cudaStreamSynchronize(st));
   });
+}
+
+sg_status sg_matrix_info(const sg_handle* h, int32_t* sell, int64_t* stored) {
+  if (!h) return SG_EINVAL;
+  if (!h->have_A) return SG_ESTATE;
+  if (sell) *sell = h->A.sptr ? 1 : 0;
+  if (stored) *stored = h->A.sptr ? h->A.sell_nnz : h->A.nnz;
+  return SG_OK;
 }
 
 sg_status sg_solve(sg_handle* h, const double* b, double* x,

@@ -47,7 +47,22 @@ struct DevCsr {
   float* val32 = nullptr;
   double mean_row = 0;  // row-length statistics recorded at ingest
   int32_t max_row = 0;
+  // SELL-32 copy (sliced ELLPACK, slices of 32 rows stored column-major,
+  // padding marked by column -1), built at ingest when the padding is
+  // small; null otherwise, and the SpMV then reads the CSR arrays.
+  int32_t nslices = 0;
+  int64_t sell_nnz = 0;
+  int32_t* sptr = nullptr;  // nslices + 1 entry offsets
+  int32_t* scol = nullptr;
+  double* sval = nullptr;
+  float* sval32 = nullptr;
 };
+
+// Build A's SELL-32 copy from its CSR arrays (kept when the padded size is
+// at most 1.2 nnz + 32 per slice and fits int32 offsets); frees any old one.
+void build_sell(DevCsr& A, cudaStream_t st);
+// Copy A.val into the SELL value array after a value update.
+void sell_refill_values(const DevCsr& A, cudaStream_t st);
 
 // ---------------------------------------------------------------- SpMV
 // y = (A x - theta x + c z) / gamma      (z may be null when c == 0)

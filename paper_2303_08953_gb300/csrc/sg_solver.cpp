@@ -259,9 +259,10 @@ template <typename T>
 int arnoldi_prepass(sg_handle* h, const DevCsr& M, const T* q, int k,
                     cudaStream_t st, std::vector<double>& Hh) {
   using B = Basis<T>;
-  const void* key[6] = {M.rowptr, sizeof(T) == 8 ? static_cast<const void*>(M.val)
-                                                 : static_cast<const void*>(M.val32),
-                        q, B::V(h), h->small, h->red};
+  const void* vals = sizeof(T) == 8 ? static_cast<const void*>(M.sptr ? M.sval : M.val)
+                                     : static_cast<const void*>(M.sptr ? M.sval32 : M.val32);
+  const void* key[6] = {M.sptr ? static_cast<const void*>(M.sptr) : M.rowptr, vals, q,
+                        B::V(h), h->small, h->red};
   prepass_barrier(h);  // allocate the barrier block before any capture
   sg_handle::PrepassGraph* g = nullptr;
   for (auto& c : h->graphs)

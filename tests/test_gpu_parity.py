@@ -90,6 +90,47 @@ def test_mpk_matches_oracle_with_pair(solver):
     assert np.allclose(V_g, V_o, rtol=1e-12, atol=1e-13 * np.abs(V_o).max())
 
 
+def _skewed_csr(n=3001, seed=7):
+    """Sparse rows plus one row of 900 entries: padding every slice of 32
+    rows to its longest row would more than double the stored entries."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(seed)
+    M = sp.random(n, n, density=3.0 / n, random_state=seed, format="lil")
+    M.setdiag(4.0)
+    M[5, np.sort(rng.choice(n, 900, replace=False))] = rng.standard_normal(900)
+    M = M.tocsr()
+    M.sort_indices()
+    return W.CSR(n, M.indptr.astype(np.int32), M.indices.astype(np.int32),
+                 M.data.astype(np.float64))
+
+
+@pytest.mark.parametrize("kind", ["stencil", "skewed"])
+def test_spmv_storage_choice_and_value_update(solver, kind):
+    """SELL-32 for a stencil, CSR for a skewed pattern; both match the
+    oracle, before and after a value update on the same pattern."""
+    A = W.stencil3d_convdiff(11) if kind == "stencil" else _skewed_csr()
+    op = _analyze(solver, A)
+    sell, stored = solver.matrix_info()
+    assert sell == (kind == "stencil")
+    if sell:
+        assert A.nnz <= stored <= 1.2 * A.nnz + 32 * ((A.n + 31) // 32)
+    else:
+        assert stored == A.nnz
+    rng = np.random.default_rng(5)
+    x = rng.uniform(-1, 1, A.n)
+    for _ in range(2):
+        y = host(solver.spmv_newton(dev(x), 0.7, 1.9))
+        ref = (O.spmv(op, x) - 0.7 * x) / 1.9
+        scale = (np.abs(op) @ np.abs(x) + 0.7 * np.abs(x)) / 1.9
+        assert np.all(np.abs(y - ref) <= 1e-14 * scale + 1e-300)
+        r = host(solver.residual(dev(x), dev(x)))
+        assert np.all(np.abs(r - (x - O.spmv(op, x))) <= 1e-14 * (np.abs(op) @ np.abs(x) + 1))
+        new = rng.standard_normal(A.nnz)
+        solver.update_values(new)
+        A = W.CSR(A.n, A.rowptr, A.colind, new)
+        op = O.as_operator(A)
+
+
 def test_spmv_empty_rows(solver):
     # rows with no entries produce zero (times 1/gamma) plus the shift part
     rowptr = np.array([0, 1, 1, 3, 3], np.int32)
