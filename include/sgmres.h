@@ -110,6 +110,11 @@ typedef struct {
   int32_t n_ritz;
   /* time spent per phase (ms, host wall clock around stream syncs)       */
   double t_prepass_ms, t_mpk_ms, t_ortho_ms, t_host_ms, t_total_ms;
+  /* FP32_IR: Krylov columns run with the FP64 basis after the refinement
+   * stalled (two refinement steps that did not halve the true residual,
+   * the sign that kappa(A) eps_32 is near 1); 0 when it never did.
+   * Included in iters; not in the paper. */
+  int32_t fp64_iters;
 } sg_result;
 
 /* ----------------------------------------------------------- lifecycle */

@@ -79,7 +79,7 @@ class sg_result(C.Structure):
                 ("gamma", _D), ("n_ritz", C.c_int32),
                 ("t_prepass_ms", C.c_double), ("t_mpk_ms", C.c_double),
                 ("t_ortho_ms", C.c_double), ("t_host_ms", C.c_double),
-                ("t_total_ms", C.c_double)]
+                ("t_total_ms", C.c_double), ("fp64_iters", C.c_int32)]
 
 
 def _load():
@@ -211,6 +211,7 @@ class SolveInfo:
     ritz: np.ndarray
     gamma: np.ndarray
     times_ms: dict = field(default_factory=dict)
+    fp64_iters: int = 0
 
 
 def _torch():
@@ -376,7 +377,8 @@ class Solver:
             ritz=rre[:nr] + 1j * rim[:nr], gamma=gam[:nr].copy(),
             times_ms=dict(prepass=res.t_prepass_ms, mpk=res.t_mpk_ms,
                           ortho=res.t_ortho_ms, host=res.t_host_ms,
-                          total=res.t_total_ms))
+                          total=res.t_total_ms),
+            fp64_iters=res.fp64_iters)
         return x, info
 
     def solve(self, b, x0=None, stream=None, hist_cap=1 << 16, **kw):

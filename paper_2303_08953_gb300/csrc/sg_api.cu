@@ -146,6 +146,7 @@ void fill_result(const sg::SolveLog& L, sg_result* r) {
   r->t_ortho_ms = L.t_ortho;
   r->t_host_ms = L.t_host;
   r->t_total_ms = L.t_total;
+  r->fp64_iters = L.fp64_iters;
 }
 
 sg_status run_solve(sg_handle* h, bool adjoint, const double* b, double* x,

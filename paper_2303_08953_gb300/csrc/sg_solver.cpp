@@ -364,9 +364,13 @@ Shifts make_shifts(const std::vector<double>& Hh, int ldh, int steps,
 // cycle restarts from an FP64 residual: one iterative-refinement step per
 // cycle.  cycle_tol > 0 ends a cycle once the implicit residual has
 // dropped by that factor relative to the cycle's own start.
+// cycle_tol > 0: a cycle also ends once its implicit residual has dropped
+// by that factor (the inner solve of a refinement step).  stall > 0: the
+// solve stops (log.stalled) when a cycle's true residual is above `stall`
+// times the one two cycles earlier.
 template <typename T>
 void solve_impl(sg_handle* h, const DevCsr& M, const SolveOpts& o,
-                double cycle_tol, cudaStream_t st, SolveLog& log) {
+                double cycle_tol, double stall, cudaStream_t st, SolveLog& log) {
   using B = Basis<T>;
   const double t0 = now_ms();
   const int64_t n = M.n;
@@ -615,6 +619,11 @@ void solve_impl(sg_handle* h, const DevCsr& M, const SolveOpts& o,
     }
     if (total >= max_iters) break;
     if (beta == 0.0) { log.converged = true; break; }
+    const size_t nc = log.cycle_relres.size();
+    if (stall > 0.0 && nc >= 3 && rel_true > stall * log.cycle_relres[nc - 3]) {
+      log.stalled = true;
+      break;
+    }
   }
   log.iters = total;
   log.restarts = static_cast<int>(log.cycle_relres.size()) - 1;
@@ -628,7 +637,7 @@ void solve_fp64(sg_handle* h, const DevCsr& M, const SolveOpts& o,
                 cudaStream_t st, SolveLog& log) {
   const int kritz = std::min(o.s > 0 ? o.s : o.s_max, o.m);
   ensure_workspace(h, M.n, o.m, std::max(kritz, 1));
-  solve_impl<double>(h, M, o, 0.0, st, log);
+  solve_impl<double>(h, M, o, 0.0, 0.0, st, log);
 }
 
 void solve_fp32_ir(sg_handle* h, const DevCsr& M, const SolveOpts& o,
@@ -650,8 +659,40 @@ void solve_fp32_ir(sg_handle* h, const DevCsr& M, const SolveOpts& o,
   o32.omega = std::min(o.omega, omega32);
   o32.omega_est = std::min(o.omega_est, omega32);
   o32.max_iters = o.max_iters > 0 ? o.max_iters : max_refine * o.m;
-  solve_impl<float>(h, M, o32, inner_tol, st, log);
+  // Refinement with an FP32 inner solve contracts only while
+  // kappa(A) eps_32 < 1; when two refinement steps together fail to halve
+  // the true residual, the remaining iterations run with the FP64 basis
+  // from the current x (same method, fresh Ritz values), so the solve
+  // still reaches tol whenever the FP64 solve does.
+  solve_impl<float>(h, M, o32, inner_tol, 0.5, st, log);
   log.refinements = static_cast<int>(log.cycle_relres.size());
+  const int left = o32.max_iters - log.iters;
+  if (log.converged || !log.stalled || left <= 0) return;
+  const double scale = log.final_relres;  // residual now / initial residual
+  if (!(scale > 0.0)) return;
+  const int kritz64 = std::min(o.s > 0 ? o.s : o.s_max, o.m);
+  ensure_workspace(h, M.n, o.m, std::max(kritz64, 1));
+  SolveOpts o64 = o;
+  o64.tol = o.tol / scale;
+  o64.max_iters = left;
+  SolveLog l64;
+  solve_impl<double>(h, M, o64, 0.0, 0.0, st, l64);
+  for (double r : l64.relres_hist) log.relres_hist.push_back(r * scale);
+  for (double r : l64.cycle_relres) log.cycle_relres.push_back(r * scale);
+  log.cycle_iters.insert(log.cycle_iters.end(), l64.cycle_iters.begin(), l64.cycle_iters.end());
+  log.s_eff_hist.insert(log.s_eff_hist.end(), l64.s_eff_hist.begin(), l64.s_eff_hist.end());
+  log.p1_hist.insert(log.p1_hist.end(), l64.p1_hist.begin(), l64.p1_hist.end());
+  log.s_hist.insert(log.s_hist.end(), l64.s_hist.begin(), l64.s_hist.end());
+  log.iters += l64.iters;
+  log.fp64_iters = l64.iters;
+  log.restarts = static_cast<int>(log.cycle_relres.size()) - 1;
+  log.converged = l64.converged;
+  log.final_relres = l64.final_relres * scale;
+  log.t_prepass += l64.t_prepass;
+  log.t_mpk += l64.t_mpk;
+  log.t_ortho += l64.t_ortho;
+  log.t_host += l64.t_host;
+  log.t_total += l64.t_total;
 }
 
 }  // namespace sg

@@ -70,6 +70,8 @@ struct SolveLog {
   std::vector<double> relres_hist, cycle_relres, ritz_re, ritz_im, gamma;
   std::vector<int> s_eff_hist, p1_hist, s_hist, cycle_iters;
   double t_prepass = 0, t_mpk = 0, t_ortho = 0, t_host = 0, t_total = 0;
+  bool stalled = false;  // a refinement stall ended the FP32-basis solve
+  int fp64_iters = 0;    // columns run with the FP64 basis after a stall
 };
 
 void ensure_workspace(sg_handle* h, int64_t n, int m, int k);

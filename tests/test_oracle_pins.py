@@ -444,6 +444,31 @@ def test_loss_gradients_match_central_differences():
         assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3)
 
 
+def test_sparse_loss_matches_dense_and_central_differences():
+    """The sparse-LU form of the loss and gradient agrees with the dense
+    one (itself pinned by central differences above), and its perturbed
+    losses give central differences that match its own gradient."""
+    A, rng = W.aniso2d(20)
+    b = rng.uniform(-1, 1, A.n)
+    xt = rng.uniform(-1, 1, A.n)
+    L0, dv, db, x0 = O.loss_gradients(A, b, xt)
+    S = O.SparseLoss(A, b, xt)
+    L1, dv1, db1, x1 = S.gradients()
+    assert abs(L1 - L0) <= 1e-12 * abs(L0)
+    assert np.linalg.norm(dv1 - dv) <= 1e-10 * np.linalg.norm(dv)
+    assert np.linalg.norm(db1 - db) <= 1e-10 * np.linalg.norm(db)
+    h = 1e-6
+    for k in range(4):
+        d = np.random.default_rng(100 + k).standard_normal(A.nnz)
+        e = np.random.default_rng(200 + k).standard_normal(A.n)
+        fd = (S.loss(h * d, h * e) - S.loss(-h * d, -h * e)) / (2 * h)
+        fd_dense = (O.loss_gradients(W.CSR(A.n, A.rowptr, A.colind, A.val + h * d), b + h * e, xt)[0]
+                    - O.loss_gradients(W.CSR(A.n, A.rowptr, A.colind, A.val - h * d), b - h * e, xt)[0]) / (2 * h)
+        an = dv1 @ d + db1 @ e
+        assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3)
+        assert abs(fd - fd_dense) <= 1e-6 * max(abs(an), 1e-3)
+
+
 # ----------------------------------------------- planted-mistake checks
 def _pair_pin_fails():
     try:

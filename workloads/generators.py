@@ -282,10 +282,12 @@ def config_c4(n=1024):
 
 def config_c5(N=4_194_304):
     """Random banded sparse matrix, N rows, 24 off-diagonals within +-4096;
-    x* from the seed-4 stream after the values; m=120, s auto."""
+    x* from the seed-4 stream after the values, then the loss target
+    x_t ~ U(-1,1) of the adjoint run; m=120, s auto."""
     A, rng = random_band(N)
     xs = uniform_vector(A.n, rng)
-    return dict(name=f"c5_randband_{N}", A=A, xstar=xs,
+    xt = uniform_vector(A.n, rng)
+    return dict(name=f"c5_randband_{N}", A=A, xstar=xs, xtarget=xt,
                 b=rhs_from_solution(A, xs), m=120, s=0, s_min=1, s_max=120,
                 tol=1e-10)
 
