@@ -151,6 +151,11 @@ def workload(grid):
                "x0": "zero", "l2": "inputs larger than L2 (A 175 MB, Q 4 GB)"}
 
 
+# DRAM bytes per row of the FP64 block dot (i = 107, s = 106) from one ncu
+# capture at n = 2^20: read 2,307,088,000 + write 5,562,112 bytes.
+DOT64_DRAM_BYTES_PER_ROW = (2_307_088_000 + 5_562_112) / (1 << 20)
+
+
 def spmv_bytes(A):
     return 12 * A.nnz + 4 * (A.n + 1) + 8 * A.n + 8 * A.n
 
@@ -308,7 +313,11 @@ def run_ours(args):
         "kernel": f"block_dot FP64 (W = Q^T X, i={i_blk}, s={s_blk})",
         "bound": "alu", "achieved": round(ach, 4),
         "peak": round(FP64_ALU_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-        "frac": round(ach / FP64_ALU_PEAK_TFLOPS, 4), "traffic": None,
+        "frac": round(ach / FP64_ALU_PEAK_TFLOPS, 4),
+        "traffic": int(round(DOT64_DRAM_BYTES_PER_ROW * n)),
+        "traffic_source": "ncu dram__bytes_read+write of dot_tile_kernel at "
+                          "n = 2^20 (same i, s), scaled by rows to this n "
+                          "(profiles/dot_tile_fp64_n1M_i107_s106.md)",
         "peak_source": "derived: 152 SMs x 2.07 GHz x 4 FP64 flop/clk/SM "
                        "(nominal 1.25 TFLOP/s FP64)"}
     del Q, X
