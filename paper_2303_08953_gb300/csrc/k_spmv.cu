@@ -14,7 +14,8 @@
 // index j as one coalesced 256-byte (values) and 128-byte (indices) line,
 // with no staging and no barriers; x is gathered through the read-only
 // path (stencil locality gives cache hits).  Up to eight entries per row
-// are loaded before the FMAs, so their gathers are in flight together.
+// are loaded before the FMAs, so their gathers are in flight together, and
+// the chunks follow the slice width exactly (no predicated-off FP64 work).
 //
 // When the padding would be large, CSR is used as is: a CTA owns a
 // contiguous block of rows and first stages that block's values and
@@ -80,8 +81,32 @@ spmv_kernel(int n, int rows_per_cta, const int* __restrict__ rowptr,
   }
 }
 
+// U consecutive entries (j .. j+U-1) of a SELL-32 row starting at k: the
+// indices and values are loaded first, then the gathers, then the FMAs, so
+// all of the chunk's loads are in flight together.  Padding (column -1)
+// is skipped per lane.
+template <int U, typename T>
+__device__ __forceinline__ void sell_chunk(const int* __restrict__ scol,
+                                           const T* __restrict__ sval,
+                                           const T* __restrict__ x, int k, T& sum) {
+  int c[U];
+  T v[U], xv[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    c[u] = ld_stream(scol + k + 32 * u);
+    v[u] = ld_stream(sval + k + 32 * u);
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) xv[u] = c[u] >= 0 ? __ldg(x + c[u]) : T(0);
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+    if (c[u] >= 0) sum = fma(v[u], xv[u], sum);
+}
+
 // Sum over the SELL-32 row `row` (entries in column order, padding
-// skipped), the same FMA sequence as the CSR walk of that row.
+// skipped), the same FMA sequence as the CSR walk of that row.  The slice
+// width is the same for the whole warp, so the chunking below is uniform
+// and issues exactly one FMA instruction per stored entry index.
 template <typename T>
 __device__ __forceinline__ T sell_row(const int* __restrict__ sptr,
                                       const int* __restrict__ scol,
@@ -89,23 +114,20 @@ __device__ __forceinline__ T sell_row(const int* __restrict__ sptr,
                                       const T* __restrict__ x, int64_t row) {
   const int64_t q = row >> 5;
   const int a = sptr[q], e = sptr[q + 1];
-  const int w = (e - a) >> 5;  // slice width: the same for every lane
-  const int k0 = a + static_cast<int>(row & 31);
+  const int w = (e - a) >> 5;
+  int k = a + static_cast<int>(row & 31);
   T sum = T(0);
-  for (int j0 = 0; j0 < w; j0 += 8) {
-    int c[8];
-    T v[8], xv[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const bool in = j0 + u < w;
-      c[u] = in ? ld_stream(scol + k0 + 32 * (j0 + u)) : -1;
-      v[u] = in ? ld_stream(sval + k0 + 32 * (j0 + u)) : T(0);
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) xv[u] = c[u] >= 0 ? __ldg(x + c[u]) : T(0);
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-      if (c[u] >= 0) sum = fma(v[u], xv[u], sum);
+  int j = 0;
+  for (; j + 8 <= w; j += 8, k += 256) sell_chunk<8>(scol, sval, x, k, sum);
+  switch (w - j) {
+    case 7: sell_chunk<7>(scol, sval, x, k, sum); break;
+    case 6: sell_chunk<6>(scol, sval, x, k, sum); break;
+    case 5: sell_chunk<5>(scol, sval, x, k, sum); break;
+    case 4: sell_chunk<4>(scol, sval, x, k, sum); break;
+    case 3: sell_chunk<3>(scol, sval, x, k, sum); break;
+    case 2: sell_chunk<2>(scol, sval, x, k, sum); break;
+    case 1: sell_chunk<1>(scol, sval, x, k, sum); break;
+    default: break;
   }
   return sum;
 }

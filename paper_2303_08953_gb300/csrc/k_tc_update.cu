@@ -17,8 +17,12 @@
 //   warp 8 (one lane) issues the TMA loads of a 2-stage ring,
 //   warps 4-7 split each Q tile into hi/lo,
 //   warp 9 (one lane) issues the MMAs into one of two TMEM accumulators,
-//   warps 0-3 (the TMEM lane owners) read an accumulator back and write X
-//   while the next tile accumulates into the other.
+//   warps 0-3 (the TMEM lane owners) read an accumulator back while the
+//   next tile accumulates into the other.  The tile of X goes through
+//   shared memory both ways: a TMA load (beta != 0) issued as soon as the
+//   previous tile's store has read the buffer, the update in place, and a
+//   TMA store, so HBM sees whole 512-byte column segments in flight instead
+//   of the epilogue threads' dependent loads.
 // Every wait is time-bounded; a timeout records an error flag, the roles
 // stop, in-flight copies and MMAs are drained and the TMEM is freed.
 #include <cudaTypedefs.h>
@@ -46,17 +50,19 @@ struct __align__(8) UpdShared {
   uint64_t empty[kStages];
   uint64_t accf[2];
   uint64_t acce[2];
+  uint64_t xfull;
   uint64_t done;
   uint32_t tmem_base;
   int fail;
+  int epi_stop;  // the epilogue warps' common stop decision
 };
 
 __global__ void __launch_bounds__(kThreads, 1)
 tc_update_kernel(const __grid_constant__ CUtensorMap mapQ,
                  const __grid_constant__ CUtensorMap mapWh,
-                 const __grid_constant__ CUtensorMap mapWl, int64_t n, int i, int s,
-                 int BN, float* __restrict__ X, int64_t ldx, float alpha, float beta,
-                 int* __restrict__ err) {
+                 const __grid_constant__ CUtensorMap mapWl,
+                 const __grid_constant__ CUtensorMap mapX, int64_t n, int i, int s,
+                 int BN, float alpha, float beta, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char dsmem[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -84,8 +90,10 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapQ,
       mbar_init(&sh.accf[b], 1);
       mbar_init(&sh.acce[b], 128);
     }
+    mbar_init(&sh.xfull, 1);
     mbar_init(&sh.done, 1);
     sh.fail = 0;
+    sh.epi_stop = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -105,6 +113,8 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapQ,
   auto stAlo = [&](int q) { return base + q * stage_bytes + 2 * a_bytes; };
   auto stB = [&](int q) { return base + q * stage_bytes + 3 * a_bytes; };
   auto stBlo = [&](int q) { return base + q * stage_bytes + 3 * a_bytes + b_bytes; };
+  float* xs = reinterpret_cast<float*>(base + kStages * stage_bytes);  // [BN][128]
+  const uint32_t x_bytes = static_cast<uint32_t>(kRows * BN * 4);
   auto fail_now = [&]() {
     sh.fail = 1;
     atomicExch(err, 1);
@@ -209,16 +219,33 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapQ,
     }
   } else {
     // ------------------------------------------------ epilogue (warps 0-3)
+    auto row0_of = [&](int lt) {
+      return (static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(lt) * gridDim.x) * kRows;
+    };
+    const bool load_x = beta != 0.0f;
+    int x_issued = 0;        // (thread 0) X loads issued
+    bool x_pending = false;  // (thread 0) one of them has not been waited for
+    if (tid == 0 && load_x && my_tiles > 0) {
+      mbar_expect_tx(&sh.xfull, x_bytes);
+      tma_load_2d(xs, &mapX, &sh.xfull, static_cast<int>(row0_of(0)), 0);
+      ++x_issued;
+      x_pending = true;
+    }
+    const int r = warp * 32 + lane;  // this thread's row of the tile
     for (int lt = 0; lt < my_tiles; ++lt) {
-      if (*reinterpret_cast<volatile int*>(&sh.fail)) break;
       const int b = lt & 1;
-      if (!mbar_wait(&sh.accf[b], static_cast<uint32_t>((lt / 2) & 1))) {
-        fail_now();
-        break;
-      }
+      const bool ok = !*reinterpret_cast<volatile int*>(&sh.fail) &&
+                      mbar_wait(&sh.accf[b], static_cast<uint32_t>((lt / 2) & 1)) &&
+                      (!load_x || mbar_wait(&sh.xfull, static_cast<uint32_t>(lt & 1)));
+      if (!ok) fail_now();
+      // one decision for all 128 epilogue threads (they meet at named
+      // barriers below): thread 0 snapshots the flag between two barriers
+      named_sync(1, 128);
+      if (tid == 0) sh.epi_stop = *reinterpret_cast<volatile int*>(&sh.fail);
+      named_sync(1, 128);
+      if (*reinterpret_cast<volatile int*>(&sh.epi_stop)) break;
+      if (tid == 0) x_pending = false;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int64_t row = (static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(lt) * gridDim.x) * kRows +
-                          warp * 32 + lane;
       for (int c0 = 0; c0 < BN; c0 += 16) {
         uint32_t v[16];
         const uint32_t taddr = tmem + (static_cast<uint32_t>(warp * 32) << 16) +
@@ -230,21 +257,36 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapQ,
               "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (row < n) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int col = c0 + j;
-            if (col < s) {
-              float* p = X + row + static_cast<int64_t>(col) * ldx;
-              float y = alpha * __uint_as_float(v[j]);
-              if (beta != 0.0f) y = fmaf(beta, *p, y);
-              *p = y;
-            }
-          }
+        for (int j = 0; j < 16; ++j) {
+          float* p = xs + (c0 + j) * kRows + r;
+          const float y = alpha * __uint_as_float(v[j]);
+          *p = load_x ? fmaf(beta, *p, y) : y;
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(&sh.acce[b]);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      named_sync(1, 128);
+      if (tid == 0) {
+        // rows >= n and columns >= s of the box are not written
+        tma_store_2d(&mapX, xs, static_cast<int>(row0_of(lt)), 0);
+        bulk_commit();
+        bulk_wait_read();
+        if (load_x && lt + 1 < my_tiles) {
+          mbar_expect_tx(&sh.xfull, x_bytes);
+          tma_load_2d(xs, &mapX, &sh.xfull, static_cast<int>(row0_of(lt + 1)), 0);
+          ++x_issued;
+          x_pending = true;
+        }
+      }
+      named_sync(1, 128);  // the buffer is free (beta == 0) or being refilled
+    }
+    if (tid == 0) {
+      // after a failure, let the X load in flight land before the shared
+      // memory is released (the k-th load completes phase k of xfull)
+      if (x_pending) mbar_wait(&sh.xfull, static_cast<uint32_t>((x_issued - 1) & 1));
+      bulk_wait_all();
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -291,7 +333,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 bool make_map(CUtensorMap* map, const float* base, int64_t inner, int64_t outer,
-              int64_t ld, int box_inner, int box_outer) {
+              int64_t ld, int box_inner, int box_outer,
+              CUtensorMapSwizzle swz = CU_TENSOR_MAP_SWIZZLE_128B) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(outer)};
@@ -299,7 +342,7 @@ bool make_map(CUtensorMap* map, const float* base, int64_t inner, int64_t outer,
   cuuint32_t box[2] = {static_cast<cuuint32_t>(box_inner), static_cast<cuuint32_t>(box_outer)};
   cuuint32_t estr[2] = {1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims,
-            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
          CUDA_SUCCESS;
 }
@@ -326,7 +369,7 @@ bool tc_update_supported(int64_t n, const float* Q, int64_t ldq, int i, const fl
   if (n < kRows || i < 1 || s < 1 || s > kMaxN) return false;
   if (reinterpret_cast<uintptr_t>(Q) & 15) return false;
   if ((ldq * 4) & 15) return false;
-  (void)X; (void)ldx;
+  if ((reinterpret_cast<uintptr_t>(X) & 15) || ((ldx * 4) & 15)) return false;
   return encode_fn() != nullptr;
 }
 
@@ -345,21 +388,25 @@ void tc_update(int64_t n, const float* Q, int64_t ldq, int i, const double* W, i
   split_w_kernel<<<64, 256, 0, st>>>(i, s, W, ldw, hi, lo, ldp, upper ? 1 : 0);
   SG_LAUNCH_CHECK();
   const int BN = (s + 15) / 16 * 16;
-  CUtensorMap mq, mh, ml;
+  CUtensorMap mq, mh, ml, mx;
   SG_REQUIRE(make_map(&mq, Q, n, i, ldq, 32, kKC) && make_map(&mh, hi, ldp, s, ldp, kKC, BN) &&
-                 make_map(&ml, lo, ldp, s, ldp, kKC, BN),
+                 make_map(&ml, lo, ldp, s, ldp, kKC, BN) &&
+                 make_map(&mx, X, n, s, ldx, kRows, BN, CU_TENSOR_MAP_SWIZZLE_NONE),
              SG_ECUDA, "cuTensorMapEncodeTiled failed");
-  const int smem = kStages * (3 * kRows * kKC * 4 + 2 * BN * kKC * 4) + 1024;
+  auto smem_for = [](int bn) {
+    return kStages * (3 * kRows * kKC * 4 + 2 * bn * kKC * 4) + kRows * bn * 4 + 1024;
+  };
+  const int smem = smem_for(BN);
   static bool configured = false;
   if (!configured) {
     SG_CUDA(cudaFuncSetAttribute(tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kStages * (3 * kRows * kKC * 4 + 2 * kMaxN * kKC * 4) + 1024));
+                                 smem_for(kMaxN)));
     configured = true;
   }
   const int64_t tiles = (n + kRows - 1) / kRows;
   int grid = device_sm_count();
   if (grid > tiles) grid = static_cast<int>(tiles);
-  tc_update_kernel<<<grid, kThreads, smem, st>>>(mq, mh, ml, n, i, s, BN, X, ldx,
+  tc_update_kernel<<<grid, kThreads, smem, st>>>(mq, mh, ml, mx, n, i, s, BN,
                                                   static_cast<float>(alpha),
                                                   static_cast<float>(beta), err_flag());
   SG_LAUNCH_CHECK();
