@@ -57,6 +57,21 @@ typedef enum {
  * squares and the estimator stay FP64).  Not in the paper. */
 typedef enum { SG_PREC_FP64 = 0, SG_PREC_FP32_IR = 1 } sg_precision;
 
+/* Matrix equilibration A' = D_r A D_c (Eq. equil, Sec. 4.3).
+ * SCALAR: A' = A / alpha, alpha = max |theta| over the pre-pass Ritz
+ *   values; for the monomial and standard Newton bases this is the
+ *   constant scaling coefficient gamma = alpha, and it leaves the scaled
+ *   Newton basis unchanged (its gamma is relative).
+ * COLUMN: D_r = I, D_c = diag(1 / ||A(:, j)||_2): the solver runs on
+ *   A' y = b and returns x = D_c y (forward solves only; D_c is built from
+ *   the transpose, deterministically, on first use).
+ * Residuals and tol refer to the original system in both cases. */
+typedef enum {
+  SG_EQUIL_NONE = 0,
+  SG_EQUIL_SCALAR = 1,
+  SG_EQUIL_COLUMN = 2
+} sg_equil;
+
 typedef struct sg_handle sg_handle;
 
 /* Square CSR matrix, 0-based, columns sorted within each row. */
@@ -85,6 +100,7 @@ typedef struct {
   int32_t max_refine;  /* FP32_IR: cap on refinement steps                 */
   int32_t vectors_on_device; /* 1: b/x/g/lam of sg_solve* are device ptrs */
   void* stream;        /* cudaStream_t or NULL                             */
+  int32_t equilibrate; /* an sg_equil value; default NONE                   */
 } sg_opts;
 
 /* Outputs.  The array members are caller-owned buffers that may be NULL;

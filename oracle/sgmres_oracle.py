@@ -456,11 +456,16 @@ class SolveResult:
 def adaptive_sgmres(A, b, x0=None, m=60, s=10, tol=1e-10, *,
                     basis=BASIS_SCALED_NEWTON, omega=OMEGA,
                     omega_est=OMEGA_EST, eps=EPS64, s_min=1, s_max=None,
-                    max_iters=None, cond="ice", diagnostics=False):
+                    max_iters=None, cond="ice", diagnostics=False,
+                    scalar_equil=False):
     """Adaptive s-step GMRES(m) (Alg. 4) with restarts.
 
     s > 0: fixed initial step size s0 (Ritz pre-pass of s0 steps);
     s == 0: s0* from the estimator (Sec. 3.5) over s_max Ritz values.
+    scalar_equil: scalar equilibration A' = A / alpha, alpha = max |theta|
+    (Eq. equil), in the equivalent form Sec. 4.3 states: the monomial and
+    standard Newton bases take the constant scaling coefficient alpha; the
+    scaled Newton basis is unchanged.
     """
     A = as_operator(A)
     n = b.size
@@ -496,6 +501,8 @@ def adaptive_sgmres(A, b, x0=None, m=60, s=10, tol=1e-10, *,
             ritz = leja_order(ritz_values(Hk, steps))
             gam_sn = scaling_coefficients(ritz)
             theta, gamma = basis_shifts(basis, ritz, gam_sn)
+            if scalar_equil and basis != BASIS_SCALED_NEWTON:
+                gamma = np.full(len(gamma), float(np.max(np.abs(ritz))))
             res.ritz, res.gamma = ritz, gamma
             if s > 0:
                 cur_s = min(s, steps)
@@ -566,6 +573,51 @@ def adaptive_sgmres(A, b, x0=None, m=60, s=10, tol=1e-10, *,
     res.restarts = cycle - 1
     res.final_relres = res.cycle_relres[-1]
     return res
+
+
+# ------------------------------------------------------------ equilibration
+def column_scaling(A):
+    """Column equilibration of Eq. (equil), Sec. 4.3: D_r = I and
+    D_c = diag(1 / ||A(:, j)||_2) (a column with no entries keeps 1).
+    Returns the diagonal of D_c."""
+    op = as_operator(A)
+    norms = np.sqrt(np.asarray(op.multiply(op).sum(axis=0)).ravel())
+    d = np.ones(op.shape[1])
+    nz = norms > 0
+    d[nz] = 1.0 / norms[nz]
+    return d
+
+
+def scalar_scaling(A, b, x0=None, k=10):
+    """Scalar equilibration of Eq. (equil), Sec. 4.3: A' = A / alpha with
+    alpha = max |theta| over the Ritz values of the same k-step pre-pass
+    the solver runs (from the normalised initial residual)."""
+    op = as_operator(A)
+    x = np.zeros(b.size) if x0 is None else np.asarray(x0, dtype=np.float64)
+    r = b - spmv(op, x)
+    Hk, steps = arnoldi_mgs(op, r / np.linalg.norm(r), k)
+    return float(np.max(np.abs(ritz_values(Hk, steps))))
+
+
+def equilibrated_sgmres(A, b, mode, x0=None, **kw):
+    """Alg. 4 on the equilibrated system of Eq. (equil):
+    'scalar': A' = A / alpha in the equivalent form of Sec. 4.3 (constant
+    scaling coefficient alpha for the monomial and Newton bases);
+    'column': A' = A D_c, A' y = b, x = D_c y.
+    Both keep ||b - A x|| / ||b - A x0|| equal to the scaled system's
+    relative residual.  Returns (SolveResult with x in the original
+    unknowns, the scaling: alpha or the diagonal of D_c)."""
+    op = as_operator(A)
+    if mode == "scalar":
+        res = adaptive_sgmres(op, b, x0, scalar_equil=True, **kw)
+        return res, float(np.max(np.abs(res.ritz)))
+    if mode == "column":
+        d = column_scaling(op)
+        y0 = None if x0 is None else np.asarray(x0, dtype=np.float64) / d
+        res = adaptive_sgmres(op @ sp.diags(d), b, y0, **kw)
+        res.x = d * res.x
+        return res, d
+    raise ValueError(mode)
 
 
 def mgs_gmres(A, b, x0=None, m=60, tol=1e-10, max_iters=None):

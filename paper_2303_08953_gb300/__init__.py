@@ -26,6 +26,7 @@ STATUS_NAMES = {0: "SG_OK", 1: "SG_EINVAL", 2: "SG_ENOMEM", 3: "SG_ECUDA",
                 4: "SG_ENOCONV", 5: "SG_ENUMERIC", 6: "SG_ESTATE"}
 BASES = {"scaled_newton": 0, "newton": 1, "monomial": 2}
 PRECISIONS = {"fp64": 0, "fp32_ir": 1}
+EQUILIBRATIONS = {"none": 0, "scalar": 1, "column": 2}
 
 EXPORTED = (
     "sg_default_opts", "sg_create", "sg_destroy", "sg_last_error",
@@ -58,7 +59,7 @@ class sg_opts(C.Structure):
                 ("omega_est", C.c_double), ("basis", C.c_int32),
                 ("precision", C.c_int32), ("inner_tol", C.c_double),
                 ("max_refine", C.c_int32), ("vectors_on_device", C.c_int32),
-                ("stream", C.c_void_p)]
+                ("stream", C.c_void_p), ("equilibrate", C.c_int32)]
 
 
 _D = C.POINTER(C.c_double)
@@ -316,7 +317,8 @@ class Solver:
     @staticmethod
     def make_opts(m=60, s=10, s_min=1, s_max=0, tol=1e-10, max_iters=0,
                   omega=1e7, omega_est=1e7, basis="scaled_newton",
-                  precision="fp64", inner_tol=1e-4, max_refine=20):
+                  precision="fp64", inner_tol=1e-4, max_refine=20,
+                  equilibrate="none"):
         o = sg_opts()
         lib.sg_default_opts(C.byref(o))
         o.m, o.s, o.s_min, o.s_max = m, s, s_min, s_max
@@ -326,6 +328,8 @@ class Solver:
         o.precision = (PRECISIONS[precision] if isinstance(precision, str)
                        else precision)
         o.inner_tol, o.max_refine = inner_tol, max_refine
+        o.equilibrate = (EQUILIBRATIONS[equilibrate] if isinstance(equilibrate, str)
+                         else equilibrate)
         return o
 
     def _solve(self, fn, b, x0, opts, stream, hist_cap):

@@ -188,7 +188,12 @@ struct DotPlan {
 // FP64 (wide = false): 16 x 16 tiles, one output per thread -- the FP64
 // pipe, not shared memory, is the limit, and 16-wide tiles pad i and s
 // less.  FP32: 32 x 32 tiles with 2 x 2 outputs per thread.
-DotPlan plan_dot(int64_t n, int i, int s, bool wide) {
+// The split count S fills one wave of resident CTAs (8 of 256 threads per
+// SM) as evenly as it can: S = floor(slots / working tiles), so every SM
+// runs floor or ceil of the average and the last SM to finish is at most
+// one CTA behind (a rounding-up rule left up to a seventh of the SMs idle
+// for the last CTA's duration).  sym: only the upper tiles work.
+DotPlan plan_dot(int64_t n, int i, int s, bool wide, bool sym) {
   DotPlan p;
   if (i <= 8) { p.cfg = CFG_NARROW_M; p.BM = 8; p.BN = 32; }
   else if (s <= 8) { p.cfg = CFG_NARROW_N; p.BM = 64; p.BN = 8; }
@@ -196,9 +201,11 @@ DotPlan plan_dot(int64_t n, int i, int s, bool wide) {
   else { p.cfg = CFG_SQ; p.BM = 32; p.BN = 32; }
   p.tm = (i + p.BM - 1) / p.BM;
   p.tn = (s + p.BN - 1) / p.BN;
-  const int64_t tiles = static_cast<int64_t>(p.tm) * p.tn;
-  const int64_t target = static_cast<int64_t>(device_sm_count()) * 6;
-  int64_t S = (target + tiles - 1) / tiles;
+  const bool sym_tiles = sym && i == s && (p.cfg == CFG_SQ || p.cfg == CFG_SQ16);
+  const int64_t tiles = sym_tiles ? static_cast<int64_t>(p.tm) * (p.tm + 1) / 2
+                                  : static_cast<int64_t>(p.tm) * p.tn;
+  const int64_t slots = static_cast<int64_t>(device_sm_count()) * (2048 / kThreads);
+  int64_t S = slots / tiles;
   const int64_t maxS = (n + 4 * BK - 1) / (4 * BK);  // >= 4 stages per split
   if (S > maxS) S = maxS;
   if (S < 1) S = 1;
@@ -268,7 +275,7 @@ void block_dot_impl(int64_t n, const T* Q, int64_t ldq, int i, const T* X,
     launch_reduce(i, s, S, part, W, ldw, false, st);
     return;
   }
-  DotPlan p = plan_dot(n, i, s, sizeof(T) == 4);
+  DotPlan p = plan_dot(n, i, s, sizeof(T) == 4, sym);
   const bool exact = sym && sizeof(T) == 4;   // Gram of FP32 vectors
   if (sym && ((p.cfg != CFG_SQ && p.cfg != CFG_SQ16) || i != s)) sym = false;
   SG_REQUIRE(static_cast<int64_t>(p.S) * i * s <= part_cap, SG_EINVAL,
@@ -466,7 +473,7 @@ void block_dot_capped(int64_t n, const double* Q, int64_t ldq, int i,
                               sizeof(double) * i, st));
     return;
   }
-  DotPlan p = plan_dot(n, i, s, false);
+  DotPlan p = plan_dot(n, i, s, false, false);
   const int64_t maxS = part_cap / (static_cast<int64_t>(i) * s);
   if (p.S > maxS) {
     int64_t rows = (n + maxS - 1) / maxS;
@@ -479,8 +486,13 @@ void block_dot_capped(int64_t n, const double* Q, int64_t ldq, int i,
 }
 
 int64_t block_dot_part_size(int64_t n, int i, int s) {
-  const DotPlan a = plan_dot(n, i, s, false), b = plan_dot(n, i, s, true);
-  int64_t need = static_cast<int64_t>(a.S > b.S ? a.S : b.S) * i * s;
+  int64_t S = 1;
+  for (int w = 0; w < 2; ++w)
+    for (int y = 0; y < 2; ++y) {
+      const DotPlan a = plan_dot(n, i, s, w == 1, y == 1);
+      if (a.S > S) S = a.S;
+    }
+  int64_t need = S * i * s;
   const int64_t tc = tc_dot_part_size(n, i, s);
   return need > tc ? need : tc;
 }

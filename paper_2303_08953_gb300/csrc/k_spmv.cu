@@ -639,6 +639,61 @@ void sell_refill_values(const DevCsr& A, cudaStream_t st) {
   SG_LAUNCH_CHECK();
 }
 
+namespace {
+
+__global__ void colnorm_kernel(int n, const int* __restrict__ rowptr,
+                               const double* __restrict__ val, double* __restrict__ d) {
+  for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < n;
+       r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    double ss = 0.0;
+    for (int k = rowptr[r]; k < rowptr[r + 1]; ++k) ss = fma(val[k], val[k], ss);
+    d[r] = ss > 0.0 ? 1.0 / sqrt(ss) : 1.0;
+  }
+}
+
+__global__ void scale_cols_kernel(int64_t cnt, const int* __restrict__ col,
+                                  const double* __restrict__ val,
+                                  const double* __restrict__ d, double* __restrict__ out) {
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < cnt;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int c = col[k];
+    out[k] = c >= 0 ? val[k] * d[c] : 0.0;
+  }
+}
+
+__global__ void diag_kernel(int64_t n, const double* __restrict__ d,
+                            const double* x, double* y, int div) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    y[i] = div ? x[i] / d[i] : x[i] * d[i];
+}
+
+}  // namespace
+
+void column_scale_factors(const DevCsr& AT, double* d, cudaStream_t st) {
+  colnorm_kernel<<<device_sm_count() * 8, kThreads, 0, st>>>(AT.n, AT.rowptr, AT.val, d);
+  SG_LAUNCH_CHECK();
+}
+
+void scale_columns(const DevCsr& A, const double* d, DevCsr& E, cudaStream_t st) {
+  const int g = device_sm_count() * 8;
+  if (A.nnz) {
+    scale_cols_kernel<<<g, kThreads, 0, st>>>(A.nnz, A.colind, A.val, d, E.val);
+    SG_LAUNCH_CHECK();
+  }
+  if (A.sptr && E.sval) {
+    scale_cols_kernel<<<g, kThreads, 0, st>>>(A.sell_nnz, A.scol, A.sval, d, E.sval);
+    SG_LAUNCH_CHECK();
+  }
+}
+
+void diag_apply(int64_t n, const double* d, const double* x, double* y, bool div,
+                cudaStream_t st) {
+  if (n <= 0) return;
+  diag_kernel<<<device_sm_count() * 8, kThreads, 0, st>>>(n, d, x, y, div ? 1 : 0);
+  SG_LAUNCH_CHECK();
+}
+
 void arnoldi_step(const DevCsr& A, double* V, int64_t ld, int j, double* H,
                   int ldh, double* wn, double* red, int red_cap, unsigned* bar,
                   int* err, cudaStream_t st) {

@@ -94,6 +94,7 @@ sg::SolveOpts to_internal(const sg_opts* o) {
   s.omega = o->omega;
   s.omega_est = o->omega_est;
   s.eps = std::ldexp(1.0, -53);
+  s.equil = o->equilibrate;
   return s;
 }
 
@@ -107,6 +108,8 @@ void check_opts(const sg_opts* o) {
   SG_REQUIRE(o->basis >= 0 && o->basis <= 2, SG_EINVAL, "bad basis");
   SG_REQUIRE(o->precision == SG_PREC_FP64 || o->precision == SG_PREC_FP32_IR,
              SG_EINVAL, "bad precision");
+  SG_REQUIRE(o->equilibrate >= SG_EQUIL_NONE && o->equilibrate <= SG_EQUIL_COLUMN,
+             SG_EINVAL, "bad equilibrate");
 }
 
 template <typename T>
@@ -149,6 +152,68 @@ void fill_result(const sg::SolveLog& L, sg_result* r) {
   r->fp64_iters = L.fp64_iters;
 }
 
+// A^T on the device (built on first use; values follow A's)
+void ensure_transpose(sg_handle* h, cudaStream_t st) {
+  if (h->have_AT) return;
+  h->AT.n = h->A.n;
+  h->AT.nnz = h->A.nnz;
+  SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&h->AT.rowptr), sizeof(int32_t) * (h->A.n + 1)));
+  SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&h->AT.colind), sizeof(int32_t) * std::max<int64_t>(h->A.nnz, 1)));
+  SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&h->AT.val), sizeof(double) * std::max<int64_t>(h->A.nnz, 1)));
+  int32_t* counts = nullptr;
+  SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&counts), sizeof(int32_t) * (h->A.n + 1)));
+  try {
+    sg::csr_transpose(h->A, h->AT, counts, st);
+    SG_CUDA(cudaStreamSynchronize(st));
+  } catch (...) {
+    cudaFree(counts);
+    throw;
+  }
+  cudaFree(counts);
+  h->AT.mean_row = h->A.mean_row;
+  sg::build_sell(h->AT, st);
+  if (h->A.val32) make_val32(h->AT, st);
+  h->have_AT = true;
+}
+
+// the column-equilibrated matrix A D_c (its own value arrays only)
+void free_equil(sg_handle* h) {
+  if (!h->have_AE && !h->dcol) return;
+  h->drop_graphs();
+  sg::DevCsr& E = h->AE;
+  if (E.val) cudaFree(E.val);
+  if (E.sval) cudaFree(E.sval);
+  if (E.val32) cudaFree(E.val32);
+  if (E.sval32) cudaFree(E.sval32);
+  if (h->dcol) cudaFree(h->dcol);
+  h->dcol = nullptr;
+  E = sg::DevCsr();
+  h->have_AE = false;
+}
+
+void ensure_equil(sg_handle* h, cudaStream_t st) {
+  if (h->have_AE) return;
+  ensure_transpose(h, st);
+  try {
+    SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&h->dcol), sizeof(double) * h->A.n));
+    sg::column_scale_factors(h->AT, h->dcol, st);
+    sg::DevCsr& E = h->AE;
+    E = h->A;  // pattern arrays are shared with A
+    E.val = E.sval = nullptr;
+    E.val32 = E.sval32 = nullptr;
+    SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&E.val), sizeof(double) * std::max<int64_t>(h->A.nnz, 1)));
+    if (h->A.sptr)
+      SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&E.sval), sizeof(double) * h->A.sell_nnz));
+    sg::scale_columns(h->A, h->dcol, E, st);
+    SG_CUDA(cudaStreamSynchronize(st));
+    h->have_AE = true;
+  } catch (...) {
+    h->have_AE = true;  // let free_equil release what was allocated
+    free_equil(h);
+    throw;
+  }
+}
+
 sg_status run_solve(sg_handle* h, bool adjoint, const double* b, double* x,
                     const sg_opts* opts, sg_result* res) {
   sg_status st_code = SG_OK;
@@ -160,29 +225,15 @@ sg_status run_solve(sg_handle* h, bool adjoint, const double* b, double* x,
     SG_CUDA(cudaSetDevice(h->device));
     cudaStream_t st = pick(h, opts->stream);
     const sg::DevCsr* M = &h->A;
+    const bool colscale = opts->equilibrate == SG_EQUIL_COLUMN;
+    SG_REQUIRE(!(adjoint && colscale), SG_EINVAL,
+               "column equilibration applies to forward solves only");
     if (adjoint) {
-      if (!h->have_AT) {
-        h->AT.n = h->A.n;
-        h->AT.nnz = h->A.nnz;
-        SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&h->AT.rowptr), sizeof(int32_t) * (h->A.n + 1)));
-        SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&h->AT.colind), sizeof(int32_t) * std::max<int64_t>(h->A.nnz, 1)));
-        SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&h->AT.val), sizeof(double) * std::max<int64_t>(h->A.nnz, 1)));
-        int32_t* counts = nullptr;
-        SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&counts), sizeof(int32_t) * (h->A.n + 1)));
-        try {
-          sg::csr_transpose(h->A, h->AT, counts, st);
-          SG_CUDA(cudaStreamSynchronize(st));
-        } catch (...) {
-          cudaFree(counts);
-          throw;
-        }
-        cudaFree(counts);
-        h->AT.mean_row = h->A.mean_row;
-        sg::build_sell(h->AT, st);
-        if (h->A.val32) make_val32(h->AT, st);
-        h->have_AT = true;
-      }
+      ensure_transpose(h, st);
       M = &h->AT;
+    } else if (colscale) {
+      ensure_equil(h, st);
+      M = &h->AE;
     }
     const int64_t n = M->n;
     sg::SolveOpts o = to_internal(opts);
@@ -191,6 +242,7 @@ sg_status run_solve(sg_handle* h, bool adjoint, const double* b, double* x,
     const bool dev = opts->vectors_on_device != 0;
     copy_in(h->bvec, b, n, dev, st);
     copy_in(h->xvec, static_cast<const double*>(x), n, dev, st);
+    if (colscale) sg::diag_apply(n, h->dcol, h->xvec, h->xvec, true, st);  // y0 = D_c^-1 x0
     if (opts->precision == SG_PREC_FP32_IR) {
       if (!M->val32) make_val32(*const_cast<sg::DevCsr*>(M), st);
       sg::solve_fp32_ir(h, *M, o, opts->inner_tol > 0 ? opts->inner_tol : 1e-4,
@@ -198,6 +250,7 @@ sg_status run_solve(sg_handle* h, bool adjoint, const double* b, double* x,
     } else {
       sg::solve_fp64(h, *M, o, st, log);
     }
+    if (colscale) sg::diag_apply(n, h->dcol, h->xvec, h->xvec, false, st);  // x = D_c y
     SG_CUDA(cudaMemcpyAsync(x, h->xvec, sizeof(double) * n,
                             dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
     SG_CUDA(cudaStreamSynchronize(st));
@@ -258,6 +311,7 @@ void sg_destroy(sg_handle* h) {
   cudaSetDevice(h->device);
   if (h->own) cudaStreamSynchronize(h->own);
   h->drop_graphs();
+  free_equil(h);
   free_csr(h->A);
   free_csr(h->AT);
   double* d[] = {h->Q, h->V, h->Y, h->bvec, h->xvec, h->rvec, h->part, h->red, h->small, h->dvec};
@@ -298,6 +352,7 @@ sg_status sg_analyze(sg_handle* h, const sg_csr* A) {
       }
     }
     h->drop_graphs();
+    free_equil(h);
     free_csr(h->A);
     free_csr(h->AT);
     h->have_A = h->have_AT = false;
@@ -328,6 +383,7 @@ sg_status sg_update_values(sg_handle* h, const double* val, int32_t on_device) {
     SG_REQUIRE(val || h->A.nnz == 0, SG_EINVAL, "val is NULL");
     SG_CUDA(cudaSetDevice(h->device));
     cudaStream_t st = h->own;
+    free_equil(h);  // the equilibrated values follow A's
     if (h->A.nnz) copy_in(h->A.val, val, h->A.nnz, on_device != 0, st);
     sg::sell_refill_values(h->A, st);
     if (h->A.val32) make_val32(h->A, st);

@@ -64,6 +64,16 @@ void build_sell(DevCsr& A, cudaStream_t st);
 // Copy A.val into the SELL value array after a value update.
 void sell_refill_values(const DevCsr& A, cudaStream_t st);
 
+// Column equilibration (Eq. equil): d[j] = 1 / ||A(:, j)||_2 from the rows
+// of AT (1 for an empty column), summed in row order (deterministic).
+void column_scale_factors(const DevCsr& AT, double* d, cudaStream_t st);
+// E.val = A.val * d[col] (and the SELL values when A has them; E shares
+// A's pattern arrays, its value arrays are allocated by the caller).
+void scale_columns(const DevCsr& A, const double* d, DevCsr& E, cudaStream_t st);
+// y[i] = x[i] * d[i] (mul) or x[i] / d[i] (div), in place allowed.
+void diag_apply(int64_t n, const double* d, const double* x, double* y, bool div,
+                cudaStream_t st);
+
 // ---------------------------------------------------------------- SpMV
 // y = (A x - theta x + c z) / gamma      (z may be null when c == 0)
 void spmv_newton(const DevCsr& A, const double* x, const double* z,

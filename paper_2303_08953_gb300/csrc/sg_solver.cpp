@@ -333,7 +333,7 @@ struct Shifts {
 };
 
 Shifts make_shifts(const std::vector<double>& Hh, int ldh, int steps,
-                   int basis) {
+                   int basis, int equil) {
   Shifts sh;
   std::vector<double> re(steps), im(steps);
   if (hessenberg_eigvals(Hh.data(), ldh, steps, re.data(), im.data()) != 0)
@@ -353,6 +353,14 @@ Shifts make_shifts(const std::vector<double>& Hh, int ldh, int steps,
     std::fill(gm.begin(), gm.end(), 1.0);
   } else if (basis == SG_BASIS_NEWTON) {
     std::fill(gm.begin(), gm.end(), 1.0);
+  }
+  if (equil == SG_EQUIL_SCALAR && basis != SG_BASIS_SCALED_NEWTON) {
+    // A' = A / alpha (Eq. equil): the basis of A' is the basis of A with
+    // the constant scaling coefficient alpha = max |theta| (Sec. 4.3);
+    // the scaled Newton coefficients are relative and do not change
+    double alpha = 0.0;
+    for (int t = 0; t < steps; ++t) alpha = std::max(alpha, std::hypot(sh.re[t], sh.im[t]));
+    if (alpha > 0.0) std::fill(gm.begin(), gm.end(), alpha);
   }
   basis_steps(steps, th_re.data(), th_im.data(), gm.data(), sh.steps);
   return sh;
@@ -428,7 +436,7 @@ void solve_impl(sg_handle* h, const DevCsr& M, const SolveOpts& o,
       const double tp = now_ms();
       std::vector<double> Hp;
       const int steps = arnoldi_prepass<T>(h, M, Qb, kritz, st, Hp);
-      sh = make_shifts(Hp, kritz + 1, steps, o.basis);
+      sh = make_shifts(Hp, kritz + 1, steps, o.basis, o.equil);
       if (o.s > 0) {
         cur_s = std::min(o.s, steps);
       } else {

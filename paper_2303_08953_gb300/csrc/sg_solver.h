@@ -48,6 +48,11 @@ struct sg_handle {
     cudaGraphExec_t exec = nullptr;
   };
   std::vector<PrepassGraph> graphs;
+  // column equilibration: A' = A D_c shares A's pattern arrays and owns
+  // its scaled values; dcol = diag(D_c)
+  sg::DevCsr AE;
+  bool have_AE = false;
+  double* dcol = nullptr;
   void drop_graphs() {
     for (auto& g : graphs)
       if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -59,6 +64,7 @@ namespace sg {
 
 struct SolveOpts {
   int m, s, s_min, s_max, max_iters, basis;
+  int equil = 0;  // sg_equil: SCALAR acts here (gamma = max |theta|)
   double tol, omega, omega_est, eps;
 };
 

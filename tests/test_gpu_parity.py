@@ -399,6 +399,58 @@ def test_solve_other_bases(solver, basis):
     _compare(ro, x, info, c["A"], c["b"])
 
 
+def _xrel_from_residuals(A, b, x, relres):
+    """Two solutions whose residuals are both <= relres ||b|| differ by at
+    most 2 relres ||A^-1|| ||b||: the x tolerance when the two sides use
+    differently rounded (equilibrated) matrices."""
+    Ad = O.as_operator(A).toarray()
+    inv = 1.0 / np.linalg.svd(Ad, compute_uv=False)[-1]
+    return 2.0 * relres * inv * np.linalg.norm(b) / np.linalg.norm(x)
+
+
+@pytest.mark.parametrize("mode,basis,s,grid", [
+    ("scalar", "monomial", 6, "c1"), ("scalar", "newton", 6, "c1"),
+    ("scalar", "scaled_newton", 10, "c1"),
+    ("column", "scaled_newton", 20, "aniso"), ("column", "monomial", 6, "aniso")])
+def test_equilibrated_solve_matches_oracle(solver, mode, basis, s, grid):
+    """Eq. (equil): scalar scaling (gamma = max|theta| for the monomial and
+    Newton bases, no change for scaled Newton, as Sec. 4.3 states) gives
+    the oracle's decisions and solution; column scaling (A D_c y = b,
+    x = D_c y) too, with D_c rounded independently on each side, so x is
+    held to the residual-implied bound.  (On the 24^2 anisotropic matrix a
+    partial-Cholesky kappa lands within rounding of Omega at s = 20, so the
+    scalar cases use the 24^2 nonsymmetric stencil, as the basis tests do.)"""
+    if grid == "c1":
+        c = W.config_c1(24)
+        A, rng = c["A"], np.random.default_rng(17)
+    else:
+        A, rng = W.aniso2d(24)
+    b = rng.uniform(-1, 1, A.n)
+    x0 = rng.uniform(-0.1, 0.1, A.n)
+    _analyze(solver, A)
+    kw = dict(m=40 if grid == "c1" else 60, s=s, tol=1e-10, basis=basis)
+    ro, _ = O.equilibrated_sgmres(A, b, mode, x0=x0, **kw)
+    x, info = solver.solve(b, x0=x0, equilibrate=mode, **kw)
+    assert info.converged
+    xrel = 1e-9 if mode == "scalar" else max(1e-9, _xrel_from_residuals(A, b, ro.x, 1e-10))
+    _compare(ro, x, info, A, b, x0=x0, xrel=xrel)
+
+
+def test_column_equilibration_rejects_adjoint_and_follows_value_updates(solver):
+    A, rng = W.aniso2d(16)
+    b = rng.uniform(-1, 1, A.n)
+    _analyze(solver, A)
+    with pytest.raises(sg.SgError):
+        solver.solve_adjoint(b, m=40, s=8, tol=1e-10, equilibrate="column")
+    new = W.aniso2d(16, seed=11)[0].val   # same pattern, other conductivities
+    solver.update_values(new)
+    A2 = W.CSR(A.n, A.rowptr, A.colind, new)
+    ro, _ = O.equilibrated_sgmres(A2, b, "column", m=40, s=8, tol=1e-10)
+    x, info = solver.solve(b, m=40, s=8, tol=1e-10, equilibrate="column")
+    assert info.converged and ro.converged
+    _compare(ro, x, info, A2, b, xrel=max(1e-9, _xrel_from_residuals(A2, b, ro.x, 1e-10)))
+
+
 def test_solve_paper_test1_monomial_s6(solver):
     lam = np.linspace(0.1, 10.0, 10000)
     A = W.diagonal(lam)

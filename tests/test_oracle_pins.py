@@ -12,6 +12,7 @@ import math
 import os
 
 import numpy as np
+import scipy.sparse as sp
 import pytest
 
 import workloads as W
@@ -422,6 +423,61 @@ def test_estimator_drives_first_block():
                           s_max=30, diagnostics=True)
     assert 4 <= r.s0 <= 30 and r.converged
     assert max(r.loo) < 1e-12
+
+
+# ------------------------------------------------------ equilibration
+def test_column_scaling_gives_unit_columns():
+    """Eq. (equil) with D_r = I: every non-empty column of A D_c has unit
+    2-norm; an empty column keeps the factor 1."""
+    A, _ = W.random_band(3001, k=6, band=200)
+    op = O.as_operator(A).tolil()
+    op[:, 7] = 0.0                      # an empty column
+    op = op.tocsr()
+    op.eliminate_zeros()
+    d = O.column_scaling(op)
+    norms = np.linalg.norm((op @ sp.diags(d)).toarray(), axis=0)
+    assert d[7] == 1.0 and norms[7] == 0.0
+    keep = np.arange(op.shape[1]) != 7
+    assert np.all(np.abs(norms[keep] - 1.0) <= 4e-16 * 8)
+
+
+def test_scalar_scaling_normalises_the_ritz_values():
+    """Scalar equilibration divides A by alpha = max |theta|: the same
+    pre-pass on A / alpha gives Ritz values of largest modulus 1."""
+    c = W.config_c1(24)
+    alpha = O.scalar_scaling(c["A"], c["b"], k=12)
+    op = O.as_operator(c["A"]) / alpha
+    r = c["b"] / np.linalg.norm(c["b"])
+    H, steps = O.arnoldi_mgs(op, r, 12)
+    assert abs(np.max(np.abs(O.ritz_values(H, steps))) - 1.0) <= 1e-12
+
+
+def test_equilibration_follows_the_papers_observations():
+    """Sec. 4.3 on the explicitly scaled matrix A / alpha: the scaled
+    Newton basis is insensitive to scalar scaling (its gamma is relative),
+    the monomial basis gains a larger adapted step from the normalised
+    spectrum, and the constant-gamma form the paper states as equivalent
+    makes the same step-size decisions.  Every equilibrated solve reaches
+    tol on the original system."""
+    A, rng = W.aniso2d(32)
+    b = rng.uniform(-1, 1, A.n)
+    op = O.as_operator(A)
+    kw = dict(m=60, s=20, tol=1e-10)
+    alpha = O.scalar_scaling(A, b, k=20)
+    assert alpha > 100
+    r0 = O.adaptive_sgmres(A, b, basis="scaled_newton", **kw)
+    r1 = O.adaptive_sgmres(op / alpha, b / alpha, basis="scaled_newton", **kw)
+    assert r0.s_hist == r1.s_hist and r0.iters == r1.iters
+    m0 = O.adaptive_sgmres(A, b, basis="monomial", **kw)
+    m1 = O.adaptive_sgmres(op / alpha, b / alpha, basis="monomial", **kw)
+    assert max(m1.s_hist) > max(m0.s_hist)
+    m2, alpha2 = O.equilibrated_sgmres(A, b, "scalar", basis="monomial", **kw)
+    assert abs(alpha2 - alpha) <= 1e-12 * alpha
+    assert m2.s_hist[:len(m1.s_hist) // 2] == m1.s_hist[:len(m1.s_hist) // 2]
+    c1, d = O.equilibrated_sgmres(A, b, "column", basis="scaled_newton", **kw)
+    for r in (r1, m1, m2, c1):
+        assert r.converged
+        assert np.linalg.norm(b - op @ r.x) <= 1.01e-10 * np.linalg.norm(b)
 
 
 # ------------------------------------------------------ adjoint gradient
