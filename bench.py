@@ -152,8 +152,8 @@ def workload(grid):
 
 
 # DRAM bytes per row of the FP64 block dot (i = 107, s = 106) from one ncu
-# capture at n = 2^20: read 2,307,088,000 + write 5,562,112 bytes.
-DOT64_DRAM_BYTES_PER_ROW = (2_307_088_000 + 5_562_112) / (1 << 20)
+# capture at n = 2^20: read 2,291,351,000 + write 5,751,296 bytes.
+DOT64_DRAM_BYTES_PER_ROW = (2_291_351_000 + 5_751_296) / (1 << 20)
 
 
 def spmv_bytes(A):

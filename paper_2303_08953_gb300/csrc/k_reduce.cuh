@@ -32,6 +32,49 @@ __device__ double block_sum_d(double v) {
   return total;
 }
 
+// Sum over a large block with few FP64 instructions (the FP64 pipe is the
+// scarce one on this chip): every thread parks its value in shared memory,
+// then one warp adds THREADS / 32 values per lane in index order and
+// combines the lanes with shuffles.  Every thread receives the result.
+template <int THREADS>
+__device__ double block_sum_few_d(double v) {
+  __shared__ double park[THREADS];
+  __shared__ double total;
+  park[threadIdx.x] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+#pragma unroll 8
+    for (int i = threadIdx.x; i < THREADS; i += 32) t += park[i];
+    t = warp_sum_d<THREADS>(t);
+    if (threadIdx.x == 0) total = t;
+  }
+  __syncthreads();
+  return total;
+}
+
+// Fixed-order sum of G per-block partials by one warp (few FP64
+// instructions); every thread receives it.
+template <int THREADS>
+__device__ double sum_partials_few_d(const double* __restrict__ p, int G) {
+  __shared__ double total;
+  __syncthreads();  // every thread has read the previous total
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (int i = threadIdx.x; i < G; i += 32) t += p[i];
+    t = warp_sum_d<THREADS>(t);
+    if (threadIdx.x == 0) total = t;
+  }
+  __syncthreads();
+  return total;
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
 // Fixed-order sum of G per-block partials; every thread receives it.
 template <int THREADS>
 __device__ double sum_partials_d(const double* __restrict__ p, int G) {

@@ -301,13 +301,13 @@ arnoldi_step_kernel(int n, int rows_per_cta, const int* __restrict__ rowptr,
     __syncthreads();
   }
   {
-    const double sw = block_sum_d<kCoopThreads>(static_cast<double>(accw));
-    const double sv = block_sum_d<kCoopThreads>(static_cast<double>(accv));
+    const double sw = block_sum_few_d<kCoopThreads>(static_cast<double>(accw));
+    const double sv = block_sum_few_d<kCoopThreads>(static_cast<double>(accv));
     if (t == 0) { pWW[blockIdx.x] = sw; pA[blockIdx.x] = sv; }
   }
   grid_barrier(bar, G, err);
   if (blockIdx.x == 0) {
-    const double ww = sum_partials_d<kCoopThreads>(pWW, G);
+    const double ww = sum_partials_few_d<kCoopThreads>(pWW, G);
     if (t == 0) wn[j] = sqrt(ww);
   }
   // MGS phases l = 0..j (four independent element streams per thread)
@@ -316,7 +316,7 @@ arnoldi_step_kernel(int n, int rows_per_cta, const int* __restrict__ rowptr,
   double* pin = pA;
   double* pout = pB;
   for (int l = 0; l <= j; ++l) {
-    const double h = sum_partials_d<kCoopThreads>(pin, G);
+    const double h = sum_partials_few_d<kCoopThreads>(pin, G);
     if (blockIdx.x == 0 && t == 0) H[l + static_cast<int64_t>(j) * ldh] = h;
     const T ht = static_cast<T>(h);
     const T* vl = V + static_cast<int64_t>(l) * ld;
@@ -344,17 +344,197 @@ arnoldi_step_kernel(int n, int rows_per_cta, const int* __restrict__ rowptr,
       w[i] = wi;
       acc = fma(l < j ? vn[i] : wi, wi, acc);
     }
-    const double tot = block_sum_d<kCoopThreads>(static_cast<double>(acc));
+    const double tot = block_sum_few_d<kCoopThreads>(static_cast<double>(acc));
     if (t == 0) pout[blockIdx.x] = tot;
     grid_barrier(bar, G, err);
     double* tmp = pin; pin = pout; pout = tmp;
   }
   // normalise
-  const double nrm = sqrt(sum_partials_d<kCoopThreads>(pin, G));
+  const double nrm = sqrt(sum_partials_few_d<kCoopThreads>(pin, G));
   if (blockIdx.x == 0 && t == 0) H[(j + 1) + static_cast<int64_t>(j) * ldh] = nrm;
   const double inv = 1.0 / nrm;
   for (int64_t i = i0; i < n; i += stride)
     w[i] = static_cast<T>(static_cast<double>(w[i]) * inv);
+}
+
+// FP32 form of the same step with grouped lookahead: the MGS projections
+// are taken kGrp basis vectors per grid barrier.  With d_k = v_k.w and the
+// group's Gram entries G_kq = v_k.v_q (q < k), all summed in the pass that
+// precedes the group, the MGS coefficients follow exactly by forward
+// substitution, h_k = d_k - sum_{q<k} G_kq h_q (what MGS computes, in
+// another rounding order); w then loses the group in MGS order,
+// w -= h_0 v_0, w -= h_1 v_1, ...  One barrier per group instead of one
+// per vector: the FP32 step is barrier-bound, not bandwidth-bound, and
+// reads every basis vector twice either way.
+constexpr int kGrp = 4;
+// per block, kNP sums: d_k = v_k.w at k (k < kGrp), then the Gram entry
+// v_k.v_q (q < k) at kGrp + k(k-1)/2 + q; the norm pass uses slot 0
+constexpr int kNP = kGrp + kGrp * (kGrp - 1) / 2;
+
+__device__ __forceinline__ void group_sums(const float* __restrict__ V, int64_t ld, int64_t row,
+                                           int l, int g, float wi, float* acc) {
+  float v[kGrp];
+#pragma unroll
+  for (int k = 0; k < kGrp; ++k) v[k] = k < g ? V[row + static_cast<int64_t>(l + k) * ld] : 0.0f;
+#pragma unroll
+  for (int k = 0; k < kGrp; ++k) {
+    acc[k] = fmaf(v[k], wi, acc[k]);
+#pragma unroll
+    for (int q = 0; q < k; ++q) acc[kGrp + k * (k - 1) / 2 + q] = fmaf(v[k], v[q], acc[kGrp + k * (k - 1) / 2 + q]);
+  }
+}
+
+template <bool SELL>
+__global__ void __launch_bounds__(kCoopThreads, 1)
+arnoldi_step_grouped_kernel(int n, int rows_per_cta, const int* __restrict__ rowptr,
+                            const int* __restrict__ colind, const float* __restrict__ val,
+                            float* __restrict__ V, int64_t ld, int j,
+                            double* __restrict__ H, int ldh, double* __restrict__ wn,
+                            double* __restrict__ red, unsigned* bar, int* err,
+                            int64_t rows32) {
+  extern __shared__ __align__(16) unsigned char coop_smem[];
+  __shared__ double swarp[kCoopThreads / 32][kNP];
+  __shared__ double ssum[kNP];
+  __shared__ double hs[kGrp];
+  const int G = gridDim.x;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const float* vj = V + static_cast<int64_t>(j) * ld;
+  float* w = V + static_cast<int64_t>(j + 1) * ld;
+  double* pin = red;
+  double* pout = red + static_cast<int64_t>(G) * kNP;
+  double* pW = red + 2 * static_cast<int64_t>(G) * kNP;
+  const int64_t stride = static_cast<int64_t>(G) * kCoopThreads;
+  const int64_t i0 = blockIdx.x * static_cast<int64_t>(kCoopThreads) + t;
+
+  // block sums of acc[0..np) -> dst[blockIdx.x * dstride + p]: FP32
+  // shuffles within each warp, FP64 only in the one warp that combines
+  // the 32 warp sums (FP64 instructions in every warp made the FP64 pipe
+  // the limit of this FP32 kernel)
+  auto block_partials = [&](const float* acc, int np, double* dst, int dstride) {
+    for (int p = 0; p < np; ++p) {
+      const float v = warp_sum_f(acc[p]);
+      if (lane == 0) swarp[warp][p] = static_cast<double>(v);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int p = 0; p < np; ++p) {
+        const double v = warp_sum_d<kCoopThreads>(swarp[lane][p]);
+        if (lane == 0) dst[static_cast<int64_t>(blockIdx.x) * dstride + p] = v;
+      }
+    }
+    __syncthreads();
+  };
+  // fixed-order sums over the G blocks' partials -> ssum[0..np)
+  auto gather = [&](const double* src, int np) {
+    if (warp < np) {
+      double v = 0.0;
+      for (int c = lane; c < G; c += 32) v += src[static_cast<int64_t>(c) * kNP + warp];
+      v = warp_sum_d<kCoopThreads>(v);
+      if (lane == 0) ssum[warp] = v;
+    }
+    __syncthreads();
+  };
+
+  const int ncols = j + 1;  // basis vectors v_0 .. v_j to project out
+  int g1 = ncols < kGrp ? ncols : kGrp;
+  // phase 0: w = A v_j; partials of w.w and of group 0's dots and Gram
+  {
+    float acc[kNP];
+#pragma unroll
+    for (int p = 0; p < kNP; ++p) acc[p] = 0.0f;
+    float accw[1] = {0.0f};
+    if (SELL) {
+      for (int64_t row = i0; row < rows32; row += stride) {
+        const float sum = sell_row(rowptr, colind, val, vj, row);
+        if (row < n) {
+          w[row] = sum;
+          accw[0] = fmaf(sum, sum, accw[0]);
+          group_sums(V, ld, row, 0, g1, sum, acc);
+        }
+      }
+    } else {
+      float* sval = reinterpret_cast<float*>(coop_smem);
+      int* scol = reinterpret_cast<int*>(coop_smem + sizeof(float) * kCoopStage);
+      for (int64_t r0 = static_cast<int64_t>(blockIdx.x) * rows_per_cta; r0 < n;
+           r0 += static_cast<int64_t>(G) * rows_per_cta) {
+        const int64_t r1 = (r0 + rows_per_cta < n) ? r0 + rows_per_cta : n;
+        const int k0 = rowptr[r0];
+        const int len = rowptr[r1] - k0;
+        const bool staged = len <= kCoopStage;
+        if (staged) {
+          for (int e = t; e < len; e += kCoopThreads) {
+            sval[e] = ld_stream(val + k0 + e);
+            scol[e] = ld_stream(colind + k0 + e);
+          }
+        }
+        __syncthreads();
+        for (int64_t row = r0 + t; row < r1; row += kCoopThreads) {
+          const int a = rowptr[row], b = rowptr[row + 1];
+          float sum = 0.0f;
+          if (staged) {
+            for (int k = a - k0; k < b - k0; ++k) sum = fmaf(sval[k], __ldg(vj + scol[k]), sum);
+          } else {
+            for (int k = a; k < b; ++k)
+              sum = fmaf(ld_stream(val + k), __ldg(vj + ld_stream(colind + k)), sum);
+          }
+          w[row] = sum;
+          accw[0] = fmaf(sum, sum, accw[0]);
+          group_sums(V, ld, row, 0, g1, sum, acc);
+        }
+        __syncthreads();
+      }
+    }
+    block_partials(accw, 1, pW, 1);
+    block_partials(acc, kNP, pin, kNP);
+  }
+  grid_barrier(bar, G, err);
+  if (blockIdx.x == 0 && warp == 0) {
+    double ww = 0.0;
+    for (int c = lane; c < G; c += 32) ww += pW[c];
+    ww = warp_sum_d<kCoopThreads>(ww);
+    if (lane == 0) wn[j] = sqrt(ww);
+  }
+  // groups of kGrp basis vectors
+  for (int l0 = 0; l0 < ncols; l0 += kGrp) {
+    const int gs = g1;
+    const int l1 = l0 + gs;
+    const int gn = (ncols - l1) < kGrp ? (ncols - l1) : kGrp;  // next group (0: none)
+    gather(pin, kNP);
+    if (t == 0) {
+      for (int k = 0; k < gs; ++k) {
+        double hk = ssum[k];
+        for (int q = 0; q < k; ++q) hk -= ssum[kGrp + k * (k - 1) / 2 + q] * hs[q];
+        hs[k] = hk;
+        if (blockIdx.x == 0) H[(l0 + k) + static_cast<int64_t>(j) * ldh] = hk;
+      }
+    }
+    __syncthreads();
+    float hf[kGrp];
+#pragma unroll
+    for (int k = 0; k < kGrp; ++k) hf[k] = k < gs ? static_cast<float>(hs[k]) : 0.0f;
+    float acc[kNP];
+#pragma unroll
+    for (int p = 0; p < kNP; ++p) acc[p] = 0.0f;
+    for (int64_t i = i0; i < n; i += stride) {
+      float wi = w[i];
+#pragma unroll
+      for (int k = 0; k < kGrp; ++k)
+        if (k < gs) wi = fmaf(-hf[k], V[i + static_cast<int64_t>(l0 + k) * ld], wi);
+      w[i] = wi;
+      if (gn > 0) group_sums(V, ld, i, l1, gn, wi, acc);
+      else acc[0] = fmaf(wi, wi, acc[0]);
+    }
+    block_partials(acc, kNP, pout, kNP);
+    grid_barrier(bar, G, err);
+    double* tmp = pin; pin = pout; pout = tmp;
+    g1 = gn;
+  }
+  // normalise: the last pass left the partials of ||w||^2 in slot 0
+  gather(pin, 1);
+  const double nrm = sqrt(ssum[0]);
+  if (blockIdx.x == 0 && t == 0) H[(j + 1) + static_cast<int64_t>(j) * ldh] = nrm;
+  const float inv = static_cast<float>(1.0 / nrm);
+  for (int64_t i = i0; i < n; i += stride) w[i] *= inv;
 }
 
 template <typename T, bool SELL>
@@ -362,20 +542,22 @@ void launch_arnoldi_step(const DevCsr& A, const T* val, T* V, int64_t ld, int j,
                          double* H, int ldh, double* wn, double* red, int red_cap,
                          unsigned* bar, int* err, cudaStream_t st) {
   const int smem = SELL ? 0 : kCoopStage * static_cast<int>(sizeof(T) + sizeof(int));
-  static int max_blocks[2] = {0, 0};
-  int& mb = max_blocks[sizeof(T) == 8 ? 0 : 1];
+  // FP32: the grouped-lookahead step; FP64 keeps one projection per phase,
+  // the rounding order of the MGS oracle
+  const void* fn = reinterpret_cast<const void*>(arnoldi_step_kernel<T, SELL>);
+  if constexpr (sizeof(T) == 4) fn = reinterpret_cast<const void*>(arnoldi_step_grouped_kernel<SELL>);
+  static int mb = 0;  // per instantiation
   if (!mb) {
-    SG_CUDA(cudaFuncSetAttribute(arnoldi_step_kernel<T, SELL>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    SG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
-    SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, arnoldi_step_kernel<T, SELL>,
-                                                          kCoopThreads, smem));
+    SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kCoopThreads, smem));
     mb = per_sm * device_sm_count();
     SG_REQUIRE(mb > 0, SG_ECUDA, "arnoldi step: no resident blocks");
   }
   int G = device_sm_count();  // one CTA per SM: fewer arrivals and partials
   if (G > mb) G = mb;
-  SG_REQUIRE(3 * G <= red_cap, SG_EINVAL, "arnoldi step: partials buffer too small");
+  const int need = sizeof(T) == 4 ? (2 * kNP + 1) * G : 3 * G;
+  SG_REQUIRE(need <= red_cap, SG_EINVAL, "arnoldi step: partials buffer too small");
   // rows per tile: the staged nonzeros fit with 25% slack, <= one per thread
   const double per = A.mean_row > 0 ? A.mean_row * 1.25 : 1.0;
   int rpc = static_cast<int>(kCoopStage / per);
@@ -388,8 +570,7 @@ void launch_arnoldi_step(const DevCsr& A, const T* val, T* V, int64_t ld, int j,
   void* args[] = {&n, &rpc, const_cast<int**>(&rp), const_cast<int**>(&ci),
                   const_cast<T**>(&val), &V, &ld, &j, &H, const_cast<int*>(&ldh), &wn, &red,
                   &bar, &err, &rows32};
-  SG_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(arnoldi_step_kernel<T, SELL>),
-                                      dim3(G), dim3(kCoopThreads), args, smem, st));
+  SG_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kCoopThreads), args, smem, st));
   count_launch();
 }
 

@@ -51,6 +51,11 @@ Slots slots_for(int m, int k) {
   return s;
 }
 
+// Partial sums of the streaming reductions (3 x reduction_blocks) and of
+// the cooperative pre-pass (up to 24 per SM: two ping-pong sets of the
+// grouped step's 10 sums, plus w.w).
+int red_doubles() { return 3 * reduction_blocks() + 24 * device_sm_count(); }
+
 // Largest split-partials buffer over every block shape the solver uses
 // (i <= imax rows of Q^T, s <= smax columns).
 int64_t max_part_size(int64_t n, int imax, int smax) {
@@ -78,7 +83,7 @@ void ensure_workspace(sg_handle* h, int64_t n, int m, int k) {
   const int64_t part = max_part_size(n, m + 1, k);
   dev_alloc(&h->part, part);
   h->part_cap = part;
-  dev_alloc(&h->red, static_cast<size_t>(reduction_blocks()) * 3);
+  dev_alloc(&h->red, static_cast<size_t>(red_doubles()));
   Slots sl = slots_for(m, k);
   dev_alloc(&h->small, sl.total);
   h->small_cap = sl.total;
@@ -111,7 +116,7 @@ void ensure_workspace32(sg_handle* h, int64_t n, int m, int k) {
     const int64_t part = max_part_size(n, mm + 1, kk);
     dev_alloc(&h->part, part);
     h->part_cap = part;
-    dev_alloc(&h->red, static_cast<size_t>(reduction_blocks()) * 3);
+    dev_alloc(&h->red, static_cast<size_t>(red_doubles()));
     Slots sl = slots_for(mm, kk);
     dev_alloc(&h->small, sl.total);
     h->small_cap = sl.total;
@@ -245,7 +250,7 @@ void enqueue_prepass(sg_handle* h, const DevCsr& M, const T* q, int k,
   SG_CUDA(cudaMemsetAsync(prepass_barrier(h), 0, 256, st));
   SG_CUDA(cudaMemcpyAsync(V, q, sizeof(T) * n, cudaMemcpyDeviceToDevice, st));
   for (int j = 0; j < k; ++j)
-    step_kernel<T>(M, V, ld, j, Hd, ldh, wn, h->red, 3 * reduction_blocks(),
+    step_kernel<T>(M, V, ld, j, Hd, ldh, wn, h->red, red_doubles(),
                    prepass_barrier(h), prepass_error(h), st);
 }
 

@@ -578,6 +578,25 @@ def test_fp32_ir_reaches_fp64_accuracy(solver):
     assert info.refinements >= 2
 
 
+@pytest.mark.parametrize("k", [1, 3, 4, 5, 9, 12])
+def test_fp32_prepass_ritz_values_follow_fp64_arnoldi(solver, k):
+    """The FP32 pre-pass (MGS projections taken four basis vectors per
+    grid barrier, coefficients from the group's Gram matrix) gives the Ritz
+    values of the FP64 MGS-Arnoldi oracle to FP32 accuracy; k spans partial
+    and whole groups.  Compared as sets (Leja order can swap near-ties)."""
+    c = W.config_c2(16)
+    _analyze(solver, c["A"])
+    _, info = solver.solve(c["b"], m=40, s=k, tol=1e-10, precision="fp32_ir", max_iters=k)
+    q = c["b"] / np.linalg.norm(c["b"])
+    H, steps = O.arnoldi_mgs(O.as_operator(c["A"]), q, k)
+    ref = O.ritz_values(H, steps)
+    got = info.ritz
+    assert got.size == ref.size
+    scale = np.max(np.abs(ref))
+    for z in ref:
+        assert np.min(np.abs(got - z)) <= 2e-5 * scale, (z, got)
+
+
 # ------------------------------------------------------ full-size workload
 @pytest.mark.slow
 def test_full_size_c2_sampled_and_converged(solver):
