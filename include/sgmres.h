@@ -289,6 +289,21 @@ sg_status sg_block_dot_noalloc(int64_t n, const double* Q, int64_t ldq,
                                int32_t s, double* W, int32_t ldw,
                                void* stream, char* err, int32_t err_cap);
 
+/* Failure-detection probe (a diagnostic; the paper has no counterpart).
+ * Every wait inside the library's kernels (the grid barrier of the
+ * cooperative Arnoldi step, the mbarriers of the tensor-core kernels) is
+ * time-bounded: when it runs out the kernel sets an error flag, finishes
+ * without the missing data and the call returns SG_ECUDA.  This call runs
+ * two tiny kernels on `device` whose waits cannot complete -- a grid
+ * barrier expecting one block more than is launched, and an mbarrier that
+ * nothing arrives on -- with a limit of limit_ms (clamped to 1..2000 ms),
+ * and reports in *grid_barrier_timed_out / *mbarrier_timed_out (1/0)
+ * whether each wait ran out and was reported.  The device stays usable.
+ * Errors: SG_EINVAL (NULL output), SG_ECUDA. */
+sg_status sg_probe_bounded_waits(int32_t device, double limit_ms,
+                                 int32_t* grid_barrier_timed_out,
+                                 int32_t* mbarrier_timed_out);
+
 /* Number of kernels this library has launched in the process so far (a
  * diagnostic for benchmarks: every launch goes through one counter). */
 int64_t sg_kernel_launches(void);

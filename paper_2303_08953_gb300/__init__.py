@@ -37,7 +37,19 @@ EXPORTED = (
     "sg_host_scaling_coefficients", "sg_host_estimate_step",
     "sg_kernel_launches", "sg_block_dot_noalloc", "sg_block_dot_f32",
     "sg_block_update_f32", "sg_update_values", "sg_matrix_info",
+    "sg_probe_bounded_waits",
 )
+
+
+def probe_bounded_waits(device=0, limit_ms=50.0):
+    """(grid barrier timed out, mbarrier timed out): runs the library's
+    failure-detection probe (waits that cannot complete, bounded by
+    limit_ms) and reports whether each was caught and reported."""
+    a, b = C.c_int32(0), C.c_int32(0)
+    rc = lib.sg_probe_bounded_waits(device, limit_ms, C.byref(a), C.byref(b))
+    if rc != 0:
+        raise SgError(rc, "sg_probe_bounded_waits failed")
+    return bool(a.value), bool(b.value)
 
 
 class SgError(RuntimeError):
@@ -98,6 +110,7 @@ def _load():
         "sg_analyze": (i32, [vp, C.POINTER(sg_csr)]),
         "sg_update_values": (i32, [vp, vp, i32]),
         "sg_matrix_info": (i32, [vp, C.POINTER(i32), C.POINTER(i64)]),
+        "sg_probe_bounded_waits": (i32, [i32, f64, C.POINTER(i32), C.POINTER(i32)]),
         "sg_solve": (i32, [vp, vp, vp, C.POINTER(sg_opts), C.POINTER(sg_result)]),
         "sg_solve_adjoint": (i32, [vp, vp, vp, C.POINTER(sg_opts), C.POINTER(sg_result)]),
         "sg_grad_values": (i32, [vp, vp, vp, vp, vp]),

@@ -209,7 +209,8 @@ __device__ __forceinline__ uint64_t now_ns() {
 
 // bar[0]: arrivals; bar[32]: generation (a separate 128-byte line, so the
 // pollers do not contend with the arrivals)
-__device__ void grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
+__device__ void grid_barrier(unsigned* bar, unsigned nblocks, int* err,
+                             uint64_t limit_ns = kBarrierNs) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* gen = bar + 32;
@@ -226,7 +227,7 @@ __device__ void grid_barrier(unsigned* bar, unsigned nblocks, int* err) {
       unsigned spins = 0;
       while (*gen == g) {
         __nanosleep(32);
-        if ((++spins & 255u) == 0 && now_ns() - t0 > kBarrierNs) {
+        if ((++spins & 255u) == 0 && now_ns() - t0 > limit_ns) {
           atomicExch(err, 1);
           break;
         }
@@ -850,6 +851,37 @@ __global__ void diag_kernel(int64_t n, const double* __restrict__ d,
 }
 
 }  // namespace
+
+namespace {
+
+// A grid barrier that cannot complete: it expects one block more than the
+// grid has, so every block's bounded wait runs out and sets err.
+__global__ void barrier_probe_kernel(unsigned* bar, int* err, uint64_t limit_ns) {
+  grid_barrier(bar, gridDim.x + 1, err, limit_ns);
+}
+
+}  // namespace
+
+bool probe_grid_barrier_timeout(uint64_t limit_ns, cudaStream_t st) {
+  unsigned* bar = nullptr;
+  SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&bar), 256));
+  bool timed_out = false;
+  try {
+    SG_CUDA(cudaMemsetAsync(bar, 0, 256, st));
+    int* err = reinterpret_cast<int*>(bar + 48);
+    barrier_probe_kernel<<<2, 32, 0, st>>>(bar, err, limit_ns);
+    SG_LAUNCH_CHECK();
+    int host = 0;
+    SG_CUDA(cudaMemcpyAsync(&host, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SG_CUDA(cudaStreamSynchronize(st));
+    timed_out = host != 0;
+  } catch (...) {
+    cudaFree(bar);
+    throw;
+  }
+  SG_CUDA(cudaFree(bar));
+  return timed_out;
+}
 
 void column_scale_factors(const DevCsr& AT, double* d, cudaStream_t st) {
   colnorm_kernel<<<device_sm_count() * 8, kThreads, 0, st>>>(AT.n, AT.rowptr, AT.val, d);

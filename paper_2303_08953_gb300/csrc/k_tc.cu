@@ -224,6 +224,41 @@ bool make_map(CUtensorMap* map, const float* base, int64_t rows, int64_t cols,
 
 }  // namespace
 
+namespace {
+
+// An mbarrier nothing arrives on: the bounded wait runs out and sets err.
+__global__ void mbarrier_probe_kernel(int* err, uint64_t limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&bar, 0u, limit_ns)) atomicExch(err, 1);
+}
+
+}  // namespace
+
+bool probe_mbarrier_timeout(uint64_t limit_ns, cudaStream_t st) {
+  int* err = nullptr;
+  SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&err), sizeof(int)));
+  bool timed_out = false;
+  try {
+    SG_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    mbarrier_probe_kernel<<<1, 32, 0, st>>>(err, limit_ns);
+    SG_LAUNCH_CHECK();
+    int host = 0;
+    SG_CUDA(cudaMemcpyAsync(&host, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SG_CUDA(cudaStreamSynchronize(st));
+    timed_out = host != 0;
+  } catch (...) {
+    cudaFree(err);
+    throw;
+  }
+  SG_CUDA(cudaFree(err));
+  return timed_out;
+}
+
 bool tc_dot_supported(int64_t n, const float* Q, int64_t ldq, int i, const float* X,
                       int64_t ldx, int s) {
   if (n < 8 * kBK || i < 1 || s < 1 || s > kMaxN) return false;

@@ -35,8 +35,9 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // bounded wait for the phase with the given parity to complete: gives up
-// after kWaitNs nanoseconds (or kSpinLimit attempts) and returns false
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// after limit_ns nanoseconds (or kSpinLimit attempts) and returns false
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          uint64_t limit_ns = kWaitNs) {
   const uint32_t addr = smem_u32(bar);
   const uint64_t t0 = global_ns();
   for (uint32_t it = 0; it < kSpinLimit; ++it) {
@@ -49,7 +50,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(addr), "r"(parity)
         : "memory");
     if (done) return true;
-    if ((it & 255) == 255 && global_ns() - t0 > kWaitNs) return false;
+    if ((it & 255) == 255 && global_ns() - t0 > limit_ns) return false;
   }
   return false;
 }

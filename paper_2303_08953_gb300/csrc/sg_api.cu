@@ -396,6 +396,32 @@ sg_status sg_update_values(sg_handle* h, const double* val, int32_t on_device) {
   });
 }
 
+sg_status sg_probe_bounded_waits(int32_t device, double limit_ms,
+                                 int32_t* grid_barrier_timed_out,
+                                 int32_t* mbarrier_timed_out) {
+  if (!grid_barrier_timed_out || !mbarrier_timed_out) return SG_EINVAL;
+  try {
+    SG_CUDA(cudaSetDevice(device));
+    const double ms = std::min(2000.0, std::max(1.0, limit_ms));
+    const uint64_t ns = static_cast<uint64_t>(ms * 1e6);
+    cudaStream_t st = nullptr;
+    SG_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    try {
+      *grid_barrier_timed_out = sg::probe_grid_barrier_timeout(ns, st) ? 1 : 0;
+      *mbarrier_timed_out = sg::probe_mbarrier_timeout(ns, st) ? 1 : 0;
+    } catch (...) {
+      cudaStreamDestroy(st);
+      throw;
+    }
+    SG_CUDA(cudaStreamDestroy(st));
+    return SG_OK;
+  } catch (const sg::Error& e) {
+    return e.code;
+  } catch (...) {
+    return SG_ECUDA;
+  }
+}
+
 sg_status sg_matrix_info(const sg_handle* h, int32_t* sell, int64_t* stored) {
   if (!h) return SG_EINVAL;
   if (!h->have_A) return SG_ESTATE;

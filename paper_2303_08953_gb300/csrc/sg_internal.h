@@ -70,6 +70,11 @@ void column_scale_factors(const DevCsr& AT, double* d, cudaStream_t st);
 // E.val = A.val * d[col] (and the SELL values when A has them; E shares
 // A's pattern arrays, its value arrays are allocated by the caller).
 void scale_columns(const DevCsr& A, const double* d, DevCsr& E, cudaStream_t st);
+// Failure-detection probes: a grid barrier / an mbarrier that cannot
+// complete, waited on with the given limit; true when the kernel's bounded
+// wait ran out and set its error flag.
+bool probe_grid_barrier_timeout(uint64_t limit_ns, cudaStream_t st);
+bool probe_mbarrier_timeout(uint64_t limit_ns, cudaStream_t st);
 // y[i] = x[i] * d[i] (mul) or x[i] / d[i] (div), in place allowed.
 void diag_apply(int64_t n, const double* d, const double* x, double* y, bool div,
                 cudaStream_t st);

@@ -536,6 +536,53 @@ def test_solve_max_iters_reports_noconv(solver):
     assert info.iters == 40
 
 
+def test_invariant_subspace_ends_the_solve_exactly(solver):
+    """A diagonal matrix with three distinct eigenvalues: the Krylov space
+    has dimension 3, the Ritz pre-pass stops early (h_{j+1,j} ~ 0), the
+    step size is capped by the Ritz values available, and the solve ends
+    with a residual at rounding level, as in the oracle."""
+    lam = np.repeat([1.0, 2.5, 4.0], 1000)
+    A = W.diagonal(lam)
+    b = np.random.default_rng(3).uniform(-1, 1, A.n)
+    _analyze(solver, A)
+    ro = O.adaptive_sgmres(A, b, m=20, s=8, tol=1e-12)
+    x, info = solver.solve(b, m=20, s=8, tol=1e-12)
+    assert info.converged and ro.converged
+    assert info.s0 == ro.s0 == 3 and info.iters == ro.iters <= 4
+    assert np.linalg.norm(x - b / lam) <= 1e-13 * np.linalg.norm(b / lam)
+
+
+def test_nonfinite_rhs_is_reported_and_the_handle_recovers(solver):
+    """Host-side fault injection: a NaN in b gives SG_ENUMERIC (no device
+    trap), and the same handle then solves a clean system."""
+    c = W.config_c1(16)
+    _analyze(solver, c["A"])
+    bad = c["b"].copy()
+    bad[7] = np.nan
+    with pytest.raises(sg.SgError) as e:
+        solver.solve(bad, m=20, s=4, tol=1e-10)
+    assert e.value.status == sg.SG_ENUMERIC
+    x, info = solver.solve(c["b"], m=20, s=4, tol=1e-10)
+    assert info.converged
+
+
+def test_bounded_waits_time_out_and_leave_the_device_usable(solver):
+    """Failure detection without a GPU fault: a grid barrier that expects
+    one block too many and an mbarrier nothing arrives on both run out
+    their 50 ms limit, set their error flags, return, and the context
+    keeps working (a solve follows)."""
+    import time
+    t0 = time.perf_counter()
+    gb, mb = sg.probe_bounded_waits(0, 50.0)
+    dt = time.perf_counter() - t0
+    assert gb and mb
+    assert dt < 5.0
+    c = W.config_c1(16)
+    _analyze(solver, c["A"])
+    x, info = solver.solve(c["b"], m=20, s=4, tol=1e-10)
+    assert info.converged
+
+
 def test_analyze_rejects_bad_csr(solver):
     with pytest.raises(sg.SgError):
         solver.analyze(np.array([0, 2, 1], np.int32), np.array([0, 1], np.int32),
