@@ -516,7 +516,32 @@ arnoldi_step_grouped_kernel(int n, int rows_per_cta, const int* __restrict__ row
     float acc[kNP];
 #pragma unroll
     for (int p = 0; p < kNP; ++p) acc[p] = 0.0f;
-    for (int64_t i = i0; i < n; i += stride) {
+    // two elements per iteration, so both elements' loads are in flight
+    // together (one element at a time left each thread waiting on memory)
+    int64_t i = i0;
+    for (; i + stride < n; i += 2 * stride) {
+      float wi[2], vu[2][kGrp];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        wi[e] = w[i + e * stride];
+#pragma unroll
+        for (int k = 0; k < kGrp; ++k)
+          vu[e][k] = k < gs ? V[i + e * stride + static_cast<int64_t>(l0 + k) * ld] : 0.0f;
+      }
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+#pragma unroll
+        for (int k = 0; k < kGrp; ++k)
+          if (k < gs) wi[e] = fmaf(-hf[k], vu[e][k], wi[e]);
+        w[i + e * stride] = wi[e];
+      }
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        if (gn > 0) group_sums(V, ld, i + e * stride, l1, gn, wi[e], acc);
+        else acc[0] = fmaf(wi[e], wi[e], acc[0]);
+      }
+    }
+    for (; i < n; i += stride) {
       float wi = w[i];
 #pragma unroll
       for (int k = 0; k < kGrp; ++k)

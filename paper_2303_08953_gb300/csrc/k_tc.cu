@@ -5,11 +5,12 @@
 // K-major operands (K = the n rows) of a tcgen05 MMA with M = 128 columns
 // of Q per tile and N = s (rounded up to 16).  Each CTA reduces one range
 // of rows for one 128-column tile:
-//   * one thread issues TMA loads of 32-row x 128 B tiles (128-byte
-//     swizzle) into a 3-stage ring guarded by mbarriers;
-//   * all four warps split every tile in place into a TF32 "hi" part
+//   * a producer warp (one lane) issues TMA loads of 32-row x 128 B tiles
+//     (128-byte swizzle) into a 3-stage ring guarded by mbarriers, each as
+//     soon as the MMAs of the stage's previous tile have completed;
+//   * eight warps split every tile in place into a TF32 "hi" part
 //     (low 13 mantissa bits cleared) and an exact FP32 remainder "lo";
-//   * the same elected thread issues tcgen05.mma.kind::tf32 for
+//   * one elected thread of them issues tcgen05.mma.kind::tf32 for
 //     hi*hi + lo*hi + hi*lo (the low*low term is below FP32 rounding), with
 //     the FP32 accumulator in tensor memory, and commits each stage's MMAs
 //     to an mbarrier that frees the stage;
@@ -34,7 +35,8 @@ using namespace tc;
 constexpr int kBM = 128;          // MMA M: columns of Q per tile
 constexpr int kBK = 32;           // rows per stage: 32 FP32 = one 128 B row
 constexpr int kStages = 3;
-constexpr int kThreads = 256;     // 8 warps split tiles; warps 0-3 own TMEM lanes
+constexpr int kSplit = 256;       // 8 warps split tiles; warps 0-3 own TMEM lanes
+constexpr int kThreads = kSplit + 32;  // + the TMA producer warp
 constexpr int kMaxN = 128;        // s <= 128 per launch
 
 struct __align__(8) TcShared {
@@ -43,6 +45,7 @@ struct __align__(8) TcShared {
   uint64_t done;
   uint32_t tmem_base;
   int fail;
+  int stop;  // the splitting warps' common stop decision
 };
 
 // grid: (tiles of 128 Q columns, 1, splits); block: 256 threads
@@ -76,6 +79,7 @@ tc_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
     }
     mbar_init(&sh.done, 1);
     sh.fail = 0;
+    sh.stop = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -94,70 +98,73 @@ tc_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
   auto stAlo = [&](int s) { return base + s * stage_bytes + a_bytes; };
   auto stB = [&](int s) { return base + s * stage_bytes + 2 * a_bytes; };
   auto stBlo = [&](int s) { return base + s * stage_bytes + 2 * a_bytes + b_bytes; };
-  auto issue = [&](int kb) {  // thread 0 only
-    const int s = kb % kStages;
-    mbar_expect_tx(&sh.full[s], static_cast<uint32_t>(a_bytes + b_bytes));
-    const int x = static_cast<int>(k0 + static_cast<int64_t>(kb) * kBK);
-    tma_load_2d(stA(s), &mapQ, &sh.full[s], x, m0);
-    tma_load_2d(stB(s), &mapX, &sh.full[s], x, 0);
-  };
 
-  int issued = 0;    // k-blocks whose loads were issued (thread 0's count)
-  int consumed = 0;  // k-blocks whose loads this thread saw land
-  if (tid == 0) {
-    for (; issued < kStages - 1 && issued < nk; ++issued) issue(issued);
-  }
-  bool ok = true;
-  for (int kb = 0; kb < nk; ++kb) {
-    const int s = kb % kStages;
-    const uint32_t ph = static_cast<uint32_t>((kb / kStages) & 1);
-    if (!mbar_wait(&sh.full[s], ph)) sh.fail = 1;
-    else consumed = kb + 1;
-    split_tf32<kThreads>(reinterpret_cast<float4*>(stA(s)), reinterpret_cast<float4*>(stAlo(s)),
-               a_bytes / 16, tid);
-    split_tf32<kThreads>(reinterpret_cast<float4*>(stB(s)), reinterpret_cast<float4*>(stBlo(s)),
-               b_bytes / 16, tid);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (sh.fail) { ok = false; break; }
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint64_t a = sdesc(smem_u32(stA(s))), al = sdesc(smem_u32(stAlo(s)));
-      const uint64_t b = sdesc(smem_u32(stB(s))), bl = sdesc(smem_u32(stBlo(s)));
-#pragma unroll
-      for (int k8 = 0; k8 < kBK / 8; ++k8) {  // K = 8 TF32 = 32 bytes per MMA
-        const uint64_t adv = static_cast<uint64_t>((k8 * 32) >> 4);
-        mma_tf32(tmem, a + adv, b + adv, idesc, (kb > 0 || k8 > 0) ? 1u : 0u);
-        mma_tf32(tmem, al + adv, b + adv, idesc, 1u);
-        mma_tf32(tmem, a + adv, bl + adv, idesc, 1u);
-      }
-      mma_commit(&sh.empty[s]);
-      // refill the stage used one iteration ago once its MMAs are done
-      if (issued < nk) {
-        const int rs = issued % kStages;
-        if (issued >= kStages) {
-          const uint32_t rph = static_cast<uint32_t>(((issued - kStages) / kStages) & 1);
-          if (!mbar_wait(&sh.empty[rs], rph)) sh.fail = 1;
+  if (warp == kSplit / 32) {
+    // ---------------------------------------------- TMA producer (one lane)
+    if ((tid & 31) == 0) {
+      int issued = 0;
+      for (int kb = 0; kb < nk; ++kb) {
+        if (*reinterpret_cast<volatile int*>(&sh.fail)) break;
+        const int s = kb % kStages;
+        if (kb >= kStages &&
+            !mbar_wait(&sh.empty[s], static_cast<uint32_t>(((kb / kStages) - 1) & 1))) {
+          sh.fail = 1;
+          break;
         }
-        if (!sh.fail) { issue(issued); ++issued; }
+        mbar_expect_tx(&sh.full[s], static_cast<uint32_t>(a_bytes + b_bytes));
+        const int x = static_cast<int>(k0 + static_cast<int64_t>(kb) * kBK);
+        tma_load_2d(stA(s), &mapQ, &sh.full[s], x, m0);
+        tma_load_2d(stB(s), &mapX, &sh.full[s], x, 0);
+        issued = kb + 1;
+      }
+      if (*reinterpret_cast<volatile int*>(&sh.fail)) {
+        // let this CTA's loads still in flight land (each is the latest
+        // use of its stage, so its parity identifies it)
+        for (int kb = (issued > kStages ? issued - kStages : 0); kb < issued; ++kb)
+          mbar_wait(&sh.full[kb % kStages], static_cast<uint32_t>((kb / kStages) & 1));
       }
     }
-  }
-  // every MMA this CTA issued must complete before the accumulator is read
-  // (or the tensor memory freed, on the failure path)
-  if (tid == 0) mma_commit(&sh.done);
-  __syncthreads();
-  if (!mbar_wait(&sh.done, 0)) sh.fail = 1;
-  __syncthreads();
-  const bool good = ok && !sh.fail;
-  if (!good) {
-    if (tid == 0) {
-      atomicExch(err, 1);
-      // drain this CTA's loads that are still in flight (each is the
-      // latest use of its stage, so its parity identifies it)
-      for (int kb = consumed; kb < issued; ++kb)
-        mbar_wait(&sh.full[kb % kStages], static_cast<uint32_t>((kb / kStages) & 1));
+  } else {
+    // ---------------------------------------------- split + MMA (8 warps)
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % kStages;
+      const uint32_t ph = static_cast<uint32_t>((kb / kStages) & 1);
+      if (!mbar_wait(&sh.full[s], ph)) sh.fail = 1;
+      split_tf32<kSplit>(reinterpret_cast<float4*>(stA(s)), reinterpret_cast<float4*>(stAlo(s)),
+                         a_bytes / 16, tid);
+      split_tf32<kSplit>(reinterpret_cast<float4*>(stB(s)), reinterpret_cast<float4*>(stBlo(s)),
+                         b_bytes / 16, tid);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      named_sync(1, kSplit);
+      if (tid == 0) {
+        const int stop = *reinterpret_cast<volatile int*>(&sh.fail);
+        if (!stop) {
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t a = sdesc(smem_u32(stA(s))), al = sdesc(smem_u32(stAlo(s)));
+          const uint64_t b = sdesc(smem_u32(stB(s))), bl = sdesc(smem_u32(stBlo(s)));
+#pragma unroll
+          for (int k8 = 0; k8 < kBK / 8; ++k8) {  // K = 8 TF32 = 32 bytes per MMA
+            const uint64_t adv = static_cast<uint64_t>((k8 * 32) >> 4);
+            mma_tf32(tmem, a + adv, b + adv, idesc, (kb > 0 || k8 > 0) ? 1u : 0u);
+            mma_tf32(tmem, al + adv, b + adv, idesc, 1u);
+            mma_tf32(tmem, a + adv, bl + adv, idesc, 1u);
+          }
+          mma_commit(&sh.empty[s]);  // frees the stage for the producer
+        }
+        sh.stop = stop;
+      }
+      named_sync(1, kSplit);
+      if (*reinterpret_cast<volatile int*>(&sh.stop)) break;
     }
+    // every MMA issued must complete before the accumulator is read (or
+    // the tensor memory freed, on the failure path)
+    if (tid == 0) mma_commit(&sh.done);
+    if (!mbar_wait(&sh.done, 0)) sh.fail = 1;
+  }
+  __syncthreads();
+  const bool good = !sh.fail;
+  if (!good) {
+    if (tid == 0) atomicExch(err, 1);
   } else if (warp < 4) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // TMEM lane = accumulator row m (warp w owns lanes 32w..32w+31)
@@ -319,12 +326,13 @@ void tc_dot(int64_t n, const float* Q, int64_t ldq, int i, const float* X, int64
   CUtensorMap mq, mx;
   SG_REQUIRE(make_map(&mq, Q, n, i, ldq, kBM) && make_map(&mx, X, n, s, ldx, BN), SG_ECUDA,
              "cuTensorMapEncodeTiled failed");
-  const int smem = kStages * (2 * kBM * kBK * 4 + 2 * BN * kBK * 4) + 1024;
-  static int configured = 0;
-  if (configured < smem) {
+  auto smem_for = [](int bn) { return kStages * (2 * kBM * kBK * 4 + 2 * bn * kBK * 4) + 1024; };
+  const int smem = smem_for(BN);
+  static bool configured = false;
+  if (!configured) {
     SG_CUDA(cudaFuncSetAttribute(tc_dot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kStages * (2 * kBM * kBK * 4 + 2 * kMaxN * kBK * 4) + 1024));
-    configured = smem;
+                                 smem_for(kMaxN)));
+    configured = true;
   }
   dim3 grid(tiles, 1, static_cast<unsigned>(S));
   tc_dot_kernel<<<grid, kThreads, smem, st>>>(mq, mx, n, i, s, BN, rows, part, err);

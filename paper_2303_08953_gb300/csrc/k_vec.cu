@@ -91,6 +91,24 @@ gemv_kernel(int64_t n, int k, const T* __restrict__ Q, int64_t ldq,
   }
 }
 
+// FP32 basis: the correction Q y is formed in FP32 (y rounded to FP32 once)
+// and added to the FP64 x: one FP64 add per row instead of an FP64 FMA
+// and a conversion per product, which made this HBM-sized pass FP64-bound.
+// The correction only has to be as accurate as the FP32 inner solve.
+__global__ void __launch_bounds__(kThreads)
+gemv32_kernel(int64_t n, int k, const float* __restrict__ Q, int64_t ldq,
+              const double* __restrict__ y, double* __restrict__ x) {
+  extern __shared__ float yf[];
+  for (int j = threadIdx.x; j < k; j += kThreads) yf[j] = static_cast<float>(y[j]);
+  __syncthreads();
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < n;
+       i += static_cast<int64_t>(gridDim.x) * kThreads) {
+    float acc = 0.0f;
+    for (int j = 0; j < k; ++j) acc = fmaf(Q[i + j * ldq], yf[j], acc);
+    x[i] += static_cast<double>(acc);
+  }
+}
+
 __global__ void to_f32_kernel(int64_t n, const double* __restrict__ x,
                               float* __restrict__ y, float s) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; i < n;
@@ -166,8 +184,7 @@ void gemv_n_add(int64_t n, int k, const double* Q, int64_t ldq,
 void gemv_n_add32(int64_t n, int k, const float* Q, int64_t ldq,
                   const double* y, double* x, cudaStream_t st) {
   if (k <= 0) return;
-  gemv_kernel<float><<<stream_grid(n), kThreads, sizeof(double) * k, st>>>(
-      n, k, Q, ldq, y, x);
+  gemv32_kernel<<<stream_grid(n), kThreads, sizeof(float) * k, st>>>(n, k, Q, ldq, y, x);
   SG_LAUNCH_CHECK();
 }
 
