@@ -563,6 +563,306 @@ arnoldi_step_grouped_kernel(int n, int rows_per_cta, const int* __restrict__ row
   for (int64_t i = i0; i < n; i += stride) w[i] *= inv;
 }
 
+// FP32 step with two grid barriers (the inverse compact WY form of MGS):
+// for the basis v_0..v_j, the MGS coefficients of w = A v_j satisfy
+//   h_k = d_k - sum_{q<k} G_kq h_q,  d_k = v_k.w,  G_kq = v_k.v_q,
+// so with the lower triangle L of V^T V, h = (I + L)^{-1} d: the
+// projections MGS takes one after another, in another rounding order
+// (low-synchronisation MGS of Swirydowicz, Langou, Ananthan, Yang and
+// Thomas).  Each step then reads the basis twice at full bandwidth:
+//   pass A: w = A v_j chunk by chunk (a CTA's own rows, staged with v_j in
+//           shared memory), and for every column q of the chunk the
+//           partials of v_q.w and v_q.v_j (the new Gram row);
+//   barrier; every CTA sums the partials in the same fixed order, keeps
+//           row j of the Gram matrix, and solves (I + L) h = d;
+//   pass B: w -= sum_q h_q v_q for the CTA's rows (q ascending, the MGS
+//           order per element) with the partials of ||w||^2;
+//   barrier; w /= ||w||.
+// The Gram matrix is stored packed by rows (row k at k(k-1)/2) in global
+// memory for the later steps and staged in shared memory before pass A.
+constexpr int kIcChunk = 4096;                 // rows per staged chunk
+constexpr int kIcSeg = 512;                    // rows per dot unit (16 per lane)
+constexpr int kIcNSeg = kIcChunk / kIcSeg;     // units per column per chunk
+constexpr int kIcMaxCols = 161;                // basis vectors v_0..v_j per step
+
+__host__ __device__ constexpr int ic_tri(int ncols) { return ncols * (ncols - 1) / 2; }
+
+// dynamic shared memory: sw, sv (chunk), unit slots, Gram triangle, d, h,
+// two scalars, -h in FP32
+__host__ __device__ constexpr size_t ic_smem_bytes(int ncols) {
+  return sizeof(float) * 2 * kIcChunk + sizeof(float) * 2 * ncols * kIcNSeg +
+         sizeof(double) * (ic_tri(ncols) + 2 * ncols + 8) + sizeof(float) * ncols;
+}
+
+// partials: (2 ncols + 1) per CTA for pass A, then G for the norm, then the
+// packed Gram matrix of up to kIcMaxCols vectors
+int64_t ic_red_doubles(int G) {
+  return static_cast<int64_t>(2 * kIcMaxCols + 2) * G + ic_tri(kIcMaxCols);
+}
+
+template <bool SELL>
+__global__ void __launch_bounds__(kCoopThreads, 1)
+arnoldi_step_icwy_kernel(int n, const int* __restrict__ rowptr,
+                         const int* __restrict__ colind, const float* __restrict__ val,
+                         float* __restrict__ V, int64_t ld, int j, double* __restrict__ H,
+                         int ldh, double* __restrict__ wn, double* __restrict__ red,
+                         unsigned* bar, int* err) {
+  extern __shared__ __align__(16) unsigned char coop_smem[];
+  __shared__ double swarp[kCoopThreads / 32];
+  const int ncols = j + 1;
+  const int G = gridDim.x;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  float* sw = reinterpret_cast<float*>(coop_smem);
+  float* sv = sw + kIcChunk;
+  float* slots = sv + kIcChunk;  // [unit][2]: partial v_q.w, v_q.v_j
+  double* tri = reinterpret_cast<double*>(slots + 2 * ncols * kIcNSeg);
+  double* dk = tri + ic_tri(ncols);
+  double* hk = dk + ncols;
+  double* misc = hk + ncols;  // [0]: ||A v_j||^2, [1]: ||w||^2 after projection
+  float* nh = reinterpret_cast<float*>(misc + 8);  // -h_q in FP32 for pass B
+
+  const int P = 2 * ncols + 1;
+  double* pA = red;                                                   // G x P
+  double* pN = red + static_cast<int64_t>(2 * kIcMaxCols + 1) * G;    // G
+  double* gram = red + static_cast<int64_t>(2 * kIcMaxCols + 2) * G;  // packed rows
+
+  const float* vj = V + static_cast<int64_t>(j) * ld;
+  float* w = V + static_cast<int64_t>(j + 1) * ld;
+  // this CTA's rows: whole 32-row slices, as even as possible
+  const int64_t nsl = (static_cast<int64_t>(n) + 31) / 32;
+  const int64_t r0 = 32 * (nsl * blockIdx.x / G);
+  int64_t r1 = 32 * (nsl * (blockIdx.x + 1) / G);
+  if (r1 > n) r1 = n;
+
+  // the Gram rows of the earlier steps (read during pass A's latency)
+  for (int e = t; e < ic_tri(j); e += kCoopThreads) tri[e] = gram[e];
+  for (int e = t; e < 2 * ncols * kIcNSeg; e += kCoopThreads) slots[e] = 0.0f;
+
+  // ------------------------------------------------------------ pass A
+  float accww = 0.0f;
+  for (int64_t c0 = r0; c0 < r1; c0 += kIcChunk) {
+    const int len = static_cast<int>((r1 - c0) < kIcChunk ? (r1 - c0) : kIcChunk);
+    __syncthreads();  // the previous chunk's readers are done with sw / sv
+    for (int r = t; r < len; r += kCoopThreads) {
+      const int64_t row = c0 + r;
+      float sum;
+      if (SELL) {
+        sum = sell_row(rowptr, colind, val, vj, row);
+      } else {
+        sum = 0.0f;
+        const int a = rowptr[row], b = rowptr[row + 1];
+        for (int k = a; k < b; ++k) sum = fmaf(ld_stream(val + k), __ldg(vj + ld_stream(colind + k)), sum);
+      }
+      w[row] = sum;
+      sw[r] = sum;
+      sv[r] = vj[row];
+      accww = fmaf(sum, sum, accww);
+    }
+    __syncthreads();
+    // units (q, g): 512 rows of column q; unit u always belongs to warp
+    // u % 32, so its slot is summed in chunk order
+    for (int u = warp; u < ncols * kIcNSeg; u += 32) {
+      const int q = u / kIcNSeg, g = u % kIcNSeg;
+      const int base = g * kIcSeg;
+      if (base >= len) continue;
+      const float* vq = V + static_cast<int64_t>(q) * ld + c0;
+      float d = 0.0f, gm = 0.0f;
+      if (base + kIcSeg <= len) {
+        float4 a[4];
+#pragma unroll
+        for (int it = 0; it < 4; ++it)
+          a[it] = *reinterpret_cast<const float4*>(vq + base + it * 128 + lane * 4);
+#pragma unroll
+        for (int it = 0; it < 4; ++it) {
+          const int r = base + it * 128 + lane * 4;
+          const float4 x = *reinterpret_cast<const float4*>(sw + r);
+          const float4 y = *reinterpret_cast<const float4*>(sv + r);
+          d = fmaf(a[it].x, x.x, d); d = fmaf(a[it].y, x.y, d);
+          d = fmaf(a[it].z, x.z, d); d = fmaf(a[it].w, x.w, d);
+          gm = fmaf(a[it].x, y.x, gm); gm = fmaf(a[it].y, y.y, gm);
+          gm = fmaf(a[it].z, y.z, gm); gm = fmaf(a[it].w, y.w, gm);
+        }
+      } else {
+        for (int it = 0; it < 4; ++it)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int r = base + it * 128 + lane * 4 + e;
+            if (r < len) {
+              const float a = vq[r];
+              d = fmaf(a, sw[r], d);
+              gm = fmaf(a, sv[r], gm);
+            }
+          }
+      }
+      d = warp_sum_f(d);
+      gm = warp_sum_f(gm);
+      if (lane == 0) {
+        slots[2 * u] += d;
+        slots[2 * u + 1] += gm;
+      }
+    }
+  }
+  // CTA partials: per column, the units in index order; ||A v_j||^2
+  __syncthreads();
+  for (int q = t; q < ncols; q += kCoopThreads) {
+    double d = 0.0, gm = 0.0;
+    for (int g = 0; g < kIcNSeg; ++g) {
+      d += static_cast<double>(slots[2 * (q * kIcNSeg + g)]);
+      gm += static_cast<double>(slots[2 * (q * kIcNSeg + g) + 1]);
+    }
+    pA[static_cast<int64_t>(blockIdx.x) * P + 2 * q] = d;
+    pA[static_cast<int64_t>(blockIdx.x) * P + 2 * q + 1] = gm;
+  }
+  {
+    const float v = warp_sum_f(accww);
+    if (lane == 0) swarp[warp] = static_cast<double>(v);
+    __syncthreads();
+    if (warp == 0) {
+      const double s = warp_sum_d<kCoopThreads>(swarp[lane]);
+      if (lane == 0) pA[static_cast<int64_t>(blockIdx.x) * P + 2 * ncols] = s;
+    }
+  }
+  grid_barrier(bar, G, err);
+
+  // ------------------------------------------- sums and the coefficients
+  // every CTA adds the G partials of each sum in the same fixed order
+  for (int p = warp; p < P; p += 32) {
+    double v = 0.0;
+    for (int c = lane; c < G; c += 32) v += pA[static_cast<int64_t>(c) * P + p];
+    v = warp_sum_d<kCoopThreads>(v);
+    if (lane == 0) {
+      if (p == 2 * ncols) misc[0] = v;
+      else if (p & 1) { if ((p >> 1) < j) tri[ic_tri(j) + (p >> 1)] = v; }  // Gram row j
+      else dk[p >> 1] = v;
+    }
+  }
+  __syncthreads();
+  if (blockIdx.x == 0) {
+    for (int q = t; q < j; q += kCoopThreads) gram[ic_tri(j) + q] = tri[ic_tri(j) + q];
+    if (t == 0) wn[j] = sqrt(misc[0]);
+  }
+  // forward substitution (I + L) h = d by one warp: lanes own rows
+  // k = lane + 32 m; column q's h_q is final once columns < q are applied
+  if (warp == 0) {
+    constexpr int kM = (kIcMaxCols + 31) / 32;
+    double dr[kM];
+#pragma unroll
+    for (int m = 0; m < kM; ++m) {
+      const int k = lane + 32 * m;
+      dr[m] = k < ncols ? dk[k] : 0.0;
+    }
+    for (int q = 0; q < ncols; ++q) {
+      double mine = dr[0];
+#pragma unroll
+      for (int m = 1; m < kM; ++m)
+        if (m == (q >> 5)) mine = dr[m];
+      const double hq = __shfl_sync(0xffffffffu, mine, q & 31);
+      if (lane == 0) hk[q] = hq;
+#pragma unroll
+      for (int m = 0; m < kM; ++m) {
+        const int k = lane + 32 * m;
+        if (k > q && k < ncols) dr[m] = fma(-tri[ic_tri(k) + q], hq, dr[m]);
+      }
+    }
+  }
+  __syncthreads();
+  for (int q = t; q < ncols; q += kCoopThreads) {
+    nh[q] = -static_cast<float>(hk[q]);
+    if (blockIdx.x == 0) H[q + static_cast<int64_t>(j) * ldh] = hk[q];
+  }
+  __syncthreads();
+
+  // ------------------------------------------------------------ pass B
+  float accn = 0.0f;
+  for (int64_t r = r0 + 4 * static_cast<int64_t>(t); r < r1; r += 4 * kCoopThreads) {
+    if (r + 3 < r1) {
+      float4 wv = *reinterpret_cast<const float4*>(w + r);
+      int q = 0;
+      for (; q + 8 <= ncols; q += 8) {
+        float4 vv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          vv[u] = *reinterpret_cast<const float4*>(V + static_cast<int64_t>(q + u) * ld + r);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const float h = nh[q + u];
+          wv.x = fmaf(h, vv[u].x, wv.x); wv.y = fmaf(h, vv[u].y, wv.y);
+          wv.z = fmaf(h, vv[u].z, wv.z); wv.w = fmaf(h, vv[u].w, wv.w);
+        }
+      }
+      for (; q < ncols; ++q) {
+        const float4 vv = *reinterpret_cast<const float4*>(V + static_cast<int64_t>(q) * ld + r);
+        const float h = nh[q];
+        wv.x = fmaf(h, vv.x, wv.x); wv.y = fmaf(h, vv.y, wv.y);
+        wv.z = fmaf(h, vv.z, wv.z); wv.w = fmaf(h, vv.w, wv.w);
+      }
+      *reinterpret_cast<float4*>(w + r) = wv;
+      accn = fmaf(wv.x, wv.x, accn); accn = fmaf(wv.y, wv.y, accn);
+      accn = fmaf(wv.z, wv.z, accn); accn = fmaf(wv.w, wv.w, accn);
+    } else {
+      for (int64_t rr = r; rr < r1; ++rr) {
+        float wi = w[rr];
+        for (int q = 0; q < ncols; ++q) wi = fmaf(nh[q], V[static_cast<int64_t>(q) * ld + rr], wi);
+        w[rr] = wi;
+        accn = fmaf(wi, wi, accn);
+      }
+    }
+  }
+  {
+    const float v = warp_sum_f(accn);
+    __syncthreads();  // swarp is free again
+    if (lane == 0) swarp[warp] = static_cast<double>(v);
+    __syncthreads();
+    if (warp == 0) {
+      const double s = warp_sum_d<kCoopThreads>(swarp[lane]);
+      if (lane == 0) pN[blockIdx.x] = s;
+    }
+  }
+  grid_barrier(bar, G, err);
+  if (warp == 0) {
+    double v = 0.0;
+    for (int c = lane; c < G; c += 32) v += pN[c];
+    v = warp_sum_d<kCoopThreads>(v);
+    if (lane == 0) misc[1] = v;
+  }
+  __syncthreads();
+  const double nrm = sqrt(misc[1]);
+  if (blockIdx.x == 0 && t == 0) H[(j + 1) + static_cast<int64_t>(j) * ldh] = nrm;
+  const float inv = static_cast<float>(1.0 / nrm);
+  for (int64_t r = r0 + t; r < r1; r += kCoopThreads) w[r] *= inv;
+}
+
+// The two-barrier FP32 step while the basis has at most kIcMaxCols
+// vectors and the partials buffer holds its sums; false: not launched.
+template <bool SELL>
+bool launch_arnoldi_icwy(const DevCsr& A, const float* val, float* V, int64_t ld, int j,
+                         double* H, int ldh, double* wn, double* red, int red_cap,
+                         unsigned* bar, int* err, cudaStream_t st) {
+  if (j + 1 > kIcMaxCols) return false;
+  const void* fn = reinterpret_cast<const void*>(arnoldi_step_icwy_kernel<SELL>);
+  static int mb = 0;
+  if (!mb) {
+    const int smax = static_cast<int>(ic_smem_bytes(kIcMaxCols));
+    SG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
+    int per_sm = 0;
+    SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kCoopThreads, smax));
+    mb = per_sm * device_sm_count();
+    SG_REQUIRE(mb > 0, SG_ECUDA, "arnoldi step: no resident blocks");
+  }
+  int G = device_sm_count();
+  if (G > mb) G = mb;
+  if (ic_red_doubles(G) > red_cap) return false;
+  int n = A.n;
+  const int* rp = SELL ? A.sptr : A.rowptr;
+  const int* ci = SELL ? A.scol : A.colind;
+  void* args[] = {&n, const_cast<int**>(&rp), const_cast<int**>(&ci), const_cast<float**>(&val),
+                  &V, &ld, &j, &H, const_cast<int*>(&ldh), &wn, &red, &bar, &err};
+  SG_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kCoopThreads), args,
+                                      ic_smem_bytes(j + 1), st));
+  count_launch();
+  return true;
+}
+
 template <typename T, bool SELL>
 void launch_arnoldi_step(const DevCsr& A, const T* val, T* V, int64_t ld, int j,
                          double* H, int ldh, double* wn, double* red, int red_cap,
@@ -570,6 +870,10 @@ void launch_arnoldi_step(const DevCsr& A, const T* val, T* V, int64_t ld, int j,
   const int smem = SELL ? 0 : kCoopStage * static_cast<int>(sizeof(T) + sizeof(int));
   // FP32: the grouped-lookahead step; FP64 keeps one projection per phase,
   // the rounding order of the MGS oracle
+  if constexpr (sizeof(T) == 4) {
+    if (launch_arnoldi_icwy<SELL>(A, val, V, ld, j, H, ldh, wn, red, red_cap, bar, err, st))
+      return;
+  }
   const void* fn = reinterpret_cast<const void*>(arnoldi_step_kernel<T, SELL>);
   if constexpr (sizeof(T) == 4) fn = reinterpret_cast<const void*>(arnoldi_step_grouped_kernel<SELL>);
   static int mb = 0;  // per instantiation
@@ -931,6 +1235,8 @@ void diag_apply(int64_t n, const double* d, const double* x, double* y, bool div
   diag_kernel<<<device_sm_count() * 8, kThreads, 0, st>>>(n, d, x, y, div ? 1 : 0);
   SG_LAUNCH_CHECK();
 }
+
+int64_t prepass_red_doubles() { return ic_red_doubles(device_sm_count()); }
 
 void arnoldi_step(const DevCsr& A, double* V, int64_t ld, int j, double* H,
                   int ldh, double* wn, double* red, int red_cap, unsigned* bar,

@@ -93,9 +93,14 @@ void spmv_newton32(const DevCsr& A, const float* x, const float* z, float* y,
 void arnoldi_step(const DevCsr& A, double* V, int64_t ld, int j, double* H,
                   int ldh, double* wn, double* red, int red_cap, unsigned* bar,
                   int* err, cudaStream_t st);
+// FP32 form: while j + 1 <= 161 and red holds prepass_red_doubles() the
+// step takes two grid barriers (the MGS coefficients from the basis's Gram
+// matrix, whose rows it keeps in red across the steps of one pre-pass, so
+// the steps 0..k-1 of a pre-pass run in order on one red buffer).
 void arnoldi_step32(const DevCsr& A, float* V, int64_t ld, int j, double* H,
                     int ldh, double* wn, double* red, int red_cap, unsigned* bar,
                     int* err, cudaStream_t st);
+int64_t prepass_red_doubles();
 // r = b - A x
 void residual(const DevCsr& A, const double* b, const double* x, double* r,
               cudaStream_t st);

@@ -52,9 +52,12 @@ Slots slots_for(int m, int k) {
 }
 
 // Partial sums of the streaming reductions (3 x reduction_blocks) and of
-// the cooperative pre-pass (up to 24 per SM: two ping-pong sets of the
-// grouped step's 10 sums, plus w.w).
-int red_doubles() { return 3 * reduction_blocks() + 24 * device_sm_count(); }
+// the cooperative pre-pass (the larger of the grouped step's 24 per SM and
+// the two-barrier step's partials plus its Gram rows).
+int red_doubles() {
+  return 3 * reduction_blocks() +
+         static_cast<int>(std::max<int64_t>(24 * device_sm_count(), prepass_red_doubles()));
+}
 
 // Largest split-partials buffer over every block shape the solver uses
 // (i <= imax rows of Q^T, s <= smax columns).

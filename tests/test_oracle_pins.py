@@ -98,6 +98,23 @@ def test_arnoldi_ritz_values_full_space():
     assert np.allclose(rv, ex, atol=1e-10)
 
 
+def test_arnoldi_reproduces_jacobi_matrix():
+    """Arnoldi from the unit vector at the head of a symmetric tridiagonal
+    chain is Lanczos on a Jacobi matrix: the basis is the chain's unit
+    vectors, H is the leading block of the matrix itself (entries exact),
+    and the Ritz values are the eigenvalues of that k x k block."""
+    A, a, b = W.jacobi_chain(2025)
+    q = np.zeros(A.n)
+    q[0] = 1.0
+    k = 40
+    H, steps = O.arnoldi_mgs(O.as_operator(A), q, k)
+    assert steps == k
+    T = np.diag(a[:k]) + np.diag(b[:k - 1], 1) + np.diag(b[:k - 1], -1)
+    assert np.array_equal(H[:k, :k], T) and H[k, k - 1] == b[k - 1]
+    rv = np.sort(O.ritz_values(H, steps).real)
+    assert np.allclose(rv, np.linalg.eigvalsh(T), rtol=0, atol=1e-12)
+
+
 def test_ritz_values_inside_field_of_values():
     """Ritz values lie in the field of values of A: their real parts are
     bounded by the extreme eigenvalues of the symmetric part (A + A^T)/2

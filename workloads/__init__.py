@@ -6,6 +6,6 @@ the tests and the benchmark.
 """
 from .generators import (  # noqa: F401
     CSR, stencil2d, stencil3d_convdiff, vardiff3d, aniso2d, random_band,
-    diagonal, rhs_from_solution, uniform_vector, config_c1, config_c2,
+    diagonal, jacobi_chain, rhs_from_solution, uniform_vector, config_c1, config_c2,
     config_c3, config_c4, config_c5, CONFIGS,
 )

@@ -227,6 +227,26 @@ def diagonal(eigs) -> CSR:
                np.arange(n, dtype=np.int32), eigs.copy())
 
 
+def jacobi_chain(n, stride=7919):
+    """Symmetric tridiagonal (Jacobi) matrix laid along the row chain
+    r_i = (i * stride) mod n (stride coprime to n), so consecutive chain
+    rows sit far apart: A[r_i, r_i] = a_i = 2 + (i mod 5)/4 and
+    A[r_i, r_{i+1}] = A[r_{i+1}, r_i] = b_i = 1 (i even) or 1/2 (i odd).
+    Every entry and every b_i^2 is exact in FP32.  Returns (A, a, b); the
+    chain starts at row r_0 = 0."""
+    import math
+    if math.gcd(stride, n) != 1:
+        raise ValueError("stride must be coprime to n")
+    i = np.arange(n, dtype=np.int64)
+    r = (i * stride) % n
+    a = 2.0 + (i % 5) / 4.0
+    b = np.where(i[:-1] % 2 == 0, 1.0, 0.5)
+    rows = np.concatenate([r, r[:-1], r[1:]])
+    cols = np.concatenate([r, r[1:], r[:-1]])
+    vals = np.concatenate([a, b, b])
+    return _assemble(n, rows, cols, vals), a, b
+
+
 def uniform_vector(n, rng) -> np.ndarray:
     """n draws from U(-1, 1)."""
     return rng.uniform(-1.0, 1.0, n)
