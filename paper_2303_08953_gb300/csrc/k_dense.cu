@@ -178,6 +178,108 @@ void launch_reduce(int M, int N, int S, const double* part, double* W, int ldw,
   SG_LAUNCH_CHECK();
 }
 
+// Gram matrix of FP32 vectors, G = X^T X, with the products of the
+// EXACT path (p = a b rounded plus its FMA remainder, two-sum accumulation)
+// but without the square tiles' waste: a thread owns one 4 x 4 block
+// (bi <= bj) of the upper triangle, the blocks numbered column by column
+// (block t = bj (bj + 1) / 2 + bi), so only the diagonal blocks compute
+// entries below the diagonal.  CTA (p, z) takes blocks p*128 .. p*128+127
+// over rows [z rows, (z+1) rows): it stages each 32-row slab of the
+// columns its blocks touch in shared memory (rows padded to 16 bytes) and
+// a thread forms 16 exact products per row from one float4 of each side.
+// The triangle's parts of one split are adjacent in launch order, so they
+// share the split's rows through L2.  The partial of split z holds the
+// upper triangle (entry (m, n), m <= n, at m + n s).
+constexpr int kGramMaxS = 128;
+constexpr int kGramBK = 32;
+constexpr int kGramLd = kGramMaxS + 4;
+constexpr int kGramThreads = 128;
+
+__host__ __device__ constexpr int gram_blocks(int s) { return ((s + 3) / 4) * ((s + 3) / 4 + 1) / 2; }
+
+__global__ void __launch_bounds__(kGramThreads)
+gram_exact_kernel(int64_t K, int s, const float* __restrict__ X, int64_t ldx,
+                  double* __restrict__ part, int64_t rows_per_split) {
+  __shared__ __align__(16) float Ss[kGramBK][kGramLd];
+  const int t = blockIdx.x * kGramThreads + threadIdx.x;  // block of the triangle
+  const int nb = gram_blocks(s);
+  // block t -> (bi, bj), bi <= bj
+  int bj = static_cast<int>((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+  while (bj > 0 && bj * (bj + 1) / 2 > t) --bj;
+  while ((bj + 1) * (bj + 2) / 2 <= t) ++bj;
+  const int bi = t - bj * (bj + 1) / 2;
+  const bool active = t < nb;
+  // columns this CTA reads: 0 .. 4 (last block's bj + 1)
+  int tl = blockIdx.x * kGramThreads + kGramThreads - 1;
+  if (tl > nb - 1) tl = nb - 1;
+  int bjl = static_cast<int>((sqrtf(8.0f * tl + 1.0f) - 1.0f) * 0.5f);
+  while (bjl > 0 && bjl * (bjl + 1) / 2 > tl) --bjl;
+  while ((bjl + 1) * (bjl + 2) / 2 <= tl) ++bjl;
+  const int ncol = 4 * (bjl + 1);
+  const int64_t k0 = blockIdx.y * rows_per_split;
+  const int64_t k1 = (k0 + rows_per_split < K) ? k0 + rows_per_split : K;
+  float acc[4][4], comp[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) { acc[a][b] = 0.0f; comp[a][b] = 0.0f; }
+  for (int64_t kb = k0; kb < k1; kb += kGramBK) {
+    __syncthreads();  // the previous slab has been read
+    for (int e = threadIdx.x; e < kGramBK * ncol; e += kGramThreads) {
+      const int kk = e % kGramBK, c = e / kGramBK;
+      const int64_t k = kb + kk;
+      Ss[kk][c] = (k < k1 && c < s) ? X[k + c * ldx] : 0.0f;
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll 2
+      for (int kk = 0; kk < kGramBK; ++kk) {
+        const float4 a4 = *reinterpret_cast<const float4*>(&Ss[kk][4 * bi]);
+        const float4 b4 = *reinterpret_cast<const float4*>(&Ss[kk][4 * bj]);
+        const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+        const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const float p = av[a] * bv[b];
+            const float pe = fmaf(av[a], bv[b], -p);  // exact remainder
+            float sum, e;
+            two_sum(acc[a][b], p, sum, e);
+            acc[a][b] = sum;
+            comp[a][b] += e + pe;
+          }
+      }
+    }
+  }
+  if (!active) return;
+  double* P = part + static_cast<int64_t>(blockIdx.y) * s * s;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int m = 4 * bi + a, n = 4 * bj + b;
+      if (m <= n && n < s)
+        P[m + static_cast<int64_t>(n) * s] =
+            static_cast<double>(acc[a][b]) + static_cast<double>(comp[a][b]);
+    }
+}
+
+// splits of the Gram kernel: about five 128-thread CTAs per SM in all,
+// >= 4 slabs per split
+int64_t gram_splits(int64_t n, int s, int64_t* rows) {
+  const int parts = (gram_blocks(s) + kGramThreads - 1) / kGramThreads;
+  int64_t S = (5 * static_cast<int64_t>(device_sm_count()) + parts - 1) / parts;
+  const int64_t maxS = (n + 4 * kGramBK - 1) / (4 * kGramBK);
+  if (S > maxS) S = maxS;
+  if (S < 1) S = 1;
+  int64_t r = (n + S - 1) / S;
+  r = (r + kGramBK - 1) / kGramBK * kGramBK;
+  S = (n + r - 1) / r;
+  if (rows) *rows = r;
+  return S < 1 ? 1 : S;
+}
+
 enum Cfg { CFG_SQ = 0, CFG_NARROW_M = 1, CFG_NARROW_N = 2, CFG_SQ16 = 3 };
 
 struct DotPlan {
@@ -273,6 +375,19 @@ void block_dot_impl(int64_t n, const T* Q, int64_t ldq, int i, const T* X,
     tc_dot(n, reinterpret_cast<const float*>(Q), ldq, i,
            reinterpret_cast<const float*>(X), ldx, s, part, part_cap, &S, st);
     launch_reduce(i, s, S, part, W, ldw, false, st);
+    return;
+  }
+  if (sizeof(T) == 4 && sym && i == s && s <= kGramMaxS &&
+      reinterpret_cast<const void*>(Q) == reinterpret_cast<const void*>(X)) {
+    // Gram of FP32 vectors: exact products over the upper triangle
+    int64_t rows = 0;
+    const int64_t S = gram_splits(n, s, &rows);
+    SG_REQUIRE(S * s * s <= part_cap, SG_EINVAL, "block_dot: workspace too small");
+    const int parts = (gram_blocks(s) + kGramThreads - 1) / kGramThreads;
+    gram_exact_kernel<<<dim3(parts, static_cast<unsigned>(S)), kGramThreads, 0, st>>>(
+        n, s, reinterpret_cast<const float*>(X), ldx, part, rows);
+    SG_LAUNCH_CHECK();
+    launch_reduce(s, s, static_cast<int>(S), part, W, ldw, true, st);
     return;
   }
   DotPlan p = plan_dot(n, i, s, sizeof(T) == 4, sym);
@@ -493,6 +608,10 @@ int64_t block_dot_part_size(int64_t n, int i, int s) {
       if (a.S > S) S = a.S;
     }
   int64_t need = S * i * s;
+  if (i == s && s <= kGramMaxS) {
+    const int64_t g = gram_splits(n, s, nullptr) * s * s;
+    if (g > need) need = g;
+  }
   const int64_t tc = tc_dot_part_size(n, i, s);
   return need > tc ? need : tc;
 }

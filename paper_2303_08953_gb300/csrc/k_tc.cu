@@ -6,16 +6,33 @@
 // of Q per tile and N = s (rounded up to 16).  Each CTA reduces one range
 // of rows for one 128-column tile:
 //   * a producer warp (one lane) issues TMA loads of 32-row x 128 B tiles
-//     (128-byte swizzle) into a 3-stage ring guarded by mbarriers, each as
-//     soon as the MMAs of the stage's previous tile have completed;
-//   * eight warps split every tile in place into a TF32 "hi" part
-//     (low 13 mantissa bits cleared) and an exact FP32 remainder "lo";
-//   * one elected thread of them issues tcgen05.mma.kind::tf32 for
+//     (128-byte swizzle) into a 6-stage ring guarded by mbarriers, each as
+//     soon as the MMAs of the stage's previous tile have completed; the
+//     split results live in a separate 2-slot ring (the X remainder in
+//     shared memory, Q's hi/lo in tensor memory), so the load ring only
+//     holds raw tiles and keeps ~4 of them in flight;
+//   * warps 0-3, the owners of tensor-memory lanes 0-127, read one 128 B
+//     row of the Q tile each (32 values of one column of Q), split it into
+//     a TF32 "hi" part (low 13 mantissa bits cleared) and the exact FP32
+//     remainder "lo", and store both into tensor memory, where the MMA
+//     takes its A operand: shared memory then carries Q once (the TMA
+//     write and this read) instead of three more times;
+//   * warps 4-7 write the X tile's FP32 remainder beside it in shared
+//     memory; the raw tile itself serves as the hi part, because the tensor
+//     core reads a TF32 operand from the top 19 bits of each 32-bit word
+//     (measured on this chip: the same products as an explicit split);
+//     the eight split warps signal a per-stage mbarrier and go on to the
+//     next tile;
+//   * an MMA warp (one lane) issues tcgen05.mma.kind::tf32 for
 //     hi*hi + lo*hi + hi*lo (the low*low term is below FP32 rounding), with
 //     the FP32 accumulator in tensor memory, and commits each stage's MMAs
 //     to an mbarrier that frees the stage;
 //   * the accumulator is read back with tcgen05.ld and written as one
 //     split partial; the fixed-order split reduction is the SIMT path's.
+// Shared-memory traffic per 32-row tile at i = s = 107 is ~130 KB (TMA
+// writes, the two splits, the MMA's three reads of X) where the version with
+// both splits in shared memory moved ~210 KB: shared-memory bandwidth, not
+// HBM, bounded that version.
 // Every wait is bounded: on timeout the kernel records an error code,
 // drains its own copies, frees its tensor memory and returns.
 #include <cuda.h>
@@ -34,33 +51,38 @@ using namespace tc;
 
 constexpr int kBM = 128;          // MMA M: columns of Q per tile
 constexpr int kBK = 32;           // rows per stage: 32 FP32 = one 128 B row
-constexpr int kStages = 3;
+constexpr int kStages = 6;        // load ring (Q tile + X tile)
+constexpr int kSide = 2;          // split ring (X remainder, Q hi/lo in TMEM)
 constexpr int kSplit = 256;       // 8 warps split tiles; warps 0-3 own TMEM lanes
-constexpr int kThreads = kSplit + 32;  // + the TMA producer warp
+constexpr int kThreads = kSplit + 64;  // + the TMA producer warp, the MMA warp
 constexpr int kMaxN = 128;        // s <= 128 per launch
+constexpr uint32_t kTmemCols = 256;    // accumulator 0..127, Q hi/lo slots from 128
+constexpr uint32_t kSlot0 = 128;       // split slot p: hi at 128 + 64 p, lo at + 32
 
 struct __align__(8) TcShared {
   uint64_t full[kStages];
   uint64_t empty[kStages];
+  uint64_t split[kSide];
+  uint64_t sfree[kSide];
   uint64_t done;
   uint32_t tmem_base;
   int fail;
-  int stop;  // the splitting warps' common stop decision
 };
 
-// grid: (tiles of 128 Q columns, 1, splits); block: 256 threads
+// grid: (tiles of 128 Q columns, 1, splits); block: 320 threads
 __global__ void __launch_bounds__(kThreads, 1)
 tc_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
               const __grid_constant__ CUtensorMap mapX, int64_t n, int M, int N,
               int BN, int64_t rows_per_split, double* __restrict__ part,
               int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char dsmem[];
-  // 1024-byte aligned tiles: per stage A, A_lo (128 x 128 B), B, B_lo (BN x 128 B)
+  // 1024-byte aligned tiles: per stage A (128 x 128 B) and B (BN x 128 B),
+  // then kSide B_lo slots (BN x 128 B)
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~static_cast<uintptr_t>(1023));
   const int a_bytes = kBM * kBK * 4;
   const int b_bytes = BN * kBK * 4;
-  const int stage_bytes = 2 * a_bytes + 2 * b_bytes;
+  const int stage_bytes = a_bytes + b_bytes;
   __shared__ TcShared sh;
 
   const int tid = threadIdx.x;
@@ -69,23 +91,25 @@ tc_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
   const int64_t k0 = static_cast<int64_t>(blockIdx.z) * rows_per_split;
   const int64_t k1 = (k0 + rows_per_split < n) ? k0 + rows_per_split : n;
   const int nk = static_cast<int>((k1 - k0 + kBK - 1) / kBK);
-  const uint32_t ncols = BN <= 32 ? 32 : (BN <= 64 ? 64 : 128);
   const uint32_t idesc = idesc_tf32(kBM, BN);
 
   if (tid == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      mbar_init(&sh.full[s], 1);
-      mbar_init(&sh.empty[s], 1);
+    for (int q = 0; q < kStages; ++q) {
+      mbar_init(&sh.full[q], 1);
+      mbar_init(&sh.empty[q], 1);
+    }
+    for (int p = 0; p < kSide; ++p) {
+      mbar_init(&sh.split[p], kSplit);
+      mbar_init(&sh.sfree[p], 1);
     }
     mbar_init(&sh.done, 1);
     sh.fail = 0;
-    sh.stop = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&sh.tmem_base)),
-                 "r"(ncols)
+                 "r"(kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -94,10 +118,9 @@ tc_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = sh.tmem_base;
 
-  auto stA = [&](int s) { return base + s * stage_bytes; };
-  auto stAlo = [&](int s) { return base + s * stage_bytes + a_bytes; };
-  auto stB = [&](int s) { return base + s * stage_bytes + 2 * a_bytes; };
-  auto stBlo = [&](int s) { return base + s * stage_bytes + 2 * a_bytes + b_bytes; };
+  auto stA = [&](int q) { return base + q * stage_bytes; };
+  auto stB = [&](int q) { return base + q * stage_bytes + a_bytes; };
+  auto stBlo = [&](int p) { return base + kStages * stage_bytes + p * b_bytes; };
 
   if (warp == kSplit / 32) {
     // ---------------------------------------------- TMA producer (one lane)
@@ -105,16 +128,16 @@ tc_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
       int issued = 0;
       for (int kb = 0; kb < nk; ++kb) {
         if (*reinterpret_cast<volatile int*>(&sh.fail)) break;
-        const int s = kb % kStages;
+        const int q = kb % kStages;
         if (kb >= kStages &&
-            !mbar_wait(&sh.empty[s], static_cast<uint32_t>(((kb / kStages) - 1) & 1))) {
+            !mbar_wait(&sh.empty[q], static_cast<uint32_t>(((kb / kStages) - 1) & 1))) {
           sh.fail = 1;
           break;
         }
-        mbar_expect_tx(&sh.full[s], static_cast<uint32_t>(a_bytes + b_bytes));
+        mbar_expect_tx(&sh.full[q], static_cast<uint32_t>(a_bytes + b_bytes));
         const int x = static_cast<int>(k0 + static_cast<int64_t>(kb) * kBK);
-        tma_load_2d(stA(s), &mapQ, &sh.full[s], x, m0);
-        tma_load_2d(stB(s), &mapX, &sh.full[s], x, 0);
+        tma_load_2d(stA(q), &mapQ, &sh.full[q], x, m0);
+        tma_load_2d(stB(q), &mapX, &sh.full[q], x, 0);
         issued = kb + 1;
       }
       if (*reinterpret_cast<volatile int*>(&sh.fail)) {
@@ -124,42 +147,80 @@ tc_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
           mbar_wait(&sh.full[kb % kStages], static_cast<uint32_t>((kb / kStages) & 1));
       }
     }
-  } else {
-    // ---------------------------------------------- split + MMA (8 warps)
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % kStages;
-      const uint32_t ph = static_cast<uint32_t>((kb / kStages) & 1);
-      if (!mbar_wait(&sh.full[s], ph)) sh.fail = 1;
-      split_tf32<kSplit>(reinterpret_cast<float4*>(stA(s)), reinterpret_cast<float4*>(stAlo(s)),
-                         a_bytes / 16, tid);
-      split_tf32<kSplit>(reinterpret_cast<float4*>(stB(s)), reinterpret_cast<float4*>(stBlo(s)),
-                         b_bytes / 16, tid);
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      named_sync(1, kSplit);
-      if (tid == 0) {
-        const int stop = *reinterpret_cast<volatile int*>(&sh.fail);
-        if (!stop) {
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint64_t a = sdesc(smem_u32(stA(s))), al = sdesc(smem_u32(stAlo(s)));
-          const uint64_t b = sdesc(smem_u32(stB(s))), bl = sdesc(smem_u32(stBlo(s)));
-#pragma unroll
-          for (int k8 = 0; k8 < kBK / 8; ++k8) {  // K = 8 TF32 = 32 bytes per MMA
-            const uint64_t adv = static_cast<uint64_t>((k8 * 32) >> 4);
-            mma_tf32(tmem, a + adv, b + adv, idesc, (kb > 0 || k8 > 0) ? 1u : 0u);
-            mma_tf32(tmem, al + adv, b + adv, idesc, 1u);
-            mma_tf32(tmem, a + adv, bl + adv, idesc, 1u);
-          }
-          mma_commit(&sh.empty[s]);  // frees the stage for the producer
+  } else if (warp == kSplit / 32 + 1) {
+    // ---------------------------------------------- MMA issuer (one lane)
+    if ((tid & 31) == 0) {
+      for (int kb = 0; kb < nk; ++kb) {
+        const int q = kb % kStages, p = kb % kSide;
+        if (*reinterpret_cast<volatile int*>(&sh.fail)) break;
+        if (!mbar_wait(&sh.split[p], static_cast<uint32_t>((kb / kSide) & 1))) {
+          sh.fail = 1;
+          break;
         }
-        sh.stop = stop;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t ah = tmem + kSlot0 + static_cast<uint32_t>(p * 64), al = ah + 32;
+        const uint64_t b = sdesc(smem_u32(stB(q))), bl = sdesc(smem_u32(stBlo(p)));
+#pragma unroll
+        for (int k8 = 0; k8 < kBK / 8; ++k8) {  // K = 8 TF32 = 32 bytes per MMA
+          const uint64_t adv = static_cast<uint64_t>((k8 * 32) >> 4);
+          const uint32_t ak = static_cast<uint32_t>(k8 * 8);
+          mma_tf32_tmem_a(tmem, ah + ak, b + adv, idesc, (kb > 0 || k8 > 0) ? 1u : 0u);
+          mma_tf32_tmem_a(tmem, al + ak, b + adv, idesc, 1u);
+          mma_tf32_tmem_a(tmem, ah + ak, bl + adv, idesc, 1u);
+        }
+        mma_commit(&sh.empty[q]);  // frees the stage for the producer
+        mma_commit(&sh.sfree[p]);  // and the split slot for the split warps
       }
-      named_sync(1, kSplit);
-      if (*reinterpret_cast<volatile int*>(&sh.stop)) break;
+      // completes once every MMA issued above has (the accumulator is read,
+      // or the tensor memory freed, only after it)
+      mma_commit(&sh.done);
     }
-    // every MMA issued must complete before the accumulator is read (or
-    // the tensor memory freed, on the failure path)
-    if (tid == 0) mma_commit(&sh.done);
-    if (!mbar_wait(&sh.done, 0)) sh.fail = 1;
+  } else {
+    // ---------------------------------------------- split (8 warps)
+    for (int kb = 0; kb < nk; ++kb) {
+      const int q = kb % kStages, p = kb % kSide;
+      bool bad = *reinterpret_cast<volatile int*>(&sh.fail) != 0;
+      if (!bad && !mbar_wait(&sh.full[q], static_cast<uint32_t>((kb / kStages) & 1))) {
+        sh.fail = 1;
+        bad = true;
+      }
+      // the split slot's previous tile has been consumed by its MMAs
+      if (!bad && kb >= kSide &&
+          !mbar_wait(&sh.sfree[p], static_cast<uint32_t>(((kb / kSide) - 1) & 1))) {
+        sh.fail = 1;
+        bad = true;
+      }
+      // the tensor-memory stores below are warp-collective: leave together
+      if (__any_sync(0xffffffffu, bad)) break;
+      if (warp < 4) {
+        // row tid of the Q tile: 16-byte chunk c sits at chunk c ^ (row & 7)
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const float4* row = reinterpret_cast<const float4*>(stA(q) + tid * 128);
+        float v[32];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const float4 f = row[c ^ (tid & 7)];
+          v[4 * c] = f.x; v[4 * c + 1] = f.y; v[4 * c + 2] = f.z; v[4 * c + 3] = f.w;
+        }
+        uint32_t h[32], l[32];
+        split32(v, h, l);
+        const uint32_t ta = tmem + (static_cast<uint32_t>(warp * 32) << 16) + kSlot0 +
+                            static_cast<uint32_t>(p * 64);
+        tmem_st32(ta, h);
+        tmem_st32(ta + 32, l);
+        tmem_st_wait();
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      } else {
+        split_lo_tf32<kSplit - 128>(reinterpret_cast<const float4*>(stB(q)),
+                                    reinterpret_cast<float4*>(stBlo(p)), b_bytes / 16,
+                                    tid - 128);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      }
+      mbar_arrive(&sh.split[p]);
+    }
+    // (twice the limit: after a failure the MMA warp may first spend one
+    // limit on a stage that never came)
+    if (warp < 4 && !mbar_wait(&sh.done, 0, 2 * kWaitNs)) sh.fail = 1;
   }
   __syncthreads();
   const bool good = !sh.fail;
@@ -194,7 +255,7 @@ tc_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
                  : "memory");
   }
 }
@@ -277,7 +338,8 @@ bool tc_dot_supported(int64_t n, const float* Q, int64_t ldq, int i, const float
 
 int64_t tc_dot_part_size(int64_t n, int i, int s) {
   const int tiles = (i + kBM - 1) / kBM;
-  int64_t S = (static_cast<int64_t>(device_sm_count()) * 2 + tiles - 1) / tiles;
+  // one wave: a CTA holds a whole SM (shared memory, 512 TMEM columns)
+  int64_t S = static_cast<int64_t>(device_sm_count()) / tiles;
   const int64_t maxS = n / (8 * kBK);
   if (S > maxS) S = maxS;
   if (S < 1) S = 1;
@@ -315,7 +377,8 @@ void tc_dot(int64_t n, const float* Q, int64_t ldq, int i, const float* X, int64
   int* err = tc_err_flag();
   const int BN = (s + 15) / 16 * 16;
   const int tiles = (i + kBM - 1) / kBM;
-  int64_t S = (static_cast<int64_t>(device_sm_count()) * 2 + tiles - 1) / tiles;
+  // one wave: a CTA holds a whole SM (shared memory, 512 TMEM columns)
+  int64_t S = static_cast<int64_t>(device_sm_count()) / tiles;
   const int64_t maxS = n / (8 * kBK);
   if (S > maxS) S = maxS;
   if (S < 1) S = 1;
@@ -326,8 +389,11 @@ void tc_dot(int64_t n, const float* Q, int64_t ldq, int i, const float* X, int64
   CUtensorMap mq, mx;
   SG_REQUIRE(make_map(&mq, Q, n, i, ldq, kBM) && make_map(&mx, X, n, s, ldx, BN), SG_ECUDA,
              "cuTensorMapEncodeTiled failed");
-  auto smem_for = [](int bn) { return kStages * (2 * kBM * kBK * 4 + 2 * bn * kBK * 4) + 1024; };
-  const int smem = smem_for(BN);
+  auto smem_for = [](int bn) {
+    return kStages * (kBM * kBK * 4 + bn * kBK * 4) + kSide * bn * kBK * 4 + 1024;
+  };
+  // the largest size for every s: one CTA per SM
+  const int smem = smem_for(kMaxN);
   static bool configured = false;
   if (!configured) {
     SG_CUDA(cudaFuncSetAttribute(tc_dot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

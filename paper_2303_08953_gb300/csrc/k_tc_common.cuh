@@ -117,6 +117,45 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b,
       : "memory");
 }
 
+// The same MMA with the A operand in tensor memory: row m of A in lane m,
+// its K = 8 TF32 values in 8 consecutive 32-bit columns from atmem.
+__device__ __forceinline__ void mma_tf32_tmem_a(uint32_t dtmem, uint32_t atmem, uint64_t b,
+                                                uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(dtmem),
+      "r"(atmem), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// This thread's lane, 32 consecutive 32-bit columns from taddr (32x32b
+// shape: warp w reaches lanes 32 (w % 4) .. 32 (w % 4) + 31).
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+      "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]),
+      "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]),
+      "r"(v[29]), "r"(v[30]), "r"(v[31])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// 32 FP32 values -> TF32 hi part (low 13 mantissa bits cleared) and the
+// exact FP32 remainder, as 32-bit words for tmem_st32
+__device__ __forceinline__ void split32(const float* v, uint32_t* hi, uint32_t* lo) {
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    const uint32_t h = __float_as_uint(v[k]) & 0xFFFFE000u;
+    hi[k] = h;
+    lo[k] = __float_as_uint(v[k] - __uint_as_float(h));
+  }
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -139,6 +178,23 @@ __device__ __forceinline__ void split_tf32(float4* hi, float4* lo, int count4, i
   }
 }
 
+
+// The remainder alone, for an operand whose raw FP32 words serve as the hi
+// part (kind::tf32 ignores each word's low 13 mantissa bits).
+template <int NT>
+__device__ __forceinline__ void split_lo_tf32(const float4* src, float4* lo, int count4,
+                                              int tid) {
+#pragma unroll 4
+  for (int e = tid; e < count4; e += NT) {
+    const float4 v = src[e];
+    float4 l;
+    l.x = v.x - __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+    l.y = v.y - __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+    l.z = v.z - __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+    l.w = v.w - __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+    lo[e] = l;
+  }
+}
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");

@@ -4,18 +4,18 @@
 // D (128 rows of X x s) = Q (128 rows x i) . W (i x s) on tcgen05 (kind::tf32,
 // FP32 accumulator in tensor memory).  Q is column-major, so TMA delivers
 // its tile row-contiguous: four 32-row x 32-column boxes per stage, each
-// 32 lines of 128 B (one line per column of Q, 128-byte swizzle).  The
-// split warps transpose each box into the K-major 128-byte-swizzled layout
-// the MMA reads (one 128 B row of 32 k-values per row of X) while they
-// split it into a TF32 hi part and its FP32 remainder; the lane mapping
-// (8 rows x 4 columns per warp instruction) keeps the stores free of bank
-// conflicts.  W is tiny: a prologue kernel writes its hi part and
-// remainder as FP32 arrays that TMA loads as K-major tiles.  hi*hi +
-// lo*hi + hi*lo is accumulated.
+// 32 lines of 128 B (one line per column of Q, 128-byte swizzle).  Each
+// split thread owns one row of the tile (its tensor-memory lane), gathers
+// that row's 32 values from the box (one 128 B line per column: a warp's
+// loads are conflict-free) and stores the TF32 hi part and the FP32
+// remainder into tensor memory, where the MMA takes its A operand -- the
+// transpose to the K-major layout costs no shared-memory writes.  W is
+// tiny: a prologue kernel writes its hi part and remainder as FP32 arrays
+// that TMA loads as K-major tiles.  hi*hi + lo*hi + hi*lo is accumulated.
 //
 // Persistent and warp-specialised: one CTA per SM walks 128-row tiles;
-//   warp 8 (one lane) issues the TMA loads of a 2-stage ring,
-//   warps 4-7 split each Q tile into hi/lo,
+//   warp 8 (one lane) issues the TMA loads of a 3-stage ring,
+//   warps 4-7 split each Q tile into hi/lo in tensor memory,
 //   warp 9 (one lane) issues the MMAs into one of two TMEM accumulators,
 //   warps 0-3 (the TMEM lane owners) read an accumulator back while the
 //   next tile accumulates into the other.  The tile of X goes through
@@ -40,9 +40,11 @@ using namespace tc;
 
 constexpr int kRows = 128;      // rows of X per tile (MMA M)
 constexpr int kKC = 32;         // columns of Q (K) per stage
-constexpr int kStages = 2;
+constexpr int kStages = 3;
 constexpr int kThreads = 320;   // 10 warps
 constexpr int kMaxN = 128;
+constexpr uint32_t kTmemCols = 512;  // accumulators at 0 and 128, Q hi/lo slots
+constexpr uint32_t kSlot0 = 256;     // stage q: hi at 256 + 64 q, lo at + 32
 
 struct __align__(8) UpdShared {
   uint64_t full[kStages];
@@ -68,7 +70,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapQ,
       (reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~static_cast<uintptr_t>(1023));
   constexpr int a_bytes = kRows * kKC * 4;  // 16 KB: four 4 KB boxes
   const int b_bytes = BN * kKC * 4;
-  const int stage_bytes = 3 * a_bytes + 2 * b_bytes;  // raw, hi, lo, B hi, B lo
+  const int stage_bytes = a_bytes + 2 * b_bytes;  // Q boxes, W hi, W lo
   __shared__ UpdShared sh;
 
   const int tid = threadIdx.x;
@@ -99,7 +101,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapQ,
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&sh.tmem_base)),
-                 "r"(256)
+                 "r"(kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -109,10 +111,8 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapQ,
   const uint32_t tmem = sh.tmem_base;
 
   auto stRaw = [&](int q) { return base + q * stage_bytes; };
-  auto stA = [&](int q) { return base + q * stage_bytes + a_bytes; };
-  auto stAlo = [&](int q) { return base + q * stage_bytes + 2 * a_bytes; };
-  auto stB = [&](int q) { return base + q * stage_bytes + 3 * a_bytes; };
-  auto stBlo = [&](int q) { return base + q * stage_bytes + 3 * a_bytes + b_bytes; };
+  auto stB = [&](int q) { return base + q * stage_bytes + a_bytes; };
+  auto stBlo = [&](int q) { return base + q * stage_bytes + a_bytes + b_bytes; };
   float* xs = reinterpret_cast<float*>(base + kStages * stage_bytes);  // [BN][128]
   const uint32_t x_bytes = static_cast<uint32_t>(kRows * BN * 4);
   auto fail_now = [&]() {
@@ -152,31 +152,30 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapQ,
     // ------------------------------------------------ hi/lo split of Q
     const int st = tid - 128;
     for (int c = 0; c < total; ++c) {
-      if (*reinterpret_cast<volatile int*>(&sh.fail)) break;
       const int q = c % kStages;
-      if (!mbar_wait(&sh.full[q], static_cast<uint32_t>((c / kStages) & 1))) {
+      bool bad = *reinterpret_cast<volatile int*>(&sh.fail) != 0;
+      if (!bad && !mbar_wait(&sh.full[q], static_cast<uint32_t>((c / kStages) & 1))) {
         fail_now();
-        break;
+        bad = true;
       }
-      // slot sl covers rows rb*8 .. +7 and columns kg*4 .. +3 of box g;
-      // lane -> (row r8 = lane & 7, column kq = lane >> 3)
-      const float* raw = reinterpret_cast<const float*>(stRaw(q));
-      float* hi = reinterpret_cast<float*>(stA(q));
-      float* lo = reinterpret_cast<float*>(stAlo(q));
-      const int w4 = st >> 5, ln = st & 31, r8 = ln & 7, kq = ln >> 3;
-#pragma unroll 4
-      for (int it = 0; it < 32; ++it) {
-        const int sl = it * 4 + w4;
-        const int g = sl >> 5, rb = (sl >> 3) & 3, kg = sl & 7;
-        const int r = rb * 8 + r8, k = kg * 4 + kq;
-        const float v = raw[g * 1024 + k * 32 + ((((r >> 2) ^ (k & 7)) << 2) | (r & 3))];
-        const int m = g * 32 + r;
-        const int d = m * 32 + ((((k >> 2) ^ (m & 7)) << 2) | (k & 3));
-        const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-        hi[d] = h;
-        lo[d] = v - h;
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      // the tensor-memory stores below are warp-collective: leave together
+      if (__any_sync(0xffffffffu, bad)) break;
+      // row st of the tile is row r = st & 31 of box g = st >> 5; element
+      // (r, k) sits in line k at 16-byte chunk (r >> 2) ^ (k & 7)
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const float* raw = reinterpret_cast<const float*>(stRaw(q)) + (st >> 5) * 1024;
+      const int r = st & 31;
+      float v[32];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) v[k] = raw[k * 32 + ((((r >> 2) ^ (k & 7)) << 2) | (r & 3))];
+      uint32_t h[32], l[32];
+      split32(v, h, l);
+      const uint32_t ta = tmem + (static_cast<uint32_t>((warp - 4) * 32) << 16) + kSlot0 +
+                          static_cast<uint32_t>(q * 64);
+      tmem_st32(ta, h);
+      tmem_st32(ta + 32, l);
+      tmem_st_wait();
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       mbar_arrive(&sh.split[q]);
     }
   } else if (warp == 9) {
@@ -200,14 +199,15 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapQ,
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint64_t ah = sdesc(smem_u32(stA(q))), al = sdesc(smem_u32(stAlo(q)));
+          const uint32_t ah = tmem + kSlot0 + static_cast<uint32_t>(q * 64), al = ah + 32;
           const uint64_t bh = sdesc(smem_u32(stB(q))), bl = sdesc(smem_u32(stBlo(q)));
 #pragma unroll
           for (int k8 = 0; k8 < kKC / 8; ++k8) {  // K = 8 TF32 = 32 bytes per MMA
             const uint64_t adv = static_cast<uint64_t>((k8 * 32) >> 4);
-            mma_tf32(dt, ah + adv, bh + adv, idesc, (kc > 0 || k8 > 0) ? 1u : 0u);
-            mma_tf32(dt, al + adv, bh + adv, idesc, 1u);
-            mma_tf32(dt, ah + adv, bl + adv, idesc, 1u);
+            const uint32_t ak = static_cast<uint32_t>(k8 * 8);
+            mma_tf32_tmem_a(dt, ah + ak, bh + adv, idesc, (kc > 0 || k8 > 0) ? 1u : 0u);
+            mma_tf32_tmem_a(dt, al + ak, bh + adv, idesc, 1u);
+            mma_tf32_tmem_a(dt, ah + ak, bl + adv, idesc, 1u);
           }
           mma_commit(&sh.empty[q]);
         }
@@ -293,7 +293,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapQ,
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
                  : "memory");
   }
 }
@@ -394,9 +394,11 @@ void tc_update(int64_t n, const float* Q, int64_t ldq, int i, const double* W, i
                  make_map(&mx, X, n, s, ldx, kRows, BN, CU_TENSOR_MAP_SWIZZLE_NONE),
              SG_ECUDA, "cuTensorMapEncodeTiled failed");
   auto smem_for = [](int bn) {
-    return kStages * (3 * kRows * kKC * 4 + 2 * bn * kKC * 4) + kRows * bn * 4 + 1024;
+    return kStages * (kRows * kKC * 4 + 2 * bn * kKC * 4) + kRows * bn * 4 + 1024;
   };
-  const int smem = smem_for(BN);
+  // the largest size for every s: one CTA per SM (the kernel allocates all
+  // 512 TMEM columns)
+  const int smem = smem_for(kMaxN);
   static bool configured = false;
   if (!configured) {
     SG_CUDA(cudaFuncSetAttribute(tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
