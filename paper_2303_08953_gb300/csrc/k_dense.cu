@@ -183,8 +183,9 @@ void launch_reduce(int M, int N, int S, const double* part, double* W, int ldw,
 // but without the square tiles' waste: a thread owns one 4 x 4 block
 // (bi <= bj) of the upper triangle, the blocks numbered column by column
 // (block t = bj (bj + 1) / 2 + bi), so only the diagonal blocks compute
-// entries below the diagonal.  CTA (p, z) takes blocks p*128 .. p*128+127
-// over rows [z rows, (z+1) rows): it stages each 32-row slab of the
+// entries below the diagonal.  CTA (p, z) takes blocks p*T .. p*T+T-1
+// (T = min(128, the triangle rounded up to whole warps) threads) over rows
+// [z rows, (z+1) rows): it stages each 32-row slab of the
 // columns its blocks touch in shared memory (rows padded to 16 bytes) and
 // a thread forms 16 exact products per row from one float4 of each side.
 // The triangle's parts of one split are adjacent in launch order, so they
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(kGramThreads)
 gram_exact_kernel(int64_t K, int s, const float* __restrict__ X, int64_t ldx,
                   double* __restrict__ part, int64_t rows_per_split) {
   __shared__ __align__(16) float Ss[kGramBK][kGramLd];
-  const int t = blockIdx.x * kGramThreads + threadIdx.x;  // block of the triangle
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;  // block of the triangle
   const int nb = gram_blocks(s);
   // block t -> (bi, bj), bi <= bj
   int bj = static_cast<int>((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
@@ -210,7 +211,7 @@ gram_exact_kernel(int64_t K, int s, const float* __restrict__ X, int64_t ldx,
   const int bi = t - bj * (bj + 1) / 2;
   const bool active = t < nb;
   // columns this CTA reads: 0 .. 4 (last block's bj + 1)
-  int tl = blockIdx.x * kGramThreads + kGramThreads - 1;
+  int tl = blockIdx.x * blockDim.x + blockDim.x - 1;
   if (tl > nb - 1) tl = nb - 1;
   int bjl = static_cast<int>((sqrtf(8.0f * tl + 1.0f) - 1.0f) * 0.5f);
   while (bjl > 0 && bjl * (bjl + 1) / 2 > tl) --bjl;
@@ -225,7 +226,7 @@ gram_exact_kernel(int64_t K, int s, const float* __restrict__ X, int64_t ldx,
     for (int b = 0; b < 4; ++b) { acc[a][b] = 0.0f; comp[a][b] = 0.0f; }
   for (int64_t kb = k0; kb < k1; kb += kGramBK) {
     __syncthreads();  // the previous slab has been read
-    for (int e = threadIdx.x; e < kGramBK * ncol; e += kGramThreads) {
+    for (int e = threadIdx.x; e < kGramBK * ncol; e += blockDim.x) {
       const int kk = e % kGramBK, c = e / kGramBK;
       const int64_t k = kb + kk;
       Ss[kk][c] = (k < k1 && c < s) ? X[k + c * ldx] : 0.0f;
@@ -265,11 +266,21 @@ gram_exact_kernel(int64_t K, int s, const float* __restrict__ X, int64_t ldx,
     }
 }
 
-// splits of the Gram kernel: about five 128-thread CTAs per SM in all,
-// >= 4 slabs per split
+// threads per Gram CTA: the triangle rounded up to whole warps, <= 128
+int gram_cta_threads(int s) {
+  const int t = (gram_blocks(s) + 31) / 32 * 32;
+  return t < kGramThreads ? t : kGramThreads;
+}
+
+// splits of the Gram kernel: as many CTAs as fit on the SMs at 80
+// registers a thread (up to 8 per SM), >= 4 slabs per split
 int64_t gram_splits(int64_t n, int s, int64_t* rows) {
-  const int parts = (gram_blocks(s) + kGramThreads - 1) / kGramThreads;
-  int64_t S = (5 * static_cast<int64_t>(device_sm_count()) + parts - 1) / parts;
+  const int T = gram_cta_threads(s);
+  const int parts = (gram_blocks(s) + T - 1) / T;
+  int per_sm = 65536 / (80 * T);
+  if (per_sm > 8) per_sm = 8;
+  if (per_sm < 1) per_sm = 1;
+  int64_t S = (per_sm * static_cast<int64_t>(device_sm_count()) + parts - 1) / parts;
   const int64_t maxS = (n + 4 * kGramBK - 1) / (4 * kGramBK);
   if (S > maxS) S = maxS;
   if (S < 1) S = 1;
@@ -383,8 +394,9 @@ void block_dot_impl(int64_t n, const T* Q, int64_t ldq, int i, const T* X,
     int64_t rows = 0;
     const int64_t S = gram_splits(n, s, &rows);
     SG_REQUIRE(S * s * s <= part_cap, SG_EINVAL, "block_dot: workspace too small");
-    const int parts = (gram_blocks(s) + kGramThreads - 1) / kGramThreads;
-    gram_exact_kernel<<<dim3(parts, static_cast<unsigned>(S)), kGramThreads, 0, st>>>(
+    const int nt = gram_cta_threads(s);
+    const int parts = (gram_blocks(s) + nt - 1) / nt;
+    gram_exact_kernel<<<dim3(parts, static_cast<unsigned>(S)), nt, 0, st>>>(
         n, s, reinterpret_cast<const float*>(X), ldx, part, rows);
     SG_LAUNCH_CHECK();
     launch_reduce(s, s, static_cast<int>(S), part, W, ldw, true, st);
