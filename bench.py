@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "time to relres 1e-10: FP64 vs FP32-basis+IR, fwd+adjoint; % HBM roofline"
 VALUE_IS = ("seconds per FP64 adaptive s-step GMRES solve to relres 1e-10; the FP32-basis+IR "
             "and forward+adjoint times are in fp32_ir / fwd_adjoint, the SpMV % of HBM in "
-            "roofline_spmv")
+            "roofline_spmv, the FP32-basis block kernels' rooflines in roofline_fp32")
 GRID = 128
 SOLVE_KW = dict(m=240, s=0, s_min=20, s_max=120, tol=1e-10)
 FP64_ALU_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12   # 152 SMs x 2.07 GHz x 4 flop/clk
@@ -160,6 +160,19 @@ def workload(grid):
 # DRAM bytes per row of the FP64 block dot (i = 107, s = 106) from one ncu
 # capture at n = 2^20: read 2,291,351,000 + write 5,751,296 bytes.
 DOT64_DRAM_BYTES_PER_ROW = (2_291_351_000 + 5_751_296) / (1 << 20)
+
+
+# DRAM bytes per row of the FP32 tensor-core block dot (W = Q^T X) and
+# update (X -= Q W) at i = 107, s = 106, from ncu captures at n = 2^20:
+# dot read 893,510,400 + write 4,590,336; update read 893,550,336 + write
+# 395,385,600.
+TCDOT_DRAM_BYTES_PER_ROW = (893_510_400 + 4_590_336) / (1 << 20)
+TCUPD_DRAM_BYTES_PER_ROW = (893_550_336 + 395_385_600) / (1 << 20)
+# FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz (FADD / FMUL / FFMA each one op)
+FP32_ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+# FP32 instructions per exact Gram product: product, FMA remainder, the six
+# additions of the two-sum, two additions into the compensation
+GRAM_OPS_PER_PRODUCT = 10
 
 
 def spmv_bytes(A):
@@ -362,6 +375,43 @@ def run_ours(args):
         "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
         "frac": round(gbs / hbm, 4), "traffic": None,
         "peak_source": "MEASURED_PEAKS.json hbm_gbs" if pk else "fallback"}
+
+    # the FP32-basis path's block kernels at the same block shape
+    def event_ms(fn, reps=5):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+    Q32 = torch.randn(i_blk, n, dtype=torch.float32, device=dev)
+    X32 = torch.randn(s_blk, n, dtype=torch.float32, device=dev)
+    W64 = torch.randn(s_blk, i_blk, dtype=torch.float64, device=dev)
+    t_tcd = event_ms(lambda: solver.block_dot32(Q32, X32)) / 1e3
+    t_tcu = event_ms(lambda: solver.block_update32(Q32, W64, X32)) / 1e3
+    t_gram = event_ms(lambda: solver.block_dot32(X32, X32, sym=True)) / 1e3
+    del Q32, X32, W64
+    b_tcd = 4.0 * n * (i_blk + s_blk)
+    b_tcu = 4.0 * n * (i_blk + 2 * s_blk)
+    ops_gram = GRAM_OPS_PER_PRODUCT * n * s_blk * (s_blk + 1) / 2.0
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs" if pk else "fallback"
+    out["roofline_fp32"] = [
+        {"kernel": f"tc_dot FP32 basis (W = Q^T X on tcgen05, 3xTF32, i={i_blk}, s={s_blk})",
+         "bound": "hbm", "achieved": round(b_tcd / t_tcd / 1e9, 1), "peak": hbm,
+         "unit": "GB/s", "frac": round(b_tcd / t_tcd / 1e9 / hbm, 4),
+         "traffic": int(round(TCDOT_DRAM_BYTES_PER_ROW * n)), "peak_source": hbm_src},
+        {"kernel": f"tc_update FP32 basis (X -= Q W on tcgen05, 3xTF32, i={i_blk}, s={s_blk})",
+         "bound": "hbm", "achieved": round(b_tcu / t_tcu / 1e9, 1), "peak": hbm,
+         "unit": "GB/s", "frac": round(b_tcu / t_tcu / 1e9 / hbm, 4),
+         "traffic": int(round(TCUPD_DRAM_BYTES_PER_ROW * n)), "peak_source": hbm_src},
+        {"kernel": f"gram_exact FP32 basis (X^T X, exact products, s={s_blk})",
+         "bound": "alu", "achieved": round(ops_gram / t_gram / 1e12, 2),
+         "peak": round(FP32_ALU_PEAK_TOPS, 2), "unit": "T FP32-op/s",
+         "frac": round(ops_gram / t_gram / 1e12 / FP32_ALU_PEAK_TOPS, 4), "traffic": None,
+         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz"}]
 
     # ---- end to end through the public API from host buffers
     rp, ci, va = A.rowptr, A.colind, A.val
