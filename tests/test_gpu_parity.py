@@ -248,10 +248,14 @@ def test_block_dot_f32_tensor_cores(solver, n, i, s):
         assert np.all(err <= 2.0 ** -18 * scale), (err / scale).max()
 
 
-@pytest.mark.parametrize("n,s", [(4133, 6), (70001, 33), (70001, 120)])
+@pytest.mark.parametrize("n,s", [(1, 5), (70001, 1), (4133, 6), (70001, 33), (70001, 120),
+                                 (4133, 130)])
 def test_gram_f32_is_nearly_exact(solver, n, s):
     """The FP32 Gram uses exact products and two-sum accumulation: its
-    error is at the eps_32^2 level relative to sum |x_k y_k|."""
+    error is at the eps_32^2 level relative to sum |x_k y_k|.  Up to 128
+    columns the triangle kernel computes it (one row, one column and a
+    partial last 4 x 4 block included); 130 columns take the square-tile
+    kernel."""
     rng = np.random.default_rng(400 + s)
     X = rng.standard_normal((s, n)).astype(np.float32)
     Xd = dev(X, torch.float32)
