@@ -3,13 +3,15 @@
 //
 // D (128 rows of X x s) = Q (128 rows x i) . W (i x s) on tcgen05 (kind::tf32,
 // FP32 accumulator in tensor memory).  Q is column-major, so TMA delivers
-// its tile row-contiguous: four 32-row x 32-column boxes per stage, each
-// 32 lines of 128 B (one line per column of Q, 128-byte swizzle).  Each
-// split thread owns one row of the tile (its tensor-memory lane), gathers
-// that row's 32 values from the box (one 128 B line per column: a warp's
-// loads are conflict-free) and stores the TF32 hi part and the FP32
-// remainder into tensor memory, where the MMA takes its A operand -- the
-// transpose to the K-major layout costs no shared-memory writes.  W is
+// its tile row-contiguous: one unswizzled 128-row x 32-column box per
+// stage, a 512-byte line per column of Q (TMA streams 128-byte lines at
+// only ~4.7 TB/s on this chip, 256- and 512-byte lines at the full HBM
+// rate).  Each split thread owns one row of the tile (its tensor-memory
+// lane), gathers that row's 32 values from the box (a warp reads 128
+// contiguous bytes per column: no bank conflicts) and stores the TF32 hi
+// part and the FP32 remainder into tensor memory, where the MMA takes its A
+// operand -- the transpose to the K-major layout costs no shared-memory
+// writes.  W is
 // tiny: a prologue kernel writes its hi part and remainder as FP32 arrays
 // that TMA loads as K-major tiles.  hi*hi + lo*hi + hi*lo is accumulated.
 //
@@ -135,9 +137,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapQ,
         const int lt = c / KC, kc = c % KC;
         const int64_t row0 = (static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(lt) * gridDim.x) * kRows;
         mbar_expect_tx(&sh.full[q], static_cast<uint32_t>(a_bytes + 2 * b_bytes));
-        for (int g = 0; g < 4; ++g)
-          tma_load_2d(stRaw(q) + g * 4096, &mapQ, &sh.full[q], static_cast<int>(row0 + g * 32),
-                      kc * kKC);
+        tma_load_2d(stRaw(q), &mapQ, &sh.full[q], static_cast<int>(row0), kc * kKC);
         tma_load_2d(stB(q), &mapWh, &sh.full[q], kc * kKC, 0);
         tma_load_2d(stBlo(q), &mapWl, &sh.full[q], kc * kKC, 0);
         ++issued;
@@ -160,14 +160,13 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapQ,
       }
       // the tensor-memory stores below are warp-collective: leave together
       if (__any_sync(0xffffffffu, bad)) break;
-      // row st of the tile is row r = st & 31 of box g = st >> 5; element
-      // (r, k) sits in line k at 16-byte chunk (r >> 2) ^ (k & 7)
+      // element (row st, column k) of the Q box sits at k * 128 + st (one
+      // 512-byte line per column of Q): a warp reads 128 contiguous bytes
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const float* raw = reinterpret_cast<const float*>(stRaw(q)) + (st >> 5) * 1024;
-      const int r = st & 31;
+      const float* raw = reinterpret_cast<const float*>(stRaw(q));
       float v[32];
 #pragma unroll
-      for (int k = 0; k < 32; ++k) v[k] = raw[k * 32 + ((((r >> 2) ^ (k & 7)) << 2) | (r & 3))];
+      for (int k = 0; k < 32; ++k) v[k] = raw[k * kRows + st];
       uint32_t h[32], l[32];
       split32(v, h, l);
       const uint32_t ta = tmem + (static_cast<uint32_t>((warp - 4) * 32) << 16) + kSlot0 +
@@ -389,7 +388,8 @@ void tc_update(int64_t n, const float* Q, int64_t ldq, int i, const double* W, i
   SG_LAUNCH_CHECK();
   const int BN = (s + 15) / 16 * 16;
   CUtensorMap mq, mh, ml, mx;
-  SG_REQUIRE(make_map(&mq, Q, n, i, ldq, 32, kKC) && make_map(&mh, hi, ldp, s, ldp, kKC, BN) &&
+  SG_REQUIRE(make_map(&mq, Q, n, i, ldq, kRows, kKC, CU_TENSOR_MAP_SWIZZLE_NONE) &&
+                 make_map(&mh, hi, ldp, s, ldp, kKC, BN) &&
                  make_map(&ml, lo, ldp, s, ldp, kKC, BN) &&
                  make_map(&mx, X, n, s, ldx, kRows, BN, CU_TENSOR_MAP_SWIZZLE_NONE),
              SG_ECUDA, "cuTensorMapEncodeTiled failed");
