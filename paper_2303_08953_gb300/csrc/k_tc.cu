@@ -4,35 +4,31 @@
 // Q (n x i) and X (n x s) are FP32 column-major, so Q^T and X^T are
 // K-major operands (K = the n rows) of a tcgen05 MMA with M = 128 columns
 // of Q per tile and N = s (rounded up to 16).  Each CTA reduces one range
-// of rows for one 128-column tile:
-//   * a producer warp (one lane) issues TMA loads of 32-row x 128 B tiles
-//     (128-byte swizzle) into a 6-stage ring guarded by mbarriers, each as
-//     soon as the MMAs of the stage's previous tile have completed; the
-//     split results live in a separate 2-slot ring (the X remainder in
-//     shared memory, Q's hi/lo in tensor memory), so the load ring only
-//     holds raw tiles and keeps ~4 of them in flight;
-//   * warps 0-3, the owners of tensor-memory lanes 0-127, read one 128 B
-//     row of the Q tile each (32 values of one column of Q), split it into
-//     a TF32 "hi" part (low 13 mantissa bits cleared) and the exact FP32
-//     remainder "lo", and store both into tensor memory, where the MMA
-//     takes its A operand: shared memory then carries Q once (the TMA
-//     write and this read) instead of three more times;
-//   * warps 4-7 write the X tile's FP32 remainder beside it in shared
-//     memory; the raw tile itself serves as the hi part, because the tensor
-//     core reads a TF32 operand from the top 19 bits of each 32-bit word
-//     (measured on this chip: the same products as an explicit split);
-//     the eight split warps signal a per-stage mbarrier and go on to the
-//     next tile;
+// of rows for one 128-column tile, 64 rows (K) per step:
+//   * TMA streams 128-byte lines at only ~4.7 TB/s on this chip and
+//     256-byte lines at the full HBM rate.  Q never needs the MMA's swizzled
+//     shared-memory layout (it reaches the MMA through tensor memory), so
+//     its tile arrives as one unswizzled 64-row x 128-column box (a 256-byte
+//     line per column of Q) in a 2-slot ring; X, the shared-memory operand,
+//     arrives as two 128-byte-swizzled 32-row boxes per step in a 3-slot
+//     ring.  One producer lane issues both.
+//   * warps 0-3 own tensor-memory lanes 0-127, one column of Q each: a warp
+//     first permutes its 32 rows' 16-byte chunks in place (chunk c of row m
+//     to c ^ (m & 15), read and written two rows per instruction without
+//     bank conflicts), then each thread reads its row conflict-free, splits
+//     it into a TF32 hi part (low 13 mantissa bits cleared) and the exact
+//     FP32 remainder, and stores both into tensor memory; the Q slot is
+//     freed at once;
+//   * warps 4-7 write X's FP32 remainder beside it (the raw tile is its own
+//     hi part: kind::tf32 reads the top 19 bits of each 32-bit word); the
+//     split results live in a 2-slot ring freed by the MMAs;
 //   * an MMA warp (one lane) issues tcgen05.mma.kind::tf32 for
-//     hi*hi + lo*hi + hi*lo (the low*low term is below FP32 rounding), with
-//     the FP32 accumulator in tensor memory, and commits each stage's MMAs
-//     to an mbarrier that frees the stage;
+//     hi*hi + lo*hi + hi*lo (the low*low term is below FP32 rounding), A
+//     from tensor memory, B from shared memory, with the FP32 accumulator
+//     in tensor memory, and commits each step to the mbarriers that free
+//     its X slot and split slot;
 //   * the accumulator is read back with tcgen05.ld and written as one
 //     split partial; the fixed-order split reduction is the SIMT path's.
-// Shared-memory traffic per 32-row tile at i = s = 107 is ~130 KB (TMA
-// writes, the two splits, the MMA's three reads of X) where the version with
-// both splits in shared memory moved ~210 KB: shared-memory bandwidth, not
-// HBM, bounded that version.
 // Every wait is bounded: on timeout the kernel records an error code,
 // drains its own copies, frees its tensor memory and returns.
 #include <cuda.h>
@@ -50,18 +46,21 @@ namespace {
 using namespace tc;
 
 constexpr int kBM = 128;          // MMA M: columns of Q per tile
-constexpr int kBK = 32;           // rows per stage: 32 FP32 = one 128 B row
-constexpr int kStages = 6;        // load ring (Q tile + X tile)
+constexpr int kBK = 64;           // rows per step: two 32-row MMA K blocks
+constexpr int kAStages = 2;       // Q ring (unswizzled 64 x 128 boxes)
+constexpr int kBStages = 3;       // X ring (two swizzled 32-row boxes each)
 constexpr int kSide = 2;          // split ring (X remainder, Q hi/lo in TMEM)
 constexpr int kSplit = 256;       // 8 warps split tiles; warps 0-3 own TMEM lanes
 constexpr int kThreads = kSplit + 64;  // + the TMA producer warp, the MMA warp
 constexpr int kMaxN = 128;        // s <= 128 per launch
-constexpr uint32_t kTmemCols = 256;    // accumulator 0..127, Q hi/lo slots from 128
-constexpr uint32_t kSlot0 = 128;       // split slot p: hi at 128 + 64 p, lo at + 32
+constexpr uint32_t kTmemCols = 512;    // accumulator 0..127, split slots from 128
+constexpr uint32_t kSlot0 = 128;       // slot p: Q hi at 128 + 128 p, lo at + 64
 
 struct __align__(8) TcShared {
-  uint64_t full[kStages];
-  uint64_t empty[kStages];
+  uint64_t afull[kAStages];
+  uint64_t afree[kAStages];
+  uint64_t bfull[kBStages];
+  uint64_t bfree[kBStages];
   uint64_t split[kSide];
   uint64_t sfree[kSide];
   uint64_t done;
@@ -76,17 +75,18 @@ tc_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
               int BN, int64_t rows_per_split, double* __restrict__ part,
               int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char dsmem[];
-  // 1024-byte aligned tiles: per stage A (128 x 128 B) and B (BN x 128 B),
-  // then kSide B_lo slots (BN x 128 B)
+  // 1024-byte aligned: kAStages Q slots (128 x 256 B), kBStages X slots
+  // (two BN x 128 B boxes), kSide remainder slots (two BN x 128 B blocks)
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~static_cast<uintptr_t>(1023));
-  const int a_bytes = kBM * kBK * 4;
-  const int b_bytes = BN * kBK * 4;
-  const int stage_bytes = a_bytes + b_bytes;
+  constexpr int a_bytes = kBM * kBK * 4;  // 32 KB
+  const int b_half = BN * 32 * 4;         // one 32-row X box
+  const int b_bytes = 2 * b_half;
   __shared__ TcShared sh;
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
+  const int lane = tid & 31;
   const int m0 = blockIdx.x * kBM;
   const int64_t k0 = static_cast<int64_t>(blockIdx.z) * rows_per_split;
   const int64_t k1 = (k0 + rows_per_split < n) ? k0 + rows_per_split : n;
@@ -94,9 +94,13 @@ tc_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
   const uint32_t idesc = idesc_tf32(kBM, BN);
 
   if (tid == 0) {
-    for (int q = 0; q < kStages; ++q) {
-      mbar_init(&sh.full[q], 1);
-      mbar_init(&sh.empty[q], 1);
+    for (int q = 0; q < kAStages; ++q) {
+      mbar_init(&sh.afull[q], 1);
+      mbar_init(&sh.afree[q], 128);
+    }
+    for (int q = 0; q < kBStages; ++q) {
+      mbar_init(&sh.bfull[q], 1);
+      mbar_init(&sh.bfree[q], 1);
     }
     for (int p = 0; p < kSide; ++p) {
       mbar_init(&sh.split[p], kSplit);
@@ -118,58 +122,71 @@ tc_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = sh.tmem_base;
 
-  auto stA = [&](int q) { return base + q * stage_bytes; };
-  auto stB = [&](int q) { return base + q * stage_bytes + a_bytes; };
-  auto stBlo = [&](int p) { return base + kStages * stage_bytes + p * b_bytes; };
+  auto stA = [&](int q) { return base + q * a_bytes; };
+  auto stB = [&](int q) { return base + kAStages * a_bytes + q * b_bytes; };
+  auto stBlo = [&](int p) {
+    return base + kAStages * a_bytes + kBStages * b_bytes + p * b_bytes;
+  };
+  auto failed = [&]() { return *reinterpret_cast<volatile int*>(&sh.fail) != 0; };
 
   if (warp == kSplit / 32) {
     // ---------------------------------------------- TMA producer (one lane)
-    if ((tid & 31) == 0) {
+    if (lane == 0) {
       int issued = 0;
       for (int kb = 0; kb < nk; ++kb) {
-        if (*reinterpret_cast<volatile int*>(&sh.fail)) break;
-        const int q = kb % kStages;
-        if (kb >= kStages &&
-            !mbar_wait(&sh.empty[q], static_cast<uint32_t>(((kb / kStages) - 1) & 1))) {
+        if (failed()) break;
+        const int qa = kb % kAStages, qb = kb % kBStages;
+        if ((kb >= kAStages &&
+             !mbar_wait(&sh.afree[qa], static_cast<uint32_t>(((kb / kAStages) - 1) & 1))) ||
+            (kb >= kBStages &&
+             !mbar_wait(&sh.bfree[qb], static_cast<uint32_t>(((kb / kBStages) - 1) & 1)))) {
           sh.fail = 1;
           break;
         }
-        mbar_expect_tx(&sh.full[q], static_cast<uint32_t>(a_bytes + b_bytes));
         const int x = static_cast<int>(k0 + static_cast<int64_t>(kb) * kBK);
-        tma_load_2d(stA(q), &mapQ, &sh.full[q], x, m0);
-        tma_load_2d(stB(q), &mapX, &sh.full[q], x, 0);
+        mbar_expect_tx(&sh.afull[qa], static_cast<uint32_t>(a_bytes));
+        tma_load_2d(stA(qa), &mapQ, &sh.afull[qa], x, m0);
+        mbar_expect_tx(&sh.bfull[qb], static_cast<uint32_t>(b_bytes));
+        tma_load_2d(stB(qb), &mapX, &sh.bfull[qb], x, 0);
+        tma_load_2d(stB(qb) + b_half, &mapX, &sh.bfull[qb], x + 32, 0);
         issued = kb + 1;
       }
-      if (*reinterpret_cast<volatile int*>(&sh.fail)) {
-        // let this CTA's loads still in flight land (each is the latest
-        // use of its stage, so its parity identifies it)
-        for (int kb = (issued > kStages ? issued - kStages : 0); kb < issued; ++kb)
-          mbar_wait(&sh.full[kb % kStages], static_cast<uint32_t>((kb / kStages) & 1));
+      if (failed()) {
+        // let this CTA's loads still in flight land (each is the latest use
+        // of its slot, so its parity identifies it)
+        for (int kb = (issued > kAStages ? issued - kAStages : 0); kb < issued; ++kb)
+          mbar_wait(&sh.afull[kb % kAStages], static_cast<uint32_t>((kb / kAStages) & 1));
+        for (int kb = (issued > kBStages ? issued - kBStages : 0); kb < issued; ++kb)
+          mbar_wait(&sh.bfull[kb % kBStages], static_cast<uint32_t>((kb / kBStages) & 1));
       }
     }
   } else if (warp == kSplit / 32 + 1) {
     // ---------------------------------------------- MMA issuer (one lane)
-    if ((tid & 31) == 0) {
+    if (lane == 0) {
       for (int kb = 0; kb < nk; ++kb) {
-        const int q = kb % kStages, p = kb % kSide;
-        if (*reinterpret_cast<volatile int*>(&sh.fail)) break;
+        const int qb = kb % kBStages, p = kb % kSide;
+        if (failed()) break;
         if (!mbar_wait(&sh.split[p], static_cast<uint32_t>((kb / kSide) & 1))) {
           sh.fail = 1;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t ah = tmem + kSlot0 + static_cast<uint32_t>(p * 64), al = ah + 32;
-        const uint64_t b = sdesc(smem_u32(stB(q))), bl = sdesc(smem_u32(stBlo(p)));
+        const uint32_t ah = tmem + kSlot0 + static_cast<uint32_t>(p * 128), al = ah + 64;
 #pragma unroll
-        for (int k8 = 0; k8 < kBK / 8; ++k8) {  // K = 8 TF32 = 32 bytes per MMA
-          const uint64_t adv = static_cast<uint64_t>((k8 * 32) >> 4);
-          const uint32_t ak = static_cast<uint32_t>(k8 * 8);
-          mma_tf32_tmem_a(tmem, ah + ak, b + adv, idesc, (kb > 0 || k8 > 0) ? 1u : 0u);
-          mma_tf32_tmem_a(tmem, al + ak, b + adv, idesc, 1u);
-          mma_tf32_tmem_a(tmem, ah + ak, bl + adv, idesc, 1u);
+        for (int u = 0; u < 2; ++u) {  // 32-row K blocks
+          const uint64_t b = sdesc(smem_u32(stB(qb) + u * b_half));
+          const uint64_t bl = sdesc(smem_u32(stBlo(p) + u * b_half));
+#pragma unroll
+          for (int k8 = 0; k8 < 4; ++k8) {  // K = 8 TF32 = 32 bytes per MMA
+            const uint64_t adv = static_cast<uint64_t>((k8 * 32) >> 4);
+            const uint32_t ak = static_cast<uint32_t>(u * 32 + k8 * 8);
+            mma_tf32_tmem_a(tmem, ah + ak, b + adv, idesc, (kb > 0 || u > 0 || k8 > 0) ? 1u : 0u);
+            mma_tf32_tmem_a(tmem, al + ak, b + adv, idesc, 1u);
+            mma_tf32_tmem_a(tmem, ah + ak, bl + adv, idesc, 1u);
+          }
         }
-        mma_commit(&sh.empty[q]);  // frees the stage for the producer
-        mma_commit(&sh.sfree[p]);  // and the split slot for the split warps
+        mma_commit(&sh.bfree[qb]);  // frees the X slot for the producer
+        mma_commit(&sh.sfree[p]);   // and the split slot for the split warps
       }
       // completes once every MMA issued above has (the accumulator is read,
       // or the tensor memory freed, only after it)
@@ -178,40 +195,57 @@ tc_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
   } else {
     // ---------------------------------------------- split (8 warps)
     for (int kb = 0; kb < nk; ++kb) {
-      const int q = kb % kStages, p = kb % kSide;
-      bool bad = *reinterpret_cast<volatile int*>(&sh.fail) != 0;
-      if (!bad && !mbar_wait(&sh.full[q], static_cast<uint32_t>((kb / kStages) & 1))) {
-        sh.fail = 1;
-        bad = true;
-      }
-      // the split slot's previous tile has been consumed by its MMAs
-      if (!bad && kb >= kSide &&
-          !mbar_wait(&sh.sfree[p], static_cast<uint32_t>(((kb / kSide) - 1) & 1))) {
-        sh.fail = 1;
-        bad = true;
+      const int qa = kb % kAStages, qb = kb % kBStages, p = kb % kSide;
+      bool bad = failed();
+      if (!bad) {
+        const bool ok =
+            (warp < 4 ? mbar_wait(&sh.afull[qa], static_cast<uint32_t>((kb / kAStages) & 1))
+                      : mbar_wait(&sh.bfull[qb], static_cast<uint32_t>((kb / kBStages) & 1))) &&
+            // the split slot's previous step has been consumed by its MMAs
+            (kb < kSide ||
+             mbar_wait(&sh.sfree[p], static_cast<uint32_t>(((kb / kSide) - 1) & 1)));
+        if (!ok) {
+          sh.fail = 1;
+          bad = true;
+        }
       }
       // the tensor-memory stores below are warp-collective: leave together
       if (__any_sync(0xffffffffu, bad)) break;
       if (warp < 4) {
-        // row tid of the Q tile: 16-byte chunk c sits at chunk c ^ (row & 7)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const float4* row = reinterpret_cast<const float4*>(stA(q) + tid * 128);
-        float v[32];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const float4 f = row[c ^ (tid & 7)];
-          v[4 * c] = f.x; v[4 * c + 1] = f.y; v[4 * c + 2] = f.z; v[4 * c + 3] = f.w;
+        // this warp's rows 32w .. 32w + 31 of the Q slot, 256 B each:
+        // chunk c of row m moves to c ^ (m & 15), two rows per instruction
+        float4* rows = reinterpret_cast<float4*>(stA(qa)) + warp * 32 * 16;
+#pragma unroll 4
+        for (int pr = 0; pr < 16; ++pr) {
+          const int r = 2 * pr + (lane >> 4), c = lane & 15;
+          const float4 v = rows[r * 16 + c];
+          __syncwarp();
+          rows[r * 16 + (c ^ ((warp * 32 + r) & 15))] = v;
+          __syncwarp();
         }
-        uint32_t h[32], l[32];
-        split32(v, h, l);
+        // thread tid now reads its row: chunk c at c ^ (tid & 15)
+        const float4* row = reinterpret_cast<const float4*>(stA(qa)) + tid * 16;
         const uint32_t ta = tmem + (static_cast<uint32_t>(warp * 32) << 16) + kSlot0 +
-                            static_cast<uint32_t>(p * 64);
-        tmem_st32(ta, h);
-        tmem_st32(ta + 32, l);
+                            static_cast<uint32_t>(p * 128);
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          float v[32];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const float4 f = row[(half * 8 + c) ^ (tid & 15)];
+            v[4 * c] = f.x; v[4 * c + 1] = f.y; v[4 * c + 2] = f.z; v[4 * c + 3] = f.w;
+          }
+          uint32_t h[32], l[32];
+          split32(v, h, l);
+          tmem_st32(ta + static_cast<uint32_t>(half * 32), h);
+          tmem_st32(ta + 64 + static_cast<uint32_t>(half * 32), l);
+        }
         tmem_st_wait();
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(&sh.afree[qa]);  // the Q slot is free for the producer
       } else {
-        split_lo_tf32<kSplit - 128>(reinterpret_cast<const float4*>(stB(q)),
+        split_lo_tf32<kSplit - 128>(reinterpret_cast<const float4*>(stB(qb)),
                                     reinterpret_cast<float4*>(stBlo(p)), b_bytes / 16,
                                     tid - 128);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -219,7 +253,7 @@ tc_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
       mbar_arrive(&sh.split[p]);
     }
     // (twice the limit: after a failure the MMA warp may first spend one
-    // limit on a stage that never came)
+    // limit on a step that never came)
     if (warp < 4 && !mbar_wait(&sh.done, 0, 2 * kWaitNs)) sh.fail = 1;
   }
   __syncthreads();
@@ -229,7 +263,7 @@ tc_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
   } else if (warp < 4) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     // TMEM lane = accumulator row m (warp w owns lanes 32w..32w+31)
-    const int row = warp * 32 + (tid & 31);
+    const int row = warp * 32 + lane;
     const int m = m0 + row;
     double* P = part + static_cast<int64_t>(blockIdx.z) * M * N;
     for (int c0 = 0; c0 < BN; c0 += 16) {
@@ -277,15 +311,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 bool make_map(CUtensorMap* map, const float* base, int64_t rows, int64_t cols,
-              int64_t ld, int box_cols) {
+              int64_t ld, int box_rows, int box_cols, CUtensorMapSwizzle swz) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(rows), static_cast<cuuint64_t>(cols)};
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * sizeof(float)};
-  cuuint32_t box[2] = {static_cast<cuuint32_t>(kBK), static_cast<cuuint32_t>(box_cols)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(box_rows), static_cast<cuuint32_t>(box_cols)};
   cuuint32_t estr[2] = {1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims,
-            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
          CUDA_SUCCESS;
 }
@@ -387,10 +421,11 @@ void tc_dot(int64_t n, const float* Q, int64_t ldq, int i, const float* X, int64
   S = (n + rows - 1) / rows;
   SG_REQUIRE(S * i * s <= part_cap, SG_EINVAL, "tc_dot: workspace too small");
   CUtensorMap mq, mx;
-  SG_REQUIRE(make_map(&mq, Q, n, i, ldq, kBM) && make_map(&mx, X, n, s, ldx, BN), SG_ECUDA,
-             "cuTensorMapEncodeTiled failed");
+  SG_REQUIRE(make_map(&mq, Q, n, i, ldq, kBK, kBM, CU_TENSOR_MAP_SWIZZLE_NONE) &&
+                 make_map(&mx, X, n, s, ldx, 32, BN, CU_TENSOR_MAP_SWIZZLE_128B),
+             SG_ECUDA, "cuTensorMapEncodeTiled failed");
   auto smem_for = [](int bn) {
-    return kStages * (kBM * kBK * 4 + bn * kBK * 4) + kSide * bn * kBK * 4 + 1024;
+    return kAStages * kBM * kBK * 4 + (kBStages + kSide) * bn * kBK * 4 + 1024;
   };
   // the largest size for every s: one CTA per SM
   const int smem = smem_for(kMaxN);
