@@ -47,6 +47,7 @@ constexpr int kThreads = 320;   // 10 warps
 constexpr int kMaxN = 128;
 constexpr uint32_t kTmemCols = 512;  // accumulators at 0 and 128, Q hi/lo slots
 constexpr uint32_t kSlot0 = 256;     // stage q: hi at 256 + 64 q, lo at + 32
+constexpr int kSmemBytes = 230400;   // dynamic shared memory (+1 KB alignment slack)
 
 struct __align__(8) UpdShared {
   uint64_t full[kStages];
@@ -55,6 +56,7 @@ struct __align__(8) UpdShared {
   uint64_t accf[2];
   uint64_t acce[2];
   uint64_t xfull;
+  uint64_t wfull;  // the resident W (one load per CTA)
   uint64_t done;
   uint32_t tmem_base;
   int fail;
@@ -66,13 +68,17 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapQ,
                  const __grid_constant__ CUtensorMap mapWh,
                  const __grid_constant__ CUtensorMap mapWl,
                  const __grid_constant__ CUtensorMap mapX, int64_t n, int i, int s,
-                 int BN, float alpha, float beta, int* __restrict__ err) {
+                 int BN, float alpha, float beta, int nst, int wres,
+                 int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char dsmem[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~static_cast<uintptr_t>(1023));
-  constexpr int a_bytes = kRows * kKC * 4;  // 16 KB: four 4 KB boxes
+  constexpr int a_bytes = kRows * kKC * 4;  // 16 KB: one 128 x 32 box of Q
   const int b_bytes = BN * kKC * 4;
-  const int stage_bytes = a_bytes + 2 * b_bytes;  // Q boxes, W hi, W lo
+  // nst stages of the Q ring (<= kStages).  wres: W's hi/lo chunks for
+  // all K stay resident (loaded once per CTA) ahead of a Q-only ring;
+  // otherwise every stage carries its chunk of W hi and lo as well.
+  const int stage_bytes = wres ? a_bytes : a_bytes + 2 * b_bytes;
   __shared__ UpdShared sh;
 
   const int tid = threadIdx.x;
@@ -95,6 +101,7 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapQ,
       mbar_init(&sh.acce[b], 128);
     }
     mbar_init(&sh.xfull, 1);
+    mbar_init(&sh.wfull, 1);
     mbar_init(&sh.done, 1);
     sh.fail = 0;
     sh.epi_stop = 0;
@@ -112,10 +119,15 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapQ,
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = sh.tmem_base;
 
-  auto stRaw = [&](int q) { return base + q * stage_bytes; };
-  auto stB = [&](int q) { return base + q * stage_bytes + a_bytes; };
-  auto stBlo = [&](int q) { return base + q * stage_bytes + a_bytes + b_bytes; };
-  float* xs = reinterpret_cast<float*>(base + kStages * stage_bytes);  // [BN][128]
+  const int KCr = wres ? KC : 0;  // resident W chunks
+  unsigned char* ring = base + KCr * 2 * b_bytes;
+  auto stRaw = [&](int q) { return ring + q * stage_bytes; };
+  // W hi / lo of stage q (its chunk kc when resident)
+  auto stB = [&](int q, int kc) {
+    return wres ? base + kc * 2 * b_bytes : ring + q * stage_bytes + a_bytes;
+  };
+  auto stBlo = [&](int q, int kc) { return stB(q, kc) + b_bytes; };
+  float* xs = reinterpret_cast<float*>(ring + nst * stage_bytes);  // [BN][128]
   const uint32_t x_bytes = static_cast<uint32_t>(kRows * BN * 4);
   auto fail_now = [&]() {
     sh.fail = 1;
@@ -125,36 +137,48 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapQ,
   if (warp == 8) {
     // ------------------------------------------------ TMA producer
     if (lane == 0) {
+      if (wres && total > 0) {
+        // every chunk of W hi and lo, once (2 KC boxes of BN 128-byte lines)
+        mbar_expect_tx(&sh.wfull, static_cast<uint32_t>(KC * 2 * b_bytes));
+        for (int kc = 0; kc < KC; ++kc) {
+          tma_load_2d(stB(0, kc), &mapWh, &sh.wfull, kc * kKC, 0);
+          tma_load_2d(stBlo(0, kc), &mapWl, &sh.wfull, kc * kKC, 0);
+        }
+      }
       int issued = 0;
       for (int c = 0; c < total; ++c) {
         if (*reinterpret_cast<volatile int*>(&sh.fail)) break;
-        const int q = c % kStages;
-        if (c >= kStages &&
-            !mbar_wait(&sh.empty[q], static_cast<uint32_t>(((c / kStages) - 1) & 1))) {
+        const int q = c % nst;
+        if (c >= nst &&
+            !mbar_wait(&sh.empty[q], static_cast<uint32_t>(((c / nst) - 1) & 1))) {
           fail_now();
           break;
         }
         const int lt = c / KC, kc = c % KC;
         const int64_t row0 = (static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(lt) * gridDim.x) * kRows;
-        mbar_expect_tx(&sh.full[q], static_cast<uint32_t>(a_bytes + 2 * b_bytes));
+        mbar_expect_tx(&sh.full[q], static_cast<uint32_t>(wres ? a_bytes : a_bytes + 2 * b_bytes));
         tma_load_2d(stRaw(q), &mapQ, &sh.full[q], static_cast<int>(row0), kc * kKC);
-        tma_load_2d(stB(q), &mapWh, &sh.full[q], kc * kKC, 0);
-        tma_load_2d(stBlo(q), &mapWl, &sh.full[q], kc * kKC, 0);
+        if (!wres) {
+          tma_load_2d(stB(q, kc), &mapWh, &sh.full[q], kc * kKC, 0);
+          tma_load_2d(stBlo(q, kc), &mapWl, &sh.full[q], kc * kKC, 0);
+        }
         ++issued;
       }
       if (*reinterpret_cast<volatile int*>(&sh.fail)) {
-        // drain the loads still in flight (the latest use of each stage)
-        for (int c = (issued > kStages ? issued - kStages : 0); c < issued; ++c)
-          mbar_wait(&sh.full[c % kStages], static_cast<uint32_t>((c / kStages) & 1));
+        // drain the loads still in flight (the latest use of each stage,
+        // and the resident W)
+        for (int c = (issued > nst ? issued - nst : 0); c < issued; ++c)
+          mbar_wait(&sh.full[c % nst], static_cast<uint32_t>((c / nst) & 1));
+        if (wres && total > 0) mbar_wait(&sh.wfull, 0);
       }
     }
   } else if (warp >= 4 && warp < 8) {
     // ------------------------------------------------ hi/lo split of Q
     const int st = tid - 128;
     for (int c = 0; c < total; ++c) {
-      const int q = c % kStages;
+      const int q = c % nst;
       bool bad = *reinterpret_cast<volatile int*>(&sh.fail) != 0;
-      if (!bad && !mbar_wait(&sh.full[q], static_cast<uint32_t>((c / kStages) & 1))) {
+      if (!bad && !mbar_wait(&sh.full[q], static_cast<uint32_t>((c / nst) & 1))) {
         fail_now();
         bad = true;
       }
@@ -191,15 +215,16 @@ tc_update_kernel(const __grid_constant__ CUtensorMap mapQ,
         bool ok = true;
         for (int kc = 0; kc < KC; ++kc) {
           const int c = lt * KC + kc;
-          const int q = c % kStages;
-          if (!mbar_wait(&sh.split[q], static_cast<uint32_t>((c / kStages) & 1))) {
+          const int q = c % nst;
+          if ((c == 0 && wres && !mbar_wait(&sh.wfull, 0)) ||
+              !mbar_wait(&sh.split[q], static_cast<uint32_t>((c / nst) & 1))) {
             fail_now();
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t ah = tmem + kSlot0 + static_cast<uint32_t>(q * 64), al = ah + 32;
-          const uint64_t bh = sdesc(smem_u32(stB(q))), bl = sdesc(smem_u32(stBlo(q)));
+          const uint64_t bh = sdesc(smem_u32(stB(q, kc))), bl = sdesc(smem_u32(stBlo(q, kc)));
 #pragma unroll
           for (int k8 = 0; k8 < kKC / 8; ++k8) {  // K = 8 TF32 = 32 bytes per MMA
             const uint64_t adv = static_cast<uint64_t>((k8 * 32) >> 4);
@@ -393,16 +418,21 @@ void tc_update(int64_t n, const float* Q, int64_t ldq, int i, const double* W, i
                  make_map(&ml, lo, ldp, s, ldp, kKC, BN) &&
                  make_map(&mx, X, n, s, ldx, kRows, BN, CU_TENSOR_MAP_SWIZZLE_NONE),
              SG_ECUDA, "cuTensorMapEncodeTiled failed");
-  auto smem_for = [](int bn) {
-    return kStages * (kRows * kKC * 4 + 2 * bn * kKC * 4) + kRows * bn * 4 + 1024;
-  };
-  // the largest size for every s: one CTA per SM (the kernel allocates all
-  // 512 TMEM columns)
-  const int smem = smem_for(kMaxN);
+  // one shared-memory size for every shape (one CTA per SM; the kernel
+  // allocates all 512 TMEM columns): W resident when its chunks fit beside
+  // two Q stages and the X tile, else W chunks ride in the ring
+  constexpr int smem = kSmemBytes;
+  const int avail = smem - 1024;
+  const int a_b = kRows * kKC * 4, b_b = BN * kKC * 4, x_b = kRows * BN * 4;
+  const int KC = (i + kKC - 1) / kKC;
+  int wres = (KC * 2 * b_b + 2 * a_b + x_b <= avail) ? 1 : 0;
+  int nst = wres ? (avail - KC * 2 * b_b - x_b) / a_b : (avail - x_b) / (a_b + 2 * b_b);
+  if (nst > kStages) nst = kStages;
+  SG_REQUIRE(nst >= 1, SG_EINVAL, "tc_update: shared memory too small");
   static bool configured = false;
   if (!configured) {
     SG_CUDA(cudaFuncSetAttribute(tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 smem_for(kMaxN)));
+                                 smem));
     configured = true;
   }
   const int64_t tiles = (n + kRows - 1) / kRows;
@@ -410,7 +440,7 @@ void tc_update(int64_t n, const float* Q, int64_t ldq, int i, const double* W, i
   if (grid > tiles) grid = static_cast<int>(tiles);
   tc_update_kernel<<<grid, kThreads, smem, st>>>(mq, mh, ml, mx, n, i, s, BN,
                                                   static_cast<float>(alpha),
-                                                  static_cast<float>(beta), err_flag());
+                                                  static_cast<float>(beta), nst, wres, err_flag());
   SG_LAUNCH_CHECK();
 }
 
