@@ -164,10 +164,10 @@ DOT64_DRAM_BYTES_PER_ROW = (2_291_351_000 + 5_751_296) / (1 << 20)
 
 # DRAM bytes per row of the FP32 tensor-core block dot (W = Q^T X) and
 # update (X -= Q W) at i = 107, s = 106, from ncu captures at n = 2^20:
-# dot read 893,510,400 + write 4,590,336; update read 893,546,752 + write
-# 395,079,936.
-TCDOT_DRAM_BYTES_PER_ROW = (893_510_400 + 4_590_336) / (1 << 20)
-TCUPD_DRAM_BYTES_PER_ROW = (893_546_752 + 395_079_936) / (1 << 20)
+# dot read 893,510,656 + write 3,351,552; update read 893,552,896 + write
+# 395,420,928.
+TCDOT_DRAM_BYTES_PER_ROW = (893_510_656 + 3_351_552) / (1 << 20)
+TCUPD_DRAM_BYTES_PER_ROW = (893_552_896 + 395_420_928) / (1 << 20)
 # FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz (FADD / FMUL / FFMA each one op)
 FP32_ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 # FP32 instructions per exact Gram product: product, FMA remainder, the six
