@@ -11,12 +11,15 @@
 // contiguous bytes per column: no bank conflicts) and stores the TF32 hi
 // part and the FP32 remainder into tensor memory, where the MMA takes its A
 // operand -- the transpose to the K-major layout costs no shared-memory
-// writes.  W is
-// tiny: a prologue kernel writes its hi part and remainder as FP32 arrays
-// that TMA loads as K-major tiles.  hi*hi + lo*hi + hi*lo is accumulated.
+// writes.  W is tiny: a prologue kernel writes its hi part and remainder as
+// FP32 arrays that TMA loads as K-major tiles (128-byte swizzle, the MMA's
+// B operand).  When all of W's chunks fit beside two Q stages and the X
+// tile, they are loaded once per CTA and stay resident; otherwise each
+// stage carries its chunk (re-fetching W per tile costs ~2.5x the TMA lines
+// of the tile's own data).  hi*hi + lo*hi + hi*lo is accumulated.
 //
 // Persistent and warp-specialised: one CTA per SM walks 128-row tiles;
-//   warp 8 (one lane) issues the TMA loads of a 3-stage ring,
+//   warp 8 (one lane) issues the TMA loads of a ring of up to 3 stages,
 //   warps 4-7 split each Q tile into hi/lo in tensor memory,
 //   warp 9 (one lane) issues the MMAs into one of two TMEM accumulators,
 //   warps 0-3 (the TMEM lane owners) read an accumulator back while the
