@@ -222,7 +222,7 @@ def test_block_dot_f32_matches_definition(solver, n, i, s):
 
 @pytest.mark.parametrize("n", [256, 4133, 70001, 1 << 20])
 @pytest.mark.parametrize("i,s", [(1, 1), (7, 16), (33, 120), (107, 106),
-                                 (128, 128), (241, 17)])
+                                 (128, 128), (241, 17), (240, 106)])
 def test_block_dot_f32_tensor_cores(solver, n, i, s):
     """Aligned leading dimensions take the TMA + tcgen05 path (TF32 hi/lo
     split, three products); an unaligned copy of the same data takes the
@@ -287,12 +287,14 @@ def test_block_update_f32_matches_definition(solver, n, i, s, upper):
 @pytest.mark.parametrize("n", [128, 4133, 70001, 1 << 20])
 @pytest.mark.parametrize("i,s,upper", [(1, 1, False), (7, 16, False), (33, 120, False),
                                        (107, 106, False), (128, 128, False),
-                                       (241, 17, False), (33, 33, True), (120, 120, True)])
+                                       (200, 44, False), (241, 17, False), (241, 106, False),
+                                       (33, 33, True), (120, 120, True)])
 def test_block_update_f32_tensor_cores(solver, n, i, s, upper):
     """Aligned leading dimensions take the TMA + tcgen05 update (Q tile as an
     MN-major operand, TF32 hi/lo split); an unaligned copy of the same data
     takes the FFMA path.  Both within a few FP32 roundings of the FP64
-    result."""
+    result.  W's chunks stay resident in shared memory up to (128, 128) and
+    (200, 44); (241, 106) re-fetches them every stage."""
     rng = np.random.default_rng(900 + i + s + n % 97)
     ld = (n + 3) // 4 * 4
     Q = np.zeros((i, ld), np.float32)
