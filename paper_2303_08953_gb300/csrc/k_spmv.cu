@@ -358,8 +358,9 @@ arnoldi_step_kernel(int n, int rows_per_cta, const int* __restrict__ rowptr,
     w[i] = static_cast<T>(static_cast<double>(w[i]) * inv);
 }
 
-// FP32 form of the same step with grouped lookahead: the MGS projections
-// are taken kGrp basis vectors per grid barrier.  With d_k = v_k.w and the
+// FP32 form of the same step with grouped lookahead (used for the steps
+// past the two-barrier step's basis limit, kIcMaxCols vectors): the MGS
+// projections are taken kGrp basis vectors per grid barrier.  With d_k = v_k.w and the
 // group's Gram entries G_kq = v_k.v_q (q < k), all summed in the pass that
 // precedes the group, the MGS coefficients follow exactly by forward
 // substitution, h_k = d_k - sum_{q<k} G_kq h_q (what MGS computes, in
@@ -868,8 +869,9 @@ void launch_arnoldi_step(const DevCsr& A, const T* val, T* V, int64_t ld, int j,
                          double* H, int ldh, double* wn, double* red, int red_cap,
                          unsigned* bar, int* err, cudaStream_t st) {
   const int smem = SELL ? 0 : kCoopStage * static_cast<int>(sizeof(T) + sizeof(int));
-  // FP32: the grouped-lookahead step; FP64 keeps one projection per phase,
-  // the rounding order of the MGS oracle
+  // FP32: the two-barrier step while the basis fits it, then the grouped-
+  // lookahead step; FP64 keeps one projection per phase, the rounding order
+  // of the MGS oracle
   if constexpr (sizeof(T) == 4) {
     if (launch_arnoldi_icwy<SELL>(A, val, V, ld, j, H, ldh, wn, red, red_cap, bar, err, st))
       return;

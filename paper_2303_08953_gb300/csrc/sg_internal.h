@@ -88,7 +88,7 @@ void spmv_newton32(const DevCsr& A, const float* x, const float* z, float* y,
                    float theta, float c, float gamma, cudaStream_t st);
 // One Arnoldi step of the Ritz pre-pass (cooperative launch): V[:, j+1] =
 // normalised MGS projection of A V[:, j]; writes H(0..j+1, j) (ld ldh) and
-// wn[j] = ||A v_j||.  red: >= 3 x SMs doubles; bar: 64 zeroed unsigned
+// wn[j] = ||A v_j||.  red: >= 3 x SMs doubles (FP64); bar: 64 zeroed unsigned
 // words (barrier state); err: set to 1 if a barrier wait ran out.
 void arnoldi_step(const DevCsr& A, double* V, int64_t ld, int j, double* H,
                   int ldh, double* wn, double* red, int red_cap, unsigned* bar,
