@@ -841,15 +841,12 @@ bool launch_arnoldi_icwy(const DevCsr& A, const float* val, float* V, int64_t ld
                          unsigned* bar, int* err, cudaStream_t st) {
   if (j + 1 > kIcMaxCols) return false;
   const void* fn = reinterpret_cast<const void*>(arnoldi_step_icwy_kernel<SELL>);
-  static int mb = 0;
-  if (!mb) {
-    const int smax = static_cast<int>(ic_smem_bytes(kIcMaxCols));
-    SG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
-    int per_sm = 0;
-    SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kCoopThreads, smax));
-    mb = per_sm * device_sm_count();
-    SG_REQUIRE(mb > 0, SG_ECUDA, "arnoldi step: no resident blocks");
-  }
+  const int smax = static_cast<int>(ic_smem_bytes(kIcMaxCols));
+  ensure_dynamic_smem(fn, smax);
+  int per_sm = 0;
+  SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kCoopThreads, smax));
+  const int mb = per_sm * device_sm_count();
+  SG_REQUIRE(mb > 0, SG_ECUDA, "arnoldi step: no resident blocks");
   int G = device_sm_count();
   if (G > mb) G = mb;
   if (ic_red_doubles(G) > red_cap) return false;
@@ -878,14 +875,11 @@ void launch_arnoldi_step(const DevCsr& A, const T* val, T* V, int64_t ld, int j,
   }
   const void* fn = reinterpret_cast<const void*>(arnoldi_step_kernel<T, SELL>);
   if constexpr (sizeof(T) == 4) fn = reinterpret_cast<const void*>(arnoldi_step_grouped_kernel<SELL>);
-  static int mb = 0;  // per instantiation
-  if (!mb) {
-    SG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    int per_sm = 0;
-    SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kCoopThreads, smem));
-    mb = per_sm * device_sm_count();
-    SG_REQUIRE(mb > 0, SG_ECUDA, "arnoldi step: no resident blocks");
-  }
+  ensure_dynamic_smem(fn, smem);
+  int per_sm = 0;
+  SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kCoopThreads, smem));
+  const int mb = per_sm * device_sm_count();
+  SG_REQUIRE(mb > 0, SG_ECUDA, "arnoldi step: no resident blocks");
   int G = device_sm_count();  // one CTA per SM: fewer arrivals and partials
   if (G > mb) G = mb;
   const int need = sizeof(T) == 4 ? (2 * kNP + 1) * G : 3 * G;

@@ -429,12 +429,7 @@ void tc_dot(int64_t n, const float* Q, int64_t ldq, int i, const float* X, int64
   };
   // the largest size for every s: one CTA per SM
   const int smem = smem_for(kMaxN);
-  static bool configured = false;
-  if (!configured) {
-    SG_CUDA(cudaFuncSetAttribute(tc_dot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 smem_for(kMaxN)));
-    configured = true;
-  }
+  ensure_dynamic_smem(reinterpret_cast<const void*>(tc_dot_kernel), smem);
   dim3 grid(tiles, 1, static_cast<unsigned>(S));
   tc_dot_kernel<<<grid, kThreads, smem, st>>>(mq, mx, n, i, s, BN, rows, part, err);
   SG_LAUNCH_CHECK();

@@ -432,12 +432,7 @@ void tc_update(int64_t n, const float* Q, int64_t ldq, int i, const double* W, i
   int nst = wres ? (avail - KC * 2 * b_b - x_b) / a_b : (avail - x_b) / (a_b + 2 * b_b);
   if (nst > kStages) nst = kStages;
   SG_REQUIRE(nst >= 1, SG_EINVAL, "tc_update: shared memory too small");
-  static bool configured = false;
-  if (!configured) {
-    SG_CUDA(cudaFuncSetAttribute(tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 smem));
-    configured = true;
-  }
+  ensure_dynamic_smem(reinterpret_cast<const void*>(tc_update_kernel), smem);
   const int64_t tiles = (n + kRows - 1) / kRows;
   int grid = device_sm_count();
   if (grid > tiles) grid = static_cast<int>(tiles);

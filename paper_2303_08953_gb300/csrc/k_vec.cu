@@ -1,6 +1,10 @@
 // Vector kernels: deterministic dot products and norms (warp shuffles,
 // then a fixed-order sum of per-block partials), the solution update
 // x += Q y (Alg. 4, last line) and precision conversions.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "sg_internal.h"
 
 namespace sg {
@@ -8,7 +12,6 @@ namespace sg {
 namespace {
 
 constexpr int kThreads = 256;
-int g_red_blocks = 0;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -132,26 +135,45 @@ int stream_grid(int64_t n) {
 
 }  // namespace
 
+namespace {
+constexpr int kMaxDevices = 64;
+int current_device() {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) d = 0;
+  return d;
+}
+}  // namespace
+
+// per device: a process may drive several GPUs
 int device_sm_count() {
-  static int cached = 0;
-  if (!cached) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev) !=
-            cudaSuccess || cached <= 0)
-      cached = 1;
+  static int cached[kMaxDevices] = {};
+  const int d = current_device();
+  if (!cached[d]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || v <= 0)
+      v = 1;
+    cached[d] = v;
   }
-  return cached;
+  return cached[d];
+}
+
+void ensure_dynamic_smem(const void* fn, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> set_to;  // (kernel, device) -> bytes
+  const int d = current_device();
+  std::lock_guard<std::mutex> lock(mu);
+  int& cur = set_to[{fn, d}];
+  if (cur < bytes) {
+    SG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    cur = bytes;
+  }
 }
 
 int reduction_blocks() {
   // two 256-thread CTAs per SM: enough loads in flight for a streaming
   // pass, and few partials for every consumer CTA to re-add
-  if (!g_red_blocks) {
-    g_red_blocks = device_sm_count() * 2;
-    if (g_red_blocks > 1024) g_red_blocks = 1024;
-  }
-  return g_red_blocks;
+  const int b = device_sm_count() * 2;
+  return b > 1024 ? 1024 : b;
 }
 
 void dot_partials(int64_t n, const double* x, const double* y,

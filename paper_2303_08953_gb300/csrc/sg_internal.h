@@ -182,6 +182,9 @@ void tc_update(int64_t n, const float* Q, int64_t ldq, int i, const double* W,
                cudaStream_t st);
 void tc_update_check_error(cudaStream_t st);
 
-int device_sm_count();
+int device_sm_count();  // of the current device
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) for kernel fn on the
+// current device, once per (kernel, device) and size
+void ensure_dynamic_smem(const void* fn, int bytes);
 
 }  // namespace sg
