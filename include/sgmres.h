@@ -241,12 +241,13 @@ sg_status sg_block_update(sg_handle* h, int64_t n, const double* Q,
  * sg_block_dot_f32 forms the Gram matrix X^T X from exact FP32 products
  * accumulated with compensated sums (accurate to ~eps_32^2 relative to
  * sum |x_k y_k|).  Otherwise, when the leading dimensions are multiples of
- * 4, the pointers 16-byte aligned, n >= 256 and s <= 128, it runs on the
+ * 4, the pointers 16-byte aligned, n >= 512 and s <= 128, it runs on the
  * tensor cores (TMA + tcgen05, TF32 hi/lo split: hi*hi + lo*hi + hi*lo,
- * FP32 accumulation), else in FP32 FFMA.  sg_block_update_f32 likewise
- * runs on the tensor cores when Q is 16-byte aligned with a leading
- * dimension that is a multiple of 4, n >= 128 and s <= 128 (Q tile as an
- * MN-major operand, W split into TF32 hi + FP32 remainder).  Both calls
+ * FP32 accumulation, Q's split parts in tensor memory), else in FP32 FFMA.
+ * sg_block_update_f32 likewise runs on the tensor cores when Q is 16-byte
+ * aligned with a leading dimension that is a multiple of 4, n >= 128 and
+ * s <= 128 (the Q tile's split parts in tensor memory, W split into TF32
+ * hi + FP32 remainder in shared memory).  Both calls
  * synchronise the stream before returning (a tensor-core wait timeout is
  * reported as SG_ECUDA). */
 sg_status sg_block_dot_f32(sg_handle* h, int64_t n, const float* Q,
