@@ -225,8 +225,8 @@ def test_block_dot_f32_matches_definition(solver, n, i, s):
                                  (128, 128), (241, 17), (240, 106)])
 def test_block_dot_f32_tensor_cores(solver, n, i, s):
     """Aligned leading dimensions take the TMA + tcgen05 path (TF32 hi/lo
-    split, three products); an unaligned copy of the same data takes the
-    FFMA path.  Both must sit within a few FP32 roundings of the FP64
+    split, three products) from n = 512 rows on (n = 256 stays on the FFMA
+    path); an unaligned copy of the same data takes the FFMA path.  Both must sit within a few FP32 roundings of the FP64
     product (the dropped lo*lo term is ~2^-22 of |q||x|)."""
     rng = np.random.default_rng(500 + i + s)
     ld_tc = (n + 3) // 4 * 4
