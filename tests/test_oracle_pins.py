@@ -115,6 +115,32 @@ def test_arnoldi_reproduces_jacobi_matrix():
     assert np.allclose(rv, np.linalg.eigvalsh(T), rtol=0, atol=1e-12)
 
 
+def test_mgs_coefficients_from_the_gram_matrix():
+    """The FP32 pre-pass step takes all MGS coefficients of a step at once,
+    h = (I + L)^-1 V^T w with L the strict lower triangle of V^T V.  That is
+    exactly what MGS computes one projection at a time, h_k = v_k . (w -
+    sum_{q<k} h_q v_q), for any basis, orthonormal or not: checked here in
+    FP64 on a deliberately non-orthogonal basis, where a dropped or
+    transposed Gram term would show at O(1)."""
+    rng = np.random.default_rng(11)
+    n, k = 500, 12
+    V = rng.standard_normal((n, k))
+    V /= np.linalg.norm(V, axis=0)
+    V[:, 5] += 0.3 * V[:, 2]  # far from orthogonal
+    w = rng.standard_normal(n)
+    h_mgs = np.zeros(k)
+    r = w.copy()
+    for q in range(k):
+        h_mgs[q] = V[:, q] @ r
+        r -= h_mgs[q] * V[:, q]
+    G = V.T @ V
+    L = np.tril(G, -1)
+    h_gram = np.linalg.solve(np.eye(k) + L, V.T @ w)
+    assert np.allclose(h_gram, h_mgs, rtol=0, atol=1e-12 * np.linalg.norm(w))
+    # the update with those coefficients is MGS's residual
+    assert np.allclose(w - V @ h_gram, r, rtol=0, atol=1e-12 * np.linalg.norm(w))
+
+
 def test_ritz_values_inside_field_of_values():
     """Ritz values lie in the field of values of A: their real parts are
     bounded by the extreme eigenvalues of the symmetric part (A + A^T)/2
