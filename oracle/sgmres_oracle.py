@@ -210,11 +210,12 @@ def estimator_log2_E(theta, eps=EPS64):
 
 def estimator_column_norms(theta, eps=EPS64):
     """||E_j||_2 for every column j (Sec. 3.5), evaluated from log2 E with
-    a per-column scale so that no entry overflows."""
+    a per-column scale so that no entry overflows:
+    ||E_j|| = 2^mx * sqrt(sum_i (E_ij / 2^mx)^2), mx = max_i log2 E_ij."""
     lg = estimator_log2_E(theta, eps)
     mx = np.max(lg, axis=0)
     with np.errstate(over="ignore", invalid="ignore"):
-        sc = np.sqrt(np.sum(np.exp2(lg - mx[None, :]), axis=0))
+        sc = np.sqrt(np.sum(np.exp2(2.0 * (lg - mx[None, :])), axis=0))
         return np.exp2(mx) * sc
 
 

@@ -381,7 +381,7 @@ int estimate_step(int k, const double* re, const double* im, double eps,
     }
     double acc = 0.0;
     if (std::isfinite(mx))
-      for (int i = 0; i < k; ++i) acc += std::exp2(col[i] - mx);
+      for (int i = 0; i < k; ++i) acc += std::exp2(2.0 * (col[i] - mx));
     const double nrm = std::isfinite(mx) ? std::exp2(mx) * std::sqrt(acc) : 0.0;
     if (norms) norms[j] = nrm;
     if (!crossed && !(nrm < omega_est)) { s0 = j; crossed = true; }

@@ -121,3 +121,17 @@ def test_estimator_matches_oracle(sg):
         assert np.allclose(n_l[fin], n_o[fin], rtol=1e-9)
         # clamping
         assert sg.estimate_step(rz, s_min=150, s_max=180)[0] == max(150, min(s_o, 180))
+
+
+def test_estimator_exact_pin(sg):
+    """The library's estimator against the hand-computed auxiliary matrix
+    of four Leja-ordered values (column 2-norms and the first-crossing
+    index with both clamps), independent of the oracle."""
+    from test_oracle_pins import ESTIMATOR_EXACT, LEJA4, _leja4_norms_by_hand
+    for eps in (0.1, 1e3):
+        _, nrm = sg.estimate_step(LEJA4, eps=eps, omega_est=1e300)
+        assert np.allclose(nrm, _leja4_norms_by_hand(eps), rtol=1e-14, atol=0)
+    for eps, omega, smin, smax, want in ESTIMATOR_EXACT:
+        s0, _ = sg.estimate_step(LEJA4, eps=eps, omega_est=omega, s_min=smin,
+                                 s_max=smax or 0)
+        assert s0 == want, (eps, omega, smin, smax)

@@ -210,6 +210,67 @@ def test_estimator_three_values_by_hand():
     assert np.allclose(np.exp2(O.estimator_log2_E(th, eps)), E, rtol=1e-13)
 
 
+# Four real Ritz values in a Leja order with mean 0, so that
+# rho(i,k) = |theta_i - theta_k| / |theta_k| takes the values 1/2, 1, 3/2, 2
+# and 3.  E of Eq. (auxiliarymatrix) written out entry by entry by hand
+# (rows i, columns j, both 1-based in the comments):
+#   column 1: eps (i=1, j=i), then 1, 1, 1 (j < i: empty products)
+#   column 2: eps (i=1 > ... j > i, product over k<2, k!=1: empty),
+#             2 eps (i=2: rho(2,1)), 1/2 (rho(3,1)), 3/2 (rho(4,1))
+#   column 3: 2 eps (rho(1,2)), 2 eps (rho(2,1)),
+#             3/4 eps (rho(3,1) rho(3,2)), 3/4 (rho(4,1) rho(4,2))
+#   column 4: 2 eps (rho(1,2) rho(1,3) = 2 * 1), 6 eps (rho(2,1) rho(2,3)),
+#             3/4 eps (rho(3,1) rho(3,2)), 3/2 eps (rho(4,1..3) = 3/2*1/2*2)
+LEJA4 = np.array([4.0, -4.0, 2.0, -2.0])
+
+
+def _leja4_norms_by_hand(eps):
+    return np.array([math.sqrt(3.0 + eps ** 2),
+                     math.sqrt(0.25 + 2.25 + 5.0 * eps ** 2),
+                     math.sqrt(0.5625 + 8.5625 * eps ** 2),
+                     eps * math.sqrt(4.0 + 36.0 + 0.5625 + 2.25)])
+
+
+def test_estimator_four_values_norms_by_hand():
+    assert np.array_equal(O.leja_order(LEJA4[[2, 0, 3, 1]]).real, LEJA4)
+    for eps in (0.1, 1e3, 2.0 ** -53):
+        assert np.allclose(O.estimator_column_norms(LEJA4, eps),
+                           _leja4_norms_by_hand(eps), rtol=1e-14, atol=0)
+
+
+# (eps, Omega_est, s_min, s_max, s0*): s0* is the largest j such that every
+# column l <= j has ||E_l|| < Omega_est (Sec. 3.5, first-crossing reading),
+# then clamped to [s_min, s_max].
+#   eps = 1e3: norms 1000.0015, 2236.07, 2926.17, 6543.09 (increasing)
+#   eps = 0.1: norms 1.7349, 1.5969, 0.8053, 0.6543 (decreasing)
+ESTIMATOR_EXACT = [
+    (1e3, 2500.0, 1, None, 2),     # crossing at column 3
+    (1e3, 3000.0, 1, None, 3),     # crossing at column 4
+    (1e3, 2236.0, 1, None, 1),     # column 2 just above Omega_est
+    (1e3, 2237.0, 1, None, 2),     # ... and just below
+    (1e3, 7000.0, 1, None, 4),     # no crossing: every column
+    (1e3, 7000.0, 1, 3, 3),        # clamped from above
+    (1e3, 900.0, 1, None, 1),      # crossing at column 1: clamped to s_min
+    (1e3, 900.0, 3, None, 3),      # clamped from below
+    (1e3, 2500.0, 3, 4, 3),        # s_min above the crossing wins
+    (0.1, 1.70, 1, None, 1),       # first column fails, later ones pass:
+    (0.1, 1.70, 2, None, 2),       #   the first crossing decides, not the
+    (0.1, 1.75, 1, None, 4),       #   last column below Omega_est
+]
+
+
+@pytest.mark.parametrize("eps,omega,smin,smax,want", ESTIMATOR_EXACT)
+def test_estimator_first_crossing_and_clamp_exact(eps, omega, smin, smax, want):
+    """Exact pin of the index s0* returns: any off-by-one (counting the
+    crossing column, 0- vs 1-based j) or a last-below reading fails."""
+    norms = _leja4_norms_by_hand(eps)
+    # the thresholds sit clear of the norms, so rounding cannot move s0*
+    assert np.min(np.abs(norms - omega)) > 1e-5 * omega
+    s0, _ = O.estimate_step_size(LEJA4, omega_est=omega, eps=eps,
+                                 s_min=smin, s_max=smax)
+    assert s0 == want
+
+
 @pytest.mark.parametrize("key", ["test8_estimator_uniform",
                                  "test8_estimator_lmax2000"])
 def test_estimator_paper_test8(key):
@@ -640,3 +701,37 @@ def test_planted_transposed_gram_is_caught(monkeypatch):
     r = O.adaptive_sgmres(c["A"], c["b"], m=40, s=6, tol=1e-10,
                           diagnostics=True, max_iters=200)
     assert (not r.converged) or max(r.arnoldi_res) > 1e-10
+
+
+def _estimator_pin_fails():
+    for case in ESTIMATOR_EXACT:
+        try:
+            test_estimator_first_crossing_and_clamp_exact(*case)
+        except AssertionError:
+            return True
+    return False
+
+
+@pytest.mark.parametrize("plant", ["count_crossing", "last_below",
+                                   "no_lower_clamp"])
+def test_planted_estimator_index_is_caught(monkeypatch, plant):
+    """Plants in the estimator's index (on the CPU): counting the crossing
+    column itself, taking the last column below Omega_est, and dropping the
+    clamp to s_min.  The exact pin catches each."""
+    def bad(theta, omega_est=O.OMEGA_EST, eps=O.EPS64, s_min=1, s_max=None):
+        norms = O.estimator_column_norms(theta, eps)
+        below = [j for j in range(norms.size) if norms[j] < omega_est]
+        if plant == "count_crossing":
+            s0 = next((j + 1 for j in range(norms.size)
+                       if not norms[j] < omega_est), norms.size)
+        elif plant == "last_below":
+            s0 = below[-1] + 1 if below else 0
+        else:
+            s0 = next((j for j in range(norms.size)
+                       if not norms[j] < omega_est), norms.size)
+            return (min(s0, s_max) if s_max is not None else s0), norms
+        if s_max is not None:
+            s0 = min(s0, s_max)
+        return max(s0, s_min), norms
+    monkeypatch.setattr(O, "estimate_step_size", bad)
+    assert _estimator_pin_fails()
