@@ -275,8 +275,10 @@ sg_status sg_nrm2(sg_handle* h, int64_t n, const double* x, double* out,
  *    that every GPU loading the library holds until the process exits.
  *  - Runs on the calling thread's current device and on `stream` (NULL is
  *    the legacy default stream).  The first call on a device looks up the
- *    array's device address (cudaGetSymbolAddress); make that first call
- *    before any stream capture.
+ *    array's device address (cudaGetSymbolAddress) and keeps it for the
+ *    life of the process; make that first call before any stream capture.
+ *    A cudaDeviceReset unloads the array with the module, so make no
+ *    further calls on a device after resetting it.
  *  - Requires i*s <= SG_NOALLOC_SCRATCH_DOUBLES; larger shapes return
  *    SG_EINVAL with the limit in the message.  Q, X, W: device memory.
  *  - Every call shares the one array, so calls that overlap on the GPU
