@@ -156,6 +156,22 @@ const char* sg_last_error(const sg_handle* h);
  * Errors: SG_EINVAL, SG_ENOMEM, SG_ECUDA. */
 sg_status sg_analyze(sg_handle* h, const sg_csr* A);
 
+/* Ingest one process's row block of a row-partitioned matrix (Sec. 5:
+ * rows are distributed over the processes): A->n local rows whose columns
+ * are local indices in [0, ncols), ncols >= n, as sg_host_halo_plan
+ * numbers them (owned columns first, then the halo), distinct within a
+ * row and kept in the given order.  Only the kernel-level calls run on
+ * such a handle: sg_spmv_newton and sg_residual read x (and the shift term
+ * x[row]) as the length-ncols vector [own entries; halo entries]; the
+ * solve-level calls return SG_ESTATE.  Errors as sg_analyze. */
+sg_status sg_analyze_rows(sg_handle* h, const sg_csr* A, int32_t ncols);
+
+/* dst[k] = src[idx[k]] for k < count (device arrays, idx int32): packs the
+ * entries a neighbouring process needs from this one before a halo
+ * exchange.  Runs on `stream`.  Errors: SG_EINVAL, SG_ECUDA. */
+sg_status sg_gather(const int32_t* idx, int64_t count, const double* src, double* dst,
+                    void* stream);
+
 /* Replace the values of the analysed matrix, keeping its pattern: val
  * has nnz entries (device pointer when on_device, else host).  The FP32
  * copy is refreshed and the transpose is rebuilt on the next adjoint
@@ -217,6 +233,20 @@ sg_status sg_residual(sg_handle* h, const double* b, const double* x,
 sg_status sg_mpk(sg_handle* h, const double* q, double* V, int64_t ldv,
                  int32_t s, const double* theta_re, const double* theta_im,
                  const double* gamma, void* stream);
+
+/* Ritz pre-pass alone (Sec. 3.4: Ritz values from k steps of Arnoldi):
+ * k steps of modified Gram-Schmidt Arnoldi with the analysed matrix from
+ * the unit vector q (device, n doubles), in the handle's workspace, one
+ * cooperative kernel per step (the launches of a k are captured once in a
+ * CUDA graph and replayed).  precision: SG_PREC_FP64, or SG_PREC_FP32_IR
+ * for the FP32 basis (q rounded to FP32).  H (host, ldh >= k+1, k columns,
+ * column-major) receives the (k+1) x k Hessenberg matrix, *steps the steps
+ * completed (fewer than k after an invariant subspace: h_{j+1,j} <= 1e-12
+ * of ||A v_j||).  Synchronises `stream`.  Errors: SG_EINVAL (k < 1, null
+ * pointers, ldh), SG_ESTATE (no matrix), SG_ECUDA (a barrier wait ran
+ * out). */
+sg_status sg_arnoldi(sg_handle* h, const double* q, int32_t k, int32_t precision,
+                     double* H, int32_t ldh, int32_t* steps, void* stream);
 
 /* Block dot product of BCGS (Alg. 4 'First BCGS'): W = Q^T X, with Q
  * n x i (ldq), X n x s (ldx) and W i x s (ldw), all device memory.
@@ -344,6 +374,68 @@ void sg_host_scaling_coefficients(int32_t k, const double* re,
 int32_t sg_host_estimate_step(int32_t k, const double* re, const double* im,
                               double eps, double omega_est, int32_t s_min,
                               int32_t s_max, double* norms);
+
+/* Inverse of the leading p x p block of the upper-triangular R (the
+ * triangular factor of a partial CholQR, Alg. 4 'Q_k = X Z^-1').  Returns 0,
+ * or -1 on bad arguments. */
+int32_t sg_host_upper_inverse(const double* R, int32_t ldr, int32_t p, double* Ri,
+                              int32_t ldri);
+
+/* Basis parameters of s steps of the matrix powers kernel from the
+ * Leja-ordered shifts (re, im; a conjugate pair in consecutive entries)
+ * and scaling coefficients gamma (Eq. newtonrecurrence and its pair form):
+ * per step the real shift theta[j], the coefficient c[j] of V_{j-1} (b^2 /
+ * gamma_{j-1} on a pair's second step, else 0) and the scale g[j], and the
+ * (s+1) x s change-of-basis matrix B with A V(:, 1:s) = V B (ldb >= s+1).
+ * Any output may be NULL.  Returns 0, or -1 on bad arguments. */
+int32_t sg_host_basis(int32_t s, const double* re, const double* im,
+                      const double* gamma, double* theta, double* c, double* g,
+                      double* B, int32_t ldb);
+
+/* The two BCGS passes combined (Alg. 4 'Combine both steps'):
+ * R_top = W(:, 1:q) + R'(:, 1:q) Z(1:q, 1:q) (i x q) and
+ * R_kk = Z~(1:q, 1:q) Z(1:q, 1:q) (q x q), Z and Z~ upper triangular.
+ * Returns 0, or -1 on bad arguments. */
+int32_t sg_host_combine_r(int32_t i, int32_t q, const double* W, int32_t ldw,
+                          const double* Rp, int32_t ldrp, const double* Z1,
+                          int32_t ldz1, const double* R2, int32_t ldr2,
+                          double* R_top, int32_t ldt, double* R_kk, int32_t ldk);
+
+/* New columns i..i+q-1 (1-based i) of the unrotated Hessenberg matrix H
+ * (ld >= i+q) from V = Q Rbar and A V(:, 1:q) = V B (Alg. 4 'Assemble upper
+ * Hessenberg'): H(:, new) = (Rbar B - [H_old Rbar_top; 0]) T^-1, with Rbar's
+ * first column e_i and the rest [R_top; R_kk].  Uses H's earlier columns.
+ * Returns 0, or -1 on bad arguments. */
+int32_t sg_host_assemble_hessenberg(double* H, int32_t ldh, int32_t i, int32_t q,
+                                    const double* R_top, int32_t ldt,
+                                    const double* R_kk, int32_t ldk, const double* B,
+                                    int32_t ldb);
+
+/* Least-squares update of GMRES for column j (0-based) of the unrotated
+ * H (Alg. 1 'Apply Givens'): copies rows 0..j+1 of it into Hr, applies the
+ * rotations cs/sn[0..j-1], makes rotation j, updates g (length >= j+2) and
+ * returns |g[j+1]|, the residual norm of the least-squares problem (-1 on
+ * bad arguments). */
+double sg_host_givens_column(double* Hr, int32_t ldhr, double* cs, double* sn,
+                             double* g, const double* H, int32_t ldh, int32_t j);
+
+/* y (length jj) of the triangular system Hr(0:jj, 0:jj) y = g(0:jj). */
+int32_t sg_host_givens_solve(const double* Hr, int32_t ldhr, const double* g,
+                             int32_t jj, double* y);
+
+/* Halo of a row block for the row-partitioned solve (Sec. 5: rows are
+ * distributed over processes, and every SpMV needs the entries of x that
+ * other processes own).  rows = hi - lo consecutive rows [lo, hi) in CSR
+ * with global column indices (rowptr starts at 0).  Writes the sorted
+ * distinct columns outside [lo, hi) to halo_cols (capacity >= rowptr[rows];
+ * may be NULL) and each entry's local column to local_colind (may be NULL):
+ * c - lo for an owned column, rows + its position in halo_cols otherwise,
+ * so the block is a rows x (rows + halo) matrix over [own x; halo x].
+ * Entry order is kept.  Returns the number of halo columns, -1 on bad
+ * arguments. */
+int64_t sg_host_halo_plan(int32_t rows, const int32_t* rowptr, const int32_t* colind,
+                          int32_t lo, int32_t hi, int32_t* local_colind,
+                          int32_t* halo_cols);
 
 #ifdef __cplusplus
 }

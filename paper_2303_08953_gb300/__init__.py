@@ -37,7 +37,10 @@ EXPORTED = (
     "sg_host_scaling_coefficients", "sg_host_estimate_step",
     "sg_kernel_launches", "sg_block_dot_noalloc", "sg_block_dot_f32",
     "sg_block_update_f32", "sg_update_values", "sg_matrix_info",
-    "sg_probe_bounded_waits",
+    "sg_probe_bounded_waits", "sg_arnoldi", "sg_analyze_rows", "sg_gather",
+    "sg_host_upper_inverse", "sg_host_basis", "sg_host_combine_r",
+    "sg_host_assemble_hessenberg", "sg_host_givens_column",
+    "sg_host_givens_solve", "sg_host_halo_plan",
 )
 
 
@@ -117,6 +120,7 @@ def _load():
         "sg_spmv_newton": (i32, [vp, vp, vp, vp, f64, f64, f64, vp]),
         "sg_residual": (i32, [vp, vp, vp, vp, vp]),
         "sg_mpk": (i32, [vp, vp, vp, i64, i32, _D, _D, _D, vp]),
+        "sg_arnoldi": (i32, [vp, vp, i32, i32, _D, i32, C.POINTER(i32), vp]),
         "sg_block_dot": (i32, [vp, i64, vp, i64, i32, vp, i64, i32, vp, i32, i32, vp]),
         "sg_block_update": (i32, [vp, i64, vp, i64, i32, vp, i32, vp, i64, i32,
                                   f64, f64, i32, vp]),
@@ -130,6 +134,17 @@ def _load():
         "sg_host_scaling_coefficients": (None, [i32, _D, _D, _D]),
         "sg_host_estimate_step": (i32, [i32, _D, _D, f64, f64, i32, i32, _D]),
         "sg_kernel_launches": (i64, []),
+        "sg_analyze_rows": (i32, [vp, C.POINTER(sg_csr), i32]),
+        "sg_gather": (i32, [vp, i64, vp, vp, vp]),
+        "sg_host_upper_inverse": (i32, [_D, i32, i32, _D, i32]),
+        "sg_host_basis": (i32, [i32, _D, _D, _D, _D, _D, _D, _D, i32]),
+        "sg_host_combine_r": (i32, [i32, i32, _D, i32, _D, i32, _D, i32, _D, i32,
+                                    _D, i32, _D, i32]),
+        "sg_host_assemble_hessenberg": (i32, [_D, i32, i32, i32, _D, i32, _D, i32,
+                                              _D, i32]),
+        "sg_host_givens_column": (f64, [_D, i32, _D, _D, _D, _D, i32, i32]),
+        "sg_host_givens_solve": (i32, [_D, i32, _D, i32, _D]),
+        "sg_host_halo_plan": (i64, [i32, _I, _I, i32, i32, _I, _I]),
         "sg_block_dot_noalloc": (i32, [i64, vp, i64, i32, vp, i64, i32, vp, i32,
                                        vp, C.c_char_p, i32]),
     }
@@ -204,6 +219,97 @@ def estimate_step(theta, eps=2.0 ** -53, omega_est=1e7, s_min=1, s_max=0):
     s0 = lib.sg_host_estimate_step(th.size, _dp(re), _dp(im), eps, omega_est,
                                    s_min, s_max, _dp(norms))
     return int(s0), norms[:th.size].copy()
+
+
+def _f(a):
+    """Column-major float64 copy (or view) for the host calls."""
+    return np.asfortranarray(a, dtype=np.float64)
+
+
+def _ok(rc, what):
+    if rc != 0:
+        raise SgError(SG_EINVAL, f"{what}: bad arguments")
+
+
+def upper_inverse(R, p=None):
+    """Inverse of the leading p x p block of upper-triangular R."""
+    R = _f(R)
+    p = R.shape[0] if p is None else p
+    Ri = np.zeros((p, p), order="F")
+    _ok(lib.sg_host_upper_inverse(_dp(R), R.shape[0], p, _dp(Ri), max(p, 1)), "upper_inverse")
+    return Ri
+
+
+def basis(theta, gamma, s):
+    """(theta, c, g, B) of s matrix-powers steps: per-step shift, pair
+    coefficient and scale, and the (s+1) x s change-of-basis matrix."""
+    th = np.asarray(theta, dtype=np.complex128)[:s]
+    re, im = np.ascontiguousarray(th.real), np.ascontiguousarray(th.imag)
+    gm = np.ascontiguousarray(np.asarray(gamma, dtype=np.float64)[:s])
+    t, c, g = np.zeros(s), np.zeros(s), np.zeros(s)
+    B = np.zeros((s + 1, s), order="F")
+    _ok(lib.sg_host_basis(s, _dp(re), _dp(im), _dp(gm), _dp(t), _dp(c), _dp(g),
+                          _dp(B), s + 1), "basis")
+    return t, c, g, B
+
+
+def combine_r(W, Rp, Z1, R2, q):
+    """(R_top, R_kk) of Alg. 4 'Combine both steps' (first q columns)."""
+    W, Rp, Z1, R2 = _f(W), _f(Rp), _f(Z1), _f(R2)
+    i = W.shape[0]
+    Rt = np.zeros((i, q), order="F")
+    Rk = np.zeros((q, q), order="F")
+    _ok(lib.sg_host_combine_r(i, q, _dp(W), i, _dp(Rp), Rp.shape[0], _dp(Z1), Z1.shape[0],
+                              _dp(R2), R2.shape[0], _dp(Rt), i, _dp(Rk), q), "combine_r")
+    return Rt, Rk
+
+
+def assemble_hessenberg(H, i, R_top, R_kk, B):
+    """New columns i..i+q-1 (1-based i) of H (Fortran-ordered, updated in
+    place)."""
+    assert H.flags.f_contiguous and H.dtype == np.float64
+    R_top, R_kk, B = _f(R_top), _f(R_kk), _f(B)
+    q = R_kk.shape[0]
+    _ok(lib.sg_host_assemble_hessenberg(_dp(H), H.shape[0], i, q, _dp(R_top), R_top.shape[0],
+                                        _dp(R_kk), q, _dp(B), B.shape[0]), "assemble_hessenberg")
+
+
+def givens_column(Hr, cs, sn, g, H, j):
+    """Rotate column j of H into Hr (Fortran-ordered arrays updated in
+    place); returns |g[j+1]|."""
+    assert Hr.flags.f_contiguous and H.flags.f_contiguous
+    r = lib.sg_host_givens_column(_dp(Hr), Hr.shape[0], _dp(cs), _dp(sn), _dp(g), _dp(H),
+                                  H.shape[0], j)
+    if r < 0:
+        raise SgError(SG_EINVAL, "givens_column: bad arguments")
+    return r
+
+
+def givens_solve(Hr, g, jj):
+    y = np.zeros(max(jj, 1))
+    _ok(lib.sg_host_givens_solve(_dp(Hr), Hr.shape[0], _dp(g), jj, _dp(y)), "givens_solve")
+    return y[:jj]
+
+
+def halo_plan(rowptr, colind, lo, hi):
+    """(local_colind, halo_cols) of the row block [lo, hi) (global columns)."""
+    rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(colind, dtype=np.int32)
+    loc = np.zeros(max(ci.size, 1), dtype=np.int32)
+    halo = np.zeros(max(ci.size, 1), dtype=np.int32)
+    nh = lib.sg_host_halo_plan(hi - lo, _ip(rp), _ip(ci), lo, hi, _ip(loc), _ip(halo))
+    if nh < 0:
+        raise SgError(SG_EINVAL, "halo_plan: bad arguments")
+    return loc[:ci.size].copy(), halo[:nh].copy()
+
+
+def gather(idx, src, out, stream=None):
+    """out[k] = src[idx[k]] on the device (idx an int32 CUDA tensor)."""
+    rc = lib.sg_gather(C.c_void_p(idx.data_ptr()), idx.numel(), C.c_void_p(src.data_ptr()),
+                       C.c_void_p(out.data_ptr()), _stream_ptr(stream))
+    if rc != 0:
+        raise SgError(rc, "sg_gather failed")
+    return out
 
 
 # ------------------------------------------------------------ solver
@@ -320,6 +426,17 @@ class Solver:
         else:
             v = np.ascontiguousarray(val, dtype=np.float64)
             self._check(lib.sg_update_values(self._h, C.c_void_p(v.ctypes.data), 0))
+        return self
+
+    def analyze_rows(self, rowptr, colind, val, ncols):
+        """Ingest a row block with local columns in [0, ncols) (host numpy
+        arrays; see sg_analyze_rows)."""
+        rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+        ci = np.ascontiguousarray(colind, dtype=np.int32)
+        v = np.ascontiguousarray(val, dtype=np.float64)
+        A = sg_csr(rp.size - 1, ci.size, rp.ctypes.data, ci.ctypes.data, v.ctypes.data, 0)
+        self._check(lib.sg_analyze_rows(self._h, C.byref(A), ncols))
+        self.n, self.nnz = rp.size - 1, ci.size
         return self
 
     def analyze_csr(self, A):
@@ -452,6 +569,16 @@ class Solver:
                                C.c_void_p(V.data_ptr()), self.n, s, _dp(re),
                                _dp(im), _dp(gm), _stream_ptr(stream)))
         return V
+
+    def arnoldi(self, q, k, precision="fp64", stream=None):
+        """(H, steps): k steps of the Ritz pre-pass (Sec. 3.4) from the unit
+        device vector q; H is the (k+1) x k Hessenberg matrix."""
+        H = np.zeros((k, k + 1))   # column-major (k+1) x k
+        steps = C.c_int32(0)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else precision
+        self._check(lib.sg_arnoldi(self._h, C.c_void_p(q.data_ptr()), k, prec,
+                                   _dp(H), k + 1, C.byref(steps), _stream_ptr(stream)))
+        return H.T.copy(), int(steps.value)
 
     def block_dot(self, Qt, Xt, sym=False, stream=None):
         """W = Q^T X for column-major Q (tensor (i, ld)) and X ((s, ld));

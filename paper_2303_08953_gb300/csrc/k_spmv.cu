@@ -21,6 +21,8 @@
 // contiguous block of rows and first stages that block's values and
 // column indices in shared memory with coalesced streaming loads, then
 // each thread walks its own row from shared memory.
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "k_reduce.cuh"
@@ -356,6 +358,106 @@ arnoldi_step_kernel(int n, int rows_per_cta, const int* __restrict__ rowptr,
   const double inv = 1.0 / nrm;
   for (int64_t i = i0; i < n; i += stride)
     w[i] = static_cast<T>(static_cast<double>(w[i]) * inv);
+}
+
+// The same FP64 step with w resident on chip.  CTA b owns the contiguous
+// rows [b R, (b+1) R) (R a multiple of 32, so its SELL-32 slices are whole)
+// and keeps its slice of w in shared memory from the SpMV to the final
+// normalisation.  A thread always touches the same rows, so w needs no
+// barrier of its own; each MGS phase streams only v_l (just read as the
+// previous phase's v_{l+1}, an L2 hit) and v_{l+1}, instead of reading and
+// writing w through HBM as well.  Phase order, fused next-vector dot and
+// per-CTA partials are those of arnoldi_step_kernel; only the rows a CTA
+// owns differ.
+__global__ void __launch_bounds__(kCoopThreads, 1)
+arnoldi_step_resident_kernel(int n, int rows_cta, const int* __restrict__ sptr,
+                             const int* __restrict__ scol, const double* __restrict__ sval,
+                             double* __restrict__ V, int64_t ld, int j,
+                             double* __restrict__ H, int ldh, double* __restrict__ wn,
+                             double* __restrict__ red, unsigned* bar, int* err) {
+  extern __shared__ __align__(16) unsigned char coop_smem[];
+  double* ws = reinterpret_cast<double*>(coop_smem);
+  const int G = gridDim.x;
+  const int t = threadIdx.x;
+  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * rows_cta;
+  const int64_t r1 = (r0 + rows_cta < n) ? r0 + rows_cta : n;
+  const int nr = r1 > r0 ? static_cast<int>(r1 - r0) : 0;
+  const int nr32 = (nr + 31) & ~31;   // whole slices (rows past n are padding)
+  const double* vj = V + static_cast<int64_t>(j) * ld;
+  const double* v0 = V + r0;
+  double* pWW = red;
+  double* pA = red + G;
+  double* pB = red + 2 * G;
+  // phase 0: w = A v_j on this CTA's rows, partials of w.w and v_0.w
+  double accw = 0.0, accv = 0.0;
+  for (int i = t; i < nr32; i += kCoopThreads) {
+    const double sum = sell_row(sptr, scol, sval, vj, r0 + i);
+    if (i < nr) {
+      ws[i] = sum;
+      accw = fma(sum, sum, accw);
+      accv = fma(v0[i], sum, accv);
+    }
+  }
+  {
+    const double sw = block_sum_few_d<kCoopThreads>(accw);
+    const double sv = block_sum_few_d<kCoopThreads>(accv);
+    if (t == 0) { pWW[blockIdx.x] = sw; pA[blockIdx.x] = sv; }
+  }
+  grid_barrier(bar, G, err);
+  if (blockIdx.x == 0) {
+    const double ww = sum_partials_few_d<kCoopThreads>(pWW, G);
+    if (t == 0) wn[j] = sqrt(ww);
+  }
+  // MGS phases l = 0..j: h_l from the previous phase's partials, w -= h_l
+  // v_l, partials of v_{l+1}.w (of w.w in the last phase)
+  double* pin = pA;
+  double* pout = pB;
+  for (int l = 0; l <= j; ++l) {
+    const double h = sum_partials_few_d<kCoopThreads>(pin, G);
+    if (blockIdx.x == 0 && t == 0) H[l + static_cast<int64_t>(j) * ldh] = h;
+    const double* vl = V + static_cast<int64_t>(l) * ld + r0;
+    const double* vn = V + static_cast<int64_t>(l + 1) * ld + r0;
+    double acc = 0.0;
+    int i = t;
+    if (l < j) {
+      for (; i + 3 * kCoopThreads < nr; i += 4 * kCoopThreads) {
+        double wv[4], vv[4], nv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          wv[u] = ws[i + u * kCoopThreads];
+          vv[u] = vl[i + u * kCoopThreads];
+          nv[u] = vn[i + u * kCoopThreads];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const double wi = fma(-h, vv[u], wv[u]);
+          ws[i + u * kCoopThreads] = wi;
+          acc = fma(nv[u], wi, acc);
+        }
+      }
+      for (; i < nr; i += kCoopThreads) {
+        const double wi = fma(-h, vl[i], ws[i]);
+        ws[i] = wi;
+        acc = fma(vn[i], wi, acc);
+      }
+    } else {
+      for (; i < nr; i += kCoopThreads) {
+        const double wi = fma(-h, vl[i], ws[i]);
+        ws[i] = wi;
+        acc = fma(wi, wi, acc);
+      }
+    }
+    const double tot = block_sum_few_d<kCoopThreads>(acc);
+    if (t == 0) pout[blockIdx.x] = tot;
+    grid_barrier(bar, G, err);
+    double* tmp = pin; pin = pout; pout = tmp;
+  }
+  // normalise into V's column j+1
+  const double nrm = sqrt(sum_partials_few_d<kCoopThreads>(pin, G));
+  if (blockIdx.x == 0 && t == 0) H[(j + 1) + static_cast<int64_t>(j) * ldh] = nrm;
+  const double inv = 1.0 / nrm;
+  double* w = V + static_cast<int64_t>(j + 1) * ld + r0;
+  for (int i = t; i < nr; i += kCoopThreads) w[i] = ws[i] * inv;
 }
 
 // FP32 form of the same step with grouped lookahead (used for the steps
@@ -861,10 +963,61 @@ bool launch_arnoldi_icwy(const DevCsr& A, const float* val, float* V, int64_t ld
   return true;
 }
 
+// Rows per CTA of the resident FP64 step for n rows, or 0 when a CTA's
+// slice of w would not fit in shared memory next to the kernel's static
+// reduction buffers (then the streaming step runs).  One CTA per SM, at
+// least 2048 rows per CTA (fewer CTAs, cheaper barriers, on small systems).
+int resident_rows_per_cta(int64_t n, int* grid) {
+  static std::mutex mu;
+  static std::map<int, int> limit;   // device -> dynamic bytes available
+  const int dev = current_device();
+  int avail;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = limit.find(dev);
+    if (it == limit.end()) {
+      int optin = 0;
+      SG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+      cudaFuncAttributes fa{};
+      SG_CUDA(cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(arnoldi_step_resident_kernel)));
+      it = limit.emplace(dev, optin - static_cast<int>(fa.sharedSizeBytes) - 1024).first;
+    }
+    avail = it->second;
+  }
+  const int64_t sms = device_sm_count();
+  int64_t R = (n + sms - 1) / sms;
+  if (R < 2048) R = 2048;
+  R = (R + 31) / 32 * 32;
+  if (R * static_cast<int64_t>(sizeof(double)) > avail) return 0;
+  *grid = static_cast<int>((n + R - 1) / R);
+  return static_cast<int>(R);
+}
+
 template <typename T, bool SELL>
 void launch_arnoldi_step(const DevCsr& A, const T* val, T* V, int64_t ld, int j,
                          double* H, int ldh, double* wn, double* red, int red_cap,
                          unsigned* bar, int* err, cudaStream_t st) {
+  if constexpr (sizeof(T) == 8 && SELL) {
+    int G = 0;
+    const int R = resident_rows_per_cta(A.n, &G);
+    if (R > 0 && G <= device_sm_count() && 3 * G <= red_cap) {
+      const void* fn = reinterpret_cast<const void*>(arnoldi_step_resident_kernel);
+      const int smem = R * static_cast<int>(sizeof(double));
+      ensure_dynamic_smem(fn, smem);
+      int per_sm = 0;
+      SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kCoopThreads, smem));
+      if (per_sm >= 1) {
+        int n = A.n;
+        int rc = R;
+        void* args[] = {&n, &rc, const_cast<int**>(&A.sptr), const_cast<int**>(&A.scol),
+                        const_cast<T**>(&val), &V, &ld, &j, &H, const_cast<int*>(&ldh), &wn,
+                        &red, &bar, &err};
+        SG_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kCoopThreads), args, smem, st));
+        count_launch();
+        return;
+      }
+    }
+  }
   const int smem = SELL ? 0 : kCoopStage * static_cast<int>(sizeof(T) + sizeof(int));
   // FP32: the two-barrier step while the basis fits it, then the grouped-
   // lookahead step; FP64 keeps one projection per phase, the rounding order

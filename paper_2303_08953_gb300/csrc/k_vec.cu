@@ -137,12 +137,13 @@ int stream_grid(int64_t n) {
 
 namespace {
 constexpr int kMaxDevices = 64;
+}  // namespace
+
 int current_device() {
   int d = 0;
   if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) d = 0;
   return d;
 }
-}  // namespace
 
 // per device: a process may drive several GPUs
 int device_sm_count() {
@@ -167,6 +168,23 @@ void ensure_dynamic_smem(const void* fn, int bytes) {
     SG_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     cur = bytes;
   }
+}
+
+__global__ void gather_kernel(int64_t count, const int32_t* __restrict__ idx,
+                              const double* __restrict__ src, double* __restrict__ dst) {
+  for (int64_t k = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; k < count;
+       k += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    dst[k] = __ldg(src + idx[k]);
+}
+
+void gather(const int32_t* idx, int64_t count, const double* src, double* dst,
+            cudaStream_t st) {
+  if (count <= 0) return;
+  int64_t blocks = (count + kThreads - 1) / kThreads;
+  const int64_t cap = static_cast<int64_t>(device_sm_count()) * 8;
+  if (blocks > cap) blocks = cap;
+  gather_kernel<<<static_cast<int>(blocks), kThreads, 0, st>>>(count, idx, src, dst);
+  SG_LAUNCH_CHECK();
 }
 
 int reduction_blocks() {

@@ -220,6 +220,7 @@ sg_status run_solve(sg_handle* h, bool adjoint, const double* b, double* x,
   sg::SolveLog log;
   sg_status rc = guarded(h, [&] {
     SG_REQUIRE(h->have_A, SG_ESTATE, "no matrix: call sg_analyze first");
+    SG_REQUIRE(!h->rows_only, SG_ESTATE, "a row block supports the kernel-level calls only");
     check_opts(opts);
     SG_REQUIRE(b && x, SG_EINVAL, "b/x is NULL");
     SG_CUDA(cudaSetDevice(h->device));
@@ -327,12 +328,16 @@ void sg_destroy(sg_handle* h) {
 
 const char* sg_last_error(const sg_handle* h) { return h ? h->err.c_str() : "null handle"; }
 
-sg_status sg_analyze(sg_handle* h, const sg_csr* A) {
-  if (!h) return SG_EINVAL;
+// Ingest of a square matrix (ncols = n, columns sorted in each row) or of
+// a row block of a partitioned matrix (ncols >= n, columns distinct in each
+// row but in the caller's order: local numbering of a halo block).
+static sg_status analyze_impl(sg_handle* h, const sg_csr* A, int64_t ncols, bool block) {
   return guarded(h, [&] {
     SG_REQUIRE(A && A->rowptr && A->colind && A->val, SG_EINVAL, "null CSR array");
     SG_REQUIRE(A->n >= 1, SG_EINVAL, "n must be >= 1");
     SG_REQUIRE(A->nnz >= 0 && A->nnz < (int64_t(1) << 31), SG_EINVAL, "nnz out of int32 range");
+    SG_REQUIRE(ncols >= A->n && ncols < (int64_t(1) << 31), SG_EINVAL,
+               "ncols must be in [n, 2^31)");
     SG_CUDA(cudaSetDevice(h->device));
     cudaStream_t st = h->own;
     const int64_t n = A->n, nnz = A->nnz;
@@ -343,12 +348,20 @@ sg_status sg_analyze(sg_handle* h, const sg_csr* A) {
     if (nnz) SG_CUDA(cudaMemcpy(ci.data(), A->colind, sizeof(int32_t) * nnz, kind));
     SG_REQUIRE(rp[0] == 0 && rp[n] == nnz, SG_EINVAL, "rowptr must start at 0 and end at nnz");
     int32_t maxrow = 0;
+    std::vector<int32_t> row;
     for (int64_t r = 0; r < n; ++r) {
       SG_REQUIRE(rp[r + 1] >= rp[r], SG_EINVAL, "rowptr not non-decreasing");
       maxrow = std::max(maxrow, rp[r + 1] - rp[r]);
       for (int32_t k = rp[r]; k < rp[r + 1]; ++k) {
-        SG_REQUIRE(ci[k] >= 0 && ci[k] < n, SG_EINVAL, "column index out of range");
-        SG_REQUIRE(k == rp[r] || ci[k] > ci[k - 1], SG_EINVAL, "columns not sorted/unique in a row");
+        SG_REQUIRE(ci[k] >= 0 && ci[k] < ncols, SG_EINVAL, "column index out of range");
+        SG_REQUIRE(block || k == rp[r] || ci[k] > ci[k - 1], SG_EINVAL,
+                   "columns not sorted/unique in a row");
+      }
+      if (block) {
+        row.assign(ci.begin() + rp[r], ci.begin() + rp[r + 1]);
+        std::sort(row.begin(), row.end());
+        SG_REQUIRE(std::adjacent_find(row.begin(), row.end()) == row.end(), SG_EINVAL,
+                   "repeated column in a row");
       }
     }
     h->drop_graphs();
@@ -373,7 +386,30 @@ sg_status sg_analyze(sg_handle* h, const sg_csr* A) {
     sg::build_sell(D, st);
     SG_CUDA(cudaStreamSynchronize(st));
     h->have_A = true;
+    h->rows_only = block;
+    h->ncols = ncols;
   });
+}
+
+sg_status sg_analyze(sg_handle* h, const sg_csr* A) {
+  if (!h) return SG_EINVAL;
+  return analyze_impl(h, A, A ? A->n : 0, false);
+}
+
+sg_status sg_analyze_rows(sg_handle* h, const sg_csr* A, int32_t ncols) {
+  if (!h) return SG_EINVAL;
+  return analyze_impl(h, A, ncols, true);
+}
+
+sg_status sg_gather(const int32_t* idx, int64_t count, const double* src, double* dst,
+                    void* stream) {
+  if (count < 0 || (count > 0 && (!idx || !src || !dst))) return SG_EINVAL;
+  try {
+    sg::gather(idx, count, src, dst, static_cast<cudaStream_t>(stream));
+  } catch (const sg::Error& e) {
+    return e.code;
+  }
+  return SG_OK;
 }
 
 sg_status sg_update_values(sg_handle* h, const double* val, int32_t on_device) {
@@ -497,6 +533,28 @@ sg_status sg_mpk(sg_handle* h, const double* q, double* V, int64_t ldv,
                       V + static_cast<int64_t>(j + 1) * ldv, steps[j].theta, steps[j].c,
                       steps[j].gamma, st);
     }
+  });
+}
+
+sg_status sg_arnoldi(sg_handle* h, const double* q, int32_t k, int32_t precision,
+                     double* H, int32_t ldh, int32_t* steps, void* stream) {
+  if (!h) return SG_EINVAL;
+  return guarded(h, [&] {
+    SG_REQUIRE(h->have_A, SG_ESTATE, "no matrix");
+    SG_REQUIRE(!h->rows_only, SG_ESTATE, "a row block supports the kernel-level calls only");
+    SG_REQUIRE(q && H && steps && k >= 1 && ldh >= k + 1, SG_EINVAL, "bad Arnoldi arguments");
+    SG_REQUIRE(precision == SG_PREC_FP64 || precision == SG_PREC_FP32_IR, SG_EINVAL,
+               "unknown precision");
+    SG_CUDA(cudaSetDevice(h->device));
+    cudaStream_t st = pick(h, stream);
+    const bool fp32 = precision == SG_PREC_FP32_IR;
+    if (fp32 && !h->A.val32) make_val32(h->A, st);
+    std::vector<double> Hh;
+    const int done = sg::ritz_prepass(h, h->A, q, k, fp32, st, Hh);
+    for (int c = 0; c < k; ++c)
+      for (int r = 0; r <= k; ++r)
+        H[r + static_cast<int64_t>(c) * ldh] = Hh[r + static_cast<size_t>(c) * (k + 1)];
+    *steps = done;
   });
 }
 
@@ -645,6 +703,71 @@ int32_t sg_host_estimate_step(int32_t k, const double* re, const double* im,
                               int32_t s_max, double* norms) {
   if (k < 0 || (k > 0 && (!re || !im))) return -1;
   return sg::estimate_step(k, re, im, eps, omega_est, s_min, s_max, norms);
+}
+
+int32_t sg_host_upper_inverse(const double* R, int32_t ldr, int32_t p, double* Ri,
+                              int32_t ldri) {
+  if (p < 0 || (p > 0 && (!R || !Ri || ldr < p || ldri < p))) return -1;
+  if (p > 0) sg::upper_inverse(R, ldr, p, Ri, ldri);
+  return 0;
+}
+
+int32_t sg_host_basis(int32_t s, const double* re, const double* im,
+                      const double* gamma, double* theta, double* c, double* g,
+                      double* B, int32_t ldb) {
+  if (s < 0 || (s > 0 && (!re || !im || !gamma))) return -1;
+  if (B && ldb < s + 1) return -1;
+  std::vector<sg::BasisStep> st;
+  sg::basis_steps(s, re, im, gamma, st);
+  for (int j = 0; j < s; ++j) {
+    if (theta) theta[j] = st[j].theta;
+    if (c) c[j] = st[j].c;
+    if (g) g[j] = st[j].gamma;
+  }
+  if (B && s > 0) sg::change_of_basis(st, s, B, ldb);
+  return 0;
+}
+
+int32_t sg_host_combine_r(int32_t i, int32_t q, const double* W, int32_t ldw,
+                          const double* Rp, int32_t ldrp, const double* Z1,
+                          int32_t ldz1, const double* R2, int32_t ldr2,
+                          double* R_top, int32_t ldt, double* R_kk, int32_t ldk) {
+  if (i < 1 || q < 1 || !W || !Rp || !Z1 || !R2 || !R_top || !R_kk || ldw < i ||
+      ldrp < i || ldz1 < q || ldr2 < q || ldt < i || ldk < q)
+    return -1;
+  sg::combine_r(i, q, W, ldw, Rp, ldrp, Z1, ldz1, R2, ldr2, R_top, ldt, R_kk, ldk);
+  return 0;
+}
+
+int32_t sg_host_assemble_hessenberg(double* H, int32_t ldh, int32_t i, int32_t q,
+                                    const double* R_top, int32_t ldt,
+                                    const double* R_kk, int32_t ldk, const double* B,
+                                    int32_t ldb) {
+  if (!H || !R_top || !R_kk || !B || i < 1 || q < 1 || ldh < i + q || ldt < i ||
+      ldk < q || ldb < q + 1)
+    return -1;
+  sg::assemble_hessenberg(H, ldh, i, q, R_top, ldt, R_kk, ldk, B, ldb);
+  return 0;
+}
+
+double sg_host_givens_column(double* Hr, int32_t ldhr, double* cs, double* sn,
+                             double* g, const double* H, int32_t ldh, int32_t j) {
+  if (!Hr || !cs || !sn || !g || !H || j < 0 || ldhr < j + 2 || ldh < j + 2) return -1.0;
+  return sg::givens_column(Hr, ldhr, cs, sn, g, H, ldh, j);
+}
+
+int32_t sg_host_givens_solve(const double* Hr, int32_t ldhr, const double* g,
+                             int32_t jj, double* y) {
+  if (jj < 0 || (jj > 0 && (!Hr || !g || !y || ldhr < jj))) return -1;
+  sg::givens_solve(Hr, ldhr, g, jj, y);
+  return 0;
+}
+
+int64_t sg_host_halo_plan(int32_t rows, const int32_t* rowptr, const int32_t* colind,
+                          int32_t lo, int32_t hi, int32_t* local_colind,
+                          int32_t* halo_cols) {
+  if (rows < 0 || hi - lo != rows || !rowptr || (rowptr[rows] > 0 && !colind)) return -1;
+  return sg::halo_plan(rows, rowptr, colind, lo, hi, local_colind, halo_cols);
 }
 
 }  // extern "C"

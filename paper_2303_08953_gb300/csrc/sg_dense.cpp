@@ -469,9 +469,9 @@ void Givens::reset(int m_, double beta) {
   g[0] = beta;
 }
 
-double Givens::add_column(const double* H, int ldh, int j) {
-  const int ld = m + 1;
-  double* h = &Hr[static_cast<size_t>(j) * ld];
+double givens_column(double* Hr, int ldhr, double* cs, double* sn, double* g,
+                     const double* H, int ldh, int j) {
+  double* h = Hr + static_cast<size_t>(j) * ldhr;
   for (int r = 0; r <= j + 1; ++r) h[r] = at(H, ldh, r, j);
   for (int l = 0; l < j; ++l) {
     const double t = cs[l] * h[l] + sn[l] * h[l + 1];
@@ -489,13 +489,62 @@ double Givens::add_column(const double* H, int ldh, int j) {
   return std::fabs(g[j + 1]);
 }
 
-void Givens::solve(int jj, double* y) const {
-  const int ld = m + 1;
+void givens_solve(const double* Hr, int ldhr, const double* g, int jj, double* y) {
   for (int r = jj - 1; r >= 0; --r) {
     double acc = g[r];
-    for (int c = r + 1; c < jj; ++c) acc -= Hr[r + static_cast<size_t>(c) * ld] * y[c];
-    y[r] = acc / Hr[r + static_cast<size_t>(r) * ld];
+    for (int c = r + 1; c < jj; ++c) acc -= Hr[r + static_cast<size_t>(c) * ldhr] * y[c];
+    y[r] = acc / Hr[r + static_cast<size_t>(r) * ldhr];
   }
+}
+
+double Givens::add_column(const double* H, int ldh, int j) {
+  return givens_column(Hr.data(), m + 1, cs.data(), sn.data(), g.data(), H, ldh, j);
+}
+
+void Givens::solve(int jj, double* y) const {
+  givens_solve(Hr.data(), m + 1, g.data(), jj, y);
+}
+
+void combine_r(int i, int q, const double* W, int ldw, const double* Rp, int ldrp,
+               const double* Z1, int ldz1, const double* R2, int ldr2, double* R_top,
+               int ldt, double* R_kk, int ldk) {
+  for (int c = 0; c < q; ++c) {
+    for (int r = 0; r < i; ++r) {
+      double acc = W[r + static_cast<int64_t>(c) * ldw];
+      for (int t = 0; t <= c; ++t)
+        acc += Rp[r + static_cast<int64_t>(t) * ldrp] * Z1[t + static_cast<int64_t>(c) * ldz1];
+      R_top[r + static_cast<int64_t>(c) * ldt] = acc;
+    }
+    for (int r = 0; r < q; ++r) {
+      double acc = 0.0;
+      for (int t = r; t <= c; ++t)
+        acc += R2[r + static_cast<int64_t>(t) * ldr2] * Z1[t + static_cast<int64_t>(c) * ldz1];
+      R_kk[r + static_cast<int64_t>(c) * ldk] = acc;
+    }
+  }
+}
+
+int64_t halo_plan(int rows, const int32_t* rowptr, const int32_t* colind, int32_t lo,
+                  int32_t hi, int32_t* local_colind, int32_t* halo_cols) {
+  const int64_t nnz = rowptr[rows];
+  std::vector<int32_t> halo;
+  for (int64_t k = 0; k < nnz; ++k)
+    if (colind[k] < lo || colind[k] >= hi) halo.push_back(colind[k]);
+  std::sort(halo.begin(), halo.end());
+  halo.erase(std::unique(halo.begin(), halo.end()), halo.end());
+  if (halo_cols) std::copy(halo.begin(), halo.end(), halo_cols);
+  if (local_colind) {
+    for (int64_t k = 0; k < nnz; ++k) {
+      const int32_t c = colind[k];
+      if (c >= lo && c < hi) {
+        local_colind[k] = c - lo;
+      } else {
+        const auto it = std::lower_bound(halo.begin(), halo.end(), c);
+        local_colind[k] = rows + static_cast<int32_t>(it - halo.begin());
+      }
+    }
+  }
+  return static_cast<int64_t>(halo.size());
 }
 
 }  // namespace sg

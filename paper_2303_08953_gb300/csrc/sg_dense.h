@@ -55,6 +55,29 @@ void assemble_hessenberg(double* H, int ldh, int i, int q,
                          const double* R_top, int ldt, const double* R_kk,
                          int ldk, const double* B, int ldb);
 
+// R_top = W(:, 1:q) + R'(:, 1:q) Z(1:q, 1:q) (i x q) and R_kk = Z~ Z(1:q, 1:q)
+// (q x q, upper triangular): the two BCGS passes combined (Alg. 4
+// 'Combine both steps').  Z and Z~ are upper triangular.
+void combine_r(int i, int q, const double* W, int ldw, const double* Rp, int ldrp,
+               const double* Z1, int ldz1, const double* R2, int ldr2, double* R_top,
+               int ldt, double* R_kk, int ldk);
+
+// Column j of the unrotated H (rows 0..j+1) into Hr, rotated by the
+// previous rotations; a new rotation annihilates Hr(j+1, j) and updates g.
+// Returns |g[j+1]| (Alg. 1 'Apply Givens').
+double givens_column(double* Hr, int ldhr, double* cs, double* sn, double* g,
+                     const double* H, int ldh, int j);
+// y of the leading jj x jj triangular system Hr y = g.
+void givens_solve(const double* Hr, int ldhr, const double* g, int jj, double* y);
+
+// Halo of a block of consecutive rows [lo, hi) of a row-partitioned CSR
+// (columns global): the sorted distinct columns outside [lo, hi) into
+// halo_cols (may be NULL), and each entry's local column into
+// local_colind (may be NULL): c - lo for an owned column, rows + its
+// position in halo_cols otherwise.  Returns the number of halo columns.
+int64_t halo_plan(int rows, const int32_t* rowptr, const int32_t* colind, int32_t lo,
+                  int32_t hi, int32_t* local_colind, int32_t* halo_cols);
+
 // Least-squares state of GMRES: rotated Hessenberg, rotations, g.
 struct Givens {
   int m = 0;

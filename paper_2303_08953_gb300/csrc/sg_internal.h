@@ -182,7 +182,12 @@ void tc_update(int64_t n, const float* Q, int64_t ldq, int i, const double* W,
                cudaStream_t st);
 void tc_update_check_error(cudaStream_t st);
 
+// dst[k] = src[idx[k]], k < count (device arrays).
+void gather(const int32_t* idx, int64_t count, const double* src, double* dst,
+            cudaStream_t st);
+
 int device_sm_count();  // of the current device
+int current_device();
 // cudaFuncSetAttribute(MaxDynamicSharedMemorySize) for kernel fn on the
 // current device, once per (kernel, device) and size
 void ensure_dynamic_smem(const void* fn, int bytes);

@@ -564,20 +564,8 @@ void solve_impl(sg_handle* h, const DevCsr& M, const SolveOpts& o,
           // R_top = W(:, 1:q) + R'(:, 1:q) Z(1:q, 1:q); R_kk = Z~ Z(1:q, 1:q)
           Rtop.assign(static_cast<size_t>(i) * q, 0.0);
           Rkk.assign(static_cast<size_t>(q) * q, 0.0);
-          for (int c = 0; c < q; ++c) {
-            for (int r = 0; r < i; ++r) {
-              double acc = Wh[r + static_cast<int64_t>(c) * i];
-              for (int t = 0; t <= c; ++t)
-                acc += Rph[r + static_cast<int64_t>(t) * i] * Z1[t + static_cast<int64_t>(c) * ldr];
-              Rtop[r + static_cast<int64_t>(c) * i] = acc;
-            }
-            for (int r = 0; r <= c; ++r) {
-              double acc = 0.0;
-              for (int t = r; t <= c; ++t)
-                acc += R2[r + static_cast<int64_t>(t) * p1] * Z1[t + static_cast<int64_t>(c) * ldr];
-              Rkk[r + static_cast<int64_t>(c) * q] = acc;
-            }
-          }
+          combine_r(i, q, Wh.data(), i, Rph.data(), i, Z1.data(), ldr, R2.data(), p1,
+                    Rtop.data(), i, Rkk.data(), q);
           upper_inverse(R2.data(), p1, q, Zinv.data(), q);
           std::memcpy(hb + sl.Z, Zinv.data(), sizeof(double) * q * q);
           log.t_host += now_ms() - th1;
@@ -648,6 +636,19 @@ void solve_impl(sg_handle* h, const DevCsr& M, const SolveOpts& o,
 }
 
 }  // namespace
+
+int ritz_prepass(sg_handle* h, const DevCsr& M, const double* q, int k, bool fp32,
+                 cudaStream_t st, std::vector<double>& H) {
+  const int64_t n = M.n;
+  if (fp32) {
+    ensure_workspace32(h, n, k, k);
+    to_f32(n, q, h->Q32, 1.0f, st);
+    return arnoldi_prepass<float>(h, M, h->Q32, k, st, H);
+  }
+  ensure_workspace(h, n, k, k);
+  SG_CUDA(cudaMemcpyAsync(h->Q, q, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  return arnoldi_prepass<double>(h, M, h->Q, k, st, H);
+}
 
 void solve_fp64(sg_handle* h, const DevCsr& M, const SolveOpts& o,
                 cudaStream_t st, SolveLog& log) {

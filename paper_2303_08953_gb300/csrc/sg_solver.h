@@ -12,6 +12,8 @@ struct sg_handle {
   sg::DevCsr A;      // the analysed matrix
   sg::DevCsr AT;     // its transpose (built on the first adjoint call)
   bool have_A = false, have_AT = false;
+  bool rows_only = false;  // A is a row block (sg_analyze_rows): kernel-level calls only
+  int64_t ncols = 0;       // columns of A (n for a square matrix)
   std::string err;
 
   // workspace (sized on demand, kept until destroy)
@@ -84,6 +86,13 @@ void ensure_workspace(sg_handle* h, int64_t n, int m, int k);
 void count_launches(long long k);
 long long launches_so_far();
 void ensure_workspace32(sg_handle* h, int64_t n, int m, int k);
+
+// Ritz pre-pass alone (Sec. 3.4): k steps of MGS-Arnoldi with M from the
+// unit vector q (device, FP64; rounded to FP32 for the FP32 basis) in the
+// workspace basis.  Fills H ((k+1) x k, ld k+1, host) and returns the
+// steps completed.
+int ritz_prepass(sg_handle* h, const DevCsr& M, const double* q, int k, bool fp32,
+                 cudaStream_t st, std::vector<double>& H);
 
 // FP64 adaptive s-step GMRES on matrix M (A or A^T): b, x device vectors
 // of the workspace (x in: x0, out: solution).

@@ -685,6 +685,85 @@ def test_prepass_reproduces_jacobi_matrix(solver, precision, n, k):
     assert np.allclose(np.sort(got.real), ref, rtol=0, atol=1e-11 * np.max(np.abs(ref)))
 
 
+ARNOLDI_CASES = {
+    # one CTA (2025 rows), two CTAs of 2048 rows, 16 CTAs, and 151 CTAs
+    # whose last one holds a ragged 1603 rows (rows per CTA rounded to 32)
+    "stencil2d_45": lambda: W.stencil2d(45, 45),
+    "stencil2d_64": lambda: W.stencil2d(64, 64),
+    "convdiff3d_32": lambda: W.stencil3d_convdiff(32),
+    "randband_400003": lambda: W.random_band(400_003, k=24, band=4096)[0],
+}
+
+
+@pytest.mark.parametrize("name", list(ARNOLDI_CASES))
+@pytest.mark.parametrize("k", [1, 12])
+def test_arnoldi_hessenberg_matches_oracle(solver, name, k):
+    """sg_arnoldi (the Ritz pre-pass, Sec. 3.4) against the oracle's
+    MGS-Arnoldi, entry by entry.  Two runs of MGS-Arnoldi that differ only
+    in rounding order have Hessenberg columns j that differ by about
+    u kappa(K_{j+2}) ||A||, K the normalised Krylov matrix [q, Aq, ...]
+    (a first-order perturbation of its QR factor); the tolerance is 8 times
+    that, and at least 1e-12 ||A||_1.  The first columns are thus held to
+    a few ulps of ||A||, where a wrong projection would show at O(1)."""
+    A = ARNOLDI_CASES[name]()
+    op = _analyze(solver, A)
+    q = np.random.default_rng(31).uniform(-1, 1, A.n)
+    q /= np.linalg.norm(q)
+    H, steps = solver.arnoldi(dev(q), k)
+    Ho, so = O.arnoldi_mgs(op, q, k)
+    assert steps == so == k
+    anorm = abs(op).sum(axis=0).max()
+    K = [q]
+    for _ in range(k):
+        v = op @ K[-1]
+        K.append(v / np.linalg.norm(v))
+    K = np.column_stack(K)
+    for j in range(k):
+        tol = max(8 * 2.0 ** -53 * np.linalg.cond(K[:, :j + 2]) * anorm, 1e-12 * anorm)
+        assert np.all(np.abs(H[:, j] - Ho[:, j]) <= tol), (j, np.abs(H[:, j] - Ho[:, j]).max(), tol)
+
+
+@pytest.mark.parametrize("n,k", [(2025, 70), (884_737, 40)])
+def test_arnoldi_reproduces_jacobi_matrix_exactly(solver, n, k):
+    """From the head of a symmetric tridiagonal chain, FP64 Arnoldi is
+    Lanczos on a Jacobi matrix: every projection, coupling and norm is exact,
+    so H equals the chain's leading block entry for entry (884,737 rows
+    spread the chain over every CTA of the resident step)."""
+    A, a, b = W.jacobi_chain(n)
+    _analyze(solver, A)
+    q = np.zeros(n)
+    q[0] = 1.0
+    H, steps = solver.arnoldi(dev(q), k)
+    assert steps == k
+    T = np.diag(a[:k]) + np.diag(b[:k - 1], 1) + np.diag(b[:k - 1], -1)
+    assert np.array_equal(H[:k, :k], T) and H[k, k - 1] == b[k - 1]
+    assert np.all(H[k, :k - 1] == 0.0)
+
+
+def test_arnoldi_stops_at_an_invariant_subspace(solver):
+    """A diagonal matrix with 5 distinct eigenvalues: the Krylov space of
+    any start vector has dimension 5, so the pre-pass stops after 5 steps
+    (h_65 below 1e-12 of ||A v_5||), like the oracle."""
+    lam = np.repeat([1.0, 2.0, 3.5, 5.0, 8.0], 600)
+    A = W.diagonal(lam)
+    op = _analyze(solver, A)
+    q = np.random.default_rng(5).uniform(-1, 1, A.n)
+    q /= np.linalg.norm(q)
+    _, steps = solver.arnoldi(dev(q), 9)
+    _, so = O.arnoldi_mgs(op, q, 9)
+    assert steps == so == 5
+
+
+def test_arnoldi_rejects_bad_arguments(solver):
+    A = W.stencil2d(8, 8)
+    _analyze(solver, A)
+    q = dev(np.ones(A.n) / 8.0)
+    with pytest.raises(sg.SgError):
+        solver.arnoldi(q, 0)
+    with pytest.raises(sg.SgError):
+        solver.arnoldi(q, 3, precision=7)
+
+
 # ------------------------------------------------------ full-size workload
 @pytest.mark.slow
 def test_full_size_c2_sampled_and_converged(solver):
