@@ -1,13 +1,19 @@
-"""Benchmark: time to relative residual 1e-10 of the adaptive s-step GMRES
-on the 3D 7-point convection-diffusion system (128^3 grid, N = 2,097,152,
-nnz = 14,581,760; m = 240, scaled Newton basis, s estimated in [20, 120]).
+"""Benchmark: time to relative residual 1e-10 of the adaptive s-step GMRES.
+
+Headline workload: the unstructured random-band system, N = 4,194,304 rows
+with 24 off-diagonal entries per row at distinct offsets within +-4096 and
+a 1.1x dominant diagonal (nnz = 104,857,600), m = 120, scaled Newton basis,
+s estimated from a 120-step Ritz pre-pass, tol 1e-10.
 
 One step = one complete solve from x0 = 0 (Ritz pre-pass, estimator, every
 block and restart) with A and b resident in HBM.  The FP64 solve gives
 `value`; the FP32-basis + FP64-refinement solve and the forward + adjoint
-pair are reported beside it on the same system.
+pair (loss 0.5 ||x - x_t||^2) are reported beside it on the same system,
+and the 128^3 convection-diffusion system (m = 240, s in [20, 120]) as a
+secondary line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--config c5|c2|c3] [--with-c3]
 
 N > 1 (under torchrun): every rank solves its own copy (replicas), the
 reported time is the max over ranks.  --impl reference times the CPU oracle
@@ -36,9 +42,26 @@ METRIC = "time to relres 1e-10: FP64 vs FP32-basis+IR, fwd+adjoint; % HBM roofli
 VALUE_IS = ("seconds per FP64 adaptive s-step GMRES solve to relres 1e-10; the FP32-basis+IR "
             "and forward+adjoint times are in fp32_ir / fwd_adjoint, the SpMV % of HBM in "
             "roofline_spmv, the FP32-basis block kernels' rooflines in roofline_fp32")
-GRID = 128
-SOLVE_KW = dict(m=240, s=0, s_min=20, s_max=120, tol=1e-10)
+
+# workloads: generator, solver options, bench label
+WORKLOADS = {
+    "c5": dict(label="randband_4194304_k24_band4096",
+               opts=dict(m=120, s=0, s_min=1, s_max=120, tol=1e-10),
+               s_desc="auto[1,120]", seed=4),
+    "c2": dict(label="convdiff3d_128^3",
+               opts=dict(m=240, s=0, s_min=20, s_max=120, tol=1e-10),
+               s_desc="auto[20,120]", seed=1),
+    "c3": dict(label="vardiff3d_192^3",
+               opts=dict(m=200, s=0, s_min=1, s_max=60, tol=1e-10, max_iters=20000),
+               s_desc="auto[1,60]", seed=2),
+}
 FP64_ALU_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12   # 152 SMs x 2.07 GHz x 4 flop/clk
+# FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz (FADD / FMUL / FFMA each one op)
+FP32_ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+# FP32 instructions per exact Gram product: product, FMA remainder, the six
+# additions of the two-sum, two additions into the compensation
+GRAM_OPS_PER_PRODUCT = 10
+PREPASS_STEPS = 120
 
 
 def parse():
@@ -47,13 +70,18 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--grid", type=int, default=GRID)
+    p.add_argument("--config", default="c5", choices=list(WORKLOADS))
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-variants", action="store_true")
+    p.add_argument("--no-secondary", action="store_true")
+    p.add_argument("--with-c3", action="store_true",
+                   help="also time the 192^3 mixed-precision system (minutes)")
     p.add_argument("--case", default=None,
-                   choices=["solve-fp64", "solve-fp32ir", "spmv", "dot64",
-                            "upd64", "dot32", "gram32", "upd32"],
+                   choices=["solve-fp64", "solve-fp32ir", "prepass64", "prepass32",
+                            "spmv", "dot64", "gram64", "upd64", "dot32", "gram32", "upd32"],
                    help="run one small workload for a profiler and exit")
+    p.add_argument("--rows", type=int, default=None,
+                   help="rows of the --case workload (random band recipe)")
     return p.parse_args()
 
 
@@ -147,66 +175,79 @@ def max_over_ranks(v, world):
     return float(t.item())
 
 
-def workload(grid):
+def make_workload(name, rows=None):
+    """The seeded system of workload `name` (rows: a smaller instance of the
+    random-band recipe) and the bench line's config record."""
     import workloads as W
-    c = W.config_c2(grid)
+    spec = WORKLOADS[name]
+    if name == "c5":
+        c = W.config_c5(rows) if rows else W.config_c5()
+    elif name == "c2":
+        c = W.config_c2(128)
+    else:
+        c = W.config_c3(192)
     A = c["A"]
-    return c, {"workload": f"convdiff3d_{grid}^3", "n": int(A.n),
-               "nnz": int(A.nnz), "m": SOLVE_KW["m"], "s": "auto[20,120]",
-               "basis": "scaled_newton", "tol": SOLVE_KW["tol"],
-               "x0": "zero", "l2": "inputs larger than L2 (A 175 MB, Q 4 GB)"}
-
-
-# DRAM bytes per row of the FP64 block dot (i = 107, s = 106) from one ncu
-# capture at n = 2^20: read 2,291,351,000 + write 5,751,296 bytes.
-DOT64_DRAM_BYTES_PER_ROW = (2_291_351_000 + 5_751_296) / (1 << 20)
-
-
-# DRAM bytes per row of the FP32 tensor-core block dot (W = Q^T X) and
-# update (X -= Q W) at i = 107, s = 106, from ncu captures at n = 2^20:
-# dot read 893,510,656 + write 3,351,552; update read 893,552,896 + write
-# 395,420,928.
-TCDOT_DRAM_BYTES_PER_ROW = (893_510_656 + 3_351_552) / (1 << 20)
-TCUPD_DRAM_BYTES_PER_ROW = (893_552_896 + 395_420_928) / (1 << 20)
-# FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz (FADD / FMUL / FFMA each one op)
-FP32_ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
-# FP32 instructions per exact Gram product: product, FMA remainder, the six
-# additions of the two-sum, two additions into the compensation
-GRAM_OPS_PER_PRODUCT = 10
+    cfg = {"workload": spec["label"] if not rows else f"randband_{rows}_k24_band4096",
+           "n": int(A.n), "nnz": int(A.nnz), "m": spec["opts"]["m"],
+           "s": spec["s_desc"], "basis": "scaled_newton", "tol": spec["opts"]["tol"],
+           "x0": "zero", "precision_of_value": "fp64",
+           "l2": f"inputs larger than L2 (A {(12 * A.nnz + 4 * A.n) / 1e6:.0f} MB)"}
+    return c, cfg, dict(spec["opts"])
 
 
 def spmv_bytes(A):
+    """Algorithmic bytes of one FP64 SpMV: values + indices, row pointers,
+    x read once, y written once."""
     return 12 * A.nnz + 4 * (A.n + 1) + 8 * A.n + 8 * A.n
 
 
+def prepass_flops(A, k):
+    """FP64 flops of k MGS-Arnoldi steps (Sec. 3.4): per step j one SpMV
+    (2 nnz), j+1 projections (dot and update, 4 N each), the norm of w
+    (2 N) and its scaling (N)."""
+    return sum(2 * A.nnz + 4 * A.n * (j + 1) + 3 * A.n for j in range(k))
+
+
+def prepass_bytes(A, k):
+    """Algorithmic HBM bytes of the same k steps: the SpMV, every basis
+    vector read once per step, the new vector written once."""
+    return sum(spmv_bytes(A) - 8 * A.n + 8 * A.n * (j + 1) + 8 * A.n for j in range(k))
+
+
+# DRAM bytes per launch of the resident FP64 pre-pass step, per row, from
+# an ncu capture (profiles/arnoldi_step_resident_fp64_randband_1M.md);
+# None until that capture exists.
+PREPASS_DRAM_BYTES_PER_ROW = None
+
+
 # ------------------------------------------------------------ CPU oracle
-# Krylov columns the 128^3 solve takes to reach 1e-10 (the oracle and the
-# library take identical step-size decisions, so both need this many).
-FULL_SOLVE_COLUMNS = 649
-SAMPLE = dict(m=240, s=20, tol=1e-10, max_iters=60)
+# The oracle's complete solve of the headline workload takes minutes on the
+# host (it is plain numpy, one projection at a time), so the CPU baseline is
+# a complete oracle solve of the same recipe with fewer rows, scaled by rows
+# to the full system.  Every oracle operation of the solve (CSR product,
+# dot, update, Gram, triangular solve) costs O(rows) at fixed decisions.
+SAMPLE_ROWS = 262_144
 
 
-def cpu_oracle_sample(c):
-    """The oracle, as it stands, on a bounded sample of the same solve:
-    s fixed at 20 (20-step Ritz pre-pass), stopped after 60 Krylov
-    columns (3 blocks).  Returns (seconds, columns)."""
+def cpu_oracle_sample(name):
+    """(seconds, effective threads, oracle result, rows) of one complete
+    oracle solve of the workload recipe at SAMPLE_ROWS rows (c5) or of the
+    workload itself (c2/c3 are not sampled this way)."""
     from oracle import sgmres_oracle as O
-    t0 = time.perf_counter()
-    r = O.adaptive_sgmres(c["A"], c["b"], **SAMPLE)
-    return time.perf_counter() - t0, r.iters
+    c, _, opts = make_workload(name, rows=SAMPLE_ROWS if name == "c5" else None)
+    t0, c0 = time.perf_counter(), os.times()
+    r = O.adaptive_sgmres(c["A"], c["b"], **opts)
+    dt, c1 = time.perf_counter() - t0, os.times()
+    cpu = (c1.user - c0.user) + (c1.system - c0.system)
+    return dt, cpu / dt if dt > 0 else 1.0, r, int(c["A"].n)
 
 
-def sample_text(dt, its, full):
-    return (f"oracle FP64 solve of the same system with s fixed at 20 "
-            f"(20-step Ritz pre-pass) stopped after {its} Krylov columns: "
-            f"{dt:.2f} s, scaled by columns to the full solve's {full}")
-
-
-def oracle_threads():
-    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
-        if os.environ.get(var):
-            return int(os.environ[var])
-    return os.cpu_count()
+def sample_text(dt, rows, full_rows, r):
+    return (f"complete oracle FP64 solve (oracle/sgmres_oracle.py adaptive_sgmres, "
+            f"Ritz pre-pass + estimator + every block) of the same random-band recipe "
+            f"at {rows} rows: {dt:.1f} s, {r.iters} Krylov columns, s0 {r.s0}, "
+            f"blocks {list(map(int, r.s_hist))}, relres {r.final_relres:.2e}; "
+            f"scaled by rows x{full_rows / rows:g} to the {full_rows}-row system")
 
 
 # ------------------------------------------------------------ our arm
@@ -216,26 +257,21 @@ def run_ours(args):
     world, rank, local = dist_setup(args)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    c, cfg = workload(args.grid)
+    c, cfg, opts = make_workload(args.config)
     A = c["A"]
     solver = sg.Solver(local)
     solver.analyze_csr(A)
     b = torch.as_tensor(c["b"], dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2
     stream = torch.cuda.current_stream()
-
-    def one(**kw):
-        x, info = solver.solve(b, **SOLVE_KW, **kw)
-        return x, info
-
     launches = [0]
 
-    def timed(kw, steps, warm):
+    def timed(fn, steps, warm):
         for _ in range(warm):
-            one(**kw)
+            fn()
         torch.cuda.synchronize()
         barrier(world)
-        times, info = [], None
+        times, res = [], None
         l0 = sg.kernel_launches()
         for _ in range(steps):
             flush.zero_()
@@ -243,32 +279,37 @@ def run_ours(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            x, info = one(**kw)
+            res = fn()
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
         launches[0] = (sg.kernel_launches() - l0) // max(1, steps)
         barrier(world)
-        return times, x, info
+        return times, res
+
+    def solve(prec="fp64", sv=solver, rhs=b, o=opts):
+        return sv.solve(rhs, precision=prec, **o)
 
     # ---- headline: FP64 solve
     clocks = ClockSampler(local)
-    times, x, info = timed({}, args.steps, args.warmup)
+    times, (x, info) = timed(solve, args.steps, args.warmup)
     n_launch = launches[0]
     clk = clocks.stop()
     ms_step = max_over_ranks(sum(times) / len(times), world)
     xs = c["xstar"]
-    err = float(np.linalg.norm(x.cpu().numpy() - xs) / np.linalg.norm(xs))
+    xh = x.cpu().numpy()
+    err = float(np.linalg.norm(xh - xs) / np.linalg.norm(xs))
     out = {
         "metric": METRIC, "value": ms_step / 1e3, "unit": "s", "value_is": VALUE_IS,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic (seeded generator, x* ~ U(-1,1) seed 1, b = A x*)",
+        "data": f"synthetic (seeded generator, seed {WORKLOADS[args.config]['seed']}; "
+                f"x* ~ U(-1,1), b = A x*)",
         "config": cfg,
         "solve": {"converged": info.converged, "iters": info.iters,
                   "restarts": info.restarts, "s0": info.s0,
-                  "s_hist_first": [int(v) for v in info.s_hist[:6]],
+                  "s_hist_first": [int(v) for v in info.s_hist[:8]],
                   "final_relres": info.final_relres, "x_err_vs_xstar": err,
                   "phase_ms": {k: round(v, 2) for k, v in info.times_ms.items()},
                   "step_ms_all": [round(t, 2) for t in times],
@@ -280,41 +321,32 @@ def run_ours(args):
 
     # ---- variants on the same system
     if not args.no_variants:
-        t32, x32, i32 = timed({"precision": "fp32_ir"}, args.steps, 1)
-        e32 = float(np.linalg.norm(x32.cpu().numpy() - xs) / np.linalg.norm(xs))
+        t32, (x32, i32) = timed(lambda: solve("fp32_ir"), args.steps, 1)
+        x32h = x32.cpu().numpy()
         out["fp32_ir"] = {
             "time_s": max_over_ranks(sum(t32) / len(t32), world) / 1e3,
             "iters": i32.iters, "refinements": i32.refinements,
-            "s0": i32.s0, "final_relres": i32.final_relres,
-            "x_err_vs_xstar": e32,
-            "x_err_vs_fp64": float(np.linalg.norm(x32.cpu().numpy()
-                                                  - x.cpu().numpy())
-                                   / np.linalg.norm(x.cpu().numpy())),
+            "fp64_iters": i32.fp64_iters, "s0": i32.s0,
+            "final_relres": i32.final_relres,
+            "x_err_vs_xstar": float(np.linalg.norm(x32h - xs) / np.linalg.norm(xs)),
+            "x_err_vs_fp64": float(np.linalg.norm(x32h - xh) / np.linalg.norm(xh)),
             "phase_ms": {k: round(v, 2) for k, v in i32.times_ms.items()}}
-        # loss L = 0.5 ||x - x_t||^2 with x_t ~ U(-1,1) drawn after x* from
-        # x*'s seeded stream (the differentiation workloads' loss); a target
-        # of x* itself would make dL/dx the forward error, which lies in a
-        # few slow eigenmodes and gives an ill-conditioned adjoint Krylov
-        # basis from its first columns
-        import workloads as W
-        rng_t = np.random.default_rng(1)
-        W.uniform_vector(len(xs), rng_t)
-        xt = torch.as_tensor(W.uniform_vector(len(xs), rng_t), device=dev)
+        # loss L = 0.5 ||x - x_t||^2 with the workload's target x_t ~ U(-1,1)
+        # (drawn after x* from its seeded stream)
+        xt = torch.as_tensor(c["xtarget"], device=dev)
         fa = []
         for prec in ("fp32_ir", "fp64"):
-            ts = []
-            for k in range(max(1, args.steps // 2) + 1):
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                xf, inf1 = solver.solve(b, precision=prec, **SOLVE_KW)
-                g = xf - xt   # dL/dx
-                lam, inf2 = solver.solve_adjoint(g, precision=prec, **SOLVE_KW)
-                dval = solver.grad_values(lam, xf)
-                torch.cuda.synchronize()
-                if k:
-                    ts.append(time.perf_counter() - t0)
+            def pair(prec=prec):
+                # the adjoint reuses the forward solve's Ritz values (A^T
+                # has A's eigenvalues) instead of its own pre-pass
+                xf, inf1 = solver.solve(b, precision=prec, **opts)
+                lam, inf2 = solver.solve_adjoint(xf - xt, precision=prec, ritz=inf1.ritz,
+                                                 **opts)
+                solver.grad_values(lam, xf)
+                return inf1, inf2
+            ts, (inf1, inf2) = timed(pair, max(1, args.steps // 2), 1)
             fa.append({"precision": prec,
-                       "time_s": max_over_ranks(sum(ts) / len(ts), world),
+                       "time_s": max_over_ranks(sum(ts) / len(ts), world) / 1e3,
                        "fwd_iters": inf1.iters, "adj_iters": inf2.iters,
                        "fwd_relres": inf1.final_relres,
                        "adj_relres": inf2.final_relres,
@@ -323,60 +355,66 @@ def run_ours(args):
                        "adj_phase_ms": {k: round(v, 2) for k, v in inf2.times_ms.items()}})
         out["fwd_adjoint"] = fa
 
-    # ---- roofline of the dominant kernel (FP64 block dot, FP64 pipe)
-    n = A.n
-    i_blk, s_blk = 107, 106
-    Q = torch.randn(i_blk, n, dtype=torch.float64, device=dev)
-    X = torch.randn(s_blk, n, dtype=torch.float64, device=dev)
-    for _ in range(2):
-        solver.block_dot(Q, X)
+    # ---- roofline of the dominant kernel: the FP64 Ritz pre-pass step (one
+    # cooperative MGS-Arnoldi launch per step, Sec. 3.4), timed over the
+    # 120 launches of the pre-pass with CUDA events on the launching stream
+    q = b / torch.linalg.vector_norm(b)
+    solver.arnoldi(q, PREPASS_STEPS)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    reps = 5
+    reps = 3
     e0.record(stream)
     for _ in range(reps):
-        solver.block_dot(Q, X)
+        solver.arnoldi(q, PREPASS_STEPS)
     e1.record(stream)
     torch.cuda.synchronize()
-    t_dot = e0.elapsed_time(e1) / reps / 1e3
-    flops = 2.0 * n * i_blk * s_blk
-    ach = flops / t_dot / 1e12
+    t_pre = e0.elapsed_time(e1) / reps / 1e3
+    t_launch = t_pre / PREPASS_STEPS
+    fl = prepass_flops(A, PREPASS_STEPS) / PREPASS_STEPS
+    by = prepass_bytes(A, PREPASS_STEPS) / PREPASS_STEPS
+    pk = measured_peaks()
+    hbm = pk["hbm_gbs"] if pk else 6800.0
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs" if pk else "fallback"
+    ach = fl / t_launch / 1e12
     out["roofline"] = {
-        "kernel": f"block_dot FP64 (W = Q^T X, i={i_blk}, s={s_blk})",
+        "kernel": f"arnoldi_step FP64 (Ritz pre-pass step, mean of the {PREPASS_STEPS} "
+                  f"launches of one pre-pass)",
         "bound": "alu", "achieved": round(ach, 4),
         "peak": round(FP64_ALU_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
         "frac": round(ach / FP64_ALU_PEAK_TFLOPS, 4),
-        "traffic": int(round(DOT64_DRAM_BYTES_PER_ROW * n)),
-        "traffic_source": "ncu dram__bytes_read+write of dot_tile_kernel at "
-                          "n = 2^20 (same i, s), scaled by rows to this n "
-                          "(profiles/dot_tile_fp64_n1M_i107_s106.md)",
+        "traffic": (int(round(PREPASS_DRAM_BYTES_PER_ROW * A.n))
+                    if PREPASS_DRAM_BYTES_PER_ROW else None),
+        "launch_ms": round(t_launch * 1e3, 4),
+        "algorithmic_flops_per_launch": int(fl),
+        "algorithmic_bytes_per_launch": int(by),
+        "hbm_frac": round(by / t_launch / 1e9 / hbm, 4),
         "peak_source": "derived: 152 SMs x 2.07 GHz x 4 FP64 flop/clk/SM "
                        "(nominal 1.25 TFLOP/s FP64)"}
-    del Q, X
+
     # secondary: the MPK's SpMV against HBM
+    n = A.n
     xv = torch.rand(n, dtype=torch.float64, device=dev)
     yv = torch.empty_like(xv)
     for _ in range(5):
         solver.spmv_newton(xv, 0.3, 1.1, out=yv)
     torch.cuda.synchronize()
-    reps = 50
+    reps = 30
     e0.record(stream)
     for _ in range(reps):
         solver.spmv_newton(xv, 0.3, 1.1, out=yv)
     e1.record(stream)
     torch.cuda.synchronize()
     t_sp = e0.elapsed_time(e1) / reps / 1e3
-    pk = measured_peaks()
-    hbm = pk["hbm_gbs"] if pk else 6800.0
     gbs = spmv_bytes(A) / t_sp / 1e9
     out["roofline_spmv"] = {
         "kernel": "spmv_newton FP64 (one MPK step)", "bound": "hbm",
         "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
-        "frac": round(gbs / hbm, 4), "traffic": None,
-        "peak_source": "MEASURED_PEAKS.json hbm_gbs" if pk else "fallback"}
+        "frac": round(gbs / hbm, 4), "traffic": None, "peak_source": hbm_src}
+    del xv, yv
 
-    # the FP32-basis path's block kernels at the same block shape
+    # the block kernels at the 128^3 system's second-block shape
+    # (i = 107, s = 106) on 2^21 rows
     def event_ms(fn, reps=5):
         for _ in range(2):
             fn()
@@ -387,30 +425,47 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
-    Q32 = torch.randn(i_blk, n, dtype=torch.float32, device=dev)
-    X32 = torch.randn(s_blk, n, dtype=torch.float32, device=dev)
+    nb, i_blk, s_blk = 1 << 21, 107, 106
+    solver.n = nb
+    Q64 = torch.randn(i_blk, nb, dtype=torch.float64, device=dev)
+    X64 = torch.randn(s_blk, nb, dtype=torch.float64, device=dev)
+    t_dot = event_ms(lambda: solver.block_dot(Q64, X64)) / 1e3
+    t_g64 = event_ms(lambda: solver.block_dot(X64, X64, sym=True)) / 1e3
+    del Q64, X64
+    Q32 = torch.randn(i_blk, nb, dtype=torch.float32, device=dev)
+    X32 = torch.randn(s_blk, nb, dtype=torch.float32, device=dev)
     W64 = torch.randn(s_blk, i_blk, dtype=torch.float64, device=dev)
     t_tcd = event_ms(lambda: solver.block_dot32(Q32, X32)) / 1e3
     t_tcu = event_ms(lambda: solver.block_update32(Q32, W64, X32)) / 1e3
     t_gram = event_ms(lambda: solver.block_dot32(X32, X32, sym=True)) / 1e3
     del Q32, X32, W64
-    b_tcd = 4.0 * n * (i_blk + s_blk)
-    b_tcu = 4.0 * n * (i_blk + 2 * s_blk)
-    ops_gram = GRAM_OPS_PER_PRODUCT * n * s_blk * (s_blk + 1) / 2.0
-    hbm_src = "MEASURED_PEAKS.json hbm_gbs" if pk else "fallback"
+    solver.n = A.n
+    f_dot = 2.0 * nb * i_blk * s_blk
+    f_g64 = nb * s_blk * (s_blk + 1.0)
+    out["roofline_block_fp64"] = [
+        {"kernel": f"block_dot FP64 (W = Q^T X, i={i_blk}, s={s_blk}, n=2^21)",
+         "bound": "alu", "achieved": round(f_dot / t_dot / 1e12, 4),
+         "peak": round(FP64_ALU_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+         "frac": round(f_dot / t_dot / 1e12 / FP64_ALU_PEAK_TFLOPS, 4)},
+        {"kernel": f"Gram FP64 (X^T X upper triangle, s={s_blk}, n=2^21)",
+         "bound": "alu", "achieved": round(f_g64 / t_g64 / 1e12, 4),
+         "peak": round(FP64_ALU_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+         "frac": round(f_g64 / t_g64 / 1e12 / FP64_ALU_PEAK_TFLOPS, 4)}]
+    b_tcd = 4.0 * nb * (i_blk + s_blk)
+    b_tcu = 4.0 * nb * (i_blk + 2 * s_blk)
+    ops_gram = GRAM_OPS_PER_PRODUCT * nb * s_blk * (s_blk + 1) / 2.0
     out["roofline_fp32"] = [
         {"kernel": f"tc_dot FP32 basis (W = Q^T X on tcgen05, 3xTF32, i={i_blk}, s={s_blk})",
          "bound": "hbm", "achieved": round(b_tcd / t_tcd / 1e9, 1), "peak": hbm,
-         "unit": "GB/s", "frac": round(b_tcd / t_tcd / 1e9 / hbm, 4),
-         "traffic": int(round(TCDOT_DRAM_BYTES_PER_ROW * n)), "peak_source": hbm_src},
+         "unit": "GB/s", "frac": round(b_tcd / t_tcd / 1e9 / hbm, 4), "peak_source": hbm_src},
         {"kernel": f"tc_update FP32 basis (X -= Q W on tcgen05, 3xTF32, i={i_blk}, s={s_blk})",
          "bound": "hbm", "achieved": round(b_tcu / t_tcu / 1e9, 1), "peak": hbm,
-         "unit": "GB/s", "frac": round(b_tcu / t_tcu / 1e9 / hbm, 4),
-         "traffic": int(round(TCUPD_DRAM_BYTES_PER_ROW * n)), "peak_source": hbm_src},
-        {"kernel": f"gram_exact FP32 basis (X^T X, exact products, s={s_blk})",
+         "unit": "GB/s", "frac": round(b_tcu / t_tcu / 1e9 / hbm, 4), "peak_source": hbm_src},
+        {"kernel": f"Gram FP32 basis (X^T X, s={s_blk})",
          "bound": "alu", "achieved": round(ops_gram / t_gram / 1e12, 2),
          "peak": round(FP32_ALU_PEAK_TOPS, 2), "unit": "T FP32-op/s",
-         "frac": round(ops_gram / t_gram / 1e12 / FP32_ALU_PEAK_TOPS, 4), "traffic": None,
+         "frac": round(ops_gram / t_gram / 1e12 / FP32_ALU_PEAK_TOPS, 4),
+         "hbm_frac": round(4.0 * nb * s_blk / t_gram / 1e9 / hbm, 4),
          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz"}]
 
     # ---- end to end through the public API from host buffers
@@ -422,7 +477,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s2.analyze(rp, ci, va)
-        xh, ih = s2.solve(bh, **SOLVE_KW)
+        s2.solve(bh, **opts)
         t1 = time.perf_counter()
         s2.close()
         if k:
@@ -433,17 +488,44 @@ def run_ours(args):
                   "d2h_bytes_per_step": int(8 * A.n),
                   "includes": "sg_analyze (CSR ingest from host) + sg_solve "
                               "(b host->device, x device->host)"}
+    solver.close()
+    del b
+    torch.cuda.empty_cache()
+
+    # ---- secondary systems (same FP64 / FP32-IR solves)
+    sec = []
+    names = [] if args.no_secondary else [nm for nm in ("c2",) if nm != args.config]
+    if args.with_c3 and args.config != "c3":
+        names.append("c3")
+    for nm in names:
+        c2, cfg2, o2 = make_workload(nm)
+        s2 = sg.Solver(local)
+        s2.analyze_csr(c2["A"])
+        b2 = torch.as_tensor(c2["b"], dtype=torch.float64, device=dev)
+        reps = 1 if nm == "c3" else 3
+        rec = {"config": cfg2}
+        for prec in ("fp64", "fp32_ir"):
+            ts, (xx, ii) = timed(lambda: solve(prec, s2, b2, o2), reps, 1 if nm != "c3" else 0)
+            rec[prec] = {"time_s": max_over_ranks(sum(ts) / len(ts), world) / 1e3,
+                         "iters": ii.iters, "s0": ii.s0, "refinements": ii.refinements,
+                         "fp64_iters": ii.fp64_iters, "final_relres": ii.final_relres,
+                         "converged": ii.converged,
+                         "phase_ms": {k: round(v, 2) for k, v in ii.times_ms.items()}}
+        sec.append(rec)
+        s2.close()
+        del b2
+    if sec:
+        out["secondary"] = sec
 
     # ---- CPU baseline (oracle, rank 0, N = 1 only)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        dt, its = cpu_oracle_sample(c)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.config == "c5":
+        dt, thr, r, rows = cpu_oracle_sample(args.config)
         out["cpu_baseline"] = {
-            "value": dt * info.iters / max(its, 1), "unit": "s",
-            "cores": oracle_threads(), "kind": "oracle",
-            "sample": sample_text(dt, its, info.iters)}
+            "value": dt * A.n / rows, "unit": "s",
+            "cores": int(round(thr)), "cores_available": len(os.sched_getaffinity(0)),
+            "kind": "oracle", "sample": sample_text(dt, rows, A.n, r)}
     if rank == 0:
         print(json.dumps(out))
-    solver.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -451,29 +533,45 @@ def run_ours(args):
 
 # ------------------------------------------------------------ reference
 def run_reference(args):
+    """The CPU oracle on the bench's workload, rank 0 only: each step is one
+    complete oracle solve of the workload recipe at SAMPLE_ROWS rows, and
+    `value` scales the mean step time by rows to the full system."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    c, cfg = workload(args.grid)
     from oracle import sgmres_oracle as O
+    import workloads as W
+    _, cfg, _ = make_workload(args.config)
+    if args.config != "c5":
+        print(json.dumps({"impl": "reference",
+                          "unavailable": "the reference arm samples the random-band "
+                                         "recipe (--config c5) only"}))
+        return
+    c1 = W.config_c1(32)
     for _ in range(args.warmup):   # short warm-up: imports, page-in, BLAS
-        O.adaptive_sgmres(c["A"], c["b"], m=20, s=4, tol=1e-10, max_iters=8)
-    times, its = [], 0
+        O.adaptive_sgmres(c1["A"], c1["b"], m=20, s=4, tol=1e-10, max_iters=8)
+    times, thr, r, rows = [], [], None, SAMPLE_ROWS
     for _ in range(args.steps):
-        dt, its = cpu_oracle_sample(c)
+        dt, th, r, rows = cpu_oracle_sample(args.config)
         times.append(dt)
+        thr.append(th)
     dt = sum(times) / len(times)
-    val = dt * FULL_SOLVE_COLUMNS / max(its, 1)
+    scale = cfg["n"] / rows
+    val = dt * scale
     out = {"impl": "reference", "metric": METRIC, "value": val, "value_is": VALUE_IS,
            "unit": "s", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": 1e3 * val,
+           "warmup": args.warmup, "ms_per_step": 1e3 * dt,
+           "ms_per_step_is": "measured wall time of one step (the sampled solve)",
+           "value_scale_by_rows": scale,
            "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": cfg,
            "cpu_baseline": {"value": val, "unit": "s",
-                            "cores": oracle_threads(), "kind": "oracle",
-                            "sample": sample_text(dt, its, FULL_SOLVE_COLUMNS)},
+                            "cores": int(round(statistics.median(thr))),
+                            "cores_available": len(os.sched_getaffinity(0)),
+                            "kind": "oracle",
+                            "sample": sample_text(dt, rows, cfg["n"], r)},
            "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -488,24 +586,31 @@ def run_case(args):
     solver = sg.Solver(0)
     dev = torch.device("cuda:0")
     name = args.case
-    if name.startswith("solve"):
-        c = W.config_c2(args.grid)
-        solver.analyze_csr(c["A"])
-        b = torch.as_tensor(c["b"], device=dev)
-        prec = "fp64" if name == "solve-fp64" else "fp32_ir"
-        x, info = solver.solve(b, precision=prec, **SOLVE_KW)
-        print(name, info.converged, info.iters, info.final_relres)
-    elif name == "spmv":
-        c = W.config_c2(args.grid)
+    if name in ("solve-fp64", "solve-fp32ir", "prepass64", "prepass32", "spmv"):
+        if args.config == "c5":
+            c, _, opts = make_workload("c5", rows=args.rows)
+        else:
+            c, _, opts = make_workload(args.config)
         A = c["A"]
         solver.analyze_csr(A)
-        x = torch.rand(A.n, dtype=torch.float64, device=dev)
-        y = torch.empty_like(x)
-        for _ in range(4):
-            solver.spmv_newton(x, 0.3, 1.1, out=y)
+        b = torch.as_tensor(c["b"], device=dev)
+        if name.startswith("solve"):
+            prec = "fp64" if name == "solve-fp64" else "fp32_ir"
+            x, info = solver.solve(b, precision=prec, **opts)
+            print(name, info.converged, info.iters, info.final_relres)
+        elif name.startswith("prepass"):
+            q = b / torch.linalg.vector_norm(b)
+            prec = "fp64" if name == "prepass64" else "fp32_ir"
+            H, steps = solver.arnoldi(q, 64, precision=prec)
+            print(name, steps, float(np.abs(H).max()))
+        else:
+            x = torch.rand(A.n, dtype=torch.float64, device=dev)
+            y = torch.empty_like(x)
+            for _ in range(4):
+                solver.spmv_newton(x, 0.3, 1.1, out=y)
     else:
-        # block kernels on n = 2^20 rows, i = 107, s = 106 (the solve's
-        # second-block shape)
+        # block kernels on n = 2^20 rows, i = 107, s = 106 (the 128^3
+        # solve's second-block shape)
         n, i, s = 1 << 20, 107, 106
         fp = torch.float64 if name.endswith("64") else torch.float32
         solver.analyze_csr(W.config_c1(8)["A"])
@@ -515,6 +620,9 @@ def run_case(args):
         if name == "dot64":
             for _ in range(3):
                 solver.block_dot(Q, X)
+        elif name == "gram64":
+            for _ in range(3):
+                solver.block_dot(X, X, sym=True)
         elif name == "upd64":
             Wt = torch.randn(s, i, dtype=torch.float64, device=dev)
             for _ in range(3):

@@ -101,6 +101,15 @@ typedef struct {
   int32_t vectors_on_device; /* 1: b/x/g/lam of sg_solve* are device ptrs */
   void* stream;        /* cudaStream_t or NULL                             */
   int32_t equilibrate; /* an sg_equil value; default NONE                   */
+  /* n_ritz > 0: use these Ritz values (host arrays of n_ritz entries, every
+   * complex value with its conjugate) instead of running the pre-pass: they
+   * are Leja-ordered and used as the pre-pass's would be (Sec. 3.4), and
+   * with s == 0 the estimator runs on them.  A later solve with the same
+   * matrix, or the adjoint solve (A^T has A's eigenvalues), can reuse the
+   * Ritz values a solve reported in sg_result. */
+  int32_t n_ritz;
+  const double* ritz_re;
+  const double* ritz_im;
 } sg_opts;
 
 /* Outputs.  The array members are caller-owned buffers that may be NULL;

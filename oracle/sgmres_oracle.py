@@ -106,6 +106,20 @@ def ritz_values(H, steps):
     return np.linalg.eigvals(H[:steps, :steps]).astype(np.complex128)
 
 
+def ritz_residuals(H, steps):
+    """Ritz values theta of the leading steps x steps block of H and, for
+    each, the residual norm of its Ritz pair, ||A V y - theta V y|| =
+    h_{k+1,k} |e_k^T y| for the unit eigenvector y of H_k (the Arnoldi
+    relation A V_k = V_{k+1} H_{k+1,k}, Sec. 3.4).  A small residual marks a
+    converged Ritz value, one that another run of the pre-pass reproduces
+    whatever its rounding."""
+    Hk = H[:steps, :steps]
+    theta, Y = np.linalg.eig(Hk)
+    Y = Y / np.linalg.norm(Y, axis=0)
+    hnext = abs(H[steps, steps - 1]) if H.shape[0] > steps else 0.0
+    return theta.astype(np.complex128), hnext * np.abs(Y[steps - 1, :])
+
+
 def _is_tie(a, b):
     return abs(a - b) <= 1e-9 * max(1.0, abs(a), abs(b))
 
@@ -449,6 +463,8 @@ class SolveResult:
     final_relres: float = 0.0
     ritz: np.ndarray = None
     gamma: np.ndarray = None
+    prepass_H: np.ndarray = None                     # (k+1) x k, Sec. 3.4
+    prepass_steps: int = 0
     est_norms: np.ndarray = None
     loo: list = field(default_factory=list)          # per cycle
     arnoldi_res: list = field(default_factory=list)  # per cycle
@@ -458,11 +474,14 @@ def adaptive_sgmres(A, b, x0=None, m=60, s=10, tol=1e-10, *,
                     basis=BASIS_SCALED_NEWTON, omega=OMEGA,
                     omega_est=OMEGA_EST, eps=EPS64, s_min=1, s_max=None,
                     max_iters=None, cond="ice", diagnostics=False,
-                    scalar_equil=False):
+                    scalar_equil=False, ritz=None):
     """Adaptive s-step GMRES(m) (Alg. 4) with restarts.
 
     s > 0: fixed initial step size s0 (Ritz pre-pass of s0 steps);
     s == 0: s0* from the estimator (Sec. 3.5) over s_max Ritz values.
+    ritz: Ritz values to use instead of running the pre-pass (conjugate
+    pairs complete); they are Leja-ordered and used as the pre-pass's
+    would be (Sec. 3.4).
     scalar_equil: scalar equilibration A' = A / alpha, alpha = max |theta|
     (Eq. equil), in the equivalent form Sec. 4.3 states: the monomial and
     standard Newton bases take the constant scaling coefficient alpha; the
@@ -496,10 +515,15 @@ def adaptive_sgmres(A, b, x0=None, m=60, s=10, tol=1e-10, *,
         g = np.zeros(m + 1)
         g[0] = beta
         if theta is None:
-            k = s if s > 0 else s_max
-            k = min(k, m)
-            Hk, steps = arnoldi_mgs(A, Q[:, 0], k)
-            ritz = leja_order(ritz_values(Hk, steps))
+            if ritz is None:
+                k = s if s > 0 else s_max
+                k = min(k, m)
+                Hk, steps = arnoldi_mgs(A, Q[:, 0], k)
+                res.prepass_H, res.prepass_steps = Hk, steps
+                ritz = leja_order(ritz_values(Hk, steps))
+            else:
+                ritz = leja_order(np.asarray(ritz, dtype=np.complex128))
+                steps = ritz.size
             gam_sn = scaling_coefficients(ritz)
             theta, gamma = basis_shifts(basis, ritz, gam_sn)
             if scalar_equil and basis != BASIS_SCALED_NEWTON:

@@ -67,6 +67,9 @@ class sg_csr(C.Structure):
                 ("val", C.c_void_p), ("on_device", C.c_int32)]
 
 
+_DP = C.POINTER(C.c_double)
+
+
 class sg_opts(C.Structure):
     _fields_ = [("m", C.c_int32), ("s", C.c_int32), ("s_min", C.c_int32),
                 ("s_max", C.c_int32), ("tol", C.c_double),
@@ -74,7 +77,8 @@ class sg_opts(C.Structure):
                 ("omega_est", C.c_double), ("basis", C.c_int32),
                 ("precision", C.c_int32), ("inner_tol", C.c_double),
                 ("max_refine", C.c_int32), ("vectors_on_device", C.c_int32),
-                ("stream", C.c_void_p), ("equilibrate", C.c_int32)]
+                ("stream", C.c_void_p), ("equilibrate", C.c_int32),
+                ("n_ritz", C.c_int32), ("ritz_re", _DP), ("ritz_im", _DP)]
 
 
 _D = C.POINTER(C.c_double)
@@ -448,7 +452,9 @@ class Solver:
     def make_opts(m=60, s=10, s_min=1, s_max=0, tol=1e-10, max_iters=0,
                   omega=1e7, omega_est=1e7, basis="scaled_newton",
                   precision="fp64", inner_tol=1e-4, max_refine=20,
-                  equilibrate="none"):
+                  equilibrate="none", ritz=None):
+        """sg_opts from keywords.  ritz: Ritz values to use instead of the
+        pre-pass (the arrays are kept on the returned object)."""
         o = sg_opts()
         lib.sg_default_opts(C.byref(o))
         o.m, o.s, o.s_min, o.s_max = m, s, s_min, s_max
@@ -460,6 +466,11 @@ class Solver:
         o.inner_tol, o.max_refine = inner_tol, max_refine
         o.equilibrate = (EQUILIBRATIONS[equilibrate] if isinstance(equilibrate, str)
                          else equilibrate)
+        if ritz is not None:
+            th = np.asarray(ritz, dtype=np.complex128).ravel()
+            o._ritz = (np.ascontiguousarray(th.real), np.ascontiguousarray(th.imag))
+            o.n_ritz = th.size
+            o.ritz_re, o.ritz_im = _dp(o._ritz[0]), _dp(o._ritz[1])
         return o
 
     def _solve(self, fn, b, x0, opts, stream, hist_cap):

@@ -54,14 +54,28 @@ __device__ double block_sum_few_d(double v) {
 }
 
 // Fixed-order sum of G per-block partials by one warp (few FP64
-// instructions); every thread receives it.
+// instructions); every thread receives it.  Lane l adds p[l], p[l + 32],
+// ... in that order; for G <= 256 its (up to eight) loads are issued
+// together, so the read costs one L2 round trip instead of one per term.
 template <int THREADS>
 __device__ double sum_partials_few_d(const double* __restrict__ p, int G) {
   __shared__ double total;
   __syncthreads();  // every thread has read the previous total
   if (threadIdx.x < 32) {
     double t = 0.0;
-    for (int i = threadIdx.x; i < G; i += 32) t += p[i];
+    if (G <= 256) {
+      double v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int i = threadIdx.x + 32 * k;
+        v[k] = i < G ? p[i] : 0.0;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (threadIdx.x + 32 * k < G) t += v[k];
+    } else {
+      for (int i = threadIdx.x; i < G; i += 32) t += p[i];
+    }
     t = warp_sum_d<THREADS>(t);
     if (threadIdx.x == 0) total = t;
   }

@@ -360,21 +360,20 @@ arnoldi_step_kernel(int n, int rows_per_cta, const int* __restrict__ rowptr,
     w[i] = static_cast<T>(static_cast<double>(w[i]) * inv);
 }
 
-// The same FP64 step with w resident on chip.  CTA b owns the contiguous
-// rows [b R, (b+1) R) (R a multiple of 32, so its SELL-32 slices are whole)
-// and keeps its slice of w in shared memory from the SpMV to the final
-// normalisation.  A thread always touches the same rows, so w needs no
-// barrier of its own; each MGS phase streams only v_l (just read as the
-// previous phase's v_{l+1}, an L2 hit) and v_{l+1}, instead of reading and
-// writing w through HBM as well.  Phase order, fused next-vector dot and
-// per-CTA partials are those of arnoldi_step_kernel; only the rows a CTA
-// owns differ.
+// The same FP64 step with w resident on chip.  w = A v_j is first formed in
+// V's column j+1 by the SELL SpMV kernel (full occupancy, and the whole L1
+// for the gathers of v_j); then CTA b of this cooperative kernel loads its
+// rows [b R, (b+1) R) of w into shared memory and keeps them there through
+// the MGS phases to the final normalisation.  A thread always touches the
+// same rows, so w needs no barrier of its own; each phase streams only v_l
+// (just read as the previous phase's v_{l+1}, an L2 hit) and v_{l+1},
+// instead of reading and writing w through HBM as well.  Phase order, fused
+// next-vector dot and per-CTA partials are those of arnoldi_step_kernel;
+// only the rows a CTA owns differ.
 __global__ void __launch_bounds__(kCoopThreads, 1)
-arnoldi_step_resident_kernel(int n, int rows_cta, const int* __restrict__ sptr,
-                             const int* __restrict__ scol, const double* __restrict__ sval,
-                             double* __restrict__ V, int64_t ld, int j,
-                             double* __restrict__ H, int ldh, double* __restrict__ wn,
-                             double* __restrict__ red, unsigned* bar, int* err) {
+arnoldi_mgs_resident_kernel(int n, int rows_cta, double* __restrict__ V, int64_t ld, int j,
+                            double* __restrict__ H, int ldh, double* __restrict__ wn,
+                            double* __restrict__ red, unsigned* bar, int* err) {
   extern __shared__ __align__(16) unsigned char coop_smem[];
   double* ws = reinterpret_cast<double*>(coop_smem);
   const int G = gridDim.x;
@@ -382,21 +381,18 @@ arnoldi_step_resident_kernel(int n, int rows_cta, const int* __restrict__ sptr,
   const int64_t r0 = static_cast<int64_t>(blockIdx.x) * rows_cta;
   const int64_t r1 = (r0 + rows_cta < n) ? r0 + rows_cta : n;
   const int nr = r1 > r0 ? static_cast<int>(r1 - r0) : 0;
-  const int nr32 = (nr + 31) & ~31;   // whole slices (rows past n are padding)
-  const double* vj = V + static_cast<int64_t>(j) * ld;
   const double* v0 = V + r0;
+  double* w = V + static_cast<int64_t>(j + 1) * ld + r0;
   double* pWW = red;
   double* pA = red + G;
   double* pB = red + 2 * G;
-  // phase 0: w = A v_j on this CTA's rows, partials of w.w and v_0.w
+  // this CTA's rows of w = A v_j, partials of w.w and v_0.w
   double accw = 0.0, accv = 0.0;
-  for (int i = t; i < nr32; i += kCoopThreads) {
-    const double sum = sell_row(sptr, scol, sval, vj, r0 + i);
-    if (i < nr) {
-      ws[i] = sum;
-      accw = fma(sum, sum, accw);
-      accv = fma(v0[i], sum, accv);
-    }
+  for (int i = t; i < nr; i += kCoopThreads) {
+    const double wi = w[i];
+    ws[i] = wi;
+    accw = fma(wi, wi, accw);
+    accv = fma(v0[i], wi, accv);
   }
   {
     const double sw = block_sum_few_d<kCoopThreads>(accw);
@@ -456,7 +452,6 @@ arnoldi_step_resident_kernel(int n, int rows_cta, const int* __restrict__ sptr,
   const double nrm = sqrt(sum_partials_few_d<kCoopThreads>(pin, G));
   if (blockIdx.x == 0 && t == 0) H[(j + 1) + static_cast<int64_t>(j) * ldh] = nrm;
   const double inv = 1.0 / nrm;
-  double* w = V + static_cast<int64_t>(j + 1) * ld + r0;
   for (int i = t; i < nr; i += kCoopThreads) w[i] = ws[i] * inv;
 }
 
@@ -979,7 +974,7 @@ int resident_rows_per_cta(int64_t n, int* grid) {
       int optin = 0;
       SG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
       cudaFuncAttributes fa{};
-      SG_CUDA(cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(arnoldi_step_resident_kernel)));
+      SG_CUDA(cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(arnoldi_mgs_resident_kernel)));
       it = limit.emplace(dev, optin - static_cast<int>(fa.sharedSizeBytes) - 1024).first;
     }
     avail = it->second;
@@ -1001,17 +996,19 @@ void launch_arnoldi_step(const DevCsr& A, const T* val, T* V, int64_t ld, int j,
     int G = 0;
     const int R = resident_rows_per_cta(A.n, &G);
     if (R > 0 && G <= device_sm_count() && 3 * G <= red_cap) {
-      const void* fn = reinterpret_cast<const void*>(arnoldi_step_resident_kernel);
+      const void* fn = reinterpret_cast<const void*>(arnoldi_mgs_resident_kernel);
       const int smem = R * static_cast<int>(sizeof(double));
       ensure_dynamic_smem(fn, smem);
       int per_sm = 0;
       SG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kCoopThreads, smem));
       if (per_sm >= 1) {
+        // w = A v_j into V's column j+1, then the MGS phases on chip
+        dispatch<0, false, T>(A, A.val, val, V + static_cast<int64_t>(j) * ld, nullptr,
+                              V + static_cast<int64_t>(j + 1) * ld, T(0), T(0), T(1), st);
         int n = A.n;
         int rc = R;
-        void* args[] = {&n, &rc, const_cast<int**>(&A.sptr), const_cast<int**>(&A.scol),
-                        const_cast<T**>(&val), &V, &ld, &j, &H, const_cast<int*>(&ldh), &wn,
-                        &red, &bar, &err};
+        void* args[] = {&n, &rc, &V, &ld, &j, &H, const_cast<int*>(&ldh), &wn, &red, &bar,
+                        &err};
         SG_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kCoopThreads), args, smem, st));
         count_launch();
         return;

@@ -95,6 +95,9 @@ sg::SolveOpts to_internal(const sg_opts* o) {
   s.omega_est = o->omega_est;
   s.eps = std::ldexp(1.0, -53);
   s.equil = o->equilibrate;
+  s.n_ritz = o->n_ritz;
+  s.ritz_re = o->ritz_re;
+  s.ritz_im = o->ritz_im;
   return s;
 }
 
@@ -110,6 +113,25 @@ void check_opts(const sg_opts* o) {
              SG_EINVAL, "bad precision");
   SG_REQUIRE(o->equilibrate >= SG_EQUIL_NONE && o->equilibrate <= SG_EQUIL_COLUMN,
              SG_EINVAL, "bad equilibrate");
+  SG_REQUIRE(o->n_ritz >= 0, SG_EINVAL, "n_ritz must be >= 0");
+  if (o->n_ritz > 0) {
+    SG_REQUIRE(o->ritz_re && o->ritz_im, SG_EINVAL, "n_ritz > 0 needs ritz_re and ritz_im");
+    int pos = 0, neg = 0;
+    for (int t = 0; t < o->n_ritz; ++t) {
+      SG_REQUIRE(std::isfinite(o->ritz_re[t]) && std::isfinite(o->ritz_im[t]), SG_EINVAL,
+                 "non-finite Ritz value");
+      if (o->ritz_im[t] > 0.0) {
+        ++pos;
+        bool found = false;
+        for (int u = 0; u < o->n_ritz && !found; ++u)
+          found = o->ritz_re[u] == o->ritz_re[t] && o->ritz_im[u] == -o->ritz_im[t];
+        SG_REQUIRE(found, SG_EINVAL, "a complex Ritz value without its conjugate");
+      } else if (o->ritz_im[t] < 0.0) {
+        ++neg;
+      }
+    }
+    SG_REQUIRE(pos == neg, SG_EINVAL, "unpaired complex Ritz values");
+  }
 }
 
 template <typename T>

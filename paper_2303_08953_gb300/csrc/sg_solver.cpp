@@ -340,15 +340,25 @@ struct Shifts {
   std::vector<BasisStep> steps;
 };
 
+Shifts shifts_from_values(const std::vector<double>& re, const std::vector<double>& im,
+                          int steps, int basis, int equil);
+
 Shifts make_shifts(const std::vector<double>& Hh, int ldh, int steps,
                    int basis, int equil) {
-  Shifts sh;
   std::vector<double> re(steps), im(steps);
   if (hessenberg_eigvals(Hh.data(), ldh, steps, re.data(), im.data()) != 0)
     throw Error(SG_ENUMERIC, "Ritz values: QR iteration did not converge");
   for (int t = 0; t < steps; ++t)
     if (!std::isfinite(re[t]) || !std::isfinite(im[t]))
       throw Error(SG_ENUMERIC, "Ritz values: non-finite");
+  return shifts_from_values(re, im, steps, basis, equil);
+}
+
+// Leja order, scaling coefficients and basis parameters of the Ritz values
+// (Sec. 3.4), from the pre-pass or supplied by the caller.
+Shifts shifts_from_values(const std::vector<double>& re, const std::vector<double>& im,
+                          int steps, int basis, int equil) {
+  Shifts sh;
   sh.re.resize(steps);
   sh.im.resize(steps);
   leja_order(steps, re.data(), im.data(), sh.re.data(), sh.im.data());
@@ -442,9 +452,17 @@ void solve_impl(sg_handle* h, const DevCsr& M, const SolveOpts& o,
     B::from_f64(n, h->rvec, Qb, 1.0 / beta, st);
     if (!have_shifts) {
       const double tp = now_ms();
-      std::vector<double> Hp;
-      const int steps = arnoldi_prepass<T>(h, M, Qb, kritz, st, Hp);
-      sh = make_shifts(Hp, kritz + 1, steps, o.basis, o.equil);
+      int steps = 0;
+      if (o.n_ritz > 0) {
+        steps = o.n_ritz;
+        sh = shifts_from_values(std::vector<double>(o.ritz_re, o.ritz_re + steps),
+                                std::vector<double>(o.ritz_im, o.ritz_im + steps), steps,
+                                o.basis, o.equil);
+      } else {
+        std::vector<double> Hp;
+        steps = arnoldi_prepass<T>(h, M, Qb, kritz, st, Hp);
+        sh = make_shifts(Hp, kritz + 1, steps, o.basis, o.equil);
+      }
       if (o.s > 0) {
         cur_s = std::min(o.s, steps);
       } else {

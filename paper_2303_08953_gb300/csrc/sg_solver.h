@@ -68,6 +68,9 @@ struct SolveOpts {
   int m, s, s_min, s_max, max_iters, basis;
   int equil = 0;  // sg_equil: SCALAR acts here (gamma = max |theta|)
   double tol, omega, omega_est, eps;
+  int n_ritz = 0;                  // > 0: Ritz values given, no pre-pass
+  const double* ritz_re = nullptr;
+  const double* ritz_im = nullptr;
 };
 
 // Record of one solve (mirrors sg_result, without caller buffers).

@@ -233,3 +233,94 @@ def test_full_size_c5_fp32_ir_forward_and_adjoint(solver):
     for k in rng.choice(A.nnz, 5000, replace=False):
         r = np.searchsorted(A.rowptr, k, side="right") - 1
         assert dval[k] == -lh[r] * xh[A.colind[k]]
+
+
+# ------------------------------------------- full-size decision parity
+def _golden(name):
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", f"fullsize_{name}.json")
+    with open(path) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("name", ["c5", "c2"])
+def test_full_size_decisions_match_oracle(solver, name):
+    """The FP64 solve of the full-size workload against the oracle's run
+    (tests/golden/fullsize_<name>.json, written by make_fullsize_golden.py
+    from oracle/ alone), both from the oracle's Ritz values: a 120-step
+    Arnoldi pre-pass amplifies rounding-order differences through its
+    Krylov basis (kappa grows several-fold per step), so its unconverged
+    Ritz values are not reproducible and neither is anything decided from
+    them; the pre-pass itself is checked on its converged Ritz values
+    below.  Given the same Ritz values: step size s0 from the estimator
+    (Sec. 3.5), every block's p and p' (Alg. 3 inside Alg. 4), columns per
+    cycle and restarts identical; per-cycle true residuals within 1e-8
+    relative or the FP64 evaluation floor; implicit residuals within 1e-6;
+    the solution within 1e-9 relative, checked through what that bound
+    implies on 1024 sampled entries (their RMS error, scaled to the whole
+    vector), on ||x|| and on eight seeded Gaussian functionals u.x
+    (|u.(x - x_o)| <= ||u|| 1e-9 ||x_o||)."""
+    g = _golden(name)
+    c = W.CONFIGS[name]()
+    A, b = c["A"], c["b"]
+    assert A.n == g["n"] and A.nnz == g["nnz"]
+    solver.analyze_csr(A)
+    ritz = np.asarray(g["ritz_re"]) + 1j * np.asarray(g["ritz_im"])
+    xd, info = solver.solve(dev(b), ritz=ritz, **g["opts"])
+    assert np.array_equal(info.ritz, ritz)        # Leja order kept
+    assert info.converged == g["converged"]
+    assert info.s0 == g["s0"]
+    assert list(info.s_hist) == g["s_hist"]
+    assert list(info.p1_hist) == g["p1_hist"]
+    assert list(info.s_eff_hist) == g["s_eff_hist"]
+    assert info.iters == g["iters"] and info.restarts == g["restarts"]
+    assert list(info.cycle_iters) == g["cycle_iters"]
+    # FP64 evaluation floor of ||b - A x|| / ||b|| (see residual_floor in
+    # test_gpu_parity.py), with the exact solution x* standing in for x
+    op = O.as_operator(A)
+    k = int(np.max(np.diff(op.indptr)))
+    floor = 2 * (k + 11) * 2.0 ** -53 * np.linalg.norm(
+        np.abs(b) + abs(op) @ np.abs(c["xstar"])) / np.linalg.norm(b)
+    co = np.array(g["cycle_relres"])
+    assert np.all(np.abs(info.cycle_relres - co) <= np.maximum(1e-8 * co, floor))
+    ho = np.array(g["relres_hist"])
+    assert info.relres_hist.size == ho.size
+    assert np.all(np.abs(info.relres_hist - ho) <= np.maximum(1e-6 * ho, floor))
+    x = host(xd)
+    xo_norm = g["x_norm"]
+    idx = np.asarray(g["x_idx"])
+    d = x[idx] - np.asarray(g["x_sample"])
+    assert np.sqrt(A.n * np.mean(d * d)) <= 1e-9 * xo_norm
+    assert abs(np.linalg.norm(x) - xo_norm) <= 1e-9 * xo_norm
+    for k_, fo in enumerate(g["x_functionals"]):
+        u = np.random.default_rng([g["sample_seed"], k_]).standard_normal(A.n)
+        assert abs(u @ x - fo) <= np.linalg.norm(u) * 1e-9 * xo_norm
+
+
+@pytest.mark.parametrize("name", ["c5", "c2"])
+def test_full_size_prepass_converged_ritz_values(solver, name):
+    """The library's own 120-step pre-pass (Sec. 3.4) on the full-size
+    workload: every Ritz value the oracle's pre-pass has converged (Ritz-pair
+    residual below 1e-9 of the largest modulus) is matched by one of the
+    library's within ten times that residual (plus 1e-10 of the largest
+    modulus); and the library's solve from its own Ritz values reaches the
+    tolerance with a solution near the seeded exact solution x* (forward
+    error <= kappa(A) x relres; 1000 tol bounds it for these systems)."""
+    g = _golden(name)
+    c = W.CONFIGS[name]()
+    A, b = c["A"], c["b"]
+    solver.analyze_csr(A)
+    xd, info = solver.solve(dev(b), **g["opts"])
+    assert info.converged and info.final_relres <= g["opts"]["tol"]
+    th = np.asarray(g["prepass_ritz_re"]) + 1j * np.asarray(g["prepass_ritz_im"])
+    res = np.asarray(g["prepass_ritz_residual"])
+    scale = np.max(np.abs(th))
+    conv = res <= 1e-9 * scale
+    assert conv.sum() >= 2
+    got = info.ritz
+    for z, r in zip(th[conv], res[conv]):
+        assert np.min(np.abs(got - z)) <= 10 * r + 1e-10 * scale, (z, r)
+    x = host(xd)
+    xs = c["xstar"]
+    assert np.linalg.norm(x - xs) <= 1000 * g["opts"]["tol"] * np.linalg.norm(xs)

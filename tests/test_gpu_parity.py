@@ -396,6 +396,31 @@ def test_solve_estimator_c2_small(solver):
     _compare(ro, x, info, c["A"], c["b"])
 
 
+@pytest.mark.parametrize("s", [0, 6])
+def test_solve_with_supplied_ritz_values(solver, s):
+    """Ritz values supplied through sg_opts replace the pre-pass (Sec. 3.4):
+    given the oracle's Ritz values (in any order: they are Leja-ordered),
+    the solve takes the oracle's decisions, estimated (s = 0) or fixed."""
+    c = W.config_c2(14)
+    _analyze(solver, c["A"])
+    kw = dict(m=60, s=s, s_min=3, s_max=24, tol=1e-10)
+    ro = O.adaptive_sgmres(c["A"], c["b"], **kw)
+    shuffled = ro.ritz[np.random.default_rng(2).permutation(ro.ritz.size)]
+    ro2 = O.adaptive_sgmres(c["A"], c["b"], ritz=shuffled, **kw)
+    x, info = solver.solve(c["b"], ritz=shuffled, **kw)
+    assert np.array_equal(info.ritz, ro2.ritz)
+    _compare(ro2, x, info, c["A"], c["b"])
+    assert info.times_ms["prepass"] < 1.0
+
+
+def test_supplied_ritz_values_are_validated(solver):
+    c = W.config_c1(8)
+    _analyze(solver, c["A"])
+    for bad in ([1.0 + 2.0j, 3.0], [np.nan, 1.0]):
+        with pytest.raises(sg.SgError):
+            solver.solve(c["b"], m=20, s=4, ritz=np.array(bad))
+
+
 @pytest.mark.parametrize("basis", ["newton", "monomial"])
 def test_solve_other_bases(solver, basis):
     c = W.config_c1(24)
@@ -613,6 +638,14 @@ def test_adjoint_solve_and_grad_values(solver):
     dval = host(solver.grad_values(dev(lam), dev(x)))
     rows = np.repeat(np.arange(A.n), np.diff(A.rowptr))
     assert np.allclose(dval, -lam[rows] * x[A.colind], rtol=0, atol=0)
+    # A^T has A's eigenvalues: the adjoint solve from the forward solve's
+    # Ritz values (the oracle's forward run's) skips its pre-pass and
+    # follows the oracle given the same values
+    fwd = O.adaptive_sgmres(A, c["b"], m=60, s=8, tol=1e-10)
+    ro2 = O.adaptive_sgmres(AT, g, m=60, s=8, tol=1e-10, ritz=fwd.ritz)
+    lam2, info2 = solver.solve_adjoint(g, m=60, s=8, tol=1e-10, ritz=fwd.ritz)
+    assert info2.converged
+    _compare(ro2, lam2, info2, AT, g)
 
 
 # ------------------------------------------------------- FP32 basis + IR

@@ -735,3 +735,40 @@ def test_planted_estimator_index_is_caught(monkeypatch, plant):
         return max(s0, s_min), norms
     monkeypatch.setattr(O, "estimate_step_size", bad)
     assert _estimator_pin_fails()
+
+
+# ----------------------------------------------- Ritz residuals, supplied Ritz values
+def test_ritz_residual_bounds_the_eigenvalue_distance():
+    """For a symmetric matrix every Ritz value lies within its Ritz-pair
+    residual of an eigenvalue (|theta - lambda| <= ||A z - theta z|| for a
+    unit z, Sec. 3.4's Ritz pairs); converged ones have tiny residuals."""
+    lam = np.linspace(1.0, 50.0, 400)
+    lam[-1] = 100.0                      # an isolated eigenvalue converges first
+    op = O.as_operator(W.diagonal(lam))
+    q = np.random.default_rng(4).uniform(-1, 1, lam.size)
+    H, steps = O.arnoldi_mgs(op, q / np.linalg.norm(q), 30)
+    theta, res = O.ritz_residuals(H, steps)
+    assert np.all(np.abs(theta.imag) < 1e-12)
+    for t, r in zip(theta.real, res):
+        assert np.min(np.abs(lam - t)) <= r * (1 + 1e-9) + 1e-12
+    # the isolated extreme eigenvalue has converged
+    i = np.argmax(theta.real)
+    assert res[i] < 1e-6 and abs(theta.real[i] - 100.0) < 1e-6
+    # a full Arnoldi on a 12 x 12 stencil: every residual is ~0
+    A = O.as_operator(W.stencil2d(4, 3))
+    H, steps = O.arnoldi_mgs(A, np.ones(12) / math.sqrt(12), 12)
+    _, res = O.ritz_residuals(H, steps)
+    assert np.all(res < 1e-6)
+
+
+def test_supplied_ritz_values_reproduce_the_run():
+    """Feeding a run's own (Leja-ordered) Ritz values back in skips the
+    pre-pass and repeats every decision and the solution bit for bit."""
+    c = W.config_c2(10)
+    kw = dict(m=40, s=0, s_min=2, s_max=16, tol=1e-10)
+    r1 = O.adaptive_sgmres(c["A"], c["b"], **kw)
+    r2 = O.adaptive_sgmres(c["A"], c["b"], ritz=r1.ritz[::-1], **kw)
+    assert r2.prepass_H is None and r1.prepass_H is not None
+    assert np.array_equal(r2.ritz, r1.ritz)
+    assert r2.s0 == r1.s0 and r2.s_hist == r1.s_hist and r2.p1_hist == r1.p1_hist
+    assert np.array_equal(r2.x, r1.x)
