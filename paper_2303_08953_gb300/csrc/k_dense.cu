@@ -378,6 +378,22 @@ void block_dot_impl(int64_t n, const T* Q, int64_t ldq, int i, const T* X,
                               sizeof(double) * i, st));
     return;
   }
+  if (sizeof(T) == 8 && !tc_disabled() &&
+      oz_dot_supported(n, reinterpret_cast<const double*>(Q), ldq, i,
+                       reinterpret_cast<const double*>(X), ldx, s) &&
+      oz_dot_pays(n, i, s, sym && i == s)) {
+    // FP64 products on the tensor cores, exact digit slices; the column
+    // exponents sit after the split partials.  A Gram comes out exactly
+    // symmetric (both triangles are the same exact sums).
+    const int64_t need = oz_dot_part_size(n, i, s);
+    SG_REQUIRE(need + (oz_exp_ints(i, s) + 1) / 2 <= part_cap, SG_EINVAL,
+               "block_dot: workspace too small");
+    int S = 0;
+    oz_dot(n, reinterpret_cast<const double*>(Q), ldq, i, reinterpret_cast<const double*>(X),
+           ldx, s, reinterpret_cast<int*>(part + need), part, need, &S, st);
+    launch_reduce(i, s, S, part, W, ldw, false, st);
+    return;
+  }
   if (sizeof(T) == 4 && !sym && !tc_disabled() &&
       tc_dot_supported(n, reinterpret_cast<const float*>(Q), ldq, i,
                        reinterpret_cast<const float*>(X), ldx, s)) {
@@ -625,7 +641,9 @@ int64_t block_dot_part_size(int64_t n, int i, int s) {
     if (g > need) need = g;
   }
   const int64_t tc = tc_dot_part_size(n, i, s);
-  return need > tc ? need : tc;
+  const int64_t oz = oz_dot_part_size(n, i, s) + (oz_exp_ints(i, s) + 1) / 2;
+  need = need > tc ? need : tc;
+  return need > oz ? need : oz;
 }
 
 void block_dot(int64_t n, const double* Q, int64_t ldq, int i,

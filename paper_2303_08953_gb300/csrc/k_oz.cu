@@ -1,0 +1,610 @@
+// FP64 block dot product W = Q^T X on the tensor cores, exactly: the BCGS
+// projections and Gram matrices of Alg. 4 for the FP64 basis.
+//
+// GB300's FP64 pipe gives ~1.26 TFLOP/s, so the FP64 block products are
+// FP64-ALU bound; its BF16 tensor cores give ~1.9 PFLOP/s.  Every FP64
+// value is written exactly (to 62 bits below its column's largest
+// magnitude) as a sum of eight 8-bit digit slices, each slice a BF16 tile:
+//   x = 2^(e - 62) * sum_{t=1..8} d_t 256^(8 - t),   |d_t| <= 128 integers,
+// with e the exponent of the column's largest |x| (balanced digits: a digit
+// >= 128 becomes d - 256 and carries one into the next higher digit).  A
+// digit product is an integer of at most 2^14, exact in the MMA's FP32
+// accumulator; products of equal level l = t + u have the same weight
+// 256^(16 - l), so the MMA sums them into one FP32 accumulator per level.
+// A level has at most 8 digit pairs, so its sum over 128 rows stays within
+// 8 * 128 * 2^14 = 2^24: every level sum is an exact integer in FP32.  Every
+// 128 rows the eight level sums are read from tensor memory and added,
+// with their weights 256^(9 - l), into an exact integer per output (two
+// int64 halves); levels above 9 (weights below 2^-56 of the leading term)
+// are not formed.  The result is the dot product of the 62-bit truncations,
+// exact up to the final conversion to FP64 -- more accurate than an FP64
+// FMA chain.
+//
+// Tile: 128 columns of Q (MMA M) x 32 columns of X (MMA N) per CTA, 64 rows
+// (K) per stage; one CTA per SM (the tile uses all 512 tensor-memory
+// columns); splits of the rows across CTAs are reduced afterwards in a
+// fixed order, like the other block dots.
+//   * warp 8 (one lane) streams Q and X tiles with TMA: four 16-row x 128
+//     (Q) or x 32 (X) boxes per stage, 128-byte swizzled, so every thread
+//     reads its column conflict-free;
+//   * warps 0-7 cut the tiles into digits: Q's into eight tensor-memory
+//     slices (the MMA's A operand, lane = Q column, two BF16 digits per
+//     32-bit column; warps w and w+4 share lanes 32 (w % 4) .. + 31 and take
+//     one half of the rows each), X's into eight 128-byte-swizzled
+//     shared-memory slices (the MMA's B operand, double-buffered; warp w
+//     takes rows 8w .. 8w + 7); every 128 rows they read the level sums,
+//     16 output columns each;
+//   * warp 9 (one lane) issues the 36 digit-pair MMAs per 16-row K step.
+// Every wait is bounded: on timeout the kernel records an error, drains
+// its own copies, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <mutex>
+
+#include "k_tc_common.cuh"
+#include "sg_internal.h"
+
+namespace sg {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kOM = 128;          // columns of Q per tile (MMA M)
+constexpr int kON = 32;           // columns of X per tile (MMA N)
+constexpr int kOK = 64;           // rows per stage
+constexpr int kDig = 8;           // digit slices per value
+constexpr int kLev = 8;           // levels l = 2..9 kept
+constexpr int kChunk = 2;         // stages per exact level sum (128 rows)
+constexpr int kXStages = 2;       // X staging / B slice ring
+constexpr int kOThreads = 320;    // warps 0-7 split, 8 TMA, 9 MMA
+constexpr uint32_t kOTmemCols = 512;
+constexpr uint32_t kAccCol = 0;     // level L = l - 2 at column 32 L
+constexpr uint32_t kACol = 256;     // digit slice t (0-based) at 256 + 32 t
+constexpr int kQBox = 16 * kOM * 8;           // one 16-row Q box: 16 KB
+constexpr int kQBytes = 4 * kQBox;            // 64 KB per stage
+constexpr int kXBox = 16 * kON * 8;           // 4 KB
+constexpr int kXBytes = 4 * kXBox;            // 16 KB
+constexpr int kBSlice = kON * 128;            // 32 rows x 64 BF16: 4 KB
+constexpr int kBBytes = kDig * kBSlice;       // 32 KB
+constexpr int kOzSmem = kQBytes + kXStages * (kXBytes + kBBytes) + 1024;
+
+struct __align__(8) OzShared {
+  uint64_t qfull, qfree;
+  uint64_t xfull[kXStages], xfree[kXStages];
+  uint64_t afull, afree;
+  uint64_t bfull[kXStages], bfree[kXStages];
+  uint64_t accfull, accfree;
+  uint64_t done;
+  uint32_t tmem_base;
+  int fail;
+};
+
+// Instruction descriptor: kind::f16 with BF16 A and B, FP32 accumulator,
+// K-major A and B.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16_tmem_a(uint32_t dtmem, uint32_t atmem, uint64_t b,
+                                                uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(dtmem),
+      "r"(atmem), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// x relative to 2^e (|x| < 2^e) as the signed integer m = x 2^(62 - e),
+// |m| < 2^62, truncated toward zero.
+__device__ __forceinline__ int64_t scaled62(double x, int e) {
+  const uint64_t bits = static_cast<uint64_t>(__double_as_longlong(x));
+  const int E = static_cast<int>((bits >> 52) & 0x7FF);
+  uint64_t m = 0;
+  if (E != 0 && E != 0x7FF) {
+    const uint64_t mant = (bits & ((uint64_t(1) << 52) - 1)) | (uint64_t(1) << 52);
+    const int sh = E - 1013 - e;   // <= 9 when |x| < 2^e
+    if (sh >= 0) m = sh < 10 ? mant << sh : 0;
+    else if (sh > -64) m = mant >> (-sh);
+  }
+  return (bits >> 63) ? -static_cast<int64_t>(m) : static_cast<int64_t>(m);
+}
+
+// Balanced base-256 digits of m, most significant first, as BF16 bit
+// patterns: m = sum_t d[t] 256^(7-t) with d[1..7] in [-128, 127] and
+// |d[0]| <= 65.  Adding 128 to each of the seven low bytes of m makes every
+// byte b of the sum a digit plus 128 (the carries do the balancing); a
+// digit d becomes the FP32 value d exactly through the full-rate magic
+// constant 1.5 2^23, and its BF16 pattern is the FP32 value's top half (d
+// has at most 8 significant bits).
+__device__ __forceinline__ void digit_bits(int64_t m, uint32_t* hb) {
+  const uint64_t s = static_cast<uint64_t>(m) + 0x0080808080808080ull;
+  const uint32_t lo = static_cast<uint32_t>(s);
+  const uint32_t hi = static_cast<uint32_t>(s >> 32);
+  const int top = static_cast<int>(static_cast<int64_t>(s) >> 56);   // signed
+  hb[0] = __float_as_uint(__int_as_float(0x4B400000 + top) - 12582912.0f);
+#pragma unroll
+  for (int t = 1; t < 8; ++t) {
+    const uint32_t byte = (t < 4) ? ((hi >> (8 * (3 - t))) & 0xFFu) : ((lo >> (8 * (7 - t))) & 0xFFu);
+    hb[t] = __float_as_uint(__int_as_float(0x4B400000 + static_cast<int>(byte)) -
+                            (12582912.0f + 128.0f));
+  }
+}
+
+// two BF16 patterns (from digit_bits' FP32 words) in one 32-bit word, the
+// first in the low half
+__device__ __forceinline__ uint32_t pack2(uint32_t f_lo, uint32_t f_hi) {
+  return (f_lo >> 16) | (f_hi & 0xFFFF0000u);
+}
+
+// This thread's lane, 8 consecutive 32-bit columns from taddr.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+      : "memory");
+}
+
+// This thread's lane, 16 consecutive 32-bit columns from taddr.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// grid: (tiles of 128 Q columns, tiles of 32 X columns, splits)
+__global__ void __launch_bounds__(kOThreads, 1)
+oz_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
+              const __grid_constant__ CUtensorMap mapX, int64_t n, int M, int N,
+              const int* __restrict__ eq, const int* __restrict__ ex, int64_t rows_per_split,
+              double* __restrict__ part, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char dsmem[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~static_cast<uintptr_t>(1023));
+  __shared__ OzShared sh;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+  const int m0 = blockIdx.x * kOM;
+  const int n0 = blockIdx.y * kON;
+  const int64_t k0 = static_cast<int64_t>(blockIdx.z) * rows_per_split;
+  const int64_t k1 = (k0 + rows_per_split < n) ? k0 + rows_per_split : n;
+  const int nk = static_cast<int>((k1 - k0 + kOK - 1) / kOK);
+  const uint32_t idesc = idesc_bf16(kOM, kON);
+
+  unsigned char* stQ = base;
+  auto stX = [&](int q) { return base + kQBytes + q * kXBytes; };
+  auto stB = [&](int q) { return base + kQBytes + kXStages * kXBytes + q * kBBytes; };
+  auto failed = [&]() { return *reinterpret_cast<volatile int*>(&sh.fail) != 0; };
+  auto chunk_end = [&](int k) { return (k % kChunk) == kChunk - 1 || k == nk - 1; };
+
+  if (tid == 0) {
+    mbar_init(&sh.qfull, 1);
+    mbar_init(&sh.qfree, 256);
+    for (int q = 0; q < kXStages; ++q) {
+      mbar_init(&sh.xfull[q], 1);
+      mbar_init(&sh.xfree[q], 256);
+      mbar_init(&sh.bfull[q], 256);
+      mbar_init(&sh.bfree[q], 1);
+    }
+    mbar_init(&sh.afull, 256);
+    mbar_init(&sh.afree, 1);
+    mbar_init(&sh.accfull, 1);
+    mbar_init(&sh.accfree, 256);
+    mbar_init(&sh.done, 1);
+    sh.fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&sh.tmem_base)),
+                 "r"(kOTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = sh.tmem_base;
+
+  // per-thread sums of 16 outputs (warp w reads tensor-memory lanes
+  // 32 (w % 4) .. + 31 = Q columns, and X columns 16 (w / 4) .. + 15), each
+  // as two int64 halves: ahi = sum of S_L 256^(3-L) over levels L = 0..3,
+  // alo = sum of S_L 256^(7-L) over L = 4..7 (|S_L| <= 2^24, so each half
+  // grows by < 2^50 per readout and stays exact for 2^12 readouts), and
+  // the output's V' = ahi 2^32 + alo
+  constexpr int kHalf = kON / 2;
+  int64_t alo[kHalf];
+  int64_t ahi[kHalf];
+#pragma unroll
+  for (int c = 0; c < kHalf; ++c) { alo[c] = 0; ahi[c] = 0; }
+  // level sums of the chunk just finished (MMAs complete) into the 128-bit
+  // sums; warps 0-7 each take 16 of the 32 columns
+  auto readout = [&](int c) -> bool {
+    if (!mbar_wait(&sh.accfull, static_cast<uint32_t>(c & 1))) sh.fail = 1;
+    if (__any_sync(0xffffffffu, failed())) return false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tl = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) +
+                        static_cast<uint32_t>((warp >> 2) * kHalf);
+#pragma unroll
+    for (int L = 0; L < kLev; ++L) {
+      uint32_t v[kHalf];
+      tmem_ld16(tl + kAccCol + static_cast<uint32_t>(32 * L), v);
+#pragma unroll
+      for (int cc = 0; cc < kHalf; ++cc) {
+        // an exact integer in FP32; the 32-bit conversion stays off the
+        // FP64 pipe
+        const int64_t sv = static_cast<int64_t>(__float2int_rz(__uint_as_float(v[cc])));
+        if (L < 4) ahi[cc] += sv << (8 * (3 - L));
+        else alo[cc] += sv << (8 * (7 - L));
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    mbar_arrive(&sh.accfree);
+    return true;
+  };
+
+  if (warp == 8) {
+    // ------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int k = 0; k < nk; ++k) {
+        if (failed()) break;
+        const int qx = k % kXStages;
+        if ((k >= 1 && !mbar_wait(&sh.qfree, static_cast<uint32_t>((k - 1) & 1))) ||
+            (k >= kXStages &&
+             !mbar_wait(&sh.xfree[qx], static_cast<uint32_t>(((k / kXStages) - 1) & 1)))) {
+          sh.fail = 1;
+          break;
+        }
+        const int x = static_cast<int>(k0 + static_cast<int64_t>(k) * kOK);
+        mbar_expect_tx(&sh.qfull, static_cast<uint32_t>(kQBytes));
+        for (int b = 0; b < 4; ++b) tma_load_2d(stQ + b * kQBox, &mapQ, &sh.qfull, x + 16 * b, m0);
+        mbar_expect_tx(&sh.xfull[qx], static_cast<uint32_t>(kXBytes));
+        for (int b = 0; b < 4; ++b)
+          tma_load_2d(stX(qx) + b * kXBox, &mapX, &sh.xfull[qx], x + 16 * b, n0);
+        issued = k + 1;
+      }
+      if (failed()) {
+        if (issued > 0) mbar_wait(&sh.qfull, static_cast<uint32_t>((issued - 1) & 1));
+        for (int k = (issued > kXStages ? issued - kXStages : 0); k < issued; ++k)
+          mbar_wait(&sh.xfull[k % kXStages], static_cast<uint32_t>((k / kXStages) & 1));
+      }
+    }
+  } else if (warp == 9) {
+    // ------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      for (int k = 0; k < nk; ++k) {
+        if (failed()) break;
+        const int qb = k % kXStages;
+        const int c = k / kChunk;
+        const bool first = (k % kChunk) == 0;
+        if (!mbar_wait(&sh.afull, static_cast<uint32_t>(k & 1)) ||
+            !mbar_wait(&sh.bfull[qb], static_cast<uint32_t>((k / kXStages) & 1)) ||
+            (first && c > 0 && !mbar_wait(&sh.accfree, static_cast<uint32_t>((c - 1) & 1)))) {
+          sh.fail = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t bbase = smem_u32(stB(qb));
+#pragma unroll 1
+        for (int kk = 0; kk < kOK / 16; ++kk) {
+          bool seen[kLev] = {false, false, false, false, false, false, false, false};
+#pragma unroll
+          for (int t = 0; t < kDig; ++t) {
+#pragma unroll
+            for (int u = 0; u < kDig; ++u) {
+              if (t + u > kLev - 1) continue;     // level (t+1)+(u+1) <= 9
+              const int L = t + u;
+              const uint32_t acc = (!first || kk > 0 || seen[L]) ? 1u : 0u;
+              seen[L] = true;
+              const uint64_t b = sdesc(bbase + static_cast<uint32_t>(u * kBSlice)) +
+                                 static_cast<uint64_t>((kk * 32) >> 4);
+              mma_bf16_tmem_a(tmem + kAccCol + static_cast<uint32_t>(32 * L),
+                              tmem + kACol + static_cast<uint32_t>(32 * t + 8 * kk), b, idesc,
+                              acc);
+            }
+          }
+        }
+        mma_commit(&sh.afree);        // A slices reusable
+        mma_commit(&sh.bfree[qb]);    // B slices reusable
+        if (chunk_end(k)) mma_commit(&sh.accfull);
+      }
+      mma_commit(&sh.done);
+    }
+  } else {
+    // ------------------------------------------------ split (warps 0-7)
+    // A (Q, into tensor memory): warp w covers lanes 32 (w % 4) .. + 31 (Q
+    // columns) for rows 32 (w / 4) .. + 31 (boxes 2 (w / 4), 2 (w / 4) + 1);
+    // B (X, into the shared-memory slices): warp w covers rows 8 w .. 8 w + 7
+    // (one 16-byte K chunk) of all 32 columns, lane = column.
+    const int m = (warp & 3) * 32 + lane;    // Q column m0 + m
+    const int half = warp >> 2;
+    const int eM = (m0 + m < M) ? eq[m0 + m] : -4000;
+    const int eN = (n0 + lane < N) ? ex[n0 + lane] : -4000;
+    const uint32_t tlane = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16);
+    for (int k = 0; k < nk; ++k) {
+      const int qx = k % kXStages;
+      bool bad = failed();
+      if (!bad) {
+        const bool ok =
+            mbar_wait(&sh.qfull, static_cast<uint32_t>(k & 1)) &&
+            mbar_wait(&sh.xfull[qx], static_cast<uint32_t>((k / kXStages) & 1)) &&
+            (k == 0 || mbar_wait(&sh.afree, static_cast<uint32_t>((k - 1) & 1))) &&
+            (k < kXStages ||
+             mbar_wait(&sh.bfree[qx], static_cast<uint32_t>(((k / kXStages) - 1) & 1)));
+        if (!ok) {
+          sh.fail = 1;
+          bad = true;
+        }
+      }
+      if (__any_sync(0xffffffffu, bad)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // B: rows 8 warp .. + 7 of column `lane` (box warp / 2, chunks 4 (warp
+      // % 2) .. + 3 of its 128-byte line, chunk j at (j ^ (lane & 7)))
+      {
+        const unsigned char* line = stX(qx) + (warp >> 1) * kXBox + lane * 128;
+        uint32_t pk[kDig][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int jj = 4 * (warp & 1) + j;
+          const double2 v = *reinterpret_cast<const double2*>(line + ((jj ^ (lane & 7)) << 4));
+          uint32_t h0[kDig], h1[kDig];
+          digit_bits(scaled62(v.x, eN), h0);
+          digit_bits(scaled62(v.y, eN), h1);
+#pragma unroll
+          for (int t = 0; t < kDig; ++t) pk[t][j] = pack2(h0[t], h1[t]);
+        }
+        unsigned char* bs = stB(qx);
+#pragma unroll
+        for (int t = 0; t < kDig; ++t) {
+          unsigned char* row = bs + t * kBSlice + (lane >> 3) * 1024 + (lane & 7) * 128;
+          *reinterpret_cast<uint4*>(row + ((warp ^ (lane & 7)) << 4)) =
+              make_uint4(pk[t][0], pk[t][1], pk[t][2], pk[t][3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      }
+      mbar_arrive(&sh.xfree[qx]);
+      mbar_arrive(&sh.bfull[qx]);
+      // A: column m's rows in this warp's two boxes; box b's chunk j (rows
+      // 16b+2j, +1) becomes tensor-memory column 8b+j of each slice (two
+      // BF16 digits, the lower row in the low half)
+#pragma unroll 1
+      for (int bb = 0; bb < 2; ++bb) {
+        const int b = 2 * half + bb;
+        const unsigned char* line = stQ + b * kQBox + m * 128;
+        uint32_t words[kDig][8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const double2 v = *reinterpret_cast<const double2*>(line + ((j ^ (m & 7)) << 4));
+          uint32_t h0[kDig], h1[kDig];
+          digit_bits(scaled62(v.x, eM), h0);
+          digit_bits(scaled62(v.y, eM), h1);
+#pragma unroll
+          for (int t = 0; t < kDig; ++t) words[t][j] = pack2(h0[t], h1[t]);
+        }
+#pragma unroll
+        for (int t = 0; t < kDig; ++t)
+          tmem_st8(tlane + kACol + static_cast<uint32_t>(32 * t + 8 * b), words[t]);
+      }
+      mbar_arrive(&sh.qfree);
+      tmem_st_wait();
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&sh.afull);
+      if (chunk_end(k) && !readout(k / kChunk)) break;
+    }
+  }
+  // (twice the limit: after a failure the MMA warp may first spend one
+  // limit on a step that never came)
+  if (warp < 4 && !mbar_wait(&sh.done, 0, 2 * kWaitNs)) sh.fail = 1;
+  __syncthreads();
+  const bool good = !sh.fail;
+  if (!good) {
+    if (tid == 0) atomicExch(err, 1);
+  } else if (warp < 8) {
+    const int gm = m0 + (warp & 3) * 32 + lane;
+    if (gm < M) {
+      double* P = part + static_cast<int64_t>(blockIdx.z) * M * N;
+      const int eM = eq[gm];
+#pragma unroll
+      for (int cc = 0; cc < kHalf; ++cc) {
+        const int gc = n0 + (warp >> 2) * kHalf + cc;
+        if (gc < N) {
+          // V' = ahi 2^32 + alo exactly as a 128-bit integer, then rounded
+          const int64_t carry = alo[cc] >> 32;               // floor division
+          const int64_t hi = ahi[cc] + carry;                 // V' = hi 2^32 + lo32
+          const uint32_t lo32 = static_cast<uint32_t>(alo[cc]);
+          const double v = ldexp(static_cast<double>(hi), 32) + static_cast<double>(lo32);
+          P[gm + static_cast<int64_t>(gc) * M] = (eM < -2000 || ex[gc] < -2000)
+                                                    ? 0.0
+                                                    : ldexp(v, eM + ex[gc] - 68);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kOTmemCols)
+                 : "memory");
+  }
+}
+
+// e[c] = the exponent of column c's largest magnitude (|x| < 2^e): CTA
+// (c, z) takes rows [z rows, (z+1) rows) and merges its exponent with
+// atomicMax into e[c], which starts at a large negative value (all-zero
+// columns keep it).
+__global__ void __launch_bounds__(256)
+col_exponent_kernel(int64_t n, const double* __restrict__ X, int64_t ld, int64_t rows,
+                    int* __restrict__ e) {
+  const double* col = X + static_cast<int64_t>(blockIdx.x) * ld;
+  const int64_t r0 = static_cast<int64_t>(blockIdx.y) * rows;
+  const int64_t r1 = (r0 + rows < n) ? r0 + rows : n;
+  double mx = 0.0;
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += 256) mx = fmax(mx, fabs(col[r]));
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  __shared__ double wm[8];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t = fmax(t, wm[w]);
+    if (t > 0.0) {
+      int ee = 0;
+      frexp(t, &ee);   // t = f 2^ee, f in [0.5, 1): |x| <= t < 2^ee
+      atomicMax(e + blockIdx.x, ee);
+    }
+  }
+}
+
+void col_exponents(int64_t n, const double* X, int64_t ld, int cols, int* e, cudaStream_t st) {
+  SG_CUDA(cudaMemsetAsync(e, 0x80, sizeof(int) * cols, st));   // 0x80808080: no entry yet
+  int64_t z = static_cast<int64_t>(device_sm_count()) * 8 / cols;
+  const int64_t zmax = (n + 4095) / 4096;
+  if (z > zmax) z = zmax;
+  if (z < 1) z = 1;
+  const int64_t rows = (n + z - 1) / z;
+  col_exponent_kernel<<<dim3(cols, static_cast<unsigned>((n + rows - 1) / rows)), 256, 0, st>>>(
+      n, X, ld, rows, e);
+  SG_LAUNCH_CHECK();
+}
+
+__device__ int g_oz_err;
+
+PFN_cuTensorMapEncodeTiled_v12000 oz_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                         cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// FP64 column-major matrix (rows x cols, leading dimension ld), boxes of
+// 16 rows x box_cols, 128-byte swizzle
+bool make_map64(CUtensorMap* map, const double* ptr, int64_t rows, int64_t cols, int64_t ld,
+                int box_cols) {
+  auto fn = oz_encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(rows), static_cast<cuuint64_t>(cols)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * sizeof(double)};
+  cuuint32_t box[2] = {16u, static_cast<cuuint32_t>(box_cols)};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(ptr), dims, strides,
+            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+int* oz_err_flag() {
+  static int* ptr[64] = {};
+  static std::mutex mu;
+  int dev = 0;
+  SG_CUDA(cudaGetDevice(&dev));
+  SG_REQUIRE(dev >= 0 && dev < 64, SG_ECUDA, "device index out of range");
+  std::lock_guard<std::mutex> lock(mu);
+  if (!ptr[dev]) {
+    void* p = nullptr;
+    SG_CUDA(cudaGetSymbolAddress(&p, g_oz_err));
+    ptr[dev] = static_cast<int*>(p);
+  }
+  return ptr[dev];
+}
+
+int64_t oz_splits(int64_t n, int i, int s, int64_t* rows) {
+  const int64_t tiles = static_cast<int64_t>((i + kOM - 1) / kOM) * ((s + kON - 1) / kON);
+  int64_t S = static_cast<int64_t>(device_sm_count()) / tiles;
+  const int64_t maxS = n / (4 * kOK);     // at least four stages per split
+  if (S > maxS) S = maxS;
+  // at most 2^12 level readouts per split keep the int64 halves exact
+  const int64_t minS = (n + (int64_t(kOK) * kChunk << 12) - 1) / (int64_t(kOK) * kChunk << 12);
+  if (S < minS) S = minS;
+  if (S < 1) S = 1;
+  int64_t r = (n + S - 1) / S;
+  r = (r + kOK - 1) / kOK * kOK;
+  if (rows) *rows = r;
+  return (n + r - 1) / r;
+}
+
+}  // namespace
+
+bool oz_dot_supported(int64_t n, const double* Q, int64_t ldq, int i, const double* X,
+                      int64_t ldx, int s) {
+  if (n < 8 * kOK || i < 1 || s < 1) return false;
+  if ((reinterpret_cast<uintptr_t>(Q) | reinterpret_cast<uintptr_t>(X)) & 15) return false;
+  if (((ldq * 8) & 15) || ((ldx * 8) & 15)) return false;
+  if (n > (int64_t(1) << 31) - 1) return false;
+  return oz_encode_fn() != nullptr;
+}
+
+// Whether the tensor-core form is expected to beat the FP64-pipe kernel:
+// a tile of 128 x 32 outputs costs about kStageUs per 64 rows on one SM,
+// the FP64 pipe sustains about 1 TFLOP/s (2 n i s flops; the symmetric
+// Gram n s (s+1)).
+bool oz_dot_pays(int64_t n, int i, int s, bool sym) {
+  constexpr double kStageUs = 6.0;
+  const double tiles = static_cast<double>((i + kOM - 1) / kOM) * ((s + kON - 1) / kON);
+  const double t_oz = static_cast<double>((n + kOK - 1) / kOK) * tiles * kStageUs * 1e-6 /
+                      static_cast<double>(device_sm_count());
+  const double flops = sym ? static_cast<double>(n) * s * (s + 1.0)
+                           : 2.0 * static_cast<double>(n) * i * s;
+  return t_oz < 0.8 * flops / 1.0e12;
+}
+
+int64_t oz_dot_part_size(int64_t n, int i, int s) {
+  return oz_splits(n, i, s, nullptr) * i * s;
+}
+
+int64_t oz_exp_ints(int i, int s) { return static_cast<int64_t>(i) + s; }
+
+void oz_check_error(cudaStream_t st) {
+  int* f = oz_err_flag();
+  int host = 0;
+  SG_CUDA(cudaMemcpyAsync(&host, f, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SG_CUDA(cudaStreamSynchronize(st));
+  if (host) {
+    SG_CUDA(cudaMemsetAsync(f, 0, sizeof(int), st));
+    throw Error(SG_ECUDA, "tensor-core FP64 block dot: a bounded wait ran out");
+  }
+}
+
+void oz_dot(int64_t n, const double* Q, int64_t ldq, int i, const double* X, int64_t ldx,
+            int s, int* exps, double* part, int64_t part_cap, int* nsplit, cudaStream_t st) {
+  int* err = oz_err_flag();
+  int64_t rows = 0;
+  const int64_t S = oz_splits(n, i, s, &rows);
+  SG_REQUIRE(S * i * s <= part_cap, SG_EINVAL, "oz_dot: workspace too small");
+  int* eq = exps;
+  int* ex = exps + i;
+  col_exponents(n, Q, ldq, i, eq, st);
+  if (X == Q && s <= i)
+    SG_CUDA(cudaMemcpyAsync(ex, eq, sizeof(int) * s, cudaMemcpyDeviceToDevice, st));
+  else
+    col_exponents(n, X, ldx, s, ex, st);
+  CUtensorMap mq, mx;
+  SG_REQUIRE(make_map64(&mq, Q, n, i, ldq, kOM) && make_map64(&mx, X, n, s, ldx, kON), SG_ECUDA,
+             "cuTensorMapEncodeTiled failed");
+  ensure_dynamic_smem(reinterpret_cast<const void*>(oz_dot_kernel), kOzSmem);
+  dim3 grid((i + kOM - 1) / kOM, (s + kON - 1) / kON, static_cast<unsigned>(S));
+  oz_dot_kernel<<<grid, kOThreads, kOzSmem, st>>>(mq, mx, n, i, s, eq, ex, rows, part, err);
+  SG_LAUNCH_CHECK();
+  *nsplit = static_cast<int>(S);
+}
+
+}  // namespace sg

@@ -601,6 +601,7 @@ sg_status sg_block_dot(sg_handle* h, int64_t n, const double* Q, int64_t ldq,
       h->part_cap = need;
     }
     sg::block_dot(n, Q, ldq, i, X, ldx, s, W, ldw, sym != 0, h->part, h->part_cap, st);
+    sg::oz_check_error(st);  // synchronises: reports a tensor-core timeout
   });
 }
 

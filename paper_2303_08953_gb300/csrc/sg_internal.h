@@ -172,6 +172,19 @@ void tc_dot(int64_t n, const float* Q, int64_t ldq, int i, const float* X,
             int64_t ldx, int s, double* part, int64_t part_cap, int* nsplit,
             cudaStream_t st);
 void tc_check_error(cudaStream_t st);
+// Tensor-core (tcgen05, TMA) FP64 block dot W = Q^T X from exact 8-bit
+// digit slices of both operands: split partials into `part` (part_cap
+// doubles), column exponents into `exps` (oz_exp_ints(i, s) ints), number of
+// splits in *nsplit; a bounded wait that ran out sets a device flag that
+// oz_check_error reads (and clears, then throws).
+bool oz_dot_supported(int64_t n, const double* Q, int64_t ldq, int i, const double* X,
+                      int64_t ldx, int s);
+int64_t oz_dot_part_size(int64_t n, int i, int s);
+int64_t oz_exp_ints(int i, int s);
+bool oz_dot_pays(int64_t n, int i, int s, bool sym);
+void oz_dot(int64_t n, const double* Q, int64_t ldq, int i, const double* X, int64_t ldx,
+            int s, int* exps, double* part, int64_t part_cap, int* nsplit, cudaStream_t st);
+void oz_check_error(cudaStream_t st);
 // Tensor-core (tcgen05, TMA) FP32 block update X = beta X + alpha Q W.
 bool tc_update_supported(int64_t n, const float* Q, int64_t ldq, int i,
                          const float* X, int64_t ldx, int s);

@@ -393,10 +393,13 @@ Shifts shifts_from_values(const std::vector<double>& re, const std::vector<doubl
 // cycle_tol > 0: a cycle also ends once its implicit residual has dropped
 // by that factor (the inner solve of a refinement step).  stall > 0: the
 // solve stops (log.stalled) when a cycle's true residual is above `stall`
-// times the one two cycles earlier.
+// times the one two cycles earlier.  first_max > 0: the solve also stops
+// (log.stalled) when the first cycle leaves a true residual above
+// first_max times the initial one.
 template <typename T>
 void solve_impl(sg_handle* h, const DevCsr& M, const SolveOpts& o,
-                double cycle_tol, double stall, cudaStream_t st, SolveLog& log) {
+                double cycle_tol, double stall, cudaStream_t st, SolveLog& log,
+                double first_max = 0.0) {
   using B = Basis<T>;
   const double t0 = now_ms();
   const int64_t n = M.n;
@@ -507,6 +510,7 @@ void solve_impl(sg_handle* h, const DevCsr& M, const SolveOpts& o,
       SG_CUDA(cudaEventRecord(h->ev[2], st));
       SG_CUDA(cudaStreamSynchronize(st));
       if (sizeof(T) == 4) { tc_check_error(st); tc_update_check_error(st); }
+      else oz_check_error(st);
       {
         float a = 0, b = 0;
         cudaEventElapsedTime(&a, h->ev[0], h->ev[1]);
@@ -557,6 +561,7 @@ void solve_impl(sg_handle* h, const DevCsr& M, const SolveOpts& o,
         SG_CUDA(cudaEventRecord(h->ev[2], st));
         SG_CUDA(cudaStreamSynchronize(st));
         if (sizeof(T) == 4) { tc_check_error(st); tc_update_check_error(st); }
+        else oz_check_error(st);
         {
           float b = 0;
           cudaEventElapsedTime(&b, h->ev[1], h->ev[2]);
@@ -646,6 +651,10 @@ void solve_impl(sg_handle* h, const DevCsr& M, const SolveOpts& o,
       log.stalled = true;
       break;
     }
+    if (first_max > 0.0 && nc == 1 && rel_true > first_max) {
+      log.stalled = true;
+      break;
+    }
   }
   log.iters = total;
   log.restarts = static_cast<int>(log.cycle_relres.size()) - 1;
@@ -694,12 +703,16 @@ void solve_fp32_ir(sg_handle* h, const DevCsr& M, const SolveOpts& o,
   o32.omega = std::min(o.omega, omega32);
   o32.omega_est = std::min(o.omega_est, omega32);
   o32.max_iters = o.max_iters > 0 ? o.max_iters : max_refine * o.m;
-  // Refinement with an FP32 inner solve contracts only while
-  // kappa(A) eps_32 < 1; when two refinement steps together fail to halve
-  // the true residual, the remaining iterations run with the FP64 basis
-  // from the current x (same method, fresh Ritz values), so the solve
-  // still reaches tol whenever the FP64 solve does.
-  solve_impl<float>(h, M, o32, inner_tol, 0.5, st, log);
+  // Refinement with an FP32 inner solve contracts the residual by about
+  // max(inner_tol, kappa(A) eps_32) per step, and only while kappa(A)
+  // eps_32 < 1.  So the remaining iterations run with the FP64 basis from
+  // the current x (same method, the FP32 pre-pass's Ritz values) when
+  //  - the first refinement step leaves more than 10 inner_tol of the
+  //    initial residual (kappa(A) eps_32 is what limits it: many slow
+  //    refinement steps would follow), or
+  //  - two refinement steps together fail to halve the true residual;
+  // the solve then still reaches tol whenever the FP64 solve does.
+  solve_impl<float>(h, M, o32, inner_tol, 0.5, st, log, 10.0 * inner_tol);
   log.refinements = static_cast<int>(log.cycle_relres.size());
   const int left = o32.max_iters - log.iters;
   if (log.converged || !log.stalled || left <= 0) return;
@@ -710,6 +723,11 @@ void solve_fp32_ir(sg_handle* h, const DevCsr& M, const SolveOpts& o,
   SolveOpts o64 = o;
   o64.tol = o.tol / scale;
   o64.max_iters = left;
+  if (o64.n_ritz == 0 && !log.ritz_re.empty()) {   // no second pre-pass
+    o64.n_ritz = static_cast<int>(log.ritz_re.size());
+    o64.ritz_re = log.ritz_re.data();
+    o64.ritz_im = log.ritz_im.data();
+  }
   SolveLog l64;
   solve_impl<double>(h, M, o64, 0.0, 0.0, st, l64);
   for (double r : l64.relres_hist) log.relres_hist.push_back(r * scale);

@@ -173,6 +173,24 @@ def _block_dot(solver, Q, X, n, sym=False):
     return W
 
 
+@pytest.mark.parametrize("n,i,s", [(70001, 107, 106), (4133, 241, 17), (9000, 3, 130)])
+def test_block_dot_fp64_tensor_cores_exact_on_integers(solver, n, i, s):
+    """The FP64 block dot on the tensor cores (8-bit digit slices, exact
+    level sums) returns exact dot products: integer inputs of magnitude up
+    to 2^15 have exact FP64 dot products (< 2^53), and every entry must
+    equal numpy's exactly.  Columns of very different magnitudes (2^-40 ..
+    2^40 scaling) check the per-column exponents."""
+    rng = np.random.default_rng(n + i + s)
+    Q = rng.integers(-2 ** 15, 2 ** 15, size=(i, n)).astype(np.float64)
+    X = rng.integers(-2 ** 15, 2 ** 15, size=(s, n)).astype(np.float64)
+    Q *= np.exp2(rng.integers(-40, 41, size=(i, 1)))
+    X *= np.exp2(rng.integers(-40, 41, size=(s, 1)))
+    Wt = host(_block_dot(solver, Q, X, n))
+    assert np.array_equal(Wt.T, Q @ X.T)
+    G = host(_block_dot(solver, X, X, n, sym=True))
+    assert np.array_equal(G, X @ X.T)
+
+
 @pytest.mark.parametrize("n,s", [(4133, 1), (4133, 31), (70001, 64), (3001, 120)])
 def test_block_dot_symmetric_gram(solver, n, s):
     rng = np.random.default_rng(s)
