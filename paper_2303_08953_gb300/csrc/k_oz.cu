@@ -558,7 +558,7 @@ bool oz_dot_supported(int64_t n, const double* Q, int64_t ldq, int i, const doub
 // the FP64 pipe sustains about 1 TFLOP/s (2 n i s flops; the symmetric
 // Gram n s (s+1)).
 bool oz_dot_pays(int64_t n, int i, int s, bool sym) {
-  constexpr double kStageUs = 6.0;
+  constexpr double kStageUs = 10.5;
   const double tiles = static_cast<double>((i + kOM - 1) / kOM) * ((s + kON - 1) / kON);
   const double t_oz = static_cast<double>((n + kOK - 1) / kOK) * tiles * kStageUs * 1e-6 /
                       static_cast<double>(device_sm_count());

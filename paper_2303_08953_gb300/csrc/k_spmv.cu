@@ -240,6 +240,40 @@ __device__ void grid_barrier(unsigned* bar, unsigned nblocks, int* err,
   __syncthreads();
 }
 
+// Grid barrier on a counter that only grows: every CTA adds one per
+// barrier, and barrier number k of the launch (counting from 0) is passed
+// once the counter reaches base + G (k + 1), base being the counter's value
+// when the launch started (known to the host, which zeroes the counter at
+// the start of a pre-pass).  No reset and no generation word: the last
+// arrival releases the waiters directly, one L2 round trip sooner than
+// grid_barrier.  The wait is time-bounded like grid_barrier's.
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ void grid_barrier_count(unsigned* ctr, unsigned target, int* err,
+                                   uint64_t limit_ns = kBarrierNs) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(ctr, 1u);
+    if (*reinterpret_cast<volatile int*>(err) == 0) {
+      const uint64_t t0 = now_ns();
+      unsigned spins = 0;
+      while (static_cast<int>(ld_acquire_u32(ctr) - target) < 0) {
+        if ((++spins & 255u) == 0 && now_ns() - t0 > limit_ns) {
+          atomicExch(err, 1);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
 constexpr int kCoopThreads = 1024;  // one CTA per SM, 32 warps in flight
 constexpr int kCoopStage = 8192;    // staged nonzeros per CTA tile
 
@@ -373,7 +407,7 @@ arnoldi_step_kernel(int n, int rows_per_cta, const int* __restrict__ rowptr,
 __global__ void __launch_bounds__(kCoopThreads, 1)
 arnoldi_mgs_resident_kernel(int n, int rows_cta, double* __restrict__ V, int64_t ld, int j,
                             double* __restrict__ H, int ldh, double* __restrict__ wn,
-                            double* __restrict__ red, unsigned* bar, int* err) {
+                            double* __restrict__ red, unsigned* ctr, unsigned base, int* err) {
   extern __shared__ __align__(16) unsigned char coop_smem[];
   double* ws = reinterpret_cast<double*>(coop_smem);
   const int G = gridDim.x;
@@ -399,7 +433,8 @@ arnoldi_mgs_resident_kernel(int n, int rows_cta, double* __restrict__ V, int64_t
     const double sv = block_sum_few_d<kCoopThreads>(accv);
     if (t == 0) { pWW[blockIdx.x] = sw; pA[blockIdx.x] = sv; }
   }
-  grid_barrier(bar, G, err);
+  unsigned target = base + static_cast<unsigned>(G);
+  grid_barrier_count(ctr, target, err);
   if (blockIdx.x == 0) {
     const double ww = sum_partials_few_d<kCoopThreads>(pWW, G);
     if (t == 0) wn[j] = sqrt(ww);
@@ -445,7 +480,8 @@ arnoldi_mgs_resident_kernel(int n, int rows_cta, double* __restrict__ V, int64_t
     }
     const double tot = block_sum_few_d<kCoopThreads>(acc);
     if (t == 0) pout[blockIdx.x] = tot;
-    grid_barrier(bar, G, err);
+    target += static_cast<unsigned>(G);
+    grid_barrier_count(ctr, target, err);
     double* tmp = pin; pin = pout; pout = tmp;
   }
   // normalise into V's column j+1
@@ -1005,10 +1041,16 @@ void launch_arnoldi_step(const DevCsr& A, const T* val, T* V, int64_t ld, int j,
         // w = A v_j into V's column j+1, then the MGS phases on chip
         dispatch<0, false, T>(A, A.val, val, V + static_cast<int64_t>(j) * ld, nullptr,
                               V + static_cast<int64_t>(j + 1) * ld, T(0), T(0), T(1), st);
+        // barriers per step j: one after the w partials, one per MGS phase
+        // (j + 1); the counter (word 16 of the barrier block, zeroed at the
+        // start of the pre-pass) has seen G (j' + 2) arrivals per earlier step
         int n = A.n;
         int rc = R;
-        void* args[] = {&n, &rc, &V, &ld, &j, &H, const_cast<int*>(&ldh), &wn, &red, &bar,
-                        &err};
+        unsigned* ctr = bar + 16;
+        unsigned base = static_cast<unsigned>(G) * static_cast<unsigned>(j) *
+                        static_cast<unsigned>(j + 3) / 2u;
+        void* args[] = {&n, &rc, &V, &ld, &j, &H, const_cast<int*>(&ldh), &wn, &red, &ctr,
+                        &base, &err};
         SG_CUDA(cudaLaunchCooperativeKernel(fn, dim3(G), dim3(kCoopThreads), args, smem, st));
         count_launch();
         return;
