@@ -201,23 +201,24 @@ def spmv_bytes(A):
     return 12 * A.nnz + 4 * (A.n + 1) + 8 * A.n + 8 * A.n
 
 
-def prepass_flops(A, k):
-    """FP64 flops of k MGS-Arnoldi steps (Sec. 3.4): per step j one SpMV
-    (2 nnz), j+1 projections (dot and update, 4 N each), the norm of w
-    (2 N) and its scaling (N)."""
-    return sum(2 * A.nnz + 4 * A.n * (j + 1) + 3 * A.n for j in range(k))
+def mgs_flops(A, k):
+    """FP64 flops of the MGS launches of a k-step pre-pass (Sec. 3.4): per
+    step j, j+1 projections (dot and update, 4 N each), the norm of w (2 N)
+    and its scaling (N)."""
+    return sum(4 * A.n * (j + 1) + 3 * A.n for j in range(k))
 
 
-def prepass_bytes(A, k):
-    """Algorithmic HBM bytes of the same k steps: the SpMV, every basis
-    vector read once per step, the new vector written once."""
-    return sum(spmv_bytes(A) - 8 * A.n + 8 * A.n * (j + 1) + 8 * A.n for j in range(k))
+def mgs_bytes(A, k):
+    """Algorithmic HBM bytes of the same MGS launches: w and the j+1 basis
+    vectors read once, the new vector written once."""
+    return sum(8 * A.n * (j + 3) for j in range(k))
 
 
-# DRAM bytes per launch of the resident FP64 pre-pass step, per row, from
-# an ncu capture (profiles/arnoldi_step_resident_fp64_randband_1M.md);
-# None until that capture exists.
-PREPASS_DRAM_BYTES_PER_ROW = None
+# DRAM bytes of one MGS launch per row and per vector it streams (j + 2
+# vectors read at step j), from the ncu capture of step j = 58 at
+# 2,097,152 rows: 1,007,194,000 + 3,276,544 bytes over 60 vectors
+# (profiles/arnoldi_mgs_resident_fp64_randband_2M_j58.md).
+MGS_DRAM_BYTES_PER_ROW_VECTOR = (1_007_194_000 + 3_276_544) / 2_097_152 / 60
 
 
 # ------------------------------------------------------------ CPU oracle
@@ -355,47 +356,16 @@ def run_ours(args):
                        "adj_phase_ms": {k: round(v, 2) for k, v in inf2.times_ms.items()}})
         out["fwd_adjoint"] = fa
 
-    # ---- roofline of the dominant kernel: the FP64 Ritz pre-pass step (one
-    # cooperative MGS-Arnoldi launch per step, Sec. 3.4), timed over the
-    # 120 launches of the pre-pass with CUDA events on the launching stream
-    q = b / torch.linalg.vector_norm(b)
-    solver.arnoldi(q, PREPASS_STEPS)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    reps = 3
-    e0.record(stream)
-    for _ in range(reps):
-        solver.arnoldi(q, PREPASS_STEPS)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t_pre = e0.elapsed_time(e1) / reps / 1e3
-    t_launch = t_pre / PREPASS_STEPS
-    fl = prepass_flops(A, PREPASS_STEPS) / PREPASS_STEPS
-    by = prepass_bytes(A, PREPASS_STEPS) / PREPASS_STEPS
-    pk = measured_peaks()
-    hbm = pk["hbm_gbs"] if pk else 6800.0
-    hbm_src = "MEASURED_PEAKS.json hbm_gbs" if pk else "fallback"
-    ach = fl / t_launch / 1e12
-    out["roofline"] = {
-        "kernel": f"arnoldi_step FP64 (Ritz pre-pass step, mean of the {PREPASS_STEPS} "
-                  f"launches of one pre-pass)",
-        "bound": "alu", "achieved": round(ach, 4),
-        "peak": round(FP64_ALU_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
-        "frac": round(ach / FP64_ALU_PEAK_TFLOPS, 4),
-        "traffic": (int(round(PREPASS_DRAM_BYTES_PER_ROW * A.n))
-                    if PREPASS_DRAM_BYTES_PER_ROW else None),
-        "launch_ms": round(t_launch * 1e3, 4),
-        "algorithmic_flops_per_launch": int(fl),
-        "algorithmic_bytes_per_launch": int(by),
-        "hbm_frac": round(by / t_launch / 1e9 / hbm, 4),
-        "peak_source": "derived: 152 SMs x 2.07 GHz x 4 FP64 flop/clk/SM "
-                       "(nominal 1.25 TFLOP/s FP64)"}
-
-    # secondary: the MPK's SpMV against HBM
+    # ---- roofline of the dominant kernel: the resident FP64 MGS launch of
+    # the Ritz pre-pass (Sec. 3.4; one launch per step, after that step's
+    # SpMV).  Its mean launch time is the pre-pass time, timed with CUDA
+    # events over the 240 launches of one pre-pass, minus its 120 SpMVs at
+    # the SpMV's own event-timed rate (below)
     n = A.n
     xv = torch.rand(n, dtype=torch.float64, device=dev)
     yv = torch.empty_like(xv)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     for _ in range(5):
         solver.spmv_newton(xv, 0.3, 1.1, out=yv)
     torch.cuda.synchronize()
@@ -406,6 +376,43 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     t_sp = e0.elapsed_time(e1) / reps / 1e3
+    q = b / torch.linalg.vector_norm(b)
+    solver.arnoldi(q, PREPASS_STEPS)
+    torch.cuda.synchronize()
+    reps = 3
+    e0.record(stream)
+    for _ in range(reps):
+        solver.arnoldi(q, PREPASS_STEPS)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_pre = e0.elapsed_time(e1) / reps / 1e3
+    t_launch = (t_pre - PREPASS_STEPS * t_sp) / PREPASS_STEPS
+    fl = mgs_flops(A, PREPASS_STEPS) / PREPASS_STEPS
+    by = mgs_bytes(A, PREPASS_STEPS) / PREPASS_STEPS
+    vec = sum(j + 2 for j in range(PREPASS_STEPS)) / PREPASS_STEPS
+    pk = measured_peaks()
+    hbm = pk["hbm_gbs"] if pk else 6800.0
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs" if pk else "fallback"
+    ach = fl / t_launch / 1e12
+    out["roofline"] = {
+        "kernel": f"arnoldi_mgs_resident_kernel FP64 (MGS phases of one Ritz pre-pass step, "
+                  f"w in shared memory; mean of the {PREPASS_STEPS} launches of one pre-pass)",
+        "bound": "alu", "achieved": round(ach, 4),
+        "peak": round(FP64_ALU_PEAK_TFLOPS, 4), "unit": "TFLOP/s",
+        "frac": round(ach / FP64_ALU_PEAK_TFLOPS, 4),
+        "traffic": int(round(MGS_DRAM_BYTES_PER_ROW_VECTOR * n * vec)),
+        "traffic_source": "ncu dram__bytes_read+write of the launch at step j = 58, 2,097,152 "
+                          "rows, per row and streamed vector, scaled to this n and the mean "
+                          "step (profiles/arnoldi_mgs_resident_fp64_randband_2M_j58.md)",
+        "launch_ms": round(t_launch * 1e3, 4),
+        "prepass_ms": round(t_pre * 1e3, 2),
+        "algorithmic_flops_per_launch": int(fl),
+        "algorithmic_bytes_per_launch": int(by),
+        "hbm_frac": round(by / t_launch / 1e9 / hbm, 4),
+        "peak_source": "derived: 152 SMs x 2.07 GHz x 4 FP64 flop/clk/SM "
+                       "(nominal 1.25 TFLOP/s FP64)"}
+
+    # secondary: the MPK's SpMV against HBM (timed above)
     gbs = spmv_bytes(A) / t_sp / 1e9
     out["roofline_spmv"] = {
         "kernel": "spmv_newton FP64 (one MPK step)", "bound": "hbm",

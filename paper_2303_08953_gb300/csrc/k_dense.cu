@@ -660,9 +660,20 @@ void block_dot32(int64_t n, const float* Q, int64_t ldq, int i,
                         st);
 }
 
+int64_t block_update_scratch(int i) { return (static_cast<int64_t>(i) + 1) / 2 + 1; }
+
 void block_update(int64_t n, const double* Q, int64_t ldq, int i,
                   const double* W, int ldw, double* X, int64_t ldx, int s,
-                  double alpha, double beta, bool upper, cudaStream_t st) {
+                  double alpha, double beta, bool upper, double* scratch,
+                  int64_t scratch_doubles, cudaStream_t st) {
+  if (n > 0 && i > 0 && s > 0 && scratch && scratch_doubles >= block_update_scratch(i) &&
+      !tc_disabled() && oz_update_supported(n, Q, ldq, i, X, ldx, s) &&
+      oz_update_pays(n, i, s, upper)) {
+    // FP64 products on the tensor cores, exact digit slices
+    oz_update(n, Q, ldq, i, W, ldw, X, ldx, s, alpha, beta, upper,
+              reinterpret_cast<int*>(scratch), st);
+    return;
+  }
   block_update_impl<double>(n, Q, ldq, i, W, ldw, X, ldx, s, alpha, beta,
                             upper, st);
 }

@@ -440,6 +440,293 @@ oz_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
   }
 }
 
+// ---------------------------------------------------------------- update
+// X = beta X + alpha Q W on the tensor cores, exactly in the same sense.
+// Output (r, c) sums Q[r,k] W[k,c] over k; with Q's digits relative to its
+// column exponents e_k (as in the dot) and W' = W 2^(e_k) cut into digits
+// relative to W' column c's exponent g_c, every product of the sum carries
+// the one weight 2^(g_c - 124), so the level sums are exact as above.
+// Tile: 128 rows (MMA M, tensor-memory lanes) x 32 columns of X (MMA N),
+// K = 64 columns of Q per chunk; one CTA per SM walks the row tiles of one
+// column tile.  W' is cut once per CTA into shared-memory B slices (one
+// 32 KB group of eight slices per K chunk, i <= 256); Q's rows arrive by
+// TMA as one unswizzled 128-row x 64-column box (a row's values are 1 KB
+// apart: a warp reads 32 consecutive rows conflict-free) and warps 0-7 cut
+// them into tensor-memory A slices; level sums are read every two chunks
+// (128 columns of Q) and the epilogue writes beta X + alpha V 2^(g_c - 68).
+constexpr int kUM = 128;
+constexpr int kUN = 32;
+constexpr int kUK = 64;
+constexpr int kUMaxK = 256;
+constexpr int kUQBytes = kUM * kUK * 8;                 // 64 KB
+constexpr int kUBChunk = kDig * kBSlice;                // 32 KB per K chunk
+constexpr int kUSmem = kUQBytes + (kUMaxK / kUK) * kUBChunk + 1024;
+
+struct __align__(8) OzUShared {
+  uint64_t qfull, qfree, afull, afree, accfull, accfree, done;
+  uint32_t tmem_base;
+  int fail;
+  int eq[kUMaxK];
+  int g[kUN];
+};
+
+// grid: (tiles of 32 X columns, row groups); row tiles g, g + G, ...
+__global__ void __launch_bounds__(kOThreads, 1)
+oz_update_kernel(const __grid_constant__ CUtensorMap mapQ, int64_t n, int i, int s,
+                 const double* __restrict__ W, int ldw, double* __restrict__ X, int64_t ldx,
+                 double alpha, double beta, int upper, const int* __restrict__ eq,
+                 int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char dsmem[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~static_cast<uintptr_t>(1023));
+  __shared__ OzUShared sh;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+  const int n0 = blockIdx.x * kUN;
+  const int64_t ntiles = (n + kUM - 1) / kUM;
+  const int G = gridDim.y;
+  const int my_tiles = static_cast<int>((ntiles - blockIdx.y + G - 1) / G);
+  const int nkc = (i + kUK - 1) / kUK;
+  const int gpt = (nkc + 1) / 2;                 // level readouts per row tile
+  const uint32_t idesc = idesc_bf16(kUM, kUN);
+  unsigned char* stQ = base;
+  unsigned char* bsl = base + kUQBytes;
+  auto failed = [&]() { return *reinterpret_cast<volatile int*>(&sh.fail) != 0; };
+
+  if (tid == 0) {
+    mbar_init(&sh.qfull, 1);
+    mbar_init(&sh.qfree, 256);
+    mbar_init(&sh.afull, 256);
+    mbar_init(&sh.afree, 1);
+    mbar_init(&sh.accfull, 1);
+    mbar_init(&sh.accfree, 256);
+    mbar_init(&sh.done, 1);
+    sh.fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&sh.tmem_base)),
+                 "r"(kOTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // W' = W 2^(e_k) (zero below the diagonal when `upper`) cut into digits
+  // relative to its column exponents g_c: B slices of every K chunk
+  if (warp < 8) {
+    for (int k = tid; k < kUMaxK; k += 256) sh.eq[k] = k < i ? eq[k] : -4000;
+    if (tid < kUN) sh.g[tid] = -2147483647;
+    uint4* z = reinterpret_cast<uint4*>(bsl);
+    for (int e = tid; e < nkc * kUBChunk / 16; e += 256) z[e] = make_uint4(0, 0, 0, 0);
+  }
+  __syncthreads();
+  auto wprime = [&](int k, int c) -> double {
+    const int gc = n0 + c;
+    if (k >= i || gc >= s || (upper && k > gc) || sh.eq[k] < -2000) return 0.0;
+    return ldexp(W[k + static_cast<int64_t>(gc) * ldw], sh.eq[k]);
+  };
+  if (warp < 8) {
+    const int c = lane;
+    double mx = 0.0;
+    for (int k = warp; k < i; k += 8) mx = fmax(mx, fabs(wprime(k, c)));
+    if (mx > 0.0) {
+      int ee = 0;
+      frexp(mx, &ee);
+      atomicMax(&sh.g[c], ee);
+    }
+  }
+  __syncthreads();
+  if (warp < 8) {
+    const int c = lane;
+    const int gc = sh.g[c] > -2000 ? sh.g[c] : -4000;
+    for (int k = warp; k < i; k += 8) {
+      uint32_t hb[kDig];
+      digit_bits(scaled62(wprime(k, c), gc), hb);
+      const int kc = k / kUK, kk = k % kUK;
+#pragma unroll
+      for (int t = 0; t < kDig; ++t) {
+        unsigned char* row = bsl + kc * kUBChunk + t * kBSlice + (c >> 3) * 1024 + (c & 7) * 128;
+        *reinterpret_cast<uint16_t*>(row + (((kk >> 3) ^ (c & 7)) << 4) + (kk & 7) * 2) =
+            static_cast<uint16_t>(hb[t] >> 16);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = sh.tmem_base;
+  const int nstages = my_tiles * nkc;
+
+  if (warp == 8) {
+    // ------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int q = 0; q < nstages; ++q) {
+        if (failed()) break;
+        if (q > 0 && !mbar_wait(&sh.qfree, static_cast<uint32_t>((q - 1) & 1))) {
+          sh.fail = 1;
+          break;
+        }
+        const int64_t rt = blockIdx.y + static_cast<int64_t>(q / nkc) * G;
+        mbar_expect_tx(&sh.qfull, static_cast<uint32_t>(kUQBytes));
+        tma_load_2d(stQ, &mapQ, &sh.qfull, static_cast<int>(rt * kUM), (q % nkc) * kUK);
+        issued = q + 1;
+      }
+      if (failed() && issued > 0)
+        mbar_wait(&sh.qfull, static_cast<uint32_t>((issued - 1) & 1));
+    }
+  } else if (warp == 9) {
+    // ------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      for (int q = 0; q < nstages; ++q) {
+        if (failed()) break;
+        const int kc = q % nkc;
+        const int grp = (q / nkc) * gpt + kc / 2;        // readout group
+        const bool fresh = (kc % 2) == 0;
+        if (!mbar_wait(&sh.afull, static_cast<uint32_t>(q & 1)) ||
+            (fresh && grp > 0 && !mbar_wait(&sh.accfree, static_cast<uint32_t>((grp - 1) & 1)))) {
+          sh.fail = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t bbase = smem_u32(bsl + kc * kUBChunk);
+#pragma unroll 1
+        for (int kk = 0; kk < kUK / 16; ++kk) {
+          bool seen[kLev] = {false, false, false, false, false, false, false, false};
+#pragma unroll
+          for (int t = 0; t < kDig; ++t) {
+#pragma unroll
+            for (int u = 0; u < kDig; ++u) {
+              if (t + u > kLev - 1) continue;
+              const int L = t + u;
+              const uint32_t acc = (!fresh || kk > 0 || seen[L]) ? 1u : 0u;
+              seen[L] = true;
+              const uint64_t b = sdesc(bbase + static_cast<uint32_t>(u * kBSlice)) +
+                                 static_cast<uint64_t>((kk * 32) >> 4);
+              mma_bf16_tmem_a(tmem + kAccCol + static_cast<uint32_t>(32 * L),
+                              tmem + kACol + static_cast<uint32_t>(32 * t + 8 * kk), b, idesc,
+                              acc);
+            }
+          }
+        }
+        mma_commit(&sh.afree);
+        if ((kc % 2) == 1 || kc == nkc - 1) mma_commit(&sh.accfull);
+      }
+      mma_commit(&sh.done);
+    }
+  } else {
+    // ------------------------------------------------ split, readout, epilogue
+    constexpr int kHalf = kUN / 2;
+    const int m = (warp & 3) * 32 + lane;       // row within the tile (lane)
+    const int hcol = warp >> 2;                  // Q columns 32 hcol .. + 31 of a chunk
+    const uint32_t tlane = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16);
+    int64_t alo[kHalf], ahi[kHalf];
+#pragma unroll
+    for (int c = 0; c < kHalf; ++c) { alo[c] = 0; ahi[c] = 0; }
+    // per output column: alpha 2^(g_c - 68) (0 for a zero column of W')
+    double ascale[kHalf];
+#pragma unroll
+    for (int cc = 0; cc < kHalf; ++cc) {
+      const int c = hcol * kHalf + cc;
+      ascale[cc] = sh.g[c] > -2000 ? alpha * ldexp(1.0, sh.g[c] - 68) : 0.0;
+    }
+    for (int q = 0; q < nstages; ++q) {
+      const int kc = q % nkc;
+      const int rtl = q / nkc;
+      bool bad = failed();
+      if (!bad) {
+        const bool ok = mbar_wait(&sh.qfull, static_cast<uint32_t>(q & 1)) &&
+                        (q == 0 || mbar_wait(&sh.afree, static_cast<uint32_t>((q - 1) & 1)));
+        if (!ok) {
+          sh.fail = 1;
+          bad = true;
+        }
+      }
+      if (__any_sync(0xffffffffu, bad)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // row m's 32 values of this warp's half chunk: Q column 32 hcol + c of
+      // the chunk at byte (32 hcol + c) * 1024 + 8 m; two columns per
+      // tensor-memory word, the lower column in the low half
+#pragma unroll 1
+      for (int hb8 = 0; hb8 < 2; ++hb8) {
+        uint32_t words[kDig][8];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+          const int ca = 32 * hcol + 16 * hb8 + 2 * w;
+          const double va = *reinterpret_cast<const double*>(stQ + ca * 1024 + m * 8);
+          const double vb = *reinterpret_cast<const double*>(stQ + (ca + 1) * 1024 + m * 8);
+          uint32_t h0[kDig], h1[kDig];
+          digit_bits(scaled62(va, sh.eq[kc * kUK + ca]), h0);
+          digit_bits(scaled62(vb, sh.eq[kc * kUK + ca + 1]), h1);
+#pragma unroll
+          for (int t = 0; t < kDig; ++t) words[t][w] = pack2(h0[t], h1[t]);
+        }
+#pragma unroll
+        for (int t = 0; t < kDig; ++t)
+          tmem_st8(tlane + kACol + static_cast<uint32_t>(32 * t + 16 * hcol + 8 * hb8), words[t]);
+      }
+      mbar_arrive(&sh.qfree);
+      tmem_st_wait();
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&sh.afull);
+      if ((kc % 2) == 1 || kc == nkc - 1) {
+        const int grp = rtl * gpt + kc / 2;
+        if (!mbar_wait(&sh.accfull, static_cast<uint32_t>(grp & 1))) sh.fail = 1;
+        if (__any_sync(0xffffffffu, failed())) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t tl = tlane + static_cast<uint32_t>(hcol * kHalf);
+#pragma unroll
+        for (int L = 0; L < kLev; ++L) {
+          uint32_t v[kHalf];
+          tmem_ld16(tl + kAccCol + static_cast<uint32_t>(32 * L), v);
+#pragma unroll
+          for (int cc = 0; cc < kHalf; ++cc) {
+            const int64_t sv = static_cast<int64_t>(__float2int_rz(__uint_as_float(v[cc])));
+            if (L < 4) ahi[cc] += sv << (8 * (3 - L));
+            else alo[cc] += sv << (8 * (7 - L));
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(&sh.accfree);
+        if (kc == nkc - 1) {
+          // epilogue of the row tile: X = beta X + alpha V' 2^(g_c - 68);
+          // X's values are loaded together first (one latency, not 16)
+          const int64_t r = (blockIdx.y + static_cast<int64_t>(rtl) * G) * kUM + m;
+          const int c0 = n0 + hcol * kHalf;
+          double* xr = X + r + static_cast<int64_t>(c0) * ldx;
+          double xv[kHalf];
+#pragma unroll
+          for (int cc = 0; cc < kHalf; ++cc)
+            xv[cc] = (beta != 0.0 && r < n && c0 + cc < s) ? xr[static_cast<int64_t>(cc) * ldx] : 0.0;
+#pragma unroll
+          for (int cc = 0; cc < kHalf; ++cc) {
+            const int64_t carry = alo[cc] >> 32;
+            const double v = static_cast<double>(ahi[cc] + carry) * 4294967296.0 +
+                             static_cast<double>(static_cast<uint32_t>(alo[cc]));
+            if (r < n && c0 + cc < s)
+              xr[static_cast<int64_t>(cc) * ldx] =
+                  beta == 0.0 ? v * ascale[cc] : fma(beta, xv[cc], v * ascale[cc]);
+            alo[cc] = 0;
+            ahi[cc] = 0;
+          }
+        }
+      }
+    }
+  }
+  if (warp < 4 && !mbar_wait(&sh.done, 0, 2 * kWaitNs)) sh.fail = 1;
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (sh.fail && tid == 0) atomicExch(err, 1);
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kOTmemCols)
+                 : "memory");
+  }
+}
+
 // e[c] = the exponent of column c's largest magnitude (|x| < 2^e): CTA
 // (c, z) takes rows [z rows, (z+1) rows) and merges its exponent with
 // atomicMax into e[c], which starts at a large negative value (all-zero
@@ -512,6 +799,21 @@ bool make_map64(CUtensorMap* map, const double* ptr, int64_t rows, int64_t cols,
          CUDA_SUCCESS;
 }
 
+// FP64 column-major matrix, boxes of 128 rows x 64 columns, no swizzle
+bool make_map64_rows(CUtensorMap* map, const double* ptr, int64_t rows, int64_t cols,
+                     int64_t ld) {
+  auto fn = oz_encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(rows), static_cast<cuuint64_t>(cols)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * sizeof(double)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(kUM), static_cast<cuuint32_t>(kUK)};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(ptr), dims, strides,
+            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 int* oz_err_flag() {
   static int* ptr[64] = {};
   static std::mutex mu;
@@ -572,6 +874,53 @@ int64_t oz_dot_part_size(int64_t n, int i, int s) {
 }
 
 int64_t oz_exp_ints(int i, int s) { return static_cast<int64_t>(i) + s; }
+
+bool oz_update_supported(int64_t n, const double* Q, int64_t ldq, int i, const double* X,
+                         int64_t ldx, int s) {
+  (void)X;
+  (void)ldx;
+  if (n < 4 * kUM || i < 1 || i > kUMaxK || s < 1) return false;
+  if ((reinterpret_cast<uintptr_t>(Q) & 15) || ((ldq * 8) & 15)) return false;
+  if (n > (int64_t(1) << 31) - 1) return false;
+  return oz_encode_fn() != nullptr;
+}
+
+// Whether the tensor-core update is expected to beat the FP64-pipe kernel.
+// One SM takes ceil(row tiles / row groups) tiles of 128 rows x 32 columns,
+// each about kTileUs plus kChunkUs per 64 columns of Q; the FP64 pipe
+// sustains about 1.05 TFLOP/s (2 n i s flops, half that for the triangle).
+bool oz_update_pays(int64_t n, int i, int s, bool upper) {
+  constexpr double kTileUs = 6.5, kChunkUs = 9.5;
+  const int64_t ct = (s + kUN - 1) / kUN;
+  const int64_t ntiles = (n + kUM - 1) / kUM;
+  int64_t G = static_cast<int64_t>(device_sm_count()) / ct;
+  if (G < 1) G = 1;
+  if (G > ntiles) G = ntiles;
+  const double per_sm = static_cast<double>((ntiles + G - 1) / G) *
+                        ((ct + device_sm_count() - 1) / device_sm_count());
+  const double t_oz = per_sm * (kTileUs + kChunkUs * ((i + kUK - 1) / kUK)) * 1e-6;
+  const double t_fp64 = (upper ? 1.0 : 2.0) * static_cast<double>(n) * i * s / 1.05e12;
+  return t_oz < 0.8 * t_fp64;
+}
+
+void oz_update(int64_t n, const double* Q, int64_t ldq, int i, const double* W, int ldw,
+               double* X, int64_t ldx, int s, double alpha, double beta, bool upper, int* exps,
+               cudaStream_t st) {
+  int* err = oz_err_flag();
+  col_exponents(n, Q, ldq, i, exps, st);
+  CUtensorMap mq;
+  SG_REQUIRE(make_map64_rows(&mq, Q, n, i, ldq), SG_ECUDA, "cuTensorMapEncodeTiled failed");
+  ensure_dynamic_smem(reinterpret_cast<const void*>(oz_update_kernel), kUSmem);
+  const int ct = (s + kUN - 1) / kUN;
+  const int64_t ntiles = (n + kUM - 1) / kUM;
+  int64_t G = static_cast<int64_t>(device_sm_count()) / ct;
+  if (G < 1) G = 1;
+  if (G > ntiles) G = ntiles;
+  dim3 grid(static_cast<unsigned>(ct), static_cast<unsigned>(G));
+  oz_update_kernel<<<grid, kOThreads, kUSmem, st>>>(mq, n, i, s, W, ldw, X, ldx, alpha, beta,
+                                                      upper ? 1 : 0, exps, err);
+  SG_LAUNCH_CHECK();
+}
 
 void oz_check_error(cudaStream_t st) {
   int* f = oz_err_flag();

@@ -580,6 +580,18 @@ sg_status sg_arnoldi(sg_handle* h, const double* q, int32_t k, int32_t precision
   });
 }
 
+namespace {
+void ensure_part(sg_handle* h, int64_t need, cudaStream_t st) {
+  if (need <= h->part_cap) return;
+  SG_CUDA(cudaStreamSynchronize(st));
+  if (h->part) cudaFree(h->part);
+  h->part = nullptr;
+  h->part_cap = 0;
+  SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&h->part), sizeof(double) * need));
+  h->part_cap = need;
+}
+}  // namespace
+
 sg_status sg_block_dot(sg_handle* h, int64_t n, const double* Q, int64_t ldq,
                        int32_t i, const double* X, int64_t ldx, int32_t s,
                        double* W, int32_t ldw, int32_t sym, void* stream) {
@@ -618,22 +630,14 @@ sg_status sg_block_update(sg_handle* h, int64_t n, const double* Q,
     SG_REQUIRE((Q && W) || i == 0, SG_EINVAL, "null Q/W");
     SG_REQUIRE(!upper || i == s, SG_EINVAL, "upper needs i == s");
     SG_CUDA(cudaSetDevice(h->device));
-    sg::block_update(n, Q, ldq, i, W, ldw, X, ldx, s, alpha, beta, upper != 0,
-                     pick(h, stream));
+    cudaStream_t st = pick(h, stream);
+    ensure_part(h, sg::block_update_scratch(i), st);
+    sg::block_update(n, Q, ldq, i, W, ldw, X, ldx, s, alpha, beta, upper != 0, h->part,
+                     h->part_cap, st);
+    sg::oz_check_error(st);  // synchronises: reports a tensor-core timeout
   });
 }
 
-namespace {
-void ensure_part(sg_handle* h, int64_t need, cudaStream_t st) {
-  if (need <= h->part_cap) return;
-  SG_CUDA(cudaStreamSynchronize(st));
-  if (h->part) cudaFree(h->part);
-  h->part = nullptr;
-  h->part_cap = 0;
-  SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&h->part), sizeof(double) * need));
-  h->part_cap = need;
-}
-}  // namespace
 
 sg_status sg_block_dot_f32(sg_handle* h, int64_t n, const float* Q,
                            int64_t ldq, int32_t i, const float* X,

@@ -152,9 +152,13 @@ void block_dot_capped(int64_t n, const double* Q, int64_t ldq, int i,
                       double* part, int64_t part_cap, cudaStream_t st);
 // X = beta X + alpha Q W (W on the device, i x s, upper-triangular if
 // `upper`, i == s)
+// (on the tensor cores when it pays; scratch: >= block_update_scratch(i)
+// doubles for Q's column exponents, may be null to force the FP64 pipe)
 void block_update(int64_t n, const double* Q, int64_t ldq, int i,
                   const double* W, int ldw, double* X, int64_t ldx, int s,
-                  double alpha, double beta, bool upper, cudaStream_t st);
+                  double alpha, double beta, bool upper, double* scratch,
+                  int64_t scratch_doubles, cudaStream_t st);
+int64_t block_update_scratch(int i);
 // FP32: runs on the tensor cores when supported (scratch: >= the
 // tc_update_scratch floats, may be null to force the FFMA kernels)
 void block_update32(int64_t n, const float* Q, int64_t ldq, int i,
@@ -182,6 +186,14 @@ bool oz_dot_supported(int64_t n, const double* Q, int64_t ldq, int i, const doub
 int64_t oz_dot_part_size(int64_t n, int i, int s);
 int64_t oz_exp_ints(int i, int s);
 bool oz_dot_pays(int64_t n, int i, int s, bool sym);
+// Tensor-core FP64 block update X = beta X + alpha Q W (W on the device, i x s,
+// upper-triangular if `upper`), from the same digit slices; exps: i ints.
+bool oz_update_supported(int64_t n, const double* Q, int64_t ldq, int i, const double* X,
+                         int64_t ldx, int s);
+bool oz_update_pays(int64_t n, int i, int s, bool upper);
+void oz_update(int64_t n, const double* Q, int64_t ldq, int i, const double* W, int ldw,
+               double* X, int64_t ldx, int s, double alpha, double beta, bool upper, int* exps,
+               cudaStream_t st);
 void oz_dot(int64_t n, const double* Q, int64_t ldq, int i, const double* X, int64_t ldx,
             int s, int* exps, double* part, int64_t part_cap, int* nsplit, cudaStream_t st);
 void oz_check_error(cudaStream_t st);

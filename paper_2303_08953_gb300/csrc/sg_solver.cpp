@@ -166,10 +166,12 @@ template <> struct Basis<double> {
                    int64_t cap, cudaStream_t st) {
     block_dot(n, Q, ldq, i, X, ldx, s, W, ldw, sym, part, cap, st);
   }
-  static void bupd(sg_handle*, int64_t n, const double* Q, int64_t ldq, int i,
+  static void bupd(sg_handle* h, int64_t n, const double* Q, int64_t ldq, int i,
                    const double* W, int ldw, double* X, int64_t ldx, int s, double al,
                    double be, bool up, cudaStream_t st) {
-    block_update(n, Q, ldq, i, W, ldw, X, ldx, s, al, be, up, st);
+    // Q's column exponents of the tensor-core form go to the (then idle)
+    // split-partials buffer
+    block_update(n, Q, ldq, i, W, ldw, X, ldx, s, al, be, up, h->part, h->part_cap, st);
   }
   static void gemv(int64_t n, int k, const double* Q, int64_t ldq, const double* y,
                    double* x, cudaStream_t st) {

@@ -223,6 +223,33 @@ def test_block_update_matches_definition(solver, n, i, s, upper):
     assert np.all(np.abs(got - ref) <= 1e-14 * scale + 1e-300)
 
 
+@pytest.mark.parametrize("n,i,s,upper", [(70001, 107, 106, False), (9000, 241, 40, False),
+                                         (20000, 120, 120, True), (4133, 64, 33, False)])
+def test_block_update_fp64_tensor_cores_exact_on_integers(solver, n, i, s, upper):
+    """The FP64 block update on the tensor cores (Q's digits relative to its
+    column exponents, W' = W 2^(e_k) cut relative to its own column
+    exponents) is exact: integer Q and W with per-column scales 2^-30 ..
+    2^30 (Q) and 2^-20 .. 2^20 (W rows, so that every product of an output
+    has one scale) give X = X - Q W equal to numpy's exact result, bit for
+    bit; the upper form skips W's lower triangle (NaN there)."""
+    rng = np.random.default_rng(3 * n + i + s)
+    Q = rng.integers(-2 ** 12, 2 ** 12, size=(i, n)).astype(np.float64)
+    Wm = rng.integers(-2 ** 12, 2 ** 12, size=(i, s)).astype(np.float64)
+    X = rng.integers(-2 ** 20, 2 ** 20, size=(s, n)).astype(np.float64)
+    sc = rng.integers(-30, 31, size=i)
+    Q *= np.exp2(sc)[:, None]
+    Wm *= np.exp2(-sc)[:, None]            # Q[r,k] W[k,c]: one scale per output
+    Wm *= np.exp2(rng.integers(-20, 21, size=s))[None, :]
+    if upper:
+        Wm = np.triu(Wm) + np.tril(np.full((i, s), np.nan), -1)
+    Wz = np.nan_to_num(Wm, nan=0.0)
+    Xd = dev(X)
+    solver.block_update(dev(Q), dev(np.ascontiguousarray(Wm.T)), Xd, alpha=-1.0, beta=1.0,
+                        upper=upper, n=n)
+    ref = X - (Q.T @ Wz).T
+    assert np.array_equal(host(Xd), ref)
+
+
 @pytest.mark.parametrize("n", [97, 4133, 70001])
 @pytest.mark.parametrize("i,s", [(1, 120), (5, 7), (9, 6), (33, 65), (121, 40)])
 def test_block_dot_f32_matches_definition(solver, n, i, s):
