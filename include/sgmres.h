@@ -350,6 +350,21 @@ sg_status sg_probe_bounded_waits(int32_t device, double limit_ms,
  * diagnostic for benchmarks: every launch goes through one counter). */
 int64_t sg_kernel_launches(void);
 
+/* Tensor-core policy of the FP64 block products (not in the paper; the
+ * paper's BCGS kernels run on CPUs).  SG_TC_AUTO (0, the default): the
+ * tensor-core form of sg_block_dot / sg_block_update (and of the solver's
+ * own block products) runs where a per-shape cost model expects it to beat
+ * the FP64 pipe; SG_TC_NEVER (1): always the FP64-pipe kernels (also what
+ * the environment variable SGMRES_NO_TC=1 selects at the first call);
+ * SG_TC_ALWAYS (2): the tensor-core form wherever its layout requirements
+ * hold.  Both forms give the same products to FP64 rounding, so this only
+ * chooses speed.  Process-wide; returns the previous policy, or -1 for an
+ * unknown value (nothing changed). */
+#define SG_TC_AUTO 0
+#define SG_TC_NEVER 1
+#define SG_TC_ALWAYS 2
+int32_t sg_set_tc_policy(int32_t policy);
+
 /* ------------------------------------------- host small dense algebra
  * Pure host functions (no handle, no GPU) used between kernels; exposed
  * so they can be checked on their own. */

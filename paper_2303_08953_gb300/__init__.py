@@ -40,7 +40,7 @@ EXPORTED = (
     "sg_probe_bounded_waits", "sg_arnoldi", "sg_analyze_rows", "sg_gather",
     "sg_host_upper_inverse", "sg_host_basis", "sg_host_combine_r",
     "sg_host_assemble_hessenberg", "sg_host_givens_column",
-    "sg_host_givens_solve", "sg_host_halo_plan",
+    "sg_host_givens_solve", "sg_host_halo_plan", "sg_set_tc_policy",
 )
 
 
@@ -138,6 +138,7 @@ def _load():
         "sg_host_scaling_coefficients": (None, [i32, _D, _D, _D]),
         "sg_host_estimate_step": (i32, [i32, _D, _D, f64, f64, i32, i32, _D]),
         "sg_kernel_launches": (i64, []),
+        "sg_set_tc_policy": (i32, [i32]),
         "sg_analyze_rows": (i32, [vp, C.POINTER(sg_csr), i32]),
         "sg_gather": (i32, [vp, i64, vp, vp, vp]),
         "sg_host_upper_inverse": (i32, [_D, i32, i32, _D, i32]),
@@ -173,6 +174,19 @@ def _ip(a: np.ndarray):
 def kernel_launches() -> int:
     """Kernels launched by the library in this process so far."""
     return int(lib.sg_kernel_launches())
+
+
+TC_POLICIES = {"auto": 0, "never": 1, "always": 2}
+
+
+def set_tc_policy(policy: str) -> str:
+    """Tensor-core policy of the FP64 block products, process-wide: "auto"
+    (cost model), "never" (FP64 pipe) or "always" (tensor cores wherever the
+    layout allows).  Returns the previous policy."""
+    old = int(lib.sg_set_tc_policy(TC_POLICIES[policy]))
+    if old < 0:
+        raise ValueError(policy)
+    return {v: k for k, v in TC_POLICIES.items()}[old]
 
 
 # ------------------------------------------------------- host algebra

@@ -19,6 +19,7 @@
 // a two-sum, so the Gram of FP32 vectors is accurate to about eps_32^2
 // relative to the sum of |products| -- the accuracy the partial Cholesky
 // bound of the FP32 basis relies on.
+#include <atomic>
 #include <cstdlib>
 
 #include "sg_internal.h"
@@ -358,14 +359,22 @@ void launch_dot(const DotPlan& p, cudaStream_t st, int64_t n, int i, int s,
   SG_LAUNCH_CHECK();
 }
 
-bool tc_disabled() {
-  static int v = -1;
+// -1: not yet read from the environment; else SG_TC_AUTO / NEVER / ALWAYS
+std::atomic<int> g_tc_policy{-1};
+
+int policy_now() {
+  int v = g_tc_policy.load();
   if (v < 0) {
     const char* e = std::getenv("SGMRES_NO_TC");
-    v = (e && e[0] == '1') ? 1 : 0;
+    const int env = (e && e[0] == '1') ? SG_TC_NEVER : SG_TC_AUTO;
+    g_tc_policy.compare_exchange_strong(v, env);
+    v = g_tc_policy.load();
   }
-  return v == 1;
+  return v;
 }
+
+bool tc_disabled() { return policy_now() == SG_TC_NEVER; }
+bool tc_forced() { return policy_now() == SG_TC_ALWAYS; }
 
 template <typename T>
 void block_dot_impl(int64_t n, const T* Q, int64_t ldq, int i, const T* X,
@@ -381,7 +390,7 @@ void block_dot_impl(int64_t n, const T* Q, int64_t ldq, int i, const T* X,
   if (sizeof(T) == 8 && !tc_disabled() &&
       oz_dot_supported(n, reinterpret_cast<const double*>(Q), ldq, i,
                        reinterpret_cast<const double*>(X), ldx, s) &&
-      oz_dot_pays(n, i, s, sym && i == s)) {
+      (tc_forced() || oz_dot_pays(n, i, s, sym && i == s))) {
     // FP64 products on the tensor cores, exact digit slices; the column
     // exponents sit after the split partials.  A Gram comes out exactly
     // symmetric (both triangles are the same exact sums).
@@ -602,6 +611,15 @@ void block_update_impl(int64_t n, const T* Q, int64_t ldq, int i,
 
 }  // namespace
 
+int tc_policy() { return policy_now(); }
+
+int set_tc_policy(int policy) {
+  if (policy != SG_TC_AUTO && policy != SG_TC_NEVER && policy != SG_TC_ALWAYS) return -1;
+  const int old = policy_now();
+  g_tc_policy.store(policy);
+  return old;
+}
+
 void block_dot_capped(int64_t n, const double* Q, int64_t ldq, int i,
                       const double* X, int64_t ldx, int s, double* W, int ldw,
                       double* part, int64_t part_cap, cudaStream_t st) {
@@ -668,7 +686,7 @@ void block_update(int64_t n, const double* Q, int64_t ldq, int i,
                   int64_t scratch_doubles, cudaStream_t st) {
   if (n > 0 && i > 0 && s > 0 && scratch && scratch_doubles >= block_update_scratch(i) &&
       !tc_disabled() && oz_update_supported(n, Q, ldq, i, X, ldx, s) &&
-      oz_update_pays(n, i, s, upper)) {
+      (tc_forced() || oz_update_pays(n, i, s, upper))) {
     // FP64 products on the tensor cores, exact digit slices
     oz_update(n, Q, ldq, i, W, ldw, X, ldx, s, alpha, beta, upper,
               reinterpret_cast<int*>(scratch), st);

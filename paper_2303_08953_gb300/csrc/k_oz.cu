@@ -135,6 +135,18 @@ __device__ __forceinline__ void digit_bits(int64_t m, uint32_t* hb) {
   }
 }
 
+// The integer value of an FP32 level sum (an exact integer, |v| < 2^24)
+// on the FP32 pipe: adding 1.5 2^25 (whose unit in the last place is 4)
+// rounds v to a multiple of 4 and leaves v / 4 in the low bits of the sum's
+// bit pattern; the remainder (-2 .. 2, exact) converts through 1.5 2^23 the
+// same way.  Profiles showed the F2I conversion occupying the FP64 pipe.
+__device__ __forceinline__ int32_t level_int(uint32_t vb) {
+  const float v = __uint_as_float(vb);
+  const float t = __fadd_rn(v, 50331648.0f);
+  const float r = __fsub_rn(v, __fsub_rn(t, 50331648.0f));
+  return 4 * (__float_as_int(t) - 0x4C400000) + (__float_as_int(__fadd_rn(r, 12582912.0f)) - 0x4B400000);
+}
+
 // two BF16 patterns (from digit_bits' FP32 words) in one 32-bit word, the
 // first in the low half
 __device__ __forceinline__ uint32_t pack2(uint32_t f_lo, uint32_t f_hi) {
@@ -240,11 +252,9 @@ oz_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
       tmem_ld16(tl + kAccCol + static_cast<uint32_t>(32 * L), v);
 #pragma unroll
       for (int cc = 0; cc < kHalf; ++cc) {
-        // an exact integer in FP32; the 32-bit conversion stays off the
-        // FP64 pipe
-        const int64_t sv = static_cast<int64_t>(__float2int_rz(__uint_as_float(v[cc])));
-        if (L < 4) ahi[cc] += sv << (8 * (3 - L));
-        else alo[cc] += sv << (8 * (7 - L));
+        const int64_t sv = level_int(v[cc]);
+        if (L < 4) ahi[cc] += sv * (int64_t(1) << (8 * (3 - L)));
+        else alo[cc] += sv * (int64_t(1) << (8 * (7 - L)));
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -445,41 +455,176 @@ oz_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
 // Output (r, c) sums Q[r,k] W[k,c] over k; with Q's digits relative to its
 // column exponents e_k (as in the dot) and W' = W 2^(e_k) cut into digits
 // relative to W' column c's exponent g_c, every product of the sum carries
-// the one weight 2^(g_c - 124), so the level sums are exact as above.
-// Tile: 128 rows (MMA M, tensor-memory lanes) x 32 columns of X (MMA N),
-// K = 64 columns of Q per chunk; one CTA per SM walks the row tiles of one
-// column tile.  W' is cut once per CTA into shared-memory B slices (one
-// 32 KB group of eight slices per K chunk, i <= 256); Q's rows arrive by
-// TMA as one unswizzled 128-row x 64-column box (a row's values are 1 KB
-// apart: a warp reads 32 consecutive rows conflict-free) and warps 0-7 cut
-// them into tensor-memory A slices; level sums are read every two chunks
-// (128 columns of Q) and the epilogue writes beta X + alpha V 2^(g_c - 68).
+// the one weight 2^(g_c - 124), so the level sums are exact as above.  The
+// digits are FP16 numbers here (integers of at most 8 bits are exact in
+// either 16-bit type; FP16's wider mantissa lets one packed subtraction
+// turn two digit bytes into two FP16 digits).
+// Tile: 128 rows (MMA M, tensor-memory lanes) x 32 columns of X (MMA N);
+// one CTA per SM walks the row tiles of one column tile in stages of 32
+// columns of Q (two MMA K steps), software-pipelined:
+//   * warp 8 (one lane) loads each stage's Q box (128 rows x 32 columns,
+//     unswizzled: a row's values are 1 KB apart, so a warp reads 32
+//     consecutive rows conflict-free) into a two-deep ring, and each
+//     tile's X box for the epilogue;
+//   * warps 0-7 cut stage q into one of two tensor-memory A buffers while
+//     warp 9 (one lane) runs stage q-1's 72 digit-pair MMAs from the other;
+//     W' is cut once per CTA into shared-memory B slices (one 32 KB group
+//     of eight slices per 64 columns of Q, i <= 256);
+//   * level sums are read every four stages (128 columns of Q) and at the
+//     end of a tile, one stage late so that the split of the next stage
+//     overlaps the last MMAs; the epilogue writes beta X + alpha V 2^(g_c-68)
+//     from the prefetched X box.
+// K steps that lie wholly beyond column i are not issued.
 constexpr int kUM = 128;
 constexpr int kUN = 32;
-constexpr int kUK = 64;
+constexpr int kUS = 32;                                 // columns of Q per stage
 constexpr int kUMaxK = 256;
-constexpr int kUQBytes = kUM * kUK * 8;                 // 64 KB
-constexpr int kUBChunk = kDig * kBSlice;                // 32 KB per K chunk
-constexpr int kUSmem = kUQBytes + (kUMaxK / kUK) * kUBChunk + 1024;
+constexpr int kUBox = kUM * kUS * 8;                    // 32 KB: a Q stage or the X tile
+constexpr int kUBChunk = kDig * kBSlice;                // 32 KB per 64 columns of Q
+constexpr uint32_t kUACol = 256;                        // A buffer b: 256 + 128 b
 
-struct __align__(8) OzUShared {
-  uint64_t qfull, qfree, afull, afree, accfull, accfree, done;
-  uint32_t tmem_base;
-  int fail;
+// per-column tables after the W' slices: Q's column exponents e_k, W'
+// column exponents g_c
+struct OzUTables {
   int eq[kUMaxK];
   int g[kUN];
 };
 
+struct __align__(8) OzUShared {
+  uint64_t qfull[2], qfree[2], afull[2], afree[2];
+  uint64_t accfull, accfree, xfull, xfree, done;
+  uint32_t tmem_base;
+  int fail;
+};
+
+// dynamic shared memory: Q ring, X box, W' slices, tables, barriers (all of
+// it dynamic, so the 1 KB alignment slack fits under the 227 KB limit)
+int oz_update_smem(int i) {
+  return 3 * kUBox + ((i + 63) / 64) * kUBChunk + static_cast<int>(sizeof(OzUTables)) +
+         static_cast<int>(sizeof(OzUShared)) + 1024;
+}
+
+__device__ __forceinline__ uint32_t f16x2_sub(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
+// Balanced base-256 digits of two numbers as FP16 pairs: w[t] holds digit
+// t (most significant first) of ma in its low half and of mb in its high
+// half.  Adding 0x80 to every byte of m makes each byte of the sum the
+// digit plus 128 (the carries do the balancing; for |m| < 2^62 the top
+// byte stays in [64, 192]).  The FP16 number with bit pattern 0x6600 + b
+// is 1536 + b exactly (the unit in the last place is 1 on [1024, 2048)),
+// so one packed subtraction of 1664 leaves the digits, exactly.
+__device__ __forceinline__ void digits_f16x2(int64_t ma, int64_t mb, uint32_t* w) {
+  const uint64_t sa = static_cast<uint64_t>(ma) + 0x8080808080808080ull;
+  const uint64_t sb = static_cast<uint64_t>(mb) + 0x8080808080808080ull;
+  const uint32_t ahi = static_cast<uint32_t>(sa >> 32), alo = static_cast<uint32_t>(sa);
+  const uint32_t bhi = static_cast<uint32_t>(sb >> 32), blo = static_cast<uint32_t>(sb);
+  constexpr uint32_t kHi = 0x66666666u;
+  constexpr uint32_t kOff = 0x66806680u;              // 1664 in both halves
+  // byte pairs (a_j, b_j) of digits 0-1, 2-3, 4-5, 6-7
+  const uint32_t p[4] = {__byte_perm(ahi, bhi, 0x6273), __byte_perm(ahi, bhi, 0x4051),
+                         __byte_perm(alo, blo, 0x6273), __byte_perm(alo, blo, 0x4051)};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    w[2 * k] = f16x2_sub(__byte_perm(p[k], kHi, 0x4140), kOff);
+    w[2 * k + 1] = f16x2_sub(__byte_perm(p[k], kHi, 0x4342), kOff);
+  }
+}
+
+// This thread's lane, 4 consecutive 32-bit columns from taddr.
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr),
+               "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3])
+               : "memory");
+}
+
+// This thread's lane, 2 consecutive 32-bit columns from taddr.
+__device__ __forceinline__ void tmem_st2(uint32_t taddr, const uint32_t* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1,%2};" ::"r"(taddr), "r"(v[0]),
+               "r"(v[1])
+               : "memory");
+}
+
+// This thread's lane, 8 consecutive 32-bit columns from taddr.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Instruction descriptor: kind::f16 with FP16 A and B, FP32 accumulator,
+// K-major A and B.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+// the same on the FP64 pipe, for results outside the normal range (kept
+// out of line so that the common path does not evaluate it)
+__device__ __noinline__ double int96_to_double_slow(int64_t hi, uint32_t lo, int e2) {
+  return ldexp(ldexp(static_cast<double>(hi), 32) + static_cast<double>(lo), e2);
+}
+
+// (hi 2^32 + lo) 2^e2 rounded to the nearest double (ties to even), in
+// integer arithmetic: the 96-bit value is normalised with a count of its
+// leading zeros, its top 53 bits are rounded with the guard bit and a
+// sticky bit, and the exponent field is added on.  Falls back to the FP64
+// pipe when the result would leave the normal range.
+__device__ __forceinline__ double int96_to_double(int64_t hi, uint32_t lo, int e2) {
+  const bool neg = hi < 0;
+  uint64_t h = static_cast<uint64_t>(hi);
+  uint32_t l = lo;
+  if (neg) {                                   // magnitude: two's complement of 96 bits
+    l = 0u - lo;
+    h = ~h + (lo == 0u ? 1u : 0u);
+  }
+  if ((h | l) == 0) return 0.0;
+  uint64_t t;
+  uint32_t low;
+  int z;
+  if (h != 0) {
+    z = __clzll(static_cast<long long>(h));    // 1 .. 63 (|hi| < 2^62)
+    if (z < 32) {
+      t = (h << z) | (static_cast<uint64_t>(l) >> (32 - z));
+      low = l << z;
+    } else {
+      t = (h << z) | (static_cast<uint64_t>(l) << (z - 32));
+      low = 0;
+    }
+  } else {
+    const int zl = __clz(static_cast<int>(l));
+    t = static_cast<uint64_t>(l) << (32 + zl);
+    low = 0;
+    z = 64 + zl;
+  }
+  // t holds the top 64 bits (MSB at bit 63) of the value times 2^(z - 32)
+  uint64_t mant = t >> 11;
+  const uint64_t up = ((t >> 10) & 1u) & (((t & 0x3FFu) | low | (mant & 1u)) != 0 ? 1u : 0u);
+  mant += up;
+  const int E = 1118 - z + e2;                 // exponent field of mant 2^(43 - z + e2)
+  if (E < 1 || E > 2045) return int96_to_double_slow(hi, lo, e2);
+  const uint64_t bits = (static_cast<uint64_t>(E - 1) << 52) + mant;
+  return __longlong_as_double(static_cast<long long>(bits | (neg ? (uint64_t(1) << 63) : 0)));
+}
+
+constexpr int kUWarps = 16;                    // split / readout / epilogue warps
+constexpr int kUThreads = (kUWarps + 2) * 32;  // + warp 16 TMA, warp 17 MMA
+constexpr int kUSplit = kUWarps * 32;
+
 // grid: (tiles of 32 X columns, row groups); row tiles g, g + G, ...
-__global__ void __launch_bounds__(kOThreads, 1)
-oz_update_kernel(const __grid_constant__ CUtensorMap mapQ, int64_t n, int i, int s,
-                 const double* __restrict__ W, int ldw, double* __restrict__ X, int64_t ldx,
-                 double alpha, double beta, int upper, const int* __restrict__ eq,
-                 int* __restrict__ err) {
+__global__ void __launch_bounds__(kUThreads, 1)
+oz_update_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUtensorMap mapX,
+                 int64_t n, int i, int s, const double* __restrict__ W, int ldw,
+                 double* __restrict__ X, int64_t ldx, double alpha, double beta, int upper,
+                 const int* __restrict__ eq, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char dsmem[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~static_cast<uintptr_t>(1023));
-  __shared__ OzUShared sh;
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int lane = tid & 31;
@@ -487,20 +632,33 @@ oz_update_kernel(const __grid_constant__ CUtensorMap mapQ, int64_t n, int i, int
   const int64_t ntiles = (n + kUM - 1) / kUM;
   const int G = gridDim.y;
   const int my_tiles = static_cast<int>((ntiles - blockIdx.y + G - 1) / G);
-  const int nkc = (i + kUK - 1) / kUK;
-  const int gpt = (nkc + 1) / 2;                 // level readouts per row tile
-  const uint32_t idesc = idesc_bf16(kUM, kUN);
-  unsigned char* stQ = base;
-  unsigned char* bsl = base + kUQBytes;
+  const int nsub = (i + kUS - 1) / kUS;          // stages per row tile
+  const int nkc = (i + 63) / 64;                 // groups of W' slices
+  const int gpt = (nsub + 3) / 4;                // level readouts per row tile
+  const bool loadx = beta != 0.0;
+  const uint32_t idesc = idesc_f16(kUM, kUN);
+  unsigned char* stX = base + 2 * kUBox;
+  unsigned char* bsl = base + 3 * kUBox;
+  OzUTables& tb = *reinterpret_cast<OzUTables*>(bsl + nkc * kUBChunk);
+  OzUShared& sh = *reinterpret_cast<OzUShared*>(bsl + nkc * kUBChunk + sizeof(OzUTables));
   auto failed = [&]() { return *reinterpret_cast<volatile int*>(&sh.fail) != 0; };
+  auto group_end = [&](int kq) { return (kq & 3) == 3 || kq == nsub - 1; };
+  // alpha = +-2^(ka - 1) folds into the exponent and the sign of the sums
+  int ka = 0;
+  const double fa = frexp(alpha, &ka);
+  const bool apow2 = fabs(fa) == 0.5;
 
   if (tid == 0) {
-    mbar_init(&sh.qfull, 1);
-    mbar_init(&sh.qfree, 256);
-    mbar_init(&sh.afull, 256);
-    mbar_init(&sh.afree, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sh.qfull[b], 1);
+      mbar_init(&sh.qfree[b], kUSplit);
+      mbar_init(&sh.afull[b], kUSplit);
+      mbar_init(&sh.afree[b], 1);
+    }
     mbar_init(&sh.accfull, 1);
-    mbar_init(&sh.accfree, 256);
+    mbar_init(&sh.accfree, kUSplit);
+    mbar_init(&sh.xfull, 1);
+    mbar_init(&sh.xfree, kUSplit);
     mbar_init(&sh.done, 1);
     sh.fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -513,42 +671,43 @@ oz_update_kernel(const __grid_constant__ CUtensorMap mapQ, int64_t n, int i, int
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   // W' = W 2^(e_k) (zero below the diagonal when `upper`) cut into digits
-  // relative to its column exponents g_c: B slices of every K chunk
-  if (warp < 8) {
-    for (int k = tid; k < kUMaxK; k += 256) sh.eq[k] = k < i ? eq[k] : -4000;
-    if (tid < kUN) sh.g[tid] = -2147483647;
+  // relative to its column exponents g_c: B slices of every 64 columns of Q
+  if (warp < kUWarps) {
+    for (int k = tid; k < kUMaxK; k += kUSplit) tb.eq[k] = k < i ? eq[k] : -4000;
+    if (tid < kUN) tb.g[tid] = -2147483647;
     uint4* z = reinterpret_cast<uint4*>(bsl);
-    for (int e = tid; e < nkc * kUBChunk / 16; e += 256) z[e] = make_uint4(0, 0, 0, 0);
+    for (int e = tid; e < nkc * kUBChunk / 16; e += kUSplit) z[e] = make_uint4(0, 0, 0, 0);
   }
   __syncthreads();
   auto wprime = [&](int k, int c) -> double {
     const int gc = n0 + c;
-    if (k >= i || gc >= s || (upper && k > gc) || sh.eq[k] < -2000) return 0.0;
-    return ldexp(W[k + static_cast<int64_t>(gc) * ldw], sh.eq[k]);
+    if (k >= i || gc >= s || (upper && k > gc) || tb.eq[k] < -2000) return 0.0;
+    return ldexp(W[k + static_cast<int64_t>(gc) * ldw], tb.eq[k]);
   };
-  if (warp < 8) {
+  if (warp < kUWarps) {
     const int c = lane;
     double mx = 0.0;
-    for (int k = warp; k < i; k += 8) mx = fmax(mx, fabs(wprime(k, c)));
+    for (int k = warp; k < i; k += kUWarps) mx = fmax(mx, fabs(wprime(k, c)));
     if (mx > 0.0) {
       int ee = 0;
       frexp(mx, &ee);
-      atomicMax(&sh.g[c], ee);
+      atomicMax(&tb.g[c], ee);
     }
   }
   __syncthreads();
-  if (warp < 8) {
+  if (warp < kUWarps) {
     const int c = lane;
-    const int gc = sh.g[c] > -2000 ? sh.g[c] : -4000;
-    for (int k = warp; k < i; k += 8) {
-      uint32_t hb[kDig];
-      digit_bits(scaled62(wprime(k, c), gc), hb);
-      const int kc = k / kUK, kk = k % kUK;
+    const int gc = tb.g[c] > -2000 ? tb.g[c] : -4000;
+    for (int k = warp; k < i; k += kUWarps) {
+      const int64_t mk = scaled62(wprime(k, c), gc);
+      uint32_t w8[kDig];
+      digits_f16x2(mk, mk, w8);
+      const int kc = k / 64, kk = k % 64;
 #pragma unroll
       for (int t = 0; t < kDig; ++t) {
         unsigned char* row = bsl + kc * kUBChunk + t * kBSlice + (c >> 3) * 1024 + (c & 7) * 128;
         *reinterpret_cast<uint16_t*>(row + (((kk >> 3) ^ (c & 7)) << 4) + (kk & 7) * 2) =
-            static_cast<uint16_t>(hb[t] >> 16);
+            static_cast<uint16_t>(w8[t] & 0xFFFFu);
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -557,43 +716,63 @@ oz_update_kernel(const __grid_constant__ CUtensorMap mapQ, int64_t n, int i, int
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = sh.tmem_base;
-  const int nstages = my_tiles * nkc;
+  const int nstages = my_tiles * nsub;
 
-  if (warp == 8) {
+  if (warp == kUWarps) {
     // ------------------------------------------------ TMA producer
     if (lane == 0) {
-      int issued = 0;
+      int nq0 = 0, nq1 = 0;
+      int nx = 0;
       for (int q = 0; q < nstages; ++q) {
         if (failed()) break;
-        if (q > 0 && !mbar_wait(&sh.qfree, static_cast<uint32_t>((q - 1) & 1))) {
+        const int b = q & 1;
+        if (q >= 2 && !mbar_wait(&sh.qfree[b], static_cast<uint32_t>(((q >> 1) - 1) & 1))) {
           sh.fail = 1;
           break;
         }
-        const int64_t rt = blockIdx.y + static_cast<int64_t>(q / nkc) * G;
-        mbar_expect_tx(&sh.qfull, static_cast<uint32_t>(kUQBytes));
-        tma_load_2d(stQ, &mapQ, &sh.qfull, static_cast<int>(rt * kUM), (q % nkc) * kUK);
-        issued = q + 1;
+        const int kq = q % nsub;
+        const int rtl = q / nsub;
+        const int rt = blockIdx.y + rtl * G;
+        mbar_expect_tx(&sh.qfull[b], static_cast<uint32_t>(kUBox));
+        tma_load_2d(base + b * kUBox, &mapQ, &sh.qfull[b], rt * kUM, kq * kUS);
+        if (b) ++nq1; else ++nq0;
+        if (loadx && kq == nsub - 1) {
+          if (rtl > 0 && !mbar_wait(&sh.xfree, static_cast<uint32_t>((rtl - 1) & 1))) {
+            sh.fail = 1;
+            break;
+          }
+          mbar_expect_tx(&sh.xfull, static_cast<uint32_t>(kUBox));
+          tma_load_2d(stX, &mapX, &sh.xfull, rt * kUM, n0);
+          ++nx;
+        }
       }
-      if (failed() && issued > 0)
-        mbar_wait(&sh.qfull, static_cast<uint32_t>((issued - 1) & 1));
+      if (failed()) {
+        // drain this CTA's copies in flight (at most one per buffer)
+        if (nq0 > 0) mbar_wait(&sh.qfull[0], static_cast<uint32_t>((nq0 - 1) & 1));
+        if (nq1 > 0) mbar_wait(&sh.qfull[1], static_cast<uint32_t>((nq1 - 1) & 1));
+        if (nx > 0) mbar_wait(&sh.xfull, static_cast<uint32_t>((nx - 1) & 1));
+      }
     }
-  } else if (warp == 9) {
+  } else if (warp == kUWarps + 1) {
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
+      int grp = 0;
       for (int q = 0; q < nstages; ++q) {
         if (failed()) break;
-        const int kc = q % nkc;
-        const int grp = (q / nkc) * gpt + kc / 2;        // readout group
-        const bool fresh = (kc % 2) == 0;
-        if (!mbar_wait(&sh.afull, static_cast<uint32_t>(q & 1)) ||
+        const int b = q & 1;
+        const int kq = q % nsub;
+        const bool fresh = (kq & 3) == 0;
+        if (!mbar_wait(&sh.afull[b], static_cast<uint32_t>((q >> 1) & 1)) ||
             (fresh && grp > 0 && !mbar_wait(&sh.accfree, static_cast<uint32_t>((grp - 1) & 1)))) {
           sh.fail = 1;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t bbase = smem_u32(bsl + kc * kUBChunk);
+        const uint32_t bbase = smem_u32(bsl + (kq >> 1) * kUBChunk);
+        const int ksteps = (i - kq * kUS) >= 17 ? 2 : 1;     // K steps holding columns < i
 #pragma unroll 1
-        for (int kk = 0; kk < kUK / 16; ++kk) {
+        for (int kk = 0; kk < ksteps; ++kk) {
+          const int kb = (kq & 1) * 2 + kk;                  // 16-column step of the 64
           bool seen[kLev] = {false, false, false, false, false, false, false, false};
 #pragma unroll
           for (int t = 0; t < kDig; ++t) {
@@ -603,117 +782,147 @@ oz_update_kernel(const __grid_constant__ CUtensorMap mapQ, int64_t n, int i, int
               const int L = t + u;
               const uint32_t acc = (!fresh || kk > 0 || seen[L]) ? 1u : 0u;
               seen[L] = true;
-              const uint64_t b = sdesc(bbase + static_cast<uint32_t>(u * kBSlice)) +
-                                 static_cast<uint64_t>((kk * 32) >> 4);
+              const uint64_t bd = sdesc(bbase + static_cast<uint32_t>(u * kBSlice)) +
+                                  static_cast<uint64_t>((kb * 32) >> 4);
               mma_bf16_tmem_a(tmem + kAccCol + static_cast<uint32_t>(32 * L),
-                              tmem + kACol + static_cast<uint32_t>(32 * t + 8 * kk), b, idesc,
-                              acc);
+                              tmem + kUACol + static_cast<uint32_t>(128 * b + 16 * t + 8 * kk), bd,
+                              idesc, acc);
             }
           }
         }
-        mma_commit(&sh.afree);
-        if ((kc % 2) == 1 || kc == nkc - 1) mma_commit(&sh.accfull);
+        mma_commit(&sh.afree[b]);
+        if (group_end(kq)) {
+          mma_commit(&sh.accfull);
+          ++grp;
+        }
       }
       mma_commit(&sh.done);
     }
   } else {
     // ------------------------------------------------ split, readout, epilogue
-    constexpr int kHalf = kUN / 2;
-    const int m = (warp & 3) * 32 + lane;       // row within the tile (lane)
-    const int hcol = warp >> 2;                  // Q columns 32 hcol .. + 31 of a chunk
+    // warp w: rows 32 (w % 4) .. + 31 (its tensor-memory lane quarter) and
+    // column group cg = w / 4: Q columns 8 cg .. 8 cg + 7 of each stage,
+    // output columns 8 cg .. 8 cg + 7 of the tile
+    constexpr int kCols = kUN / 4;
+    const int m = (warp & 3) * 32 + lane;
+    const int cg = warp >> 2;
     const uint32_t tlane = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16);
-    int64_t alo[kHalf], ahi[kHalf];
+    int64_t alo[kCols], ahi[kCols];
 #pragma unroll
-    for (int c = 0; c < kHalf; ++c) { alo[c] = 0; ahi[c] = 0; }
-    // per output column: alpha 2^(g_c - 68) (0 for a zero column of W')
-    double ascale[kHalf];
+    for (int c = 0; c < kCols; ++c) { alo[c] = 0; ahi[c] = 0; }
+    // level sums of the group ending at stage pq; the epilogue after a
+    // tile's last group
+    auto readout = [&](int pq) -> bool {
+      const int kq = pq % nsub;
+      const int rtl = pq / nsub;
+      const int grp = rtl * gpt + kq / 4;
+      if (!mbar_wait(&sh.accfull, static_cast<uint32_t>(grp & 1))) sh.fail = 1;
+      if (__any_sync(0xffffffffu, failed())) return false;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t tl = tlane + static_cast<uint32_t>(cg * kCols);
 #pragma unroll
-    for (int cc = 0; cc < kHalf; ++cc) {
-      const int c = hcol * kHalf + cc;
-      ascale[cc] = sh.g[c] > -2000 ? alpha * ldexp(1.0, sh.g[c] - 68) : 0.0;
-    }
+      for (int L = 0; L < kLev; ++L) {
+        uint32_t v[kCols];
+        tmem_ld8(tl + kAccCol + static_cast<uint32_t>(32 * L), v);
+#pragma unroll
+        for (int cc = 0; cc < kCols; ++cc) {
+          const int64_t sv = level_int(v[cc]);
+          if (L < 4) ahi[cc] += sv * (int64_t(1) << (8 * (3 - L)));
+          else alo[cc] += sv * (int64_t(1) << (8 * (7 - L)));
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&sh.accfree);
+      if (kq == nsub - 1) {
+        // epilogue of the row tile: X = beta X + alpha V' 2^(g_c - 68)
+        if (loadx && !mbar_wait(&sh.xfull, static_cast<uint32_t>(rtl & 1))) sh.fail = 1;
+        if (__any_sync(0xffffffffu, failed())) return false;
+        const int64_t r = (blockIdx.y + static_cast<int64_t>(rtl) * G) * kUM + m;
+        const int c0 = n0 + cg * kCols;
+        const double* xs = reinterpret_cast<const double*>(stX) + cg * kCols * kUM + m;
+        double* xr = X + r + static_cast<int64_t>(c0) * ldx;
+#pragma unroll
+        for (int cc = 0; cc < kCols; ++cc) {
+          // V' = (ahi + carry) 2^32 + the low 32 bits of alo
+          const int64_t hi = ahi[cc] + (alo[cc] >> 32);
+          const uint32_t lo = static_cast<uint32_t>(alo[cc]);
+          const int gcol = tb.g[cg * kCols + cc];
+          double p;
+          if (gcol < -2000) p = 0.0;
+          else if (apow2) {
+            p = int96_to_double(hi, lo, gcol - 68 + ka - 1);
+            if (fa < 0.0) p = -p;
+          } else {
+            p = int96_to_double(hi, lo, gcol - 68) * alpha;
+          }
+          if (r < n && c0 + cc < s)
+            xr[static_cast<int64_t>(cc) * ldx] = loadx ? fma(beta, xs[cc * kUM], p) : p;
+          alo[cc] = 0;
+          ahi[cc] = 0;
+        }
+        if (loadx) mbar_arrive(&sh.xfree);
+      }
+      return true;
+    };
+    int pend = -1;
+    bool stop = false;
     for (int q = 0; q < nstages; ++q) {
-      const int kc = q % nkc;
-      const int rtl = q / nkc;
+      const int b = q & 1;
+      const int kq = q % nsub;
       bool bad = failed();
       if (!bad) {
-        const bool ok = mbar_wait(&sh.qfull, static_cast<uint32_t>(q & 1)) &&
-                        (q == 0 || mbar_wait(&sh.afree, static_cast<uint32_t>((q - 1) & 1)));
+        const bool ok = mbar_wait(&sh.qfull[b], static_cast<uint32_t>((q >> 1) & 1)) &&
+                        (q < 2 || mbar_wait(&sh.afree[b], static_cast<uint32_t>(((q >> 1) - 1) & 1)));
         if (!ok) {
           sh.fail = 1;
           bad = true;
         }
       }
-      if (__any_sync(0xffffffffu, bad)) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // row m's 32 values of this warp's half chunk: Q column 32 hcol + c of
-      // the chunk at byte (32 hcol + c) * 1024 + 8 m; two columns per
-      // tensor-memory word, the lower column in the low half
-#pragma unroll 1
-      for (int hb8 = 0; hb8 < 2; ++hb8) {
-        uint32_t words[kDig][8];
-#pragma unroll
-        for (int w = 0; w < 8; ++w) {
-          const int ca = 32 * hcol + 16 * hb8 + 2 * w;
-          const double va = *reinterpret_cast<const double*>(stQ + ca * 1024 + m * 8);
-          const double vb = *reinterpret_cast<const double*>(stQ + (ca + 1) * 1024 + m * 8);
-          uint32_t h0[kDig], h1[kDig];
-          digit_bits(scaled62(va, sh.eq[kc * kUK + ca]), h0);
-          digit_bits(scaled62(vb, sh.eq[kc * kUK + ca + 1]), h1);
-#pragma unroll
-          for (int t = 0; t < kDig; ++t) words[t][w] = pack2(h0[t], h1[t]);
-        }
-#pragma unroll
-        for (int t = 0; t < kDig; ++t)
-          tmem_st8(tlane + kACol + static_cast<uint32_t>(32 * t + 16 * hcol + 8 * hb8), words[t]);
+      if (__any_sync(0xffffffffu, bad)) {
+        stop = true;
+        break;
       }
-      mbar_arrive(&sh.qfree);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // row m's 8 values: column 8 cg + c of the stage at byte
+      // (8 cg + c) * 1024 + 8 m; two columns per tensor-memory word, the
+      // lower column in the low half; a K step (16 columns) wholly past
+      // column i is not issued, so its digits are not needed
+      const int k0 = kq * kUS + kCols * cg;
+      if (kq * kUS + 16 * (cg >> 1) < i) {
+        const unsigned char* col = base + b * kUBox + kCols * cg * 1024 + m * 8;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          uint32_t words[kDig][2];
+#pragma unroll
+          for (int w = 0; w < 2; ++w) {
+            const int c = 4 * h + 2 * w;
+            const double va = *reinterpret_cast<const double*>(col + c * 1024);
+            const double vb = *reinterpret_cast<const double*>(col + (c + 1) * 1024);
+            uint32_t d8[kDig];
+            digits_f16x2(scaled62(va, tb.eq[k0 + c]), scaled62(vb, tb.eq[k0 + c + 1]), d8);
+#pragma unroll
+            for (int t = 0; t < kDig; ++t) words[t][w] = d8[t];
+          }
+#pragma unroll
+          for (int t = 0; t < kDig; ++t)
+            tmem_st2(tlane + kUACol + static_cast<uint32_t>(128 * b + 16 * t + 4 * cg + 2 * h),
+                     words[t]);
+        }
+      }
+      mbar_arrive(&sh.qfree[b]);
       tmem_st_wait();
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mbar_arrive(&sh.afull);
-      if ((kc % 2) == 1 || kc == nkc - 1) {
-        const int grp = rtl * gpt + kc / 2;
-        if (!mbar_wait(&sh.accfull, static_cast<uint32_t>(grp & 1))) sh.fail = 1;
-        if (__any_sync(0xffffffffu, failed())) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t tl = tlane + static_cast<uint32_t>(hcol * kHalf);
-#pragma unroll
-        for (int L = 0; L < kLev; ++L) {
-          uint32_t v[kHalf];
-          tmem_ld16(tl + kAccCol + static_cast<uint32_t>(32 * L), v);
-#pragma unroll
-          for (int cc = 0; cc < kHalf; ++cc) {
-            const int64_t sv = static_cast<int64_t>(__float2int_rz(__uint_as_float(v[cc])));
-            if (L < 4) ahi[cc] += sv << (8 * (3 - L));
-            else alo[cc] += sv << (8 * (7 - L));
-          }
+      mbar_arrive(&sh.afull[b]);
+      if (pend >= 0) {
+        if (!readout(pend)) {
+          stop = true;
+          break;
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        mbar_arrive(&sh.accfree);
-        if (kc == nkc - 1) {
-          // epilogue of the row tile: X = beta X + alpha V' 2^(g_c - 68);
-          // X's values are loaded together first (one latency, not 16)
-          const int64_t r = (blockIdx.y + static_cast<int64_t>(rtl) * G) * kUM + m;
-          const int c0 = n0 + hcol * kHalf;
-          double* xr = X + r + static_cast<int64_t>(c0) * ldx;
-          double xv[kHalf];
-#pragma unroll
-          for (int cc = 0; cc < kHalf; ++cc)
-            xv[cc] = (beta != 0.0 && r < n && c0 + cc < s) ? xr[static_cast<int64_t>(cc) * ldx] : 0.0;
-#pragma unroll
-          for (int cc = 0; cc < kHalf; ++cc) {
-            const int64_t carry = alo[cc] >> 32;
-            const double v = static_cast<double>(ahi[cc] + carry) * 4294967296.0 +
-                             static_cast<double>(static_cast<uint32_t>(alo[cc]));
-            if (r < n && c0 + cc < s)
-              xr[static_cast<int64_t>(cc) * ldx] =
-                  beta == 0.0 ? v * ascale[cc] : fma(beta, xv[cc], v * ascale[cc]);
-            alo[cc] = 0;
-            ahi[cc] = 0;
-          }
-        }
+        pend = -1;
       }
+      if (group_end(kq)) pend = q;
     }
+    if (!stop && pend >= 0) readout(pend);
   }
   if (warp < 4 && !mbar_wait(&sh.done, 0, 2 * kWaitNs)) sh.fail = 1;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -799,14 +1008,13 @@ bool make_map64(CUtensorMap* map, const double* ptr, int64_t rows, int64_t cols,
          CUDA_SUCCESS;
 }
 
-// FP64 column-major matrix, boxes of 128 rows x 64 columns, no swizzle
-bool make_map64_rows(CUtensorMap* map, const double* ptr, int64_t rows, int64_t cols,
-                     int64_t ld) {
+// FP64 column-major matrix, boxes of 128 rows x 32 columns, no swizzle
+bool make_map64_box(CUtensorMap* map, const double* ptr, int64_t rows, int64_t cols, int64_t ld) {
   auto fn = oz_encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(rows), static_cast<cuuint64_t>(cols)};
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * sizeof(double)};
-  cuuint32_t box[2] = {static_cast<cuuint32_t>(kUM), static_cast<cuuint32_t>(kUK)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(kUM), static_cast<cuuint32_t>(kUS)};
   cuuint32_t estr[2] = {1, 1};
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(ptr), dims, strides,
             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -877,20 +1085,21 @@ int64_t oz_exp_ints(int i, int s) { return static_cast<int64_t>(i) + s; }
 
 bool oz_update_supported(int64_t n, const double* Q, int64_t ldq, int i, const double* X,
                          int64_t ldx, int s) {
-  (void)X;
-  (void)ldx;
   if (n < 4 * kUM || i < 1 || i > kUMaxK || s < 1) return false;
-  if ((reinterpret_cast<uintptr_t>(Q) & 15) || ((ldq * 8) & 15)) return false;
+  if ((reinterpret_cast<uintptr_t>(Q) | reinterpret_cast<uintptr_t>(X)) & 15) return false;
+  if (((ldq * 8) & 15) || ((ldx * 8) & 15)) return false;
   if (n > (int64_t(1) << 31) - 1) return false;
   return oz_encode_fn() != nullptr;
 }
 
 // Whether the tensor-core update is expected to beat the FP64-pipe kernel.
 // One SM takes ceil(row tiles / row groups) tiles of 128 rows x 32 columns,
-// each about kTileUs plus kChunkUs per 64 columns of Q; the FP64 pipe
-// sustains about 1.05 TFLOP/s (2 n i s flops, half that for the triangle).
+// each about kTileUs (readout, epilogue, pipeline fill) plus kStepUs per
+// 16 columns of Q (measured: 7.9 us at 1 step, 18.5 us at 7, 33.5 us at 15).
+// The FP64-pipe kernel sustains about 1.05 TFLOP/s (2 n i s flops, half for
+// the triangle) plus its streams of Q and X at about 2 TB/s.
 bool oz_update_pays(int64_t n, int i, int s, bool upper) {
-  constexpr double kTileUs = 6.5, kChunkUs = 9.5;
+  constexpr double kTileUs = 7.0, kStepUs = 1.75;
   const int64_t ct = (s + kUN - 1) / kUN;
   const int64_t ntiles = (n + kUM - 1) / kUM;
   int64_t G = static_cast<int64_t>(device_sm_count()) / ct;
@@ -898,9 +1107,10 @@ bool oz_update_pays(int64_t n, int i, int s, bool upper) {
   if (G > ntiles) G = ntiles;
   const double per_sm = static_cast<double>((ntiles + G - 1) / G) *
                         ((ct + device_sm_count() - 1) / device_sm_count());
-  const double t_oz = per_sm * (kTileUs + kChunkUs * ((i + kUK - 1) / kUK)) * 1e-6;
-  const double t_fp64 = (upper ? 1.0 : 2.0) * static_cast<double>(n) * i * s / 1.05e12;
-  return t_oz < 0.8 * t_fp64;
+  const double t_oz = per_sm * (kTileUs + kStepUs * ((i + 15) / 16)) * 1e-6;
+  const double t_fp64 = (upper ? 1.0 : 2.0) * static_cast<double>(n) * i * s / 1.05e12 +
+                        static_cast<double>(n) * (i + 2.0 * s) * 8.0 / 2.0e12;
+  return t_oz < 0.9 * t_fp64;
 }
 
 void oz_update(int64_t n, const double* Q, int64_t ldq, int i, const double* W, int ldw,
@@ -908,17 +1118,18 @@ void oz_update(int64_t n, const double* Q, int64_t ldq, int i, const double* W, 
                cudaStream_t st) {
   int* err = oz_err_flag();
   col_exponents(n, Q, ldq, i, exps, st);
-  CUtensorMap mq;
-  SG_REQUIRE(make_map64_rows(&mq, Q, n, i, ldq), SG_ECUDA, "cuTensorMapEncodeTiled failed");
-  ensure_dynamic_smem(reinterpret_cast<const void*>(oz_update_kernel), kUSmem);
+  CUtensorMap mq, mx;
+  SG_REQUIRE(make_map64_box(&mq, Q, n, i, ldq) && make_map64_box(&mx, X, n, s, ldx), SG_ECUDA,
+             "cuTensorMapEncodeTiled failed");
+  ensure_dynamic_smem(reinterpret_cast<const void*>(oz_update_kernel), oz_update_smem(kUMaxK));
   const int ct = (s + kUN - 1) / kUN;
   const int64_t ntiles = (n + kUM - 1) / kUM;
   int64_t G = static_cast<int64_t>(device_sm_count()) / ct;
   if (G < 1) G = 1;
   if (G > ntiles) G = ntiles;
   dim3 grid(static_cast<unsigned>(ct), static_cast<unsigned>(G));
-  oz_update_kernel<<<grid, kOThreads, kUSmem, st>>>(mq, n, i, s, W, ldw, X, ldx, alpha, beta,
-                                                      upper ? 1 : 0, exps, err);
+  oz_update_kernel<<<grid, kUThreads, oz_update_smem(i), st>>>(
+      mq, mx, n, i, s, W, ldw, X, ldx, alpha, beta, upper ? 1 : 0, exps, err);
   SG_LAUNCH_CHECK();
 }
 

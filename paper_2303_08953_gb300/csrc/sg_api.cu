@@ -292,6 +292,8 @@ extern "C" {
 
 int64_t sg_kernel_launches(void) { return sg::g_launches.load(); }
 
+int32_t sg_set_tc_policy(int32_t policy) { return sg::set_tc_policy(policy); }
+
 void sg_default_opts(sg_opts* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));

@@ -159,6 +159,11 @@ void block_update(int64_t n, const double* Q, int64_t ldq, int i,
                   double alpha, double beta, bool upper, double* scratch,
                   int64_t scratch_doubles, cudaStream_t st);
 int64_t block_update_scratch(int i);
+
+// process-wide tensor-core policy of the FP64 block products (SG_TC_*);
+// set_tc_policy returns the previous one, or -1 for an unknown value
+int tc_policy();
+int set_tc_policy(int policy);
 // FP32: runs on the tensor cores when supported (scratch: >= the
 // tc_update_scratch floats, may be null to force the FFMA kernels)
 void block_update32(int64_t n, const float* Q, int64_t ldq, int i,

@@ -144,10 +144,27 @@ def test_spmv_empty_rows(solver):
 
 
 # ------------------------------------------------------ dense block kernels
+@pytest.fixture(params=["never", "always"])
+def tc_path(request):
+    """Runs a test with the FP64 block products on the FP64 pipe and on the
+    tensor cores (wherever their layout allows), whatever the cost model
+    would pick for the shape."""
+    old = sg.set_tc_policy(request.param)
+    yield request.param
+    sg.set_tc_policy(old)
+
+
+@pytest.fixture
+def tc_always():
+    old = sg.set_tc_policy("always")
+    yield
+    sg.set_tc_policy(old)
+
+
 @pytest.mark.parametrize("n", [1, 97, 4133, 70001])
 @pytest.mark.parametrize("i,s", [(1, 1), (1, 120), (5, 7), (8, 33), (9, 32),
                                  (33, 65), (121, 120), (241, 17)])
-def test_block_dot_matches_definition(solver, n, i, s):
+def test_block_dot_matches_definition(solver, tc_path, n, i, s):
     rng = np.random.default_rng(100 * i + s)
     ld = n + (7 if n > 1 else 0)
     Q = rng.standard_normal((i, ld))
@@ -158,9 +175,18 @@ def test_block_dot_matches_definition(solver, n, i, s):
     assert np.all(np.abs(Wt.T - ref) <= 1e-14 * scale + 1e-300)
 
 
+def _even_ld(A, fill=0.0):
+    """A (k, n) copied into rows of an even length (16-byte strides, which
+    the tensor-core forms need), the padding set to `fill`."""
+    k, n = A.shape
+    out = np.full((k, n + (n & 1)), fill)
+    out[:, :n] = A
+    return out
+
+
 def _block_dot(solver, Q, X, n, sym=False):
     i, ld = Q.shape
-    s = X.shape[0]
+    s = i if sym else X.shape[0]
     Qd = dev(Q)
     Xd = Qd if sym else dev(X)
     W = torch.empty((s, i), dtype=torch.float64, device=DEV)
@@ -174,7 +200,7 @@ def _block_dot(solver, Q, X, n, sym=False):
 
 
 @pytest.mark.parametrize("n,i,s", [(70001, 107, 106), (4133, 241, 17), (9000, 3, 130)])
-def test_block_dot_fp64_tensor_cores_exact_on_integers(solver, n, i, s):
+def test_block_dot_fp64_tensor_cores_exact_on_integers(solver, tc_always, n, i, s):
     """The FP64 block dot on the tensor cores (8-bit digit slices, exact
     level sums) returns exact dot products: integer inputs of magnitude up
     to 2^15 have exact FP64 dot products (< 2^53), and every entry must
@@ -185,17 +211,17 @@ def test_block_dot_fp64_tensor_cores_exact_on_integers(solver, n, i, s):
     X = rng.integers(-2 ** 15, 2 ** 15, size=(s, n)).astype(np.float64)
     Q *= np.exp2(rng.integers(-40, 41, size=(i, 1)))
     X *= np.exp2(rng.integers(-40, 41, size=(s, 1)))
-    Wt = host(_block_dot(solver, Q, X, n))
+    Wt = host(_block_dot(solver, _even_ld(Q), _even_ld(X), n))
     assert np.array_equal(Wt.T, Q @ X.T)
-    G = host(_block_dot(solver, X, X, n, sym=True))
+    G = host(_block_dot(solver, _even_ld(X), None, n, sym=True))
     assert np.array_equal(G, X @ X.T)
 
 
 @pytest.mark.parametrize("n,s", [(4133, 1), (4133, 31), (70001, 64), (3001, 120)])
-def test_block_dot_symmetric_gram(solver, n, s):
+def test_block_dot_symmetric_gram(solver, tc_path, n, s):
     rng = np.random.default_rng(s)
     X = rng.standard_normal((s, n))
-    G = host(_block_dot(solver, X, X, n, sym=True))
+    G = host(_block_dot(solver, _even_ld(X), None, n, sym=True))
     ref = X @ X.T
     assert np.array_equal(G, G.T)
     assert np.allclose(G, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
@@ -205,7 +231,7 @@ def test_block_dot_symmetric_gram(solver, n, s):
 @pytest.mark.parametrize("i,s,upper", [(1, 1, False), (3, 120, False),
                                        (121, 40, False), (33, 33, True),
                                        (120, 120, True), (7, 7, True)])
-def test_block_update_matches_definition(solver, n, i, s, upper):
+def test_block_update_matches_definition(solver, tc_path, n, i, s, upper):
     rng = np.random.default_rng(n + i + s)
     Q = rng.standard_normal((i, n))
     Wm = rng.standard_normal((i, s))          # i x s
@@ -213,19 +239,22 @@ def test_block_update_matches_definition(solver, n, i, s, upper):
         Wm = np.triu(Wm) + np.tril(np.full((i, s), np.nan), -1)
     X = rng.standard_normal((s, n))
     Wt = dev(np.ascontiguousarray(Wm.T))      # (s, i) = column-major i x s
-    Xd = dev(X)
-    solver.block_update(dev(Q), Wt, Xd, alpha=-0.7, beta=1.3 if not upper else 0.0,
-                        upper=upper, n=n)
+    Xd = dev(_even_ld(X, np.inf))
+    solver.block_update(dev(_even_ld(Q)), Wt, Xd, alpha=-0.7,
+                        beta=1.3 if not upper else 0.0, upper=upper, n=n)
     Wz = np.nan_to_num(Wm, nan=0.0)
     ref = (1.3 if not upper else 0.0) * X + (-0.7) * (Q.T @ Wz).T
     scale = np.abs(X) + 0.7 * (np.abs(Q).T @ np.abs(Wz)).T
     got = host(Xd)
-    assert np.all(np.abs(got - ref) <= 1e-14 * scale + 1e-300)
+    assert np.all(np.abs(got[:, :n] - ref) <= 1e-14 * scale + 1e-300)
+    assert np.all(got[:, n:] == np.inf)       # rows past n untouched
 
 
 @pytest.mark.parametrize("n,i,s,upper", [(70001, 107, 106, False), (9000, 241, 40, False),
-                                         (20000, 120, 120, True), (4133, 64, 33, False)])
-def test_block_update_fp64_tensor_cores_exact_on_integers(solver, n, i, s, upper):
+                                         (20000, 120, 120, True), (4133, 64, 33, False),
+                                         (513, 1, 1, False), (600, 17, 5, False),
+                                         (1000, 33, 33, True), (2049, 16, 70, False)])
+def test_block_update_fp64_tensor_cores_exact_on_integers(solver, tc_always, n, i, s, upper):
     """The FP64 block update on the tensor cores (Q's digits relative to its
     column exponents, W' = W 2^(e_k) cut relative to its own column
     exponents) is exact: integer Q and W with per-column scales 2^-30 ..
@@ -243,11 +272,13 @@ def test_block_update_fp64_tensor_cores_exact_on_integers(solver, n, i, s, upper
     if upper:
         Wm = np.triu(Wm) + np.tril(np.full((i, s), np.nan), -1)
     Wz = np.nan_to_num(Wm, nan=0.0)
-    Xd = dev(X)
-    solver.block_update(dev(Q), dev(np.ascontiguousarray(Wm.T)), Xd, alpha=-1.0, beta=1.0,
-                        upper=upper, n=n)
+    Xd = dev(_even_ld(X, np.inf))
+    solver.block_update(dev(_even_ld(Q)), dev(np.ascontiguousarray(Wm.T)), Xd, alpha=-1.0,
+                        beta=1.0, upper=upper, n=n)
     ref = X - (Q.T @ Wz).T
-    assert np.array_equal(host(Xd), ref)
+    got = host(Xd)
+    assert np.array_equal(got[:, :n], ref)
+    assert np.all(got[:, n:] == np.inf)
 
 
 @pytest.mark.parametrize("n", [97, 4133, 70001])
