@@ -575,6 +575,111 @@ update_kernel(int64_t K, int M, int N, const T* __restrict__ A, int64_t lda,
   }
 }
 
+// X = beta X + alpha Q W for a narrow Q (i <= MAXI): the tiled kernel
+// above pads the inner dimension to UK, which for i = 1 would cost UK FMAs
+// per output, and this product is bound by streaming X.  One row per
+// thread: its i values of Q in registers, W's column chunk (zero below the
+// diagonal for the triangular form) in shared memory, X read and written
+// a column at a time (coalesced along rows), eight columns per pass so that
+// their loads are in flight together.  FP64 operations per output are the
+// limit next to the stream, so the two forms the solver uses get their own
+// chains: MODE 1 (alpha = -1, beta = 1, the BCGS update) subtracts the
+// products from X one FMA at a time, k in order; MODE 2 (beta = 0, the
+// triangular products) forms the sum in k order and scales it unless
+// alpha = 1; MODE 0 forms the sum and applies alpha and beta.
+constexpr int kThinCols = 64;
+constexpr int kThinPass = 8;
+
+template <int MAXI, int MODE, typename T>
+__global__ void __launch_bounds__(kThreads)
+update_thin_kernel(int64_t n, int i, int s, const T* __restrict__ Q, int64_t ldq,
+                   const double* __restrict__ W, int ldw, T* __restrict__ X, int64_t ldx,
+                   double alpha, double beta, int upper) {
+  __shared__ T Ws[MAXI][kThinCols];
+  const int c0 = blockIdx.y * kThinCols;
+  const int cn = (s - c0 < kThinCols) ? s - c0 : kThinCols;
+  for (int e = threadIdx.x; e < MAXI * kThinCols; e += kThreads) {
+    const int k = e / kThinCols, c = e % kThinCols;
+    T v = T(0);
+    if (k < i && c < cn && !(upper && k > c0 + c))
+      v = static_cast<T>(W[k + static_cast<int64_t>(c0 + c) * ldw]);
+    Ws[k][c] = v;
+  }
+  __syncthreads();
+  const T a = static_cast<T>(alpha), b = static_cast<T>(beta);
+  auto out = [&](const T* q, int c, T x) -> T {
+    if (MODE == 1) {
+      T v = x;
+#pragma unroll
+      for (int k = 0; k < MAXI; ++k)
+        if (k < i) v = fma(-q[k], Ws[k][c], v);
+      return v;
+    }
+    T acc = T(0);
+#pragma unroll
+    for (int k = 0; k < MAXI; ++k)
+      if (k < i) acc = (k == 0) ? q[0] * Ws[0][c] : fma(q[k], Ws[k][c], acc);
+    if (MODE == 2) return alpha == 1.0 ? acc : a * acc;
+    const T v = a * acc;
+    return beta != 0.0 ? fma(b, x, v) : v;
+  };
+  for (int64_t r = static_cast<int64_t>(blockIdx.x) * kThreads + threadIdx.x; r < n;
+       r += static_cast<int64_t>(gridDim.x) * kThreads) {
+    T q[MAXI];
+#pragma unroll
+    for (int k = 0; k < MAXI; ++k) q[k] = k < i ? Q[r + k * ldq] : T(0);
+    T* xr = X + r + static_cast<int64_t>(c0) * ldx;
+    int c = 0;
+    for (; c + kThinPass <= cn; c += kThinPass) {
+      T xv[kThinPass];
+#pragma unroll
+      for (int u = 0; u < kThinPass; ++u)
+        xv[u] = (MODE != 2 && beta != 0.0) ? xr[static_cast<int64_t>(c + u) * ldx] : T(0);
+#pragma unroll
+      for (int u = 0; u < kThinPass; ++u)
+        xr[static_cast<int64_t>(c + u) * ldx] = out(q, c + u, xv[u]);
+    }
+    for (; c < cn; ++c) {
+      const T x = (MODE != 2 && beta != 0.0) ? xr[static_cast<int64_t>(c) * ldx] : T(0);
+      xr[static_cast<int64_t>(c) * ldx] = out(q, c, x);
+    }
+  }
+}
+
+template <int MAXI, typename T>
+void launch_update_thin_i(dim3 grid, int64_t n, const T* Q, int64_t ldq, int i, const double* W,
+                          int ldw, T* X, int64_t ldx, int s, double alpha, double beta, int up,
+                          cudaStream_t st) {
+  if (alpha == -1.0 && beta == 1.0)
+    update_thin_kernel<MAXI, 1, T><<<grid, kThreads, 0, st>>>(n, i, s, Q, ldq, W, ldw, X, ldx,
+                                                               alpha, beta, up);
+  else if (beta == 0.0)
+    update_thin_kernel<MAXI, 2, T><<<grid, kThreads, 0, st>>>(n, i, s, Q, ldq, W, ldw, X, ldx,
+                                                               alpha, beta, up);
+  else
+    update_thin_kernel<MAXI, 0, T><<<grid, kThreads, 0, st>>>(n, i, s, Q, ldq, W, ldw, X, ldx,
+                                                               alpha, beta, up);
+}
+
+template <typename T>
+void launch_update_thin(int64_t n, const T* Q, int64_t ldq, int i, const double* W, int ldw,
+                        T* X, int64_t ldx, int s, double alpha, double beta, bool upper,
+                        cudaStream_t st) {
+  const int cchunks = (s + kThinCols - 1) / kThinCols;
+  int64_t rb = (n + kThreads - 1) / kThreads;
+  const int64_t cap = static_cast<int64_t>(device_sm_count()) * 8 / cchunks + 1;
+  if (rb > cap) rb = cap;
+  dim3 grid(static_cast<unsigned>(rb), static_cast<unsigned>(cchunks));
+  const int up = upper ? 1 : 0;
+  if (i <= 4)
+    launch_update_thin_i<4, T>(grid, n, Q, ldq, i, W, ldw, X, ldx, s, alpha, beta, up, st);
+  else if (i <= 8)
+    launch_update_thin_i<8, T>(grid, n, Q, ldq, i, W, ldw, X, ldx, s, alpha, beta, up, st);
+  else
+    launch_update_thin_i<16, T>(grid, n, Q, ldq, i, W, ldw, X, ldx, s, alpha, beta, up, st);
+  SG_LAUNCH_CHECK();
+}
+
 template <typename T>
 void block_update_impl(int64_t n, const T* Q, int64_t ldq, int i,
                        const double* W, int ldw, T* X, int64_t ldx, int s,
@@ -586,6 +691,10 @@ void block_update_impl(int64_t n, const T* Q, int64_t ldq, int i,
     alpha = 0.0;  // X = beta X
   }
   const int ii = i > 0 ? i : 0;
+  if (sizeof(T) == 8 && ii <= 16) {
+    launch_update_thin<T>(n, Q, ldq, ii, W, ldw, X, ldx, s, alpha, beta, upper, st);
+    return;
+  }
   if (s <= 8) {
     dim3 grid(static_cast<unsigned>((n + 127) / 128), 1);
     update_kernel<128, 8, 4, 1, T><<<grid, kThreads, 0, st>>>(

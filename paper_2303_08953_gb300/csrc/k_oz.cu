@@ -41,6 +41,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "k_tc_common.cuh"
@@ -1096,8 +1097,9 @@ bool oz_update_supported(int64_t n, const double* Q, int64_t ldq, int i, const d
 // One SM takes ceil(row tiles / row groups) tiles of 128 rows x 32 columns,
 // each about kTileUs (readout, epilogue, pipeline fill) plus kStepUs per
 // 16 columns of Q (measured: 7.9 us at 1 step, 18.5 us at 7, 33.5 us at 15).
-// The FP64-pipe kernel sustains about 1.05 TFLOP/s (2 n i s flops, half for
-// the triangle) plus its streams of Q and X at about 2 TB/s.
+// The FP64-pipe kernels sustain about 1.05 TFLOP/s (2 n i s flops, half
+// for the triangle); the tiled one adds its streams of Q and X at about
+// 2 TB/s, the narrow-Q one (i <= 16) overlaps them at about 5.5 TB/s.
 bool oz_update_pays(int64_t n, int i, int s, bool upper) {
   constexpr double kTileUs = 7.0, kStepUs = 1.75;
   const int64_t ct = (s + kUN - 1) / kUN;
@@ -1108,8 +1110,10 @@ bool oz_update_pays(int64_t n, int i, int s, bool upper) {
   const double per_sm = static_cast<double>((ntiles + G - 1) / G) *
                         ((ct + device_sm_count() - 1) / device_sm_count());
   const double t_oz = per_sm * (kTileUs + kStepUs * ((i + 15) / 16)) * 1e-6;
-  const double t_fp64 = (upper ? 1.0 : 2.0) * static_cast<double>(n) * i * s / 1.05e12 +
-                        static_cast<double>(n) * (i + 2.0 * s) * 8.0 / 2.0e12;
+  const double flops = (upper ? 1.0 : 2.0) * static_cast<double>(n) * i * s;
+  const double bytes = static_cast<double>(n) * (i + 2.0 * s) * 8.0;
+  const double t_fp64 = i <= 16 ? std::max(flops / 1.05e12, bytes / 5.5e12)
+                                : flops / 1.05e12 + bytes / 2.0e12;
   return t_oz < 0.9 * t_fp64;
 }
 
