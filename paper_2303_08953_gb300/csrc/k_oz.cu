@@ -1,40 +1,40 @@
-// FP64 block dot product W = Q^T X on the tensor cores, exactly: the BCGS
-// projections and Gram matrices of Alg. 4 for the FP64 basis.
+// FP64 block products of BCGS (Alg. 4) on the tensor cores, exactly: the
+// projections W = Q^T X and Gram matrices, and the update X = beta X +
+// alpha Q W, for the FP64 basis.
 //
 // GB300's FP64 pipe gives ~1.26 TFLOP/s, so the FP64 block products are
-// FP64-ALU bound; its BF16 tensor cores give ~1.9 PFLOP/s.  Every FP64
+// FP64-ALU bound; its 16-bit tensor cores give ~1.9 PFLOP/s.  Every FP64
 // value is written exactly (to 62 bits below its column's largest
-// magnitude) as a sum of eight 8-bit digit slices, each slice a BF16 tile:
+// magnitude) as a sum of eight 8-bit digit slices, each slice an FP16 tile:
 //   x = 2^(e - 62) * sum_{t=1..8} d_t 256^(8 - t),   |d_t| <= 128 integers,
 // with e the exponent of the column's largest |x| (balanced digits: a digit
 // >= 128 becomes d - 256 and carries one into the next higher digit).  A
 // digit product is an integer of at most 2^14, exact in the MMA's FP32
 // accumulator; products of equal level l = t + u have the same weight
 // 256^(16 - l), so the MMA sums them into one FP32 accumulator per level.
-// A level has at most 8 digit pairs, so its sum over 128 rows stays within
+// A level has at most 8 digit pairs, so its sum over 128 rows stays below
 // 8 * 128 * 2^14 = 2^24: every level sum is an exact integer in FP32.  Every
 // 128 rows the eight level sums are read from tensor memory and added,
 // with their weights 256^(9 - l), into an exact integer per output (two
 // int64 halves); levels above 9 (weights below 2^-56 of the leading term)
 // are not formed.  The result is the dot product of the 62-bit truncations,
-// exact up to the final conversion to FP64 -- more accurate than an FP64
+// exact up to the final rounding to FP64 -- more accurate than an FP64
 // FMA chain.
 //
-// Tile: 128 columns of Q (MMA M) x 32 columns of X (MMA N) per CTA, 64 rows
-// (K) per stage; one CTA per SM (the tile uses all 512 tensor-memory
-// columns); splits of the rows across CTAs are reduced afterwards in a
-// fixed order, like the other block dots.
-//   * warp 8 (one lane) streams Q and X tiles with TMA: four 16-row x 128
-//     (Q) or x 32 (X) boxes per stage, 128-byte swizzled, so every thread
-//     reads its column conflict-free;
-//   * warps 0-7 cut the tiles into digits: Q's into eight tensor-memory
-//     slices (the MMA's A operand, lane = Q column, two BF16 digits per
-//     32-bit column; warps w and w+4 share lanes 32 (w % 4) .. + 31 and take
-//     one half of the rows each), X's into eight 128-byte-swizzled
-//     shared-memory slices (the MMA's B operand, double-buffered; warp w
-//     takes rows 8w .. 8w + 7); every 128 rows they read the level sums,
-//     16 output columns each;
-//   * warp 9 (one lane) issues the 36 digit-pair MMAs per 16-row K step.
+// Dot tile: 128 columns of Q (MMA M) x 32 columns of X (MMA N) per CTA,
+// 32 rows (K) per stage; one CTA per SM (the tile uses all 512
+// tensor-memory columns: 256 for the level sums, two A buffers of 128);
+// splits of the rows across CTAs are reduced afterwards in a fixed order,
+// like the other block dots.
+//   * warp 16 (one lane) streams each stage's Q and X boxes with TMA (16
+//     rows x 128 or 32 columns, 128-byte swizzled, so every thread reads
+//     its column conflict-free) into a two-deep ring;
+//   * warps 0-15 cut stage k into digits while warp 17 (one lane) runs
+//     stage k-1's 72 digit-pair MMAs: Q's into one of two tensor-memory A
+//     buffers (lane = Q column, two FP16 digits per 32-bit column), X's
+//     into one of two sets of 128-byte-swizzled shared-memory B slices;
+//     every four stages, one stage late, they read the level sums, eight
+//     output columns each.
 // Every wait is bounded: on timeout the kernel records an error, drains
 // its own copies, frees its tensor memory and returns.
 #include <cuda.h>
@@ -55,40 +55,33 @@ using namespace tc;
 
 constexpr int kOM = 128;          // columns of Q per tile (MMA M)
 constexpr int kON = 32;           // columns of X per tile (MMA N)
-constexpr int kOK = 64;           // rows per stage
+constexpr int kOK = 32;           // rows per stage (two MMA K steps)
 constexpr int kDig = 8;           // digit slices per value
 constexpr int kLev = 8;           // levels l = 2..9 kept
-constexpr int kChunk = 2;         // stages per exact level sum (128 rows)
-constexpr int kXStages = 2;       // X staging / B slice ring
-constexpr int kOThreads = 320;    // warps 0-7 split, 8 TMA, 9 MMA
+constexpr int kChunk = 4;         // stages per exact level sum (128 rows)
 constexpr uint32_t kOTmemCols = 512;
 constexpr uint32_t kAccCol = 0;     // level L = l - 2 at column 32 L
-constexpr uint32_t kACol = 256;     // digit slice t (0-based) at 256 + 32 t
+constexpr uint32_t kDACol = 256;    // A buffer b at 256 + 128 b, digit slice t at + 16 t
 constexpr int kQBox = 16 * kOM * 8;           // one 16-row Q box: 16 KB
-constexpr int kQBytes = 4 * kQBox;            // 64 KB per stage
+constexpr int kQBytes = (kOK / 16) * kQBox;   // 32 KB per stage
 constexpr int kXBox = 16 * kON * 8;           // 4 KB
-constexpr int kXBytes = 4 * kXBox;            // 16 KB
-constexpr int kBSlice = kON * 128;            // 32 rows x 64 BF16: 4 KB
+constexpr int kXBytes = (kOK / 16) * kXBox;   // 8 KB per stage
+constexpr int kBSlice = kON * 128;            // 32 rows x 64 FP16 (the stage fills 32): 4 KB
 constexpr int kBBytes = kDig * kBSlice;       // 32 KB
-constexpr int kOzSmem = kQBytes + kXStages * (kXBytes + kBBytes) + 1024;
+constexpr int kDWarps = 16;                   // split / readout warps
+constexpr int kDThreads = (kDWarps + 2) * 32; // + warp 16 TMA, warp 17 MMA
+constexpr int kDSplit = kDWarps * 32;
 
 struct __align__(8) OzShared {
-  uint64_t qfull, qfree;
-  uint64_t xfull[kXStages], xfree[kXStages];
-  uint64_t afull, afree;
-  uint64_t bfull[kXStages], bfree[kXStages];
-  uint64_t accfull, accfree;
-  uint64_t done;
+  uint64_t qfull[2], qfree[2], afull[2], afree[2];
+  uint64_t accfull, accfree, done;
   uint32_t tmem_base;
   int fail;
 };
 
-// Instruction descriptor: kind::f16 with BF16 A and B, FP32 accumulator,
-// K-major A and B.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
-         (static_cast<uint32_t>(M >> 4) << 24);
-}
+// dynamic shared memory of the dot: Q and X boxes and B slices, two of
+// each, then the barriers
+constexpr int kOzSmem = 2 * (kQBytes + kXBytes + kBBytes) + static_cast<int>(sizeof(OzShared)) + 1024;
 
 __device__ __forceinline__ void mma_bf16_tmem_a(uint32_t dtmem, uint32_t atmem, uint64_t b,
                                                 uint32_t idesc, uint32_t accumulate) {
@@ -115,27 +108,6 @@ __device__ __forceinline__ int64_t scaled62(double x, int e) {
   return (bits >> 63) ? -static_cast<int64_t>(m) : static_cast<int64_t>(m);
 }
 
-// Balanced base-256 digits of m, most significant first, as BF16 bit
-// patterns: m = sum_t d[t] 256^(7-t) with d[1..7] in [-128, 127] and
-// |d[0]| <= 65.  Adding 128 to each of the seven low bytes of m makes every
-// byte b of the sum a digit plus 128 (the carries do the balancing); a
-// digit d becomes the FP32 value d exactly through the full-rate magic
-// constant 1.5 2^23, and its BF16 pattern is the FP32 value's top half (d
-// has at most 8 significant bits).
-__device__ __forceinline__ void digit_bits(int64_t m, uint32_t* hb) {
-  const uint64_t s = static_cast<uint64_t>(m) + 0x0080808080808080ull;
-  const uint32_t lo = static_cast<uint32_t>(s);
-  const uint32_t hi = static_cast<uint32_t>(s >> 32);
-  const int top = static_cast<int>(static_cast<int64_t>(s) >> 56);   // signed
-  hb[0] = __float_as_uint(__int_as_float(0x4B400000 + top) - 12582912.0f);
-#pragma unroll
-  for (int t = 1; t < 8; ++t) {
-    const uint32_t byte = (t < 4) ? ((hi >> (8 * (3 - t))) & 0xFFu) : ((lo >> (8 * (7 - t))) & 0xFFu);
-    hb[t] = __float_as_uint(__int_as_float(0x4B400000 + static_cast<int>(byte)) -
-                            (12582912.0f + 128.0f));
-  }
-}
-
 // The integer value of an FP32 level sum (an exact integer, |v| < 2^24)
 // on the FP32 pipe: adding 1.5 2^25 (whose unit in the last place is 4)
 // rounds v to a multiple of 4 and leaves v / 4 in the low bits of the sum's
@@ -146,363 +118,6 @@ __device__ __forceinline__ int32_t level_int(uint32_t vb) {
   const float t = __fadd_rn(v, 50331648.0f);
   const float r = __fsub_rn(v, __fsub_rn(t, 50331648.0f));
   return 4 * (__float_as_int(t) - 0x4C400000) + (__float_as_int(__fadd_rn(r, 12582912.0f)) - 0x4B400000);
-}
-
-// two BF16 patterns (from digit_bits' FP32 words) in one 32-bit word, the
-// first in the low half
-__device__ __forceinline__ uint32_t pack2(uint32_t f_lo, uint32_t f_hi) {
-  return (f_lo >> 16) | (f_hi & 0xFFFF0000u);
-}
-
-// This thread's lane, 8 consecutive 32-bit columns from taddr.
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
-      : "memory");
-}
-
-// This thread's lane, 16 consecutive 32-bit columns from taddr.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-        "=r"(v[14]), "=r"(v[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// grid: (tiles of 128 Q columns, tiles of 32 X columns, splits)
-__global__ void __launch_bounds__(kOThreads, 1)
-oz_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
-              const __grid_constant__ CUtensorMap mapX, int64_t n, int M, int N,
-              const int* __restrict__ eq, const int* __restrict__ ex, int64_t rows_per_split,
-              double* __restrict__ part, int* __restrict__ err) {
-  extern __shared__ __align__(1024) unsigned char dsmem[];
-  unsigned char* base = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~static_cast<uintptr_t>(1023));
-  __shared__ OzShared sh;
-  const int tid = threadIdx.x;
-  const int warp = tid >> 5;
-  const int lane = tid & 31;
-  const int m0 = blockIdx.x * kOM;
-  const int n0 = blockIdx.y * kON;
-  const int64_t k0 = static_cast<int64_t>(blockIdx.z) * rows_per_split;
-  const int64_t k1 = (k0 + rows_per_split < n) ? k0 + rows_per_split : n;
-  const int nk = static_cast<int>((k1 - k0 + kOK - 1) / kOK);
-  const uint32_t idesc = idesc_bf16(kOM, kON);
-
-  unsigned char* stQ = base;
-  auto stX = [&](int q) { return base + kQBytes + q * kXBytes; };
-  auto stB = [&](int q) { return base + kQBytes + kXStages * kXBytes + q * kBBytes; };
-  auto failed = [&]() { return *reinterpret_cast<volatile int*>(&sh.fail) != 0; };
-  auto chunk_end = [&](int k) { return (k % kChunk) == kChunk - 1 || k == nk - 1; };
-
-  if (tid == 0) {
-    mbar_init(&sh.qfull, 1);
-    mbar_init(&sh.qfree, 256);
-    for (int q = 0; q < kXStages; ++q) {
-      mbar_init(&sh.xfull[q], 1);
-      mbar_init(&sh.xfree[q], 256);
-      mbar_init(&sh.bfull[q], 256);
-      mbar_init(&sh.bfree[q], 1);
-    }
-    mbar_init(&sh.afull, 256);
-    mbar_init(&sh.afree, 1);
-    mbar_init(&sh.accfull, 1);
-    mbar_init(&sh.accfree, 256);
-    mbar_init(&sh.done, 1);
-    sh.fail = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(&sh.tmem_base)),
-                 "r"(kOTmemCols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = sh.tmem_base;
-
-  // per-thread sums of 16 outputs (warp w reads tensor-memory lanes
-  // 32 (w % 4) .. + 31 = Q columns, and X columns 16 (w / 4) .. + 15), each
-  // as two int64 halves: ahi = sum of S_L 256^(3-L) over levels L = 0..3,
-  // alo = sum of S_L 256^(7-L) over L = 4..7 (|S_L| <= 2^24, so each half
-  // grows by < 2^50 per readout and stays exact for 2^12 readouts), and
-  // the output's V' = ahi 2^32 + alo
-  constexpr int kHalf = kON / 2;
-  int64_t alo[kHalf];
-  int64_t ahi[kHalf];
-#pragma unroll
-  for (int c = 0; c < kHalf; ++c) { alo[c] = 0; ahi[c] = 0; }
-  // level sums of the chunk just finished (MMAs complete) into the 128-bit
-  // sums; warps 0-7 each take 16 of the 32 columns
-  auto readout = [&](int c) -> bool {
-    if (!mbar_wait(&sh.accfull, static_cast<uint32_t>(c & 1))) sh.fail = 1;
-    if (__any_sync(0xffffffffu, failed())) return false;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tl = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) +
-                        static_cast<uint32_t>((warp >> 2) * kHalf);
-#pragma unroll
-    for (int L = 0; L < kLev; ++L) {
-      uint32_t v[kHalf];
-      tmem_ld16(tl + kAccCol + static_cast<uint32_t>(32 * L), v);
-#pragma unroll
-      for (int cc = 0; cc < kHalf; ++cc) {
-        const int64_t sv = level_int(v[cc]);
-        if (L < 4) ahi[cc] += sv * (int64_t(1) << (8 * (3 - L)));
-        else alo[cc] += sv * (int64_t(1) << (8 * (7 - L)));
-      }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    mbar_arrive(&sh.accfree);
-    return true;
-  };
-
-  if (warp == 8) {
-    // ------------------------------------------------ TMA producer
-    if (lane == 0) {
-      int issued = 0;
-      for (int k = 0; k < nk; ++k) {
-        if (failed()) break;
-        const int qx = k % kXStages;
-        if ((k >= 1 && !mbar_wait(&sh.qfree, static_cast<uint32_t>((k - 1) & 1))) ||
-            (k >= kXStages &&
-             !mbar_wait(&sh.xfree[qx], static_cast<uint32_t>(((k / kXStages) - 1) & 1)))) {
-          sh.fail = 1;
-          break;
-        }
-        const int x = static_cast<int>(k0 + static_cast<int64_t>(k) * kOK);
-        mbar_expect_tx(&sh.qfull, static_cast<uint32_t>(kQBytes));
-        for (int b = 0; b < 4; ++b) tma_load_2d(stQ + b * kQBox, &mapQ, &sh.qfull, x + 16 * b, m0);
-        mbar_expect_tx(&sh.xfull[qx], static_cast<uint32_t>(kXBytes));
-        for (int b = 0; b < 4; ++b)
-          tma_load_2d(stX(qx) + b * kXBox, &mapX, &sh.xfull[qx], x + 16 * b, n0);
-        issued = k + 1;
-      }
-      if (failed()) {
-        if (issued > 0) mbar_wait(&sh.qfull, static_cast<uint32_t>((issued - 1) & 1));
-        for (int k = (issued > kXStages ? issued - kXStages : 0); k < issued; ++k)
-          mbar_wait(&sh.xfull[k % kXStages], static_cast<uint32_t>((k / kXStages) & 1));
-      }
-    }
-  } else if (warp == 9) {
-    // ------------------------------------------------ MMA issuer
-    if (lane == 0) {
-      for (int k = 0; k < nk; ++k) {
-        if (failed()) break;
-        const int qb = k % kXStages;
-        const int c = k / kChunk;
-        const bool first = (k % kChunk) == 0;
-        if (!mbar_wait(&sh.afull, static_cast<uint32_t>(k & 1)) ||
-            !mbar_wait(&sh.bfull[qb], static_cast<uint32_t>((k / kXStages) & 1)) ||
-            (first && c > 0 && !mbar_wait(&sh.accfree, static_cast<uint32_t>((c - 1) & 1)))) {
-          sh.fail = 1;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t bbase = smem_u32(stB(qb));
-#pragma unroll 1
-        for (int kk = 0; kk < kOK / 16; ++kk) {
-          bool seen[kLev] = {false, false, false, false, false, false, false, false};
-#pragma unroll
-          for (int t = 0; t < kDig; ++t) {
-#pragma unroll
-            for (int u = 0; u < kDig; ++u) {
-              if (t + u > kLev - 1) continue;     // level (t+1)+(u+1) <= 9
-              const int L = t + u;
-              const uint32_t acc = (!first || kk > 0 || seen[L]) ? 1u : 0u;
-              seen[L] = true;
-              const uint64_t b = sdesc(bbase + static_cast<uint32_t>(u * kBSlice)) +
-                                 static_cast<uint64_t>((kk * 32) >> 4);
-              mma_bf16_tmem_a(tmem + kAccCol + static_cast<uint32_t>(32 * L),
-                              tmem + kACol + static_cast<uint32_t>(32 * t + 8 * kk), b, idesc,
-                              acc);
-            }
-          }
-        }
-        mma_commit(&sh.afree);        // A slices reusable
-        mma_commit(&sh.bfree[qb]);    // B slices reusable
-        if (chunk_end(k)) mma_commit(&sh.accfull);
-      }
-      mma_commit(&sh.done);
-    }
-  } else {
-    // ------------------------------------------------ split (warps 0-7)
-    // A (Q, into tensor memory): warp w covers lanes 32 (w % 4) .. + 31 (Q
-    // columns) for rows 32 (w / 4) .. + 31 (boxes 2 (w / 4), 2 (w / 4) + 1);
-    // B (X, into the shared-memory slices): warp w covers rows 8 w .. 8 w + 7
-    // (one 16-byte K chunk) of all 32 columns, lane = column.
-    const int m = (warp & 3) * 32 + lane;    // Q column m0 + m
-    const int half = warp >> 2;
-    const int eM = (m0 + m < M) ? eq[m0 + m] : -4000;
-    const int eN = (n0 + lane < N) ? ex[n0 + lane] : -4000;
-    const uint32_t tlane = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16);
-    for (int k = 0; k < nk; ++k) {
-      const int qx = k % kXStages;
-      bool bad = failed();
-      if (!bad) {
-        const bool ok =
-            mbar_wait(&sh.qfull, static_cast<uint32_t>(k & 1)) &&
-            mbar_wait(&sh.xfull[qx], static_cast<uint32_t>((k / kXStages) & 1)) &&
-            (k == 0 || mbar_wait(&sh.afree, static_cast<uint32_t>((k - 1) & 1))) &&
-            (k < kXStages ||
-             mbar_wait(&sh.bfree[qx], static_cast<uint32_t>(((k / kXStages) - 1) & 1)));
-        if (!ok) {
-          sh.fail = 1;
-          bad = true;
-        }
-      }
-      if (__any_sync(0xffffffffu, bad)) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // B: rows 8 warp .. + 7 of column `lane` (box warp / 2, chunks 4 (warp
-      // % 2) .. + 3 of its 128-byte line, chunk j at (j ^ (lane & 7)))
-      {
-        const unsigned char* line = stX(qx) + (warp >> 1) * kXBox + lane * 128;
-        uint32_t pk[kDig][4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int jj = 4 * (warp & 1) + j;
-          const double2 v = *reinterpret_cast<const double2*>(line + ((jj ^ (lane & 7)) << 4));
-          uint32_t h0[kDig], h1[kDig];
-          digit_bits(scaled62(v.x, eN), h0);
-          digit_bits(scaled62(v.y, eN), h1);
-#pragma unroll
-          for (int t = 0; t < kDig; ++t) pk[t][j] = pack2(h0[t], h1[t]);
-        }
-        unsigned char* bs = stB(qx);
-#pragma unroll
-        for (int t = 0; t < kDig; ++t) {
-          unsigned char* row = bs + t * kBSlice + (lane >> 3) * 1024 + (lane & 7) * 128;
-          *reinterpret_cast<uint4*>(row + ((warp ^ (lane & 7)) << 4)) =
-              make_uint4(pk[t][0], pk[t][1], pk[t][2], pk[t][3]);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      }
-      mbar_arrive(&sh.xfree[qx]);
-      mbar_arrive(&sh.bfull[qx]);
-      // A: column m's rows in this warp's two boxes; box b's chunk j (rows
-      // 16b+2j, +1) becomes tensor-memory column 8b+j of each slice (two
-      // BF16 digits, the lower row in the low half)
-#pragma unroll 1
-      for (int bb = 0; bb < 2; ++bb) {
-        const int b = 2 * half + bb;
-        const unsigned char* line = stQ + b * kQBox + m * 128;
-        uint32_t words[kDig][8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const double2 v = *reinterpret_cast<const double2*>(line + ((j ^ (m & 7)) << 4));
-          uint32_t h0[kDig], h1[kDig];
-          digit_bits(scaled62(v.x, eM), h0);
-          digit_bits(scaled62(v.y, eM), h1);
-#pragma unroll
-          for (int t = 0; t < kDig; ++t) words[t][j] = pack2(h0[t], h1[t]);
-        }
-#pragma unroll
-        for (int t = 0; t < kDig; ++t)
-          tmem_st8(tlane + kACol + static_cast<uint32_t>(32 * t + 8 * b), words[t]);
-      }
-      mbar_arrive(&sh.qfree);
-      tmem_st_wait();
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mbar_arrive(&sh.afull);
-      if (chunk_end(k) && !readout(k / kChunk)) break;
-    }
-  }
-  // (twice the limit: after a failure the MMA warp may first spend one
-  // limit on a step that never came)
-  if (warp < 4 && !mbar_wait(&sh.done, 0, 2 * kWaitNs)) sh.fail = 1;
-  __syncthreads();
-  const bool good = !sh.fail;
-  if (!good) {
-    if (tid == 0) atomicExch(err, 1);
-  } else if (warp < 8) {
-    const int gm = m0 + (warp & 3) * 32 + lane;
-    if (gm < M) {
-      double* P = part + static_cast<int64_t>(blockIdx.z) * M * N;
-      const int eM = eq[gm];
-#pragma unroll
-      for (int cc = 0; cc < kHalf; ++cc) {
-        const int gc = n0 + (warp >> 2) * kHalf + cc;
-        if (gc < N) {
-          // V' = ahi 2^32 + alo exactly as a 128-bit integer, then rounded
-          const int64_t carry = alo[cc] >> 32;               // floor division
-          const int64_t hi = ahi[cc] + carry;                 // V' = hi 2^32 + lo32
-          const uint32_t lo32 = static_cast<uint32_t>(alo[cc]);
-          const double v = ldexp(static_cast<double>(hi), 32) + static_cast<double>(lo32);
-          P[gm + static_cast<int64_t>(gc) * M] = (eM < -2000 || ex[gc] < -2000)
-                                                    ? 0.0
-                                                    : ldexp(v, eM + ex[gc] - 68);
-        }
-      }
-    }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (warp == 0) {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(kOTmemCols)
-                 : "memory");
-  }
-}
-
-// ---------------------------------------------------------------- update
-// X = beta X + alpha Q W on the tensor cores, exactly in the same sense.
-// Output (r, c) sums Q[r,k] W[k,c] over k; with Q's digits relative to its
-// column exponents e_k (as in the dot) and W' = W 2^(e_k) cut into digits
-// relative to W' column c's exponent g_c, every product of the sum carries
-// the one weight 2^(g_c - 124), so the level sums are exact as above.  The
-// digits are FP16 numbers here (integers of at most 8 bits are exact in
-// either 16-bit type; FP16's wider mantissa lets one packed subtraction
-// turn two digit bytes into two FP16 digits).
-// Tile: 128 rows (MMA M, tensor-memory lanes) x 32 columns of X (MMA N);
-// one CTA per SM walks the row tiles of one column tile in stages of 32
-// columns of Q (two MMA K steps), software-pipelined:
-//   * warp 8 (one lane) loads each stage's Q box (128 rows x 32 columns,
-//     unswizzled: a row's values are 1 KB apart, so a warp reads 32
-//     consecutive rows conflict-free) into a two-deep ring, and each
-//     tile's X box for the epilogue;
-//   * warps 0-7 cut stage q into one of two tensor-memory A buffers while
-//     warp 9 (one lane) runs stage q-1's 72 digit-pair MMAs from the other;
-//     W' is cut once per CTA into shared-memory B slices (one 32 KB group
-//     of eight slices per 64 columns of Q, i <= 256);
-//   * level sums are read every four stages (128 columns of Q) and at the
-//     end of a tile, one stage late so that the split of the next stage
-//     overlaps the last MMAs; the epilogue writes beta X + alpha V 2^(g_c-68)
-//     from the prefetched X box.
-// K steps that lie wholly beyond column i are not issued.
-constexpr int kUM = 128;
-constexpr int kUN = 32;
-constexpr int kUS = 32;                                 // columns of Q per stage
-constexpr int kUMaxK = 256;
-constexpr int kUBox = kUM * kUS * 8;                    // 32 KB: a Q stage or the X tile
-constexpr int kUBChunk = kDig * kBSlice;                // 32 KB per 64 columns of Q
-constexpr uint32_t kUACol = 256;                        // A buffer b: 256 + 128 b
-
-// per-column tables after the W' slices: Q's column exponents e_k, W'
-// column exponents g_c
-struct OzUTables {
-  int eq[kUMaxK];
-  int g[kUN];
-};
-
-struct __align__(8) OzUShared {
-  uint64_t qfull[2], qfree[2], afull[2], afree[2];
-  uint64_t accfull, accfree, xfull, xfree, done;
-  uint32_t tmem_base;
-  int fail;
-};
-
-// dynamic shared memory: Q ring, X box, W' slices, tables, barriers (all of
-// it dynamic, so the 1 KB alignment slack fits under the 227 KB limit)
-int oz_update_smem(int i) {
-  return 3 * kUBox + ((i + 63) / 64) * kUBChunk + static_cast<int>(sizeof(OzUTables)) +
-         static_cast<int>(sizeof(OzUShared)) + 1024;
 }
 
 __device__ __forceinline__ uint32_t f16x2_sub(uint32_t a, uint32_t b) {
@@ -616,6 +231,324 @@ __device__ __forceinline__ double int96_to_double(int64_t hi, uint32_t lo, int e
 constexpr int kUWarps = 16;                    // split / readout / epilogue warps
 constexpr int kUThreads = (kUWarps + 2) * 32;  // + warp 16 TMA, warp 17 MMA
 constexpr int kUSplit = kUWarps * 32;
+
+// grid: (tiles of 128 Q columns, tiles of 32 X columns, splits)
+__global__ void __launch_bounds__(kDThreads, 1)
+oz_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
+              const __grid_constant__ CUtensorMap mapX, int64_t n, int M, int N,
+              const int* __restrict__ eq, const int* __restrict__ ex, int64_t rows_per_split,
+              double* __restrict__ part, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char dsmem[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+  const int m0 = blockIdx.x * kOM;
+  const int n0 = blockIdx.y * kON;
+  const int64_t k0 = static_cast<int64_t>(blockIdx.z) * rows_per_split;
+  const int64_t k1 = (k0 + rows_per_split < n) ? k0 + rows_per_split : n;
+  const int nk = static_cast<int>((k1 - k0 + kOK - 1) / kOK);
+  const uint32_t idesc = idesc_f16(kOM, kON);
+  auto stQ = [&](int b) { return base + b * kQBytes; };
+  auto stX = [&](int b) { return base + 2 * kQBytes + b * kXBytes; };
+  auto stB = [&](int b) { return base + 2 * (kQBytes + kXBytes) + b * kBBytes; };
+  OzShared& sh = *reinterpret_cast<OzShared*>(base + 2 * (kQBytes + kXBytes + kBBytes));
+  auto failed = [&]() { return *reinterpret_cast<volatile int*>(&sh.fail) != 0; };
+  auto group_end = [&](int k) { return (k % kChunk) == kChunk - 1 || k == nk - 1; };
+
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sh.qfull[b], 1);
+      mbar_init(&sh.qfree[b], kDSplit);
+      mbar_init(&sh.afull[b], kDSplit);
+      mbar_init(&sh.afree[b], 1);
+    }
+    mbar_init(&sh.accfull, 1);
+    mbar_init(&sh.accfree, kDSplit);
+    mbar_init(&sh.done, 1);
+    sh.fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&sh.tmem_base)),
+                 "r"(kOTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = sh.tmem_base;
+
+  // per-thread sums of 8 outputs (warp w reads tensor-memory lanes
+  // 32 (w % 4) .. + 31 = Q columns, and X columns 8 (w / 4) .. + 7), each
+  // as two int64 halves: ahi = sum of S_L 256^(3-L) over levels L = 0..3,
+  // alo = sum of S_L 256^(7-L) over L = 4..7 (|S_L| < 2^24, so each half
+  // grows by < 2^50 per readout and stays exact for 2^12 readouts), and
+  // the output's V' = ahi 2^32 + alo
+  constexpr int kCols = kON / 4;
+  const int cg = warp >> 2;
+  int64_t alo[kCols];
+  int64_t ahi[kCols];
+#pragma unroll
+  for (int c = 0; c < kCols; ++c) { alo[c] = 0; ahi[c] = 0; }
+  auto readout = [&](int k) -> bool {
+    if (!mbar_wait(&sh.accfull, static_cast<uint32_t>((k / kChunk) & 1))) sh.fail = 1;
+    if (__any_sync(0xffffffffu, failed())) return false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tl = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) +
+                        static_cast<uint32_t>(cg * kCols);
+#pragma unroll
+    for (int L = 0; L < kLev; ++L) {
+      uint32_t v[kCols];
+      tmem_ld8(tl + kAccCol + static_cast<uint32_t>(32 * L), v);
+#pragma unroll
+      for (int cc = 0; cc < kCols; ++cc) {
+        const int64_t sv = level_int(v[cc]);
+        if (L < 4) ahi[cc] += sv * (int64_t(1) << (8 * (3 - L)));
+        else alo[cc] += sv * (int64_t(1) << (8 * (7 - L)));
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    mbar_arrive(&sh.accfree);
+    return true;
+  };
+
+  if (warp == kDWarps) {
+    // ------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int nq0 = 0, nq1 = 0;
+      for (int k = 0; k < nk; ++k) {
+        if (failed()) break;
+        const int b = k & 1;
+        if (k >= 2 && !mbar_wait(&sh.qfree[b], static_cast<uint32_t>(((k >> 1) - 1) & 1))) {
+          sh.fail = 1;
+          break;
+        }
+        const int x = static_cast<int>(k0 + static_cast<int64_t>(k) * kOK);
+        mbar_expect_tx(&sh.qfull[b], static_cast<uint32_t>(kQBytes + kXBytes));
+        for (int bx = 0; bx < kOK / 16; ++bx) {
+          tma_load_2d(stQ(b) + bx * kQBox, &mapQ, &sh.qfull[b], x + 16 * bx, m0);
+          tma_load_2d(stX(b) + bx * kXBox, &mapX, &sh.qfull[b], x + 16 * bx, n0);
+        }
+        if (b) ++nq1; else ++nq0;
+      }
+      if (failed()) {
+        // drain this CTA's copies in flight (at most one stage per buffer)
+        if (nq0 > 0) mbar_wait(&sh.qfull[0], static_cast<uint32_t>((nq0 - 1) & 1));
+        if (nq1 > 0) mbar_wait(&sh.qfull[1], static_cast<uint32_t>((nq1 - 1) & 1));
+      }
+    }
+  } else if (warp == kDWarps + 1) {
+    // ------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int grp = 0;
+      for (int k = 0; k < nk; ++k) {
+        if (failed()) break;
+        const int b = k & 1;
+        const bool fresh = (k % kChunk) == 0;
+        if (!mbar_wait(&sh.afull[b], static_cast<uint32_t>((k >> 1) & 1)) ||
+            (fresh && grp > 0 && !mbar_wait(&sh.accfree, static_cast<uint32_t>((grp - 1) & 1)))) {
+          sh.fail = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t bbase = smem_u32(stB(b));
+#pragma unroll 1
+        for (int kk = 0; kk < kOK / 16; ++kk) {
+          bool seen[kLev] = {false, false, false, false, false, false, false, false};
+#pragma unroll
+          for (int t = 0; t < kDig; ++t) {
+#pragma unroll
+            for (int u = 0; u < kDig; ++u) {
+              if (t + u > kLev - 1) continue;     // level (t+1)+(u+1) <= 9
+              const int L = t + u;
+              const uint32_t acc = (!fresh || kk > 0 || seen[L]) ? 1u : 0u;
+              seen[L] = true;
+              const uint64_t bd = sdesc(bbase + static_cast<uint32_t>(u * kBSlice)) +
+                                  static_cast<uint64_t>((kk * 32) >> 4);
+              mma_bf16_tmem_a(tmem + kAccCol + static_cast<uint32_t>(32 * L),
+                              tmem + kDACol + static_cast<uint32_t>(128 * b + 16 * t + 8 * kk),
+                              bd, idesc, acc);
+            }
+          }
+        }
+        mma_commit(&sh.afree[b]);     // A and B buffers b reusable
+        if (group_end(k)) {
+          mma_commit(&sh.accfull);
+          ++grp;
+        }
+      }
+      mma_commit(&sh.done);
+    }
+  } else {
+    // ------------------------------------------------ split, readout
+    // A (Q, into tensor memory): warp w covers lanes 32 (w % 4) .. + 31 (Q
+    // columns) for the stage's rows 8 (w / 4) .. + 7 (box (w / 4) / 2,
+    // chunks 4 ((w / 4) % 2) .. + 3 of the column's 128-byte line);
+    // B (X, into shared-memory slices): warp w takes rows 2w, 2w + 1 of all
+    // 32 columns (box w / 8, chunk w % 8), lane = column.
+    const int m = (warp & 3) * 32 + lane;    // Q column m0 + m
+    const int eM = (m0 + m < M) ? eq[m0 + m] : -4000;
+    const int eN = (n0 + lane < N) ? ex[n0 + lane] : -4000;
+    const uint32_t tlane = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16);
+    int pend = -1;
+    bool stop = false;
+    for (int k = 0; k < nk; ++k) {
+      const int b = k & 1;
+      bool bad = failed();
+      if (!bad) {
+        const bool ok = mbar_wait(&sh.qfull[b], static_cast<uint32_t>((k >> 1) & 1)) &&
+                        (k < 2 || mbar_wait(&sh.afree[b], static_cast<uint32_t>(((k >> 1) - 1) & 1)));
+        if (!ok) {
+          sh.fail = 1;
+          bad = true;
+        }
+      }
+      if (__any_sync(0xffffffffu, bad)) {
+        stop = true;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      {
+        // B: rows 2w, 2w + 1 of X column `lane`, one FP16 pair per digit at
+        // K offset 2w of the column's 128-byte swizzled row
+        const unsigned char* line = stX(b) + (warp >> 3) * kXBox + lane * 128;
+        const double2 v = *reinterpret_cast<const double2*>(line + (((warp & 7) ^ (lane & 7)) << 4));
+        uint32_t d8[kDig];
+        digits_f16x2(scaled62(v.x, eN), scaled62(v.y, eN), d8);
+        unsigned char* bs = stB(b) + (lane >> 3) * 1024 + (lane & 7) * 128 + (warp & 3) * 4;
+        const int chunk = (warp >> 2) ^ (lane & 7);
+#pragma unroll
+        for (int t = 0; t < kDig; ++t)
+          *reinterpret_cast<uint32_t*>(bs + t * kBSlice + (chunk << 4)) = d8[t];
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      }
+      {
+        // A: column m's rows 8 cg .. + 7: box cg / 2, chunks 4 (cg % 2) + j
+        // (rows 2j, 2j + 1 of the box) -> tensor-memory column 4 cg + j of
+        // each digit slice of buffer b
+        const unsigned char* line = stQ(b) + (cg >> 1) * kQBox + m * 128;
+        uint32_t words[kDig][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int jj = 4 * (cg & 1) + j;
+          const double2 v = *reinterpret_cast<const double2*>(line + ((jj ^ (m & 7)) << 4));
+          uint32_t d8[kDig];
+          digits_f16x2(scaled62(v.x, eM), scaled62(v.y, eM), d8);
+#pragma unroll
+          for (int t = 0; t < kDig; ++t) words[t][j] = d8[t];
+        }
+#pragma unroll
+        for (int t = 0; t < kDig; ++t)
+          tmem_st4(tlane + kDACol + static_cast<uint32_t>(128 * b + 16 * t + 4 * cg), words[t]);
+      }
+      mbar_arrive(&sh.qfree[b]);
+      tmem_st_wait();
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&sh.afull[b]);
+      if (pend >= 0) {
+        if (!readout(pend)) {
+          stop = true;
+          break;
+        }
+        pend = -1;
+      }
+      if (group_end(k)) pend = k;
+    }
+    if (!stop && pend >= 0) readout(pend);
+  }
+  // (twice the limit: after a failure the MMA warp may first spend one
+  // limit on a step that never came)
+  if (warp < 4 && !mbar_wait(&sh.done, 0, 2 * kWaitNs)) sh.fail = 1;
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  const bool good = !sh.fail;
+  if (!good) {
+    if (tid == 0) atomicExch(err, 1);
+  } else if (warp < kDWarps) {
+    const int gm = m0 + (warp & 3) * 32 + lane;
+    if (gm < M) {
+      double* P = part + static_cast<int64_t>(blockIdx.z) * M * N;
+      const int eM = eq[gm];
+#pragma unroll
+      for (int cc = 0; cc < kCols; ++cc) {
+        const int gc = n0 + cg * kCols + cc;
+        if (gc < N) {
+          // V' = (ahi + carry) 2^32 + the low 32 bits of alo, rounded once
+          const int64_t hi = ahi[cc] + (alo[cc] >> 32);
+          const uint32_t lo = static_cast<uint32_t>(alo[cc]);
+          P[gm + static_cast<int64_t>(gc) * M] =
+              (eM < -2000 || ex[gc] < -2000) ? 0.0 : int96_to_double(hi, lo, eM + ex[gc] - 68);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kOTmemCols)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------- update
+// X = beta X + alpha Q W on the tensor cores, exactly in the same sense.
+// Output (r, c) sums Q[r,k] W[k,c] over k; with Q's digits relative to its
+// column exponents e_k (as in the dot) and W' = W 2^(e_k) cut into digits
+// relative to W' column c's exponent g_c, every product of the sum carries
+// the one weight 2^(g_c - 124), so the level sums are exact as above.  The
+// digits are FP16 numbers here (integers of at most 8 bits are exact in
+// either 16-bit type; FP16's wider mantissa lets one packed subtraction
+// turn two digit bytes into two FP16 digits).
+// Tile: 128 rows (MMA M, tensor-memory lanes) x 32 columns of X (MMA N);
+// one CTA per SM walks the row tiles of one column tile in stages of 32
+// columns of Q (two MMA K steps), software-pipelined:
+//   * warp 8 (one lane) loads each stage's Q box (128 rows x 32 columns,
+//     unswizzled: a row's values are 1 KB apart, so a warp reads 32
+//     consecutive rows conflict-free) into a two-deep ring, and each
+//     tile's X box for the epilogue;
+//   * warps 0-7 cut stage q into one of two tensor-memory A buffers while
+//     warp 9 (one lane) runs stage q-1's 72 digit-pair MMAs from the other;
+//     W' is cut once per CTA into shared-memory B slices (one 32 KB group
+//     of eight slices per 64 columns of Q, i <= 256);
+//   * level sums are read every four stages (128 columns of Q) and at the
+//     end of a tile, one stage late so that the split of the next stage
+//     overlaps the last MMAs; the epilogue writes beta X + alpha V 2^(g_c-68)
+//     from the prefetched X box.
+// K steps that lie wholly beyond column i are not issued.
+constexpr int kUM = 128;
+constexpr int kUN = 32;
+constexpr int kUS = 32;                                 // columns of Q per stage
+constexpr int kUMaxK = 256;
+constexpr int kUBox = kUM * kUS * 8;                    // 32 KB: a Q stage or the X tile
+constexpr int kUBChunk = kDig * kBSlice;                // 32 KB per 64 columns of Q
+constexpr uint32_t kUACol = 256;                        // A buffer b: 256 + 128 b
+
+// per-column tables after the W' slices: Q's column exponents e_k, W'
+// column exponents g_c
+struct OzUTables {
+  int eq[kUMaxK];
+  int g[kUN];
+};
+
+struct __align__(8) OzUShared {
+  uint64_t qfull[2], qfree[2], afull[2], afree[2];
+  uint64_t accfull, accfree, xfull, xfree, done;
+  uint32_t tmem_base;
+  int fail;
+};
+
+// dynamic shared memory: Q ring, X box, W' slices, tables, barriers (all of
+// it dynamic, so the 1 KB alignment slack fits under the 227 KB limit)
+int oz_update_smem(int i) {
+  return 3 * kUBox + ((i + 63) / 64) * kUBChunk + static_cast<int>(sizeof(OzUTables)) +
+         static_cast<int>(sizeof(OzUShared)) + 1024;
+}
 
 // grid: (tiles of 32 X columns, row groups); row tiles g, g + G, ...
 __global__ void __launch_bounds__(kUThreads, 1)
@@ -1065,17 +998,19 @@ bool oz_dot_supported(int64_t n, const double* Q, int64_t ldq, int i, const doub
 }
 
 // Whether the tensor-core form is expected to beat the FP64-pipe kernel:
-// a tile of 128 x 32 outputs costs about kStageUs per 64 rows on one SM,
-// the FP64 pipe sustains about 1 TFLOP/s (2 n i s flops; the symmetric
-// Gram n s (s+1)).
+// a tile of 128 x 32 outputs costs about kStageUs per 32 rows on one SM
+// (measured 3.4 .. 4.0 us over i = 6 .. 240), the FP64-pipe kernels about
+// 1 TFLOP/s (2 n i s flops; the symmetric Gram n s (s+1)) plus their
+// streams of Q and X at about 2 TB/s.
 bool oz_dot_pays(int64_t n, int i, int s, bool sym) {
-  constexpr double kStageUs = 10.5;
+  constexpr double kStageUs = 3.9;
   const double tiles = static_cast<double>((i + kOM - 1) / kOM) * ((s + kON - 1) / kON);
   const double t_oz = static_cast<double>((n + kOK - 1) / kOK) * tiles * kStageUs * 1e-6 /
                       static_cast<double>(device_sm_count());
   const double flops = sym ? static_cast<double>(n) * s * (s + 1.0)
                            : 2.0 * static_cast<double>(n) * i * s;
-  return t_oz < 0.8 * flops / 1.0e12;
+  const double bytes = static_cast<double>(n) * (sym ? s : i + s) * 8.0;
+  return t_oz < 0.9 * (flops / 1.0e12 + bytes / 2.0e12);
 }
 
 int64_t oz_dot_part_size(int64_t n, int i, int s) {
@@ -1166,7 +1101,7 @@ void oz_dot(int64_t n, const double* Q, int64_t ldq, int i, const double* X, int
              "cuTensorMapEncodeTiled failed");
   ensure_dynamic_smem(reinterpret_cast<const void*>(oz_dot_kernel), kOzSmem);
   dim3 grid((i + kOM - 1) / kOM, (s + kON - 1) / kON, static_cast<unsigned>(S));
-  oz_dot_kernel<<<grid, kOThreads, kOzSmem, st>>>(mq, mx, n, i, s, eq, ex, rows, part, err);
+  oz_dot_kernel<<<grid, kDThreads, kOzSmem, st>>>(mq, mx, n, i, s, eq, ex, rows, part, err);
   SG_LAUNCH_CHECK();
   *nsplit = static_cast<int>(S);
 }
