@@ -999,14 +999,17 @@ bool oz_dot_supported(int64_t n, const double* Q, int64_t ldq, int i, const doub
 
 // Whether the tensor-core form is expected to beat the FP64-pipe kernel:
 // a tile of 128 x 32 outputs costs about kStageUs per 32 rows on one SM
-// (measured 3.4 .. 4.0 us over i = 6 .. 240), the FP64-pipe kernels about
+// (measured 3.4 .. 4.0 us over i = 6 .. 240) plus kFixedUs of setup (the
+// exponent and reduction launches, barriers, tensor memory), the FP64-pipe
+// kernels about
 // 1 TFLOP/s (2 n i s flops; the symmetric Gram n s (s+1)) plus their
 // streams of Q and X at about 2 TB/s.
 bool oz_dot_pays(int64_t n, int i, int s, bool sym) {
-  constexpr double kStageUs = 3.9;
+  constexpr double kStageUs = 3.9, kFixedUs = 15.0;
   const double tiles = static_cast<double>((i + kOM - 1) / kOM) * ((s + kON - 1) / kON);
-  const double t_oz = static_cast<double>((n + kOK - 1) / kOK) * tiles * kStageUs * 1e-6 /
-                      static_cast<double>(device_sm_count());
+  const double t_oz = (static_cast<double>((n + kOK - 1) / kOK) * tiles * kStageUs /
+                           static_cast<double>(device_sm_count()) +
+                       kFixedUs) * 1e-6;
   const double flops = sym ? static_cast<double>(n) * s * (s + 1.0)
                            : 2.0 * static_cast<double>(n) * i * s;
   const double bytes = static_cast<double>(n) * (sym ? s : i + s) * 8.0;
@@ -1031,12 +1034,13 @@ bool oz_update_supported(int64_t n, const double* Q, int64_t ldq, int i, const d
 // Whether the tensor-core update is expected to beat the FP64-pipe kernel.
 // One SM takes ceil(row tiles / row groups) tiles of 128 rows x 32 columns,
 // each about kTileUs (readout, epilogue, pipeline fill) plus kStepUs per
-// 16 columns of Q (measured: 7.9 us at 1 step, 18.5 us at 7, 33.5 us at 15).
+// 16 columns of Q (measured: 7.9 us at 1 step, 18.5 us at 7, 33.5 us at 15),
+// plus kFixedUs of setup (the exponent launch, W's digits, tensor memory).
 // The FP64-pipe kernels sustain about 1.05 TFLOP/s (2 n i s flops, half
 // for the triangle); the tiled one adds its streams of Q and X at about
 // 2 TB/s, the narrow-Q one (i <= 16) overlaps them at about 5.5 TB/s.
 bool oz_update_pays(int64_t n, int i, int s, bool upper) {
-  constexpr double kTileUs = 7.0, kStepUs = 1.75;
+  constexpr double kTileUs = 7.0, kStepUs = 1.75, kFixedUs = 15.0;
   const int64_t ct = (s + kUN - 1) / kUN;
   const int64_t ntiles = (n + kUM - 1) / kUM;
   int64_t G = static_cast<int64_t>(device_sm_count()) / ct;
@@ -1044,7 +1048,7 @@ bool oz_update_pays(int64_t n, int i, int s, bool upper) {
   if (G > ntiles) G = ntiles;
   const double per_sm = static_cast<double>((ntiles + G - 1) / G) *
                         ((ct + device_sm_count() - 1) / device_sm_count());
-  const double t_oz = per_sm * (kTileUs + kStepUs * ((i + 15) / 16)) * 1e-6;
+  const double t_oz = (per_sm * (kTileUs + kStepUs * ((i + 15) / 16)) + kFixedUs) * 1e-6;
   const double flops = (upper ? 1.0 : 2.0) * static_cast<double>(n) * i * s;
   const double bytes = static_cast<double>(n) * (i + 2.0 * s) * 8.0;
   const double t_fp64 = i <= 16 ? std::max(flops / 1.05e12, bytes / 5.5e12)
