@@ -33,22 +33,29 @@ __device__ double block_sum_d(double v) {
 }
 
 // Sum over a large block with few FP64 instructions (the FP64 pipe is the
-// scarce one on this chip): every thread parks its value in shared memory,
-// then one warp adds THREADS / 32 values per lane in index order and
-// combines the lanes with shuffles.  Every thread receives the result.
+// scarce one on this chip: one warp instruction holds a scheduler's FP64
+// unit for 64 cycles): every thread parks its value in shared memory, then
+// four warps -- one per scheduler -- each add THREADS / 128 values per lane
+// in index order and combine their lanes with shuffles, and one thread adds
+// the four quarters in order.  Every thread receives the result.
 template <int THREADS>
 __device__ double block_sum_few_d(double v) {
+  static_assert(THREADS % 128 == 0, "four warps share the values");
   __shared__ double park[THREADS];
+  __shared__ double quarter[4];
   __shared__ double total;
   park[threadIdx.x] = v;
   __syncthreads();
-  if (threadIdx.x < 32) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (w < 4) {
     double t = 0.0;
-#pragma unroll 8
-    for (int i = threadIdx.x; i < THREADS; i += 32) t += park[i];
+#pragma unroll
+    for (int k = 0; k < THREADS / 128; ++k) t += park[w * (THREADS / 4) + l + 32 * k];
     t = warp_sum_d<THREADS>(t);
-    if (threadIdx.x == 0) total = t;
+    if (l == 0) quarter[w] = t;
   }
+  __syncthreads();
+  if (threadIdx.x == 0) total = ((quarter[0] + quarter[1]) + quarter[2]) + quarter[3];
   __syncthreads();
   return total;
 }
