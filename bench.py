@@ -201,9 +201,24 @@ def make_workload(name, rows=None):
 
 
 def spmv_bytes(A):
-    """Algorithmic bytes of one FP64 SpMV: values + indices, row pointers,
-    x read once, y written once."""
-    return 12 * A.nnz + 4 * (A.n + 1) + 8 * A.n + 8 * A.n
+    """Bytes of one FP64 SpMV in the stored format: values + column indices
+    (2-byte offsets from a per-32-row-slice base when every slice's columns
+    span fewer than 65535, as the library stores them, else 4 bytes), row or
+    slice pointers, x read once, y written once."""
+    rp = np.asarray(A.rowptr, dtype=np.int64)
+    ci = np.asarray(A.colind, dtype=np.int64)
+    nsl = (A.n + 31) // 32
+    first = rp[np.minimum(np.arange(nsl) * 32, A.n)]
+    last = rp[np.minimum(np.arange(nsl) * 32 + 32, A.n)]
+    lo = np.full(nsl, np.iinfo(np.int64).max)
+    hi = np.full(nsl, -1)
+    nz = last > first
+    sl = np.repeat(np.arange(nsl), last - first)
+    np.minimum.at(lo, sl, ci)
+    np.maximum.at(hi, sl, ci)
+    narrow = bool(np.all((hi[nz] - lo[nz]) < 0xFFFF))
+    idx = 2 if narrow else 4
+    return (8 + idx) * A.nnz + (8 if narrow else 4) * (nsl + 1) + 8 * A.n + 8 * A.n
 
 
 def mgs_flops(A, k):

@@ -134,15 +134,64 @@ __device__ __forceinline__ T sell_row(const int* __restrict__ sptr,
   return sum;
 }
 
-template <int MODE, bool HAS_Z, typename T>
+// The same chunk with the columns as 16-bit offsets from the slice's base
+// (0xFFFF: padding).
+template <int U, typename T>
+__device__ __forceinline__ void sell_chunk16(int base, const uint16_t* __restrict__ soff,
+                                             const T* __restrict__ sval,
+                                             const T* __restrict__ x, int k, T& sum) {
+  unsigned o[U];
+  T v[U], xv[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    o[u] = __ldcs(soff + k + 32 * u);
+    v[u] = ld_stream(sval + k + 32 * u);
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) xv[u] = o[u] != 0xFFFFu ? __ldg(x + base + static_cast<int>(o[u])) : T(0);
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+    if (o[u] != 0xFFFFu) sum = fma(v[u], xv[u], sum);
+}
+
+template <typename T>
+__device__ __forceinline__ T sell_row16(const int* __restrict__ sptr, const int* __restrict__ sbase,
+                                        const uint16_t* __restrict__ soff,
+                                        const T* __restrict__ sval, const T* __restrict__ x,
+                                        int64_t row) {
+  const int64_t q = row >> 5;
+  const int a = sptr[q], e = sptr[q + 1];
+  const int w = (e - a) >> 5;
+  const int base = sbase[q];
+  int k = a + static_cast<int>(row & 31);
+  T sum = T(0);
+  int j = 0;
+  for (; j + 8 <= w; j += 8, k += 256) sell_chunk16<8>(base, soff, sval, x, k, sum);
+  switch (w - j) {
+    case 7: sell_chunk16<7>(base, soff, sval, x, k, sum); break;
+    case 6: sell_chunk16<6>(base, soff, sval, x, k, sum); break;
+    case 5: sell_chunk16<5>(base, soff, sval, x, k, sum); break;
+    case 4: sell_chunk16<4>(base, soff, sval, x, k, sum); break;
+    case 3: sell_chunk16<3>(base, soff, sval, x, k, sum); break;
+    case 2: sell_chunk16<2>(base, soff, sval, x, k, sum); break;
+    case 1: sell_chunk16<1>(base, soff, sval, x, k, sum); break;
+    default: break;
+  }
+  return sum;
+}
+
+// OFF16: columns from (sbase, soff) instead of scol.
+template <int MODE, bool HAS_Z, bool OFF16, typename T>
 __global__ void __launch_bounds__(kThreads)
 sell_kernel(int n, int64_t rows32, const int* __restrict__ sptr,
-            const int* __restrict__ scol, const T* __restrict__ sval,
+            const int* __restrict__ scol, const int* __restrict__ sbase,
+            const uint16_t* __restrict__ soff, const T* __restrict__ sval,
             const T* __restrict__ x, const T* __restrict__ z,
             T* __restrict__ y, T theta, T c, T inv_gamma) {
   for (int64_t row = blockIdx.x * static_cast<int64_t>(kThreads) + threadIdx.x; row < rows32;
        row += static_cast<int64_t>(gridDim.x) * kThreads) {
-    const T sum = sell_row(sptr, scol, sval, x, row);
+    const T sum = OFF16 ? sell_row16(sptr, sbase, soff, sval, x, row)
+                        : sell_row(sptr, scol, sval, x, row);
     if (row < n) {
       if (MODE == 1) {
         y[row] = z[row] - sum;
@@ -180,8 +229,13 @@ void dispatch(const DevCsr& A, const T* val, const T* sval, const T* x, const T*
     int64_t blocks = (rows32 + kThreads - 1) / kThreads;
     const int64_t cap = static_cast<int64_t>(device_sm_count()) * 64;
     if (blocks > cap) blocks = cap;
-    sell_kernel<MODE, HAS_Z, T><<<static_cast<int>(blocks < 1 ? 1 : blocks), kThreads, 0, st>>>(
-        A.n, rows32, A.sptr, A.scol, sval, x, z, y, theta, c, T(1) / gamma);
+    const int g = static_cast<int>(blocks < 1 ? 1 : blocks);
+    if (A.soff)
+      sell_kernel<MODE, HAS_Z, true, T><<<g, kThreads, 0, st>>>(
+          A.n, rows32, A.sptr, A.scol, A.sbase, A.soff, sval, x, z, y, theta, c, T(1) / gamma);
+    else
+      sell_kernel<MODE, HAS_Z, false, T><<<g, kThreads, 0, st>>>(
+          A.n, rows32, A.sptr, A.scol, A.sbase, A.soff, sval, x, z, y, theta, c, T(1) / gamma);
     SG_LAUNCH_CHECK();
     return;
   }
@@ -1271,16 +1325,88 @@ __global__ void sell_fill_kernel(int n, int64_t rows32, const int* __restrict__ 
   }
 }
 
+// per slice: the smallest stored column (0 for an all-padding slice), and
+// a flag when the slice's columns span 65535 or more
+__global__ void sell_base_kernel(int nslices, const int* __restrict__ sptr,
+                                 const int* __restrict__ scol, int* __restrict__ sbase,
+                                 int* __restrict__ wide) {
+  for (int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; q < nslices;
+       q += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    int lo = 0x7FFFFFFF, hi = -1;
+    for (int k = sptr[q]; k < sptr[q + 1]; ++k) {
+      const int c = scol[k];
+      if (c >= 0) {
+        lo = min(lo, c);
+        hi = max(hi, c);
+      }
+    }
+    if (hi < 0) lo = hi = 0;
+    sbase[q] = lo;
+    if (hi - lo >= 0xFFFF) atomicOr(wide, 1);
+  }
+}
+
+// 16-bit offsets of every stored entry from its slice's base
+__global__ void sell_off_kernel(int64_t rows32, const int* __restrict__ sptr,
+                                const int* __restrict__ scol, const int* __restrict__ sbase,
+                                uint16_t* __restrict__ soff) {
+  for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < rows32;
+       r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t q = r >> 5;
+    const int w = (sptr[q + 1] - sptr[q]) >> 5;
+    const int b = sbase[q];
+    for (int j = 0; j < w; ++j) {
+      const int k = sptr[q] + static_cast<int>(r & 31) + 32 * j;
+      const int c = scol[k];
+      soff[k] = c >= 0 ? static_cast<uint16_t>(c - b) : static_cast<uint16_t>(0xFFFF);
+    }
+  }
+}
+
 void free_sell(DevCsr& A) {
   if (A.sptr) cudaFree(A.sptr);
   if (A.scol) cudaFree(A.scol);
   if (A.sval) cudaFree(A.sval);
   if (A.sval32) cudaFree(A.sval32);
-  A.sptr = A.scol = nullptr;
+  if (A.sbase) cudaFree(A.sbase);
+  if (A.soff) cudaFree(A.soff);
+  A.sptr = A.scol = A.sbase = nullptr;
+  A.soff = nullptr;
   A.sval = nullptr;
   A.sval32 = nullptr;
   A.nslices = 0;
   A.sell_nnz = 0;
+}
+
+// The 16-bit column offsets when every slice fits them; left null otherwise.
+void build_sell_offsets(DevCsr& A, cudaStream_t st) {
+  int* wide = nullptr;
+  SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&wide), sizeof(int)));
+  int hwide = 0;
+  try {
+    SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&A.sbase), sizeof(int) * A.nslices));
+    SG_CUDA(cudaMemsetAsync(wide, 0, sizeof(int), st));
+    sell_base_kernel<<<device_sm_count() * 8, kThreads, 0, st>>>(A.nslices, A.sptr, A.scol,
+                                                                 A.sbase, wide);
+    SG_LAUNCH_CHECK();
+    SG_CUDA(cudaMemcpyAsync(&hwide, wide, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SG_CUDA(cudaStreamSynchronize(st));
+    if (!hwide) {
+      SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&A.soff), sizeof(uint16_t) * A.sell_nnz));
+      sell_off_kernel<<<device_sm_count() * 8, kThreads, 0, st>>>(
+          static_cast<int64_t>(A.nslices) * 32, A.sptr, A.scol, A.sbase, A.soff);
+      SG_LAUNCH_CHECK();
+      SG_CUDA(cudaStreamSynchronize(st));
+    }
+  } catch (...) {
+    cudaFree(wide);
+    throw;
+  }
+  cudaFree(wide);
+  if (!A.soff) {
+    cudaFree(A.sbase);
+    A.sbase = nullptr;
+  }
 }
 
 }  // namespace
@@ -1324,6 +1450,7 @@ void build_sell(DevCsr& A, cudaStream_t st) {
         A.n, rows32, A.rowptr, A.colind, A.val, A.sptr, A.scol, A.sval);
     SG_LAUNCH_CHECK();
     SG_CUDA(cudaStreamSynchronize(st));  // the host offsets go out of scope
+    build_sell_offsets(A, st);
   } catch (...) {
     free_sell(A);
     throw;

@@ -57,6 +57,8 @@ void free_csr(sg::DevCsr& A) {
   if (A.scol) cudaFree(A.scol);
   if (A.sval) cudaFree(A.sval);
   if (A.sval32) cudaFree(A.sval32);
+  if (A.sbase) cudaFree(A.sbase);
+  if (A.soff) cudaFree(A.soff);
   A = sg::DevCsr();
 }
 

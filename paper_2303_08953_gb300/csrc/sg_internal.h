@@ -56,6 +56,11 @@ struct DevCsr {
   int32_t* scol = nullptr;
   double* sval = nullptr;
   float* sval32 = nullptr;
+  // The same columns as 16-bit offsets from each slice's smallest column
+  // (0xFFFF marks padding), built when every slice spans fewer than 65535
+  // columns: the SpMV then streams 10 bytes per stored entry instead of 12.
+  int32_t* sbase = nullptr;  // nslices
+  uint16_t* soff = nullptr;
 };
 
 // Build A's SELL-32 copy from its CSR arrays (kept when the padded size is
