@@ -42,6 +42,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 
 #include "k_tc_common.cuh"
@@ -956,6 +957,12 @@ bool make_map64_box(CUtensorMap* map, const double* ptr, int64_t rows, int64_t c
          CUDA_SUCCESS;
 }
 
+// Launches of this file's tensor-core kernels since the last check: the
+// check reads the device's error flag (a synchronising copy) only after
+// one.  The flag stays set until read, so a timeout is reported by a later
+// check even if another thread's check consumed the count.
+std::atomic<int> oz_check_error_pending{0};
+
 int* oz_err_flag() {
   static int* ptr[64] = {};
   static std::mutex mu;
@@ -1074,9 +1081,11 @@ void oz_update(int64_t n, const double* Q, int64_t ldq, int i, const double* W, 
   oz_update_kernel<<<grid, kUThreads, oz_update_smem(i), st>>>(
       mq, mx, n, i, s, W, ldw, X, ldx, alpha, beta, upper ? 1 : 0, exps, err);
   SG_LAUNCH_CHECK();
+  oz_check_error_pending.fetch_add(1);
 }
 
 void oz_check_error(cudaStream_t st) {
+  if (oz_check_error_pending.exchange(0) == 0) return;
   int* f = oz_err_flag();
   int host = 0;
   SG_CUDA(cudaMemcpyAsync(&host, f, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1107,6 +1116,7 @@ void oz_dot(int64_t n, const double* Q, int64_t ldq, int i, const double* X, int
   dim3 grid((i + kOM - 1) / kOM, (s + kON - 1) / kON, static_cast<unsigned>(S));
   oz_dot_kernel<<<grid, kDThreads, kOzSmem, st>>>(mq, mx, n, i, s, eq, ex, rows, part, err);
   SG_LAUNCH_CHECK();
+  oz_check_error_pending.fetch_add(1);
   *nsplit = static_cast<int>(S);
 }
 

@@ -31,6 +31,7 @@
 //     split partial; the fixed-order split reduction is the SIMT path's.
 // Every wait is bounded: on timeout the kernel records an error code,
 // drains its own copies, frees its tensor memory and returns.
+#include <atomic>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -380,6 +381,12 @@ int64_t tc_dot_part_size(int64_t n, int i, int s) {
   return S * i * s;
 }
 
+// Launches of this file's tensor-core kernels since the last check: the
+// check reads the device's error flag (a synchronising copy) only after
+// one.  The flag stays set until read, so a timeout is reported by a later
+// check even if another thread's check consumed the count.
+std::atomic<int> tc_check_error_pending{0};
+
 int* tc_err_flag() {
   static int* ptr[64] = {};
   static std::mutex mu;
@@ -396,6 +403,7 @@ int* tc_err_flag() {
 }
 
 void tc_check_error(cudaStream_t st) {
+  if (tc_check_error_pending.exchange(0) == 0) return;
   int* f = tc_err_flag();
   int host = 0;
   SG_CUDA(cudaMemcpyAsync(&host, f, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -432,6 +440,7 @@ void tc_dot(int64_t n, const float* Q, int64_t ldq, int i, const float* X, int64
   ensure_dynamic_smem(reinterpret_cast<const void*>(tc_dot_kernel), smem);
   dim3 grid(tiles, 1, static_cast<unsigned>(S));
   tc_dot_kernel<<<grid, kThreads, smem, st>>>(mq, mx, n, i, s, BN, rows, part, err);
+  tc_check_error_pending.fetch_add(1);
   SG_LAUNCH_CHECK();
   *nsplit = static_cast<int>(S);
 }

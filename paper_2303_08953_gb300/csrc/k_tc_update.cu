@@ -30,6 +30,7 @@
 //   of the epilogue threads' dependent loads.
 // Every wait is time-bounded; a timeout records an error flag, the roles
 // stop, in-flight copies and MMAs are drained and the TMEM is freed.
+#include <atomic>
 #include <cudaTypedefs.h>
 
 #include <mutex>
@@ -374,6 +375,12 @@ bool make_map(CUtensorMap* map, const float* base, int64_t inner, int64_t outer,
          CUDA_SUCCESS;
 }
 
+// Launches of this file's tensor-core kernels since the last check: the
+// check reads the device's error flag (a synchronising copy) only after
+// one.  The flag stays set until read, so a timeout is reported by a later
+// check even if another thread's check consumed the count.
+std::atomic<int> tc_update_check_error_pending{0};
+
 int* err_flag() {
   static int* ptr[64] = {};
   static std::mutex mu;
@@ -439,10 +446,12 @@ void tc_update(int64_t n, const float* Q, int64_t ldq, int i, const double* W, i
   tc_update_kernel<<<grid, kThreads, smem, st>>>(mq, mh, ml, mx, n, i, s, BN,
                                                   static_cast<float>(alpha),
                                                   static_cast<float>(beta), nst, wres, err_flag());
+  tc_update_check_error_pending.fetch_add(1);
   SG_LAUNCH_CHECK();
 }
 
 void tc_update_check_error(cudaStream_t st) {
+  if (tc_update_check_error_pending.exchange(0) == 0) return;
   int* f = err_flag();
   int host = 0;
   SG_CUDA(cudaMemcpyAsync(&host, f, sizeof(int), cudaMemcpyDeviceToHost, st));
