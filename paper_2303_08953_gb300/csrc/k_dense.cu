@@ -149,6 +149,62 @@ dot_tile_kernel(int64_t K, int M, int N, const T* __restrict__ A,
     }
 }
 
+// Small FP64 products (8 < i, i s <= 256, or the upper triangle of a Gram
+// with s (s + 1) / 2 <= 256): one thread per needed output -- a padded tile
+// would issue FP64 instructions for idle lanes, which cost the same pipe
+// time on this chip -- and only as many warps as there are outputs.  Each
+// block stages BK rows of Q and X in shared memory per step and adds its
+// row split's products in row order; the splits are reduced in a fixed
+// order afterwards (the lower triangle of a Gram is not written).
+constexpr int kSmallOut = 256;
+constexpr int kSmallCols = 160;   // M + N: the staged rows fit 48 KB of shared memory
+
+__global__ void __launch_bounds__(kSmallOut)
+dot_small_kernel(int64_t K, int M, int N, const double* __restrict__ A, int64_t lda,
+                 const double* __restrict__ B, int64_t ldb, double* __restrict__ part,
+                 int64_t rows_per_split, int sym) {
+  extern __shared__ double small_smem[];
+  double* As = small_smem;                     // BK x (M + 1)
+  double* Bs = small_smem + BK * (M + 1);      // BK x (N + 1)
+  const int64_t k0 = blockIdx.x * rows_per_split;
+  const int64_t k1 = (k0 + rows_per_split < K) ? k0 + rows_per_split : K;
+  const int tid = threadIdx.x;
+  const int nout = sym ? N * (N + 1) / 2 : M * N;
+  // this thread's output (a, b): row-major over (a, b) with b fastest;
+  // for the Gram, the upper triangle a <= b row by row
+  int a = 0, b = 0;
+  if (sym) {
+    int t = tid, row = 0;
+    while (row < N && t >= N - row) { t -= N - row; ++row; }
+    a = row;
+    b = row + t;
+  } else {
+    a = tid / N;
+    b = tid % N;
+  }
+  const bool live = tid < nout;
+  double acc = 0.0;
+  for (int64_t kb = k0; kb < k1; kb += BK) {
+    for (int e = tid; e < BK * M; e += blockDim.x) {
+      const int kk = e % BK, mm = e / BK;
+      const int64_t k = kb + kk;
+      As[kk * (M + 1) + mm] = k < k1 ? A[k + mm * lda] : 0.0;
+    }
+    for (int e = tid; e < BK * N; e += blockDim.x) {
+      const int kk = e % BK, nn = e / BK;
+      const int64_t k = kb + kk;
+      Bs[kk * (N + 1) + nn] = k < k1 ? B[k + nn * ldb] : 0.0;
+    }
+    __syncthreads();
+    if (live) {
+#pragma unroll 8
+      for (int kk = 0; kk < BK; ++kk) acc = fma(As[kk * (M + 1) + a], Bs[kk * (N + 1) + b], acc);
+    }
+    __syncthreads();
+  }
+  if (live) part[static_cast<int64_t>(blockIdx.x) * M * N + a + static_cast<int64_t>(b) * M] = acc;
+}
+
 // W(m, n) = sum_z part[z](m, n); sym reads the upper element for both
 // (m, n) and (n, m).  One warp per output: lane l adds splits l, l+32, ...
 // in order, then a fixed xor-shuffle tree combines the lanes, so the
@@ -401,6 +457,30 @@ void block_dot_impl(int64_t n, const T* Q, int64_t ldq, int i, const T* X,
     oz_dot(n, reinterpret_cast<const double*>(Q), ldq, i, reinterpret_cast<const double*>(X),
            ldx, s, reinterpret_cast<int*>(part + need), part, need, &S, st);
     launch_reduce(i, s, S, part, W, ldw, false, st);
+    return;
+  }
+  if (sizeof(T) == 8 && i + s <= kSmallCols &&
+      (sym && i == s ? s * (s + 1) / 2 <= kSmallOut : (i > 8 && i * s <= kSmallOut))) {
+    // small FP64 products: one thread per needed output (a Q of at most
+    // eight columns keeps the narrow tile, whose idle rows are whole warps)
+    const bool tri = sym && i == s;
+    const int nout = tri ? s * (s + 1) / 2 : i * s;
+    const int threads = (nout + 31) / 32 * 32;
+    int64_t S = static_cast<int64_t>(device_sm_count()) * (2048 / threads);
+    const int64_t maxS = (n + 4 * BK - 1) / (4 * BK);
+    if (S > maxS) S = maxS;
+    if (S < 1) S = 1;
+    if (S * i * s > part_cap) S = part_cap / (static_cast<int64_t>(i) * s);
+    SG_REQUIRE(S >= 1, SG_EINVAL, "block_dot: workspace too small");
+    int64_t rows = (n + S - 1) / S;
+    rows = (rows + BK - 1) / BK * BK;
+    S = (n + rows - 1) / rows;
+    const size_t smem = sizeof(double) * BK * (i + 1 + s + 1);
+    dot_small_kernel<<<static_cast<unsigned>(S), threads, smem, st>>>(
+        n, i, s, reinterpret_cast<const double*>(Q), ldq, reinterpret_cast<const double*>(X),
+        ldx, part, rows, tri ? 1 : 0);
+    SG_LAUNCH_CHECK();
+    launch_reduce(i, s, static_cast<int>(S), part, W, ldw, tri, st);
     return;
   }
   if (sizeof(T) == 4 && !sym && !tc_disabled() &&

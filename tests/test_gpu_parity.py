@@ -162,7 +162,7 @@ def tc_always():
 
 
 @pytest.mark.parametrize("n", [1, 97, 4133, 70001])
-@pytest.mark.parametrize("i,s", [(1, 1), (1, 120), (5, 7), (8, 33), (9, 32),
+@pytest.mark.parametrize("i,s", [(1, 1), (1, 120), (5, 7), (13, 12), (8, 33), (9, 32),
                                  (33, 65), (121, 120), (241, 17)])
 def test_block_dot_matches_definition(solver, tc_path, n, i, s):
     rng = np.random.default_rng(100 * i + s)
@@ -217,7 +217,8 @@ def test_block_dot_fp64_tensor_cores_exact_on_integers(solver, tc_always, n, i, 
     assert np.array_equal(G, X @ X.T)
 
 
-@pytest.mark.parametrize("n,s", [(4133, 1), (4133, 31), (70001, 64), (3001, 120)])
+@pytest.mark.parametrize("n,s", [(4133, 1), (70001, 12), (4133, 21), (4133, 31), (70001, 64),
+                                 (3001, 120)])
 def test_block_dot_symmetric_gram(solver, tc_path, n, s):
     rng = np.random.default_rng(s)
     X = rng.standard_normal((s, n))
