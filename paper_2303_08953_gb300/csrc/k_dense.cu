@@ -687,18 +687,27 @@ update_thin_kernel(int64_t n, int i, int s, const T* __restrict__ Q, int64_t ldq
   }
   __syncthreads();
   const T a = static_cast<T>(alpha), b = static_cast<T>(beta);
+  // the triangular form needs k <= c only; the bound is the same for a
+  // whole warp, and the loops leave at it (predicated FP64 instructions
+  // would still take their pipe time)
+  auto kend = [&](int c) { return upper ? (c0 + c + 1 < i ? c0 + c + 1 : i) : i; };
   auto out = [&](const T* q, int c, T x) -> T {
+    const int ke = kend(c);
     if (MODE == 1) {
       T v = x;
 #pragma unroll
-      for (int k = 0; k < MAXI; ++k)
-        if (k < i) v = fma(-q[k], Ws[k][c], v);
+      for (int k = 0; k < MAXI; ++k) {
+        if (k >= ke) break;
+        v = fma(-q[k], Ws[k][c], v);
+      }
       return v;
     }
     T acc = T(0);
 #pragma unroll
-    for (int k = 0; k < MAXI; ++k)
-      if (k < i) acc = (k == 0) ? q[0] * Ws[0][c] : fma(q[k], Ws[k][c], acc);
+    for (int k = 0; k < MAXI; ++k) {
+      if (k >= ke) break;
+      acc = (k == 0) ? q[0] * Ws[0][c] : fma(q[k], Ws[k][c], acc);
+    }
     if (MODE == 2) return alpha == 1.0 ? acc : a * acc;
     const T v = a * acc;
     return beta != 0.0 ? fma(b, x, v) : v;
@@ -755,6 +764,8 @@ void launch_update_thin(int64_t n, const T* Q, int64_t ldq, int i, const double*
     launch_update_thin_i<4, T>(grid, n, Q, ldq, i, W, ldw, X, ldx, s, alpha, beta, up, st);
   else if (i <= 8)
     launch_update_thin_i<8, T>(grid, n, Q, ldq, i, W, ldw, X, ldx, s, alpha, beta, up, st);
+  else if (i <= 12)
+    launch_update_thin_i<12, T>(grid, n, Q, ldq, i, W, ldw, X, ldx, s, alpha, beta, up, st);
   else
     launch_update_thin_i<16, T>(grid, n, Q, ldq, i, W, ldw, X, ldx, s, alpha, beta, up, st);
   SG_LAUNCH_CHECK();
