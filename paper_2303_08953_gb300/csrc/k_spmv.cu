@@ -939,6 +939,9 @@ arnoldi_step_icwy_kernel(int n, const int* __restrict__ rowptr,
       const int k = lane + 32 * m;
       dr[m] = k < ncols ? dk[k] : 0.0;
     }
+    // the row groups m past the basis are left by a warp-uniform break:
+    // predicated FP64 instructions would still take their pipe time
+    const int mused = (ncols + 31) / 32;
     for (int q = 0; q < ncols; ++q) {
       double mine = dr[0];
 #pragma unroll
@@ -948,6 +951,7 @@ arnoldi_step_icwy_kernel(int n, const int* __restrict__ rowptr,
       if (lane == 0) hk[q] = hq;
 #pragma unroll
       for (int m = 0; m < kM; ++m) {
+        if (m >= mused) break;
         const int k = lane + 32 * m;
         if (k > q && k < ncols) dr[m] = fma(-tri[ic_tri(k) + q], hq, dr[m]);
       }
