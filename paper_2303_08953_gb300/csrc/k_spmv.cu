@@ -769,16 +769,14 @@ arnoldi_step_grouped_kernel(int n, int rows_per_cta, const int* __restrict__ row
 // The Gram matrix is stored packed by rows (row k at k(k-1)/2) in global
 // memory for the later steps and staged in shared memory before pass A.
 constexpr int kIcChunk = 4096;                 // rows per staged chunk
-constexpr int kIcSeg = 512;                    // rows per dot unit (16 per lane)
-constexpr int kIcNSeg = kIcChunk / kIcSeg;     // units per column per chunk
 constexpr int kIcMaxCols = 161;                // basis vectors v_0..v_j per step
 
 __host__ __device__ constexpr int ic_tri(int ncols) { return ncols * (ncols - 1) / 2; }
 
-// dynamic shared memory: sw, sv (chunk), unit slots, Gram triangle, d, h,
+// dynamic shared memory: sw, sv (chunk), column sums, Gram triangle, d, h,
 // two scalars, -h in FP32
 __host__ __device__ constexpr size_t ic_smem_bytes(int ncols) {
-  return sizeof(float) * 2 * kIcChunk + sizeof(float) * 2 * ncols * kIcNSeg +
+  return sizeof(float) * 2 * kIcChunk + sizeof(double) * 2 * ncols +
          sizeof(double) * (ic_tri(ncols) + 2 * ncols + 8) + sizeof(float) * ncols;
 }
 
@@ -802,8 +800,8 @@ arnoldi_step_icwy_kernel(int n, const int* __restrict__ rowptr,
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   float* sw = reinterpret_cast<float*>(coop_smem);
   float* sv = sw + kIcChunk;
-  float* slots = sv + kIcChunk;  // [unit][2]: partial v_q.w, v_q.v_j
-  double* tri = reinterpret_cast<double*>(slots + 2 * ncols * kIcNSeg);
+  double* slots = reinterpret_cast<double*>(sv + kIcChunk);  // [q][2]: v_q.w, v_q.v_j
+  double* tri = slots + 2 * ncols;
   double* dk = tri + ic_tri(ncols);
   double* hk = dk + ncols;
   double* misc = hk + ncols;  // [0]: ||A v_j||^2, [1]: ||w||^2 after projection
@@ -824,7 +822,7 @@ arnoldi_step_icwy_kernel(int n, const int* __restrict__ rowptr,
 
   // the Gram rows of the earlier steps (read during pass A's latency)
   for (int e = t; e < ic_tri(j); e += kCoopThreads) tri[e] = gram[e];
-  for (int e = t; e < 2 * ncols * kIcNSeg; e += kCoopThreads) slots[e] = 0.0f;
+  for (int e = t; e < 2 * ncols; e += kCoopThreads) slots[e] = 0.0;
 
   // ------------------------------------------------------------ pass A
   float accww = 0.0f;
@@ -847,59 +845,51 @@ arnoldi_step_icwy_kernel(int n, const int* __restrict__ rowptr,
       accww = fmaf(sum, sum, accww);
     }
     __syncthreads();
-    // units (q, g): 512 rows of column q; unit u always belongs to warp
-    // u % 32, so its slot is summed in chunk order
-    for (int u = warp; u < ncols * kIcNSeg; u += 32) {
-      const int q = u / kIcNSeg, g = u % kIcNSeg;
-      const int base = g * kIcSeg;
-      if (base >= len) continue;
+    // column q of the chunk belongs to warp q % 32: lane l adds the rows
+    // 4 l + 128 it in FP32 (eight float4 loads in flight), the lanes are
+    // combined by shuffles, and the chunk's sum is added in FP64 in chunk
+    // order
+    for (int q = warp; q < ncols; q += 32) {
       const float* vq = V + static_cast<int64_t>(q) * ld + c0;
       float d = 0.0f, gm = 0.0f;
-      if (base + kIcSeg <= len) {
-        float4 a[4];
+      if (len == kIcChunk) {
+#pragma unroll 1
+        for (int it0 = 0; it0 < kIcChunk / 128; it0 += 8) {
+          float4 a[8];
 #pragma unroll
-        for (int it = 0; it < 4; ++it)
-          a[it] = *reinterpret_cast<const float4*>(vq + base + it * 128 + lane * 4);
+          for (int u = 0; u < 8; ++u)
+            a[u] = *reinterpret_cast<const float4*>(vq + (it0 + u) * 128 + lane * 4);
 #pragma unroll
-        for (int it = 0; it < 4; ++it) {
-          const int r = base + it * 128 + lane * 4;
-          const float4 x = *reinterpret_cast<const float4*>(sw + r);
-          const float4 y = *reinterpret_cast<const float4*>(sv + r);
-          d = fmaf(a[it].x, x.x, d); d = fmaf(a[it].y, x.y, d);
-          d = fmaf(a[it].z, x.z, d); d = fmaf(a[it].w, x.w, d);
-          gm = fmaf(a[it].x, y.x, gm); gm = fmaf(a[it].y, y.y, gm);
-          gm = fmaf(a[it].z, y.z, gm); gm = fmaf(a[it].w, y.w, gm);
+          for (int u = 0; u < 8; ++u) {
+            const int r = (it0 + u) * 128 + lane * 4;
+            const float4 x = *reinterpret_cast<const float4*>(sw + r);
+            const float4 y = *reinterpret_cast<const float4*>(sv + r);
+            d = fmaf(a[u].x, x.x, d); d = fmaf(a[u].y, x.y, d);
+            d = fmaf(a[u].z, x.z, d); d = fmaf(a[u].w, x.w, d);
+            gm = fmaf(a[u].x, y.x, gm); gm = fmaf(a[u].y, y.y, gm);
+            gm = fmaf(a[u].z, y.z, gm); gm = fmaf(a[u].w, y.w, gm);
+          }
         }
       } else {
-        for (int it = 0; it < 4; ++it)
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int r = base + it * 128 + lane * 4 + e;
-            if (r < len) {
-              const float a = vq[r];
-              d = fmaf(a, sw[r], d);
-              gm = fmaf(a, sv[r], gm);
-            }
-          }
+        for (int r = lane; r < len; r += 32) {
+          const float a = vq[r];
+          d = fmaf(a, sw[r], d);
+          gm = fmaf(a, sv[r], gm);
+        }
       }
       d = warp_sum_f(d);
       gm = warp_sum_f(gm);
       if (lane == 0) {
-        slots[2 * u] += d;
-        slots[2 * u + 1] += gm;
+        slots[2 * q] += static_cast<double>(d);
+        slots[2 * q + 1] += static_cast<double>(gm);
       }
     }
   }
-  // CTA partials: per column, the units in index order; ||A v_j||^2
+  // CTA partials: per column; ||A v_j||^2
   __syncthreads();
   for (int q = t; q < ncols; q += kCoopThreads) {
-    double d = 0.0, gm = 0.0;
-    for (int g = 0; g < kIcNSeg; ++g) {
-      d += static_cast<double>(slots[2 * (q * kIcNSeg + g)]);
-      gm += static_cast<double>(slots[2 * (q * kIcNSeg + g) + 1]);
-    }
-    pA[static_cast<int64_t>(blockIdx.x) * P + 2 * q] = d;
-    pA[static_cast<int64_t>(blockIdx.x) * P + 2 * q + 1] = gm;
+    pA[static_cast<int64_t>(blockIdx.x) * P + 2 * q] = slots[2 * q];
+    pA[static_cast<int64_t>(blockIdx.x) * P + 2 * q + 1] = slots[2 * q + 1];
   }
   {
     const float v = warp_sum_f(accww);
