@@ -238,7 +238,7 @@ def mgs_bytes(A, k):
 # vectors read at step j), from the ncu capture of step j = 58 at
 # 2,097,152 rows: 1,007,194,000 + 3,276,544 bytes over 60 vectors
 # (profiles/arnoldi_mgs_resident_fp64_randband_2M_j58.md).
-MGS_DRAM_BYTES_PER_ROW_VECTOR = (1_007_194_000 + 3_276_544) / 2_097_152 / 60
+MGS_DRAM_BYTES_PER_ROW_VECTOR = (1_006_732_000 + 3_225_344) / 2_097_152 / 60
 
 
 # ------------------------------------------------------------ CPU oracle
