@@ -30,9 +30,14 @@
 //     rows x 128 or 32 columns, 128-byte swizzled, so every thread reads
 //     its column conflict-free) into a two-deep ring;
 //   * warps 0-15 cut stage k into digits while warp 17 (one lane) runs
-//     stage k-1's 72 digit-pair MMAs: Q's into one of two tensor-memory A
-//     buffers (lane = Q column, two FP16 digits per 32-bit column), X's
-//     into one of two sets of 128-byte-swizzled shared-memory B slices;
+//     stage k-1's MMAs: Q's into one of two tensor-memory A buffers (lane
+//     = Q column, two FP16 digits per 32-bit column), X's into one of two
+//     sets of 128-byte-swizzled shared-memory B slices;
+//   * the eight B slices of a stage lie one after another along N, so one
+//     MMA of N = 32 (8 - t) multiplies A's digit t by B's digits 0 .. 7 - t
+//     and, written 32 t columns into the level sums, adds each pair (t, u)
+//     to level t + u: 8 MMAs per 16 rows form the 36 digit pairs of levels
+//     0 .. 7 (36 MMAs of N = 32 would issue the same tensor work);
 //     every four stages, one stage late, they read the level sums, eight
 //     output columns each.
 // Every wait is bounded: on timeout the kernel records an error, drains
@@ -69,6 +74,7 @@ constexpr int kXBox = 16 * kON * 8;           // 4 KB
 constexpr int kXBytes = (kOK / 16) * kXBox;   // 8 KB per stage
 constexpr int kBSlice = kON * 128;            // 32 rows x 64 FP16 (the stage fills 32): 4 KB
 constexpr int kBBytes = kDig * kBSlice;       // 32 KB
+static_assert(kLev == kDig, "one MMA per digit of A covers levels t .. kLev - 1");
 constexpr int kDWarps = 16;                   // split / readout warps
 constexpr int kDThreads = (kDWarps + 2) * 32; // + warp 16 TMA, warp 17 MMA
 constexpr int kDSplit = kDWarps * 32;
@@ -250,7 +256,6 @@ oz_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
   const int64_t k0 = static_cast<int64_t>(blockIdx.z) * rows_per_split;
   const int64_t k1 = (k0 + rows_per_split < n) ? k0 + rows_per_split : n;
   const int nk = static_cast<int>((k1 - k0 + kOK - 1) / kOK);
-  const uint32_t idesc = idesc_f16(kOM, kON);
   auto stQ = [&](int b) { return base + b * kQBytes; };
   auto stX = [&](int b) { return base + 2 * kQBytes + b * kXBytes; };
   auto stB = [&](int b) { return base + 2 * (kQBytes + kXBytes) + b * kBBytes; };
@@ -359,21 +364,17 @@ oz_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
         const uint32_t bbase = smem_u32(stB(b));
 #pragma unroll 1
         for (int kk = 0; kk < kOK / 16; ++kk) {
-          bool seen[kLev] = {false, false, false, false, false, false, false, false};
+          const uint64_t bd = sdesc(bbase) + static_cast<uint64_t>((kk * 32) >> 4);
 #pragma unroll
           for (int t = 0; t < kDig; ++t) {
-#pragma unroll
-            for (int u = 0; u < kDig; ++u) {
-              if (t + u > kLev - 1) continue;     // level (t+1)+(u+1) <= 9
-              const int L = t + u;
-              const uint32_t acc = (!fresh || kk > 0 || seen[L]) ? 1u : 0u;
-              seen[L] = true;
-              const uint64_t bd = sdesc(bbase + static_cast<uint32_t>(u * kBSlice)) +
-                                  static_cast<uint64_t>((kk * 32) >> 4);
-              mma_bf16_tmem_a(tmem + kAccCol + static_cast<uint32_t>(32 * L),
-                              tmem + kDACol + static_cast<uint32_t>(128 * b + 16 * t + 8 * kk),
-                              bd, idesc, acc);
-            }
+            // A's digit t against B's digits 0 .. 7 - t in one MMA: the B
+            // slices lie one after another along N, so output column
+            // 32 u + c holds the pair (t, u), which belongs to level t + u
+            // at accumulator column 32 (t + u) + c
+            const uint32_t acc = (!fresh || kk > 0 || t > 0) ? 1u : 0u;
+            mma_bf16_tmem_a(tmem + kAccCol + static_cast<uint32_t>(32 * t),
+                            tmem + kDACol + static_cast<uint32_t>(128 * b + 16 * t + 8 * kk),
+                            bd, idesc_f16(kOM, kON * (kLev - t)), acc);
           }
         }
         mma_commit(&sh.afree[b]);     // A and B buffers b reusable
@@ -509,12 +510,14 @@ oz_dot_kernel(const __grid_constant__ CUtensorMap mapQ,
 // Tile: 128 rows (MMA M, tensor-memory lanes) x 32 columns of X (MMA N);
 // one CTA per SM walks the row tiles of one column tile in stages of 32
 // columns of Q (two MMA K steps), software-pipelined:
-//   * warp 8 (one lane) loads each stage's Q box (128 rows x 32 columns,
+//   * warp 16 (one lane) loads each stage's Q box (128 rows x 32 columns,
 //     unswizzled: a row's values are 1 KB apart, so a warp reads 32
 //     consecutive rows conflict-free) into a two-deep ring, and each
 //     tile's X box for the epilogue;
-//   * warps 0-7 cut stage q into one of two tensor-memory A buffers while
-//     warp 9 (one lane) runs stage q-1's 72 digit-pair MMAs from the other;
+//   * warps 0-15 cut stage q into one of two tensor-memory A buffers while
+//     warp 17 (one lane) runs stage q-1's MMAs from the other (8 per 16
+//     columns of Q, one per digit of Q against the consecutive digit
+//     slices of W', as in the dot);
 //     W' is cut once per CTA into shared-memory B slices (one 32 KB group
 //     of eight slices per 64 columns of Q, i <= 256);
 //   * level sums are read every four stages (128 columns of Q) and at the
@@ -571,7 +574,6 @@ oz_update_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant
   const int nkc = (i + 63) / 64;                 // groups of W' slices
   const int gpt = (nsub + 3) / 4;                // level readouts per row tile
   const bool loadx = beta != 0.0;
-  const uint32_t idesc = idesc_f16(kUM, kUN);
   unsigned char* stX = base + 2 * kUBox;
   unsigned char* bsl = base + 3 * kUBox;
   OzUTables& tb = *reinterpret_cast<OzUTables*>(bsl + nkc * kUBChunk);
@@ -708,21 +710,15 @@ oz_update_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant
 #pragma unroll 1
         for (int kk = 0; kk < ksteps; ++kk) {
           const int kb = (kq & 1) * 2 + kk;                  // 16-column step of the 64
-          bool seen[kLev] = {false, false, false, false, false, false, false, false};
+          const uint64_t bd = sdesc(bbase) + static_cast<uint64_t>((kb * 32) >> 4);
 #pragma unroll
           for (int t = 0; t < kDig; ++t) {
-#pragma unroll
-            for (int u = 0; u < kDig; ++u) {
-              if (t + u > kLev - 1) continue;
-              const int L = t + u;
-              const uint32_t acc = (!fresh || kk > 0 || seen[L]) ? 1u : 0u;
-              seen[L] = true;
-              const uint64_t bd = sdesc(bbase + static_cast<uint32_t>(u * kBSlice)) +
-                                  static_cast<uint64_t>((kb * 32) >> 4);
-              mma_bf16_tmem_a(tmem + kAccCol + static_cast<uint32_t>(32 * L),
-                              tmem + kUACol + static_cast<uint32_t>(128 * b + 16 * t + 8 * kk), bd,
-                              idesc, acc);
-            }
+            // digit t of Q against W' digits 0 .. 7 - t (consecutive along
+            // N): levels t .. 7 in one MMA
+            const uint32_t acc = (!fresh || kk > 0 || t > 0) ? 1u : 0u;
+            mma_bf16_tmem_a(tmem + kAccCol + static_cast<uint32_t>(32 * t),
+                            tmem + kUACol + static_cast<uint32_t>(128 * b + 16 * t + 8 * kk), bd,
+                            idesc_f16(kUM, kUN * (kLev - t)), acc);
           }
         }
         mma_commit(&sh.afree[b]);
