@@ -874,20 +874,53 @@ oz_update_kernel(const __grid_constant__ CUtensorMap mapQ, const __grid_constant
 __global__ void __launch_bounds__(256)
 col_exponent_kernel(int64_t n, const double* __restrict__ X, int64_t ld, int64_t rows,
                     int* __restrict__ e) {
-  const double* col = X + static_cast<int64_t>(blockIdx.x) * ld;
+  // The largest |x| is found in integer arithmetic (the FP64 pipe would
+  // bound this kernel far below HBM speed): for finite doubles, |x| orders
+  // like its bit pattern with the sign cleared.  NaNs (patterns above that
+  // of infinity) are skipped, as fmax would skip them.
+  const uint64_t* col = reinterpret_cast<const uint64_t*>(X + static_cast<int64_t>(blockIdx.x) * ld);
   const int64_t r0 = static_cast<int64_t>(blockIdx.y) * rows;
   const int64_t r1 = (r0 + rows < n) ? r0 + rows : n;
-  double mx = 0.0;
-  for (int64_t r = r0 + threadIdx.x; r < r1; r += 256) mx = fmax(mx, fabs(col[r]));
+  constexpr uint64_t kMag = 0x7FFFFFFFFFFFFFFFull, kInf = 0x7FF0000000000000ull;
+  auto take = [&](uint64_t& mx, uint64_t b) {
+    b &= kMag;
+    if (b <= kInf && b > mx) mx = b;
+  };
+  uint64_t mx = 0;
+  int64_t r = r0;
+  // one element to reach a 16-byte boundary, pairs with four loads in
+  // flight per thread, one element of tail
+  if ((reinterpret_cast<uintptr_t>(col + r) & 15) && r < r1) {
+    if (threadIdx.x == 0) take(mx, __ldg(col + r));
+    ++r;
+  }
+  const ulonglong2* pr = reinterpret_cast<const ulonglong2*>(col + r);
+  const int64_t np = (r1 - r) / 2;
+  for (int64_t p = threadIdx.x; p < np; p += 4 * 256) {
+    ulonglong2 v[4];
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-  __shared__ double wm[8];
+    for (int u = 0; u < 4; ++u)
+      v[u] = (p + u * 256 < np) ? __ldg(pr + p + u * 256) : make_ulonglong2(0, 0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      take(mx, v[u].x);
+      take(mx, v[u].y);
+    }
+  }
+  if (((r1 - r) & 1) && threadIdx.x == 0) take(mx, __ldg(col + r1 - 1));
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const uint64_t o = __shfl_xor_sync(0xffffffffu, mx, off);
+    if (o > mx) mx = o;
+  }
+  __shared__ uint64_t wm[8];
   if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < 8; ++w) t = fmax(t, wm[w]);
-    if (t > 0.0) {
+    uint64_t tb = 0;
+    for (int w = 0; w < 8; ++w) tb = wm[w] > tb ? wm[w] : tb;
+    const double t = __longlong_as_double(static_cast<long long>(tb));
+    if (tb != 0) {
       int ee = 0;
       frexp(t, &ee);   // t = f 2^ee, f in [0.5, 1): |x| <= t < 2^ee
       atomicMax(e + blockIdx.x, ee);
