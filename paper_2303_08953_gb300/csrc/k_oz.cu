@@ -1035,13 +1035,13 @@ bool oz_dot_supported(int64_t n, const double* Q, int64_t ldq, int i, const doub
 
 // Whether the tensor-core form is expected to beat the FP64-pipe kernel:
 // a tile of 128 x 32 outputs costs about kStageUs per 32 rows on one SM
-// (measured 3.4 .. 4.0 us over i = 6 .. 240) plus kFixedUs of setup (the
+// (measured 2.2 .. 2.4 us over i = 13 .. 240) plus kFixedUs of setup (the
 // exponent and reduction launches, barriers, tensor memory), the FP64-pipe
 // kernels about
 // 1 TFLOP/s (2 n i s flops; the symmetric Gram n s (s+1)) plus their
 // streams of Q and X at about 2 TB/s.
 bool oz_dot_pays(int64_t n, int i, int s, bool sym) {
-  constexpr double kStageUs = 3.9, kFixedUs = 15.0;
+  constexpr double kStageUs = 2.4, kFixedUs = 15.0;
   const double tiles = static_cast<double>((i + kOM - 1) / kOM) * ((s + kON - 1) / kON);
   const double t_oz = (static_cast<double>((n + kOK - 1) / kOK) * tiles * kStageUs /
                            static_cast<double>(device_sm_count()) +
@@ -1070,13 +1070,13 @@ bool oz_update_supported(int64_t n, const double* Q, int64_t ldq, int i, const d
 // Whether the tensor-core update is expected to beat the FP64-pipe kernel.
 // One SM takes ceil(row tiles / row groups) tiles of 128 rows x 32 columns,
 // each about kTileUs (readout, epilogue, pipeline fill) plus kStepUs per
-// 16 columns of Q (measured: 7.9 us at 1 step, 18.5 us at 7, 33.5 us at 15),
+// 16 columns of Q (measured: 7.7 us at 1 step, 14.6 us at 7, 23.4 us at 15),
 // plus kFixedUs of setup (the exponent launch, W's digits, tensor memory).
 // The FP64-pipe kernels sustain about 1.05 TFLOP/s (2 n i s flops, half
 // for the triangle); the tiled one adds its streams of Q and X at about
 // 2 TB/s, the narrow-Q one (i <= 16) overlaps them at about 5.5 TB/s.
 bool oz_update_pays(int64_t n, int i, int s, bool upper) {
-  constexpr double kTileUs = 7.0, kStepUs = 1.75, kFixedUs = 15.0;
+  constexpr double kTileUs = 6.6, kStepUs = 1.12, kFixedUs = 15.0;
   const int64_t ct = (s + kUN - 1) / kUN;
   const int64_t ntiles = (n + kUM - 1) / kUM;
   int64_t G = static_cast<int64_t>(device_sm_count()) / ct;
