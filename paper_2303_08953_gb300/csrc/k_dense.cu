@@ -329,6 +329,16 @@ int gram_cta_threads(int s) {
   return t < kGramThreads ? t : kGramThreads;
 }
 
+// Expected time of gram_exact_kernel: every thread slot of the triangle's
+// parts (idle ones included) forms 16 exact products per row, about
+// 2.66e12 slot-products per second on the whole GPU (measured at n = 2^21,
+// s = 16 .. 128, within 10 % but for s = 16).
+double gram_exact_seconds(int64_t n, int s) {
+  const int T = gram_cta_threads(s);
+  const int parts = (gram_blocks(s) + T - 1) / T;
+  return static_cast<double>(n) * parts * T * 16.0 / 2.66e12;
+}
+
 // splits of the Gram kernel: as many CTAs as fit on the SMs at 80
 // registers a thread (up to 8 per SM), >= 4 slabs per split
 int64_t gram_splits(int64_t n, int s, int64_t* rows) {
@@ -491,6 +501,20 @@ void block_dot_impl(int64_t n, const T* Q, int64_t ldq, int i, const T* X,
     tc_dot(n, reinterpret_cast<const float*>(Q), ldq, i,
            reinterpret_cast<const float*>(X), ldx, s, part, part_cap, &S, st);
     launch_reduce(i, s, S, part, W, ldw, false, st);
+    return;
+  }
+  if (sizeof(T) == 4 && sym && i == s && !tc_disabled() &&
+      reinterpret_cast<const void*>(Q) == reinterpret_cast<const void*>(X) &&
+      oz_gram32_supported(n, reinterpret_cast<const float*>(X), ldx, s) &&
+      (tc_forced() || oz_gram32_seconds(n, s) < 0.9 * gram_exact_seconds(n, s))) {
+    // Gram of FP32 vectors on the tensor cores from exact digit slices; the
+    // column exponents sit after the split partials
+    const int64_t need = oz_gram32_part_size(n, s);
+    SG_REQUIRE(need + (s + 1) / 2 <= part_cap, SG_EINVAL, "block_dot: workspace too small");
+    int S = 0;
+    oz_gram32(n, reinterpret_cast<const float*>(X), ldx, s, reinterpret_cast<int*>(part + need),
+              part, need, &S, st);
+    launch_reduce(s, s, S, part, W, ldw, true, st);
     return;
   }
   if (sizeof(T) == 4 && sym && i == s && s <= kGramMaxS &&
@@ -855,7 +879,9 @@ int64_t block_dot_part_size(int64_t n, int i, int s) {
     }
   int64_t need = S * i * s;
   if (i == s && s <= kGramMaxS) {
-    const int64_t g = gram_splits(n, s, nullptr) * s * s;
+    int64_t g = gram_splits(n, s, nullptr) * s * s;
+    const int64_t g32 = oz_gram32_part_size(n, s) + (s + 1) / 2;
+    if (g32 > g) g = g32;
     if (g > need) need = g;
   }
   const int64_t tc = tc_dot_part_size(n, i, s);

@@ -45,6 +45,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <atomic>
@@ -1022,6 +1023,500 @@ int64_t oz_splits(int64_t n, int i, int s, int64_t* rows) {
   return (n + r - 1) / r;
 }
 
+// ------------------------------------------------------------- FP32 Gram
+// G = X^T X of the FP32 basis (the CholQR Gram of Alg. 4) on the tensor
+// cores, from exact digit slices as above.  A value x of column c is taken
+// relative to the column's exponent e_c (|x| < 2^e_c) as u = x 2^(6 - e_c),
+// |u| < 64, and cut in FP32 arithmetic into six balanced base-256 digits:
+// d_t = u rounded to the nearest integer, then u <- 256 (u - d_t).  Every
+// step is exact (u - d_t by Sterbenz, |u - d_t| <= 1/2, the scalings by
+// powers of two), so |d_0| <= 64, |d_t| <= 128 and
+//   x~ = 2^(e_c - 6) * sum_{t=0..5} d_t 256^-t,   |x~ - x| <= 2^(e_c - 47):
+// every value within 2^23 of its column's largest is exact.  The digit
+// pair (t, u) belongs to level t + u; levels 0..7 are formed (the pairs of
+// levels 8..10 add less than 2^-58 max|x_m| max|x_n| to a product).  A level
+// has at most six pairs, so its sum over 128 rows stays below
+// 6 * 128 * 2^14 < 2^24 and is exact in the MMA's FP32 accumulator.  Every
+// 128 rows the level sums are added into an exact integer per output
+// (levels 0..3 and 4..7 in two int64 halves), which is rounded once:
+//   G(m, n) = 2^(e_m + e_n - 68) * sum_l S_l 256^(7 - l)   (rounded to FP64).
+// Against the exact Gram the error is at most
+// 2^-46 (max|x_m| sum_k |x_kn| + max|x_n| sum_k |x_km|)
+//   + n 2^-58 max|x_m| max|x_n| + the final rounding:
+// the accuracy class of the exact-product SIMT kernel (about
+// 2^-46 ||x_m|| ||x_n|| for vectors without extreme dynamic range).
+//
+// Tile: all s <= 128 columns of X as MMA M (operand A) against 32 of them as
+// MMA N (operand B; quarter q = columns 32q .. 32q + 31), 32 rows per stage.
+// Only the upper triangle is needed, so quarter q cuts and reads out the
+// columns 0 .. 32q + 31 alone.  Both operands are digit slices in shared
+// memory, 64-byte lines (the 32 rows of a stage of one column, 64-byte
+// swizzled): A slice t holds the lines of columns 0..127, and the quarter's
+// own 32 lines of each digit are stored once more, digit after digit, as
+// the B slices (two more all-zero slices follow).  So one MMA of
+// N = 32 (8 - t) multiplies A's digit t by B's digits 0 .. 7 - t and,
+// written 32 t columns into the level sums, adds each pair (t, u) to level
+// t + u: six MMAs per 16 rows.  One CTA per SM (224 KB of shared memory):
+//   * warp 16 (one lane) loads each stage's columns 0 .. 32q + 31 (boxes of
+//     32 rows x 32 columns, 128-byte swizzled) into a six-deep ring (a stage
+//     is 4 to 16 KB, so the ring keeps enough bytes in flight to cover the
+//     latency of HBM);
+//   * warps 0-15 cut stage k into one of two sets of digit slices (one 16-byte store per
+//     digit: eight consecutive rows of one column, packed two digits per
+//     conversion) while warp 17 (one lane)
+//     issues stage k-1's MMAs;
+//   * the level sums alternate between two sets of tensor-memory columns
+//     (8 levels x 32 columns each), so the readout of one 128-row group
+//     overlaps the next group's MMAs.
+// Every wait is bounded, as in the kernels above.
+constexpr int kGK = 32;                         // rows per stage
+constexpr int kGN = 32;                         // output columns per CTA (MMA N)
+constexpr int kGMaxS = 128;                     // columns of X (MMA M)
+constexpr int kGDig = 6;                        // digit slices kept per value
+constexpr int kGLev = 8;                        // levels 0..7
+constexpr int kGChunk = 4;                      // stages per exact level sum
+constexpr int kGBox = kGK * kGN * 4;            // one 32 x 32 FP32 box: 4 KB
+constexpr int kGStageBytes = 4 * kGBox;         // columns 0..127 of a stage: 16 KB
+constexpr int kGSliceA = kGMaxS * 64;           // A: 128 lines of 64 bytes, 8 KB
+constexpr int kGSliceB = kGN * 64;              // B: 32 lines of 64 bytes, 2 KB
+constexpr int kGBSlices = 8;                    // B digits 0..5 and two zero slices
+constexpr int kGRing = 6;                       // staged stages in flight
+constexpr int kGAOff = 0;
+constexpr int kGBOff = kGAOff + kGDig * kGSliceA;
+constexpr int kGBuf = kGBOff + kGBSlices * kGSliceB;   // 64 KB per set of slices
+constexpr int kGSlicesOff = kGRing * kGStageBytes;     // after the staging ring
+constexpr uint32_t kGSetCol = 256;              // accumulator set a at column 256 a
+constexpr int kGNonFinite = 1 << 20;            // exponent of a column holding Inf or NaN
+static_assert(kGLev * kGN <= static_cast<int>(kGSetCol), "a set of level sums fits its columns");
+
+struct __align__(8) OzGShared {
+  uint64_t full[kGRing], sfree[kGRing], afull[2], afree[2];
+  uint64_t accfull[2], accfree[2], done;
+  uint32_t tmem_base;
+  int fail;
+};
+
+constexpr int kGSmem = kGSlicesOff + 2 * kGBuf + static_cast<int>(sizeof(OzGShared)) + 1024;
+static_assert(kGBuf % 1024 == 0 && kGBOff % 1024 == 0 && kGSlicesOff % 1024 == 0,
+              "staging boxes and slices start on 1024-byte boundaries");
+static_assert(kGSmem <= 232448, "fits the 227 KB of shared memory per CTA");
+
+__device__ __forceinline__ void mma_f16_ss(uint32_t dtmem, uint64_t a, uint64_t b,
+                                           uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle (lines
+// of 64 bytes, the 16-byte chunk c of line r stored at c ^ ((r >> 1) & 3)),
+// 8-line groups 512 bytes apart (slice bases aligned to 1024 bytes).
+__device__ __forceinline__ uint64_t sdesc64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= static_cast<uint64_t>(1) << 16;                 // leading byte offset (unused)
+  d |= static_cast<uint64_t>(512 >> 4) << 32;          // stride byte offset
+  d |= static_cast<uint64_t>(1) << 46;                 // descriptor version
+  d |= static_cast<uint64_t>(4) << 61;                 // 64-byte swizzle
+  return d;
+}
+
+// grid: (quarters of 32 output columns, splits of the rows)
+__global__ void __launch_bounds__(kDThreads, 1)
+oz_gram32_kernel(const __grid_constant__ CUtensorMap mapX, int64_t n, int s,
+                 const int* __restrict__ ex, int64_t rows_per_split,
+                 double* __restrict__ part, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char dsmem[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(dsmem) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+  const int q = blockIdx.x;
+  const int64_t k0 = static_cast<int64_t>(blockIdx.y) * rows_per_split;
+  const int64_t k1 = (k0 + rows_per_split < n) ? k0 + rows_per_split : n;
+  const int nk = static_cast<int>((k1 - k0 + kGK - 1) / kGK);
+  auto stage = [&](int r) { return base + r * kGStageBytes; };
+  auto sliceA = [&](int b, int t) { return base + kGSlicesOff + b * kGBuf + kGAOff + t * kGSliceA; };
+  auto sliceB = [&](int b, int u) { return base + kGSlicesOff + b * kGBuf + kGBOff + u * kGSliceB; };
+  OzGShared& sh = *reinterpret_cast<OzGShared*>(base + kGSlicesOff + 2 * kGBuf);
+  auto failed = [&]() { return *reinterpret_cast<volatile int*>(&sh.fail) != 0; };
+  auto group_end = [&](int k) { return (k % kGChunk) == kGChunk - 1 || k == nk - 1; };
+
+  if (tid == 0) {
+    for (int r = 0; r < kGRing; ++r) {
+      mbar_init(&sh.full[r], 1);
+      mbar_init(&sh.sfree[r], kDSplit);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sh.afull[b], kDSplit);
+      mbar_init(&sh.afree[b], 1);
+      mbar_init(&sh.accfull[b], 1);
+      mbar_init(&sh.accfree[b], kDSplit);
+    }
+    mbar_init(&sh.done, 1);
+    sh.fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&sh.tmem_base)),
+                 "r"(kOTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // never written: the A lines beyond column 32q + 31 (they feed MMA rows
+  // whose outputs are not read) and B slices 6 and 7; zero them once
+  if (warp < kDWarps) {
+    const int l0 = kGN * (q + 1);
+    const int per = (kGMaxS - l0) * 4;               // 16-byte words per A slice
+    for (int e = tid; e < 2 * kGDig * per; e += kDSplit) {
+      const int sl = e / per, w = e % per;
+      *reinterpret_cast<uint4*>(sliceA(sl / kGDig, sl % kGDig) + l0 * 64 + w * 16) =
+          make_uint4(0, 0, 0, 0);
+    }
+    constexpr int perB = (kGBSlices - kGDig) * kGSliceB / 16;
+    for (int e = tid; e < 2 * perB; e += kDSplit)
+      *reinterpret_cast<uint4*>(sliceB(e / perB, kGDig) + (e % perB) * 16) = make_uint4(0, 0, 0, 0);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = sh.tmem_base;
+
+  // warp w's lanes are the columns m = 32 (w % 4) + lane (tensor-memory
+  // lanes); it cuts rows 8 (w / 4) .. + 7 of each stage and owns the
+  // outputs (m, 32q + 8 (w / 4) + c), c < 8, each as two int64 halves:
+  // ahi = sum of S_l 256^(3-l) over l = 0..3, alo = sum of S_l 256^(7-l)
+  // over l = 4..7 (|S_l| < 2^24: each half grows by < 2^48.1 per readout and
+  // stays exact for 2^14 readouts); V = ahi 2^32 + alo
+  const int m = (warp & 3) * 32 + lane;
+  const int cg = warp >> 2;
+  const bool mine = (warp & 3) <= q;   // columns 32 (w % 4) .. + 31 are within 0 .. 32q + 31
+  int64_t alo[8];
+  int64_t ahi[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) { alo[c] = 0; ahi[c] = 0; }
+  auto readout = [&](int g) -> bool {
+    const int a = g & 1;
+    if (!mbar_wait(&sh.accfull[a], static_cast<uint32_t>((g >> 1) & 1))) sh.fail = 1;
+    if (__any_sync(0xffffffffu, failed())) return false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (mine) {
+      const uint32_t tl = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) +
+                          static_cast<uint32_t>(a) * kGSetCol + static_cast<uint32_t>(cg * 8);
+#pragma unroll
+      for (int L = 0; L < kGLev; ++L) {
+        uint32_t v[8];
+        tmem_ld8(tl + static_cast<uint32_t>(kGN * L), v);
+#pragma unroll
+        for (int cc = 0; cc < 8; ++cc) {
+          const int64_t sv = level_int(v[cc]);
+          if (L < 4) ahi[cc] += sv * (int64_t(1) << (8 * (3 - L)));
+          else alo[cc] += sv * (int64_t(1) << (8 * (7 - L)));
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    mbar_arrive(&sh.accfree[a]);
+    return true;
+  };
+
+  if (warp == kDWarps) {
+    // ------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int k = 0; k < nk; ++k) {
+        if (failed()) break;
+        const int r = k % kGRing;
+        if (k >= kGRing &&
+            !mbar_wait(&sh.sfree[r], static_cast<uint32_t>((k / kGRing - 1) & 1))) {
+          sh.fail = 1;
+          break;
+        }
+        const int x = static_cast<int>(k0 + static_cast<int64_t>(k) * kGK);
+        mbar_expect_tx(&sh.full[r], static_cast<uint32_t>((q + 1) * kGBox));
+        for (int c = 0; c <= q; ++c)
+          tma_load_2d(stage(r) + c * kGBox, &mapX, &sh.full[r], x, kGN * c);
+        issued = k + 1;
+      }
+      if (failed()) {
+        // drain this CTA's copies in flight: the last stage issued into each
+        // slot (stages issued - kGRing .. issued - 1)
+        for (int k = issued - kGRing > 0 ? issued - kGRing : 0; k < issued; ++k)
+          mbar_wait(&sh.full[k % kGRing], static_cast<uint32_t>((k / kGRing) & 1));
+      }
+    }
+  } else if (warp == kDWarps + 1) {
+    // ------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int grp = 0;
+      for (int k = 0; k < nk; ++k) {
+        if (failed()) break;
+        const int b = k & 1;
+        const uint32_t a = static_cast<uint32_t>(grp & 1);
+        const bool fresh = (k % kGChunk) == 0;
+        if (!mbar_wait(&sh.afull[b], static_cast<uint32_t>((k >> 1) & 1)) ||
+            (fresh && grp >= 2 &&
+             !mbar_wait(&sh.accfree[a], static_cast<uint32_t>(((grp >> 1) - 1) & 1)))) {
+          sh.fail = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint64_t bd0 = sdesc64(smem_u32(sliceB(b, 0)));
+#pragma unroll 1
+        for (int kk = 0; kk < kGK / 16; ++kk) {
+#pragma unroll
+          for (int t = 0; t < kGDig; ++t) {
+            // A's digit t against B's digits 0 .. 7 - t: output column
+            // 32 u + c holds the pair (t, u), level t + u at column
+            // 32 (t + u) + c of the set; the first MMA of a group (t = 0,
+            // all eight levels) starts the sums afresh
+            const uint64_t ad = sdesc64(smem_u32(sliceA(b, t))) + static_cast<uint64_t>((kk * 32) >> 4);
+            const uint32_t acc = (!fresh || kk > 0 || t > 0) ? 1u : 0u;
+            mma_f16_ss(tmem + a * kGSetCol + static_cast<uint32_t>(kGN * t), ad,
+                       bd0 + static_cast<uint64_t>((kk * 32) >> 4), idesc_f16(kGMaxS, kGN * (kGLev - t)),
+                       acc);
+          }
+        }
+        mma_commit(&sh.afree[b]);     // slices b reusable
+        if (group_end(k)) {
+          mma_commit(&sh.accfull[a]);
+          ++grp;
+        }
+      }
+      mma_commit(&sh.done);
+    }
+  } else {
+    // ------------------------------------------------ split, readout
+    const int em = (mine && m < s) ? ex[m] : -4000;
+    // u = x 2^(6 - e) as two exact power-of-two scalings, both factors
+    // normal; columns that are all zero, beyond s or hold an Inf or a NaN
+    // are cut as zeros
+    const bool live = em > -2000 && em < kGNonFinite;
+    const int eb = (live && em < -50) ? 64 : 0;
+    const float f1 = __int_as_float((127 + eb) << 23);
+    const float f2 = live ? __int_as_float((127 + 6 - em - eb) << 23) : 0.0f;
+    constexpr float kRound = 12582912.0f;   // 1.5 2^23: adding it rounds |v| < 2^22 to an integer
+    int pend = -1;
+    bool stop = false;
+    for (int k = 0; k < nk; ++k) {
+      const int b = k & 1;
+      const int r = k % kGRing;
+      bool bad = failed();
+      if (!bad) {
+        const bool ok = mbar_wait(&sh.full[r], static_cast<uint32_t>((k / kGRing) & 1)) &&
+                        (k < 2 || mbar_wait(&sh.afree[b], static_cast<uint32_t>(((k >> 1) - 1) & 1)));
+        if (!ok) {
+          sh.fail = 1;
+          bad = true;
+        }
+      }
+      if (__any_sync(0xffffffffu, bad)) {
+        stop = true;
+        break;
+      }
+      if (mine) {
+        // column m's rows 8 cg .. + 7: chunks 2 cg, 2 cg + 1 of its 128-byte
+        // swizzled line in the staged boxes
+        const unsigned char* line = stage(r) + m * 128;
+        const uint4 r0 = *reinterpret_cast<const uint4*>(line + (((2 * cg) ^ (m & 7)) << 4));
+        const uint4 r1 = *reinterpret_cast<const uint4*>(line + (((2 * cg + 1) ^ (m & 7)) << 4));
+        const uint32_t v[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+        uint32_t words[kGDig][4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          // rows 2p (low half) and 2p + 1 (high half) of the word
+          float ua = live ? __fmul_rn(__fmul_rn(__uint_as_float(v[2 * p]), f1), f2) : 0.0f;
+          float ub = live ? __fmul_rn(__fmul_rn(__uint_as_float(v[2 * p + 1]), f1), f2) : 0.0f;
+#pragma unroll
+          for (int t = 0; t < kGDig; ++t) {
+            const float da = __fsub_rn(__fadd_rn(ua, kRound), kRound);
+            const float db = __fsub_rn(__fadd_rn(ub, kRound), kRound);
+            const __half2 h = __floats2half2_rn(da, db);
+            words[t][p] = *reinterpret_cast<const uint32_t*>(&h);
+            if (t + 1 < kGDig) {
+              ua = __fmul_rn(__fsub_rn(ua, da), 256.0f);
+              ub = __fmul_rn(__fsub_rn(ub, db), 256.0f);
+            }
+          }
+        }
+        // digit t of the eight rows: K chunk cg of line m of A slice t (and
+        // of line m - 32q of B slice t for the quarter's own columns);
+        // 64-byte swizzle: chunk cg of line r sits at cg ^ ((r >> 1) & 3)
+        const int off = (cg ^ ((m >> 1) & 3)) << 4;
+        unsigned char* dst = sliceA(b, 0) + m * 64 + off;
+#pragma unroll
+        for (int t = 0; t < kGDig; ++t)
+          *reinterpret_cast<uint4*>(dst + t * kGSliceA) =
+              make_uint4(words[t][0], words[t][1], words[t][2], words[t][3]);
+        if ((warp & 3) == q) {
+          unsigned char* dstb = sliceB(b, 0) + lane * 64 + off;
+#pragma unroll
+          for (int t = 0; t < kGDig; ++t)
+            *reinterpret_cast<uint4*>(dstb + t * kGSliceB) =
+                make_uint4(words[t][0], words[t][1], words[t][2], words[t][3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      }
+      mbar_arrive(&sh.sfree[r]);
+      mbar_arrive(&sh.afull[b]);
+      if (pend >= 0) {
+        if (!readout(pend)) {
+          stop = true;
+          break;
+        }
+        pend = -1;
+      }
+      if (group_end(k)) pend = k / kGChunk;
+    }
+    if (!stop && pend >= 0) readout(pend);
+  }
+  // (twice the limit: after a failure the MMA warp may first spend one
+  // limit on a step that never came)
+  if (warp < 4 && !mbar_wait(&sh.done, 0, 2 * kWaitNs)) sh.fail = 1;
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  const bool good = !sh.fail;
+  if (!good) {
+    if (tid == 0) atomicExch(err, 1);
+  } else if (warp < kDWarps && mine && m < s) {
+    double* P = part + static_cast<int64_t>(blockIdx.y) * s * s;
+    const int em = ex[m];
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) {
+      const int nn = kGN * q + 8 * cg + cc;
+      if (m <= nn && nn < s) {
+        const int en = ex[nn];
+        double val;
+        if (em >= kGNonFinite || en >= kGNonFinite) {
+          val = __longlong_as_double(0x7FF8000000000000ll);   // an Inf or NaN in either column
+        } else if (em < -2000 || en < -2000) {
+          val = 0.0;                                         // an all-zero column
+        } else {
+          // V = (ahi + carry) 2^32 + the low 32 bits of alo, rounded once
+          const int64_t hi = ahi[cc] + (alo[cc] >> 32);
+          const uint32_t lo = static_cast<uint32_t>(alo[cc]);
+          val = int96_to_double(hi, lo, em + en - 68);
+        }
+        P[m + static_cast<int64_t>(nn) * s] = val;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kOTmemCols)
+                 : "memory");
+  }
+}
+
+// e[c] for FP32 columns: the exponent of the largest magnitude (|x| < 2^e),
+// or kGNonFinite when the column holds an Inf or a NaN, merged with
+// atomicMax like the FP64 kernel (all-zero columns keep the start value).
+__global__ void __launch_bounds__(256)
+col_exponent32_kernel(int64_t n, const float* __restrict__ X, int64_t ld, int64_t rows,
+                      int* __restrict__ e) {
+  const uint32_t* col = reinterpret_cast<const uint32_t*>(X + static_cast<int64_t>(blockIdx.x) * ld);
+  const int64_t r0 = static_cast<int64_t>(blockIdx.y) * rows;
+  const int64_t r1 = (r0 + rows < n) ? r0 + rows : n;
+  // |x| orders like its bit pattern with the sign cleared; Inf and NaN
+  // patterns lie above every finite one
+  uint32_t mx = 0;
+  auto take = [&](uint32_t b) {
+    b &= 0x7FFFFFFFu;
+    mx = b > mx ? b : mx;
+  };
+  int64_t r = r0;
+  int64_t head = 0;   // elements before the first 16-byte boundary
+  while (r + head < r1 && (reinterpret_cast<uintptr_t>(col + r + head) & 15)) ++head;
+  if (threadIdx.x < head) take(__ldg(col + r + threadIdx.x));
+  r += head;
+  const uint4* p4 = reinterpret_cast<const uint4*>(col + r);
+  const int64_t nq4 = (r1 - r) / 4;
+  for (int64_t p = threadIdx.x; p < nq4; p += 4 * 256) {
+    uint4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      v[u] = (p + u * 256 < nq4) ? __ldg(p4 + p + u * 256) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      take(v[u].x);
+      take(v[u].y);
+      take(v[u].z);
+      take(v[u].w);
+    }
+  }
+  for (int64_t t = r + 4 * nq4 + threadIdx.x; t < r1; t += 256) take(__ldg(col + t));
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const uint32_t o = __shfl_xor_sync(0xffffffffu, mx, off);
+    mx = o > mx ? o : mx;
+  }
+  __shared__ uint32_t wm[8];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t tb = 0;
+    for (int w = 0; w < 8; ++w) tb = wm[w] > tb ? wm[w] : tb;
+    if (tb >= 0x7F800000u) {
+      atomicMax(e + blockIdx.x, kGNonFinite);
+    } else if (tb != 0) {
+      const int E = static_cast<int>(tb >> 23);   // |x| < 2^(E - 126); subnormals < 2^-126
+      atomicMax(e + blockIdx.x, E == 0 ? -126 : E - 126);
+    }
+  }
+}
+
+void col_exponents32(int64_t n, const float* X, int64_t ld, int cols, int* e, cudaStream_t st) {
+  SG_CUDA(cudaMemsetAsync(e, 0x80, sizeof(int) * cols, st));   // 0x80808080: no entry yet
+  int64_t z = static_cast<int64_t>(device_sm_count()) * 8 / cols;
+  const int64_t zmax = (n + 4095) / 4096;
+  if (z > zmax) z = zmax;
+  if (z < 1) z = 1;
+  const int64_t rows = (n + z - 1) / z;
+  col_exponent32_kernel<<<dim3(cols, static_cast<unsigned>((n + rows - 1) / rows)), 256, 0, st>>>(
+      n, X, ld, rows, e);
+  SG_LAUNCH_CHECK();
+}
+
+// FP32 column-major matrix (rows x cols, leading dimension ld), boxes of
+// 32 rows x 32 columns, 128-byte swizzle
+bool make_map32_gram(CUtensorMap* map, const float* ptr, int64_t rows, int64_t cols, int64_t ld) {
+  auto fn = oz_encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(rows), static_cast<cuuint64_t>(cols)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * sizeof(float)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(kGK), static_cast<cuuint32_t>(kGN)};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ptr), dims, strides,
+            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+int64_t oz_gram32_splits(int64_t n, int s, int64_t* rows) {
+  const int64_t nq = (s + kGN - 1) / kGN;
+  int64_t S = static_cast<int64_t>(device_sm_count()) / nq;
+  const int64_t maxS = n / (4 * kGK);     // at least four stages per split
+  if (S > maxS) S = maxS;
+  // at most 2^14 level readouts per split keep the int64 halves exact
+  const int64_t span = int64_t(kGK) * kGChunk << 14;
+  const int64_t minS = (n + span - 1) / span;
+  if (S < minS) S = minS;
+  if (S < 1) S = 1;
+  int64_t r = (n + S - 1) / S;
+  r = (r + kGK - 1) / kGK * kGK;
+  if (rows) *rows = r;
+  return (n + r - 1) / r;
+}
+
 }  // namespace
 
 bool oz_dot_supported(int64_t n, const double* Q, int64_t ldq, int i, const double* X,
@@ -1144,6 +1639,48 @@ void oz_dot(int64_t n, const double* Q, int64_t ldq, int i, const double* X, int
   ensure_dynamic_smem(reinterpret_cast<const void*>(oz_dot_kernel), kOzSmem);
   dim3 grid((i + kOM - 1) / kOM, (s + kON - 1) / kON, static_cast<unsigned>(S));
   oz_dot_kernel<<<grid, kDThreads, kOzSmem, st>>>(mq, mx, n, i, s, eq, ex, rows, part, err);
+  SG_LAUNCH_CHECK();
+  oz_check_error_pending.fetch_add(1);
+  *nsplit = static_cast<int>(S);
+}
+
+bool oz_gram32_supported(int64_t n, const float* X, int64_t ldx, int s) {
+  if (n < 8 * kGK || s < 1 || s > kGMaxS) return false;
+  if (reinterpret_cast<uintptr_t>(X) & 15) return false;
+  if ((ldx * 4) & 15) return false;
+  if (n > (int64_t(1) << 31) - 1) return false;
+  return oz_encode_fn() != nullptr;
+}
+
+// Expected time of the tensor-core Gram: one CTA per SM takes a quarter of
+// 32 output columns through stages of 32 rows at about kStageUs each
+// (measured 1.8 us at n = 2^19 .. 2^21, s = 16 .. 128: the cut and the
+// exact readout on the CUDA cores, not the MMAs, set it), plus kFixedUs of
+// setup (the exponent and reduction launches, tensor memory).
+double oz_gram32_seconds(int64_t n, int s) {
+  constexpr double kStageUs = 1.8, kFixedUs = 15.0;
+  const double nq = static_cast<double>((s + kGN - 1) / kGN);
+  return (static_cast<double>((n + kGK - 1) / kGK) * nq * kStageUs /
+              static_cast<double>(device_sm_count()) +
+          kFixedUs) * 1e-6;
+}
+
+int64_t oz_gram32_part_size(int64_t n, int s) {
+  return oz_gram32_splits(n, s, nullptr) * s * s;
+}
+
+void oz_gram32(int64_t n, const float* X, int64_t ldx, int s, int* exps, double* part,
+               int64_t part_cap, int* nsplit, cudaStream_t st) {
+  int* err = oz_err_flag();
+  int64_t rows = 0;
+  const int64_t S = oz_gram32_splits(n, s, &rows);
+  SG_REQUIRE(S * s * s <= part_cap, SG_EINVAL, "oz_gram32: workspace too small");
+  col_exponents32(n, X, ldx, s, exps, st);
+  CUtensorMap mx;
+  SG_REQUIRE(make_map32_gram(&mx, X, n, s, ldx), SG_ECUDA, "cuTensorMapEncodeTiled failed");
+  ensure_dynamic_smem(reinterpret_cast<const void*>(oz_gram32_kernel), kGSmem);
+  dim3 grid((s + kGN - 1) / kGN, static_cast<unsigned>(S));
+  oz_gram32_kernel<<<grid, kDThreads, kGSmem, st>>>(mx, n, s, exps, rows, part, err);
   SG_LAUNCH_CHECK();
   oz_check_error_pending.fetch_add(1);
   *nsplit = static_cast<int>(S);

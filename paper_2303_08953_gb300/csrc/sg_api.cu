@@ -658,6 +658,7 @@ sg_status sg_block_dot_f32(sg_handle* h, int64_t n, const float* Q,
     ensure_part(h, sg::block_dot_part_size(n, i, s), st);
     sg::block_dot32(n, Q, ldq, i, X, ldx, s, W, ldw, sym != 0, h->part, h->part_cap, st);
     sg::tc_check_error(st);  // synchronises: reports a tensor-core timeout
+    sg::oz_check_error(st);
   });
 }
 

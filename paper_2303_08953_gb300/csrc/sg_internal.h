@@ -207,6 +207,15 @@ void oz_update(int64_t n, const double* Q, int64_t ldq, int i, const double* W, 
 void oz_dot(int64_t n, const double* Q, int64_t ldq, int i, const double* X, int64_t ldx,
             int s, int* exps, double* part, int64_t part_cap, int* nsplit, cudaStream_t st);
 void oz_check_error(cudaStream_t st);
+// Tensor-core FP32 Gram G = X^T X (s <= 128 columns) from exact digit
+// slices: split partials of the upper triangle (entry (m, n), m <= n, at
+// m + n s) into `part`, column exponents into `exps` (s ints); a bounded
+// wait that ran out sets the flag oz_check_error reads.
+bool oz_gram32_supported(int64_t n, const float* X, int64_t ldx, int s);
+double oz_gram32_seconds(int64_t n, int s);
+int64_t oz_gram32_part_size(int64_t n, int s);
+void oz_gram32(int64_t n, const float* X, int64_t ldx, int s, int* exps, double* part,
+               int64_t part_cap, int* nsplit, cudaStream_t st);
 // Tensor-core (tcgen05, TMA) FP32 block update X = beta X + alpha Q W.
 bool tc_update_supported(int64_t n, const float* Q, int64_t ldq, int i,
                          const float* X, int64_t ldx, int s);

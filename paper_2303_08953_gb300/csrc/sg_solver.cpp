@@ -511,7 +511,7 @@ void solve_impl(sg_handle* h, const DevCsr& M, const SolveOpts& o,
       fetch(Gd, static_cast<int64_t>(s_eff) * s_eff, hb + static_cast<int64_t>(i) * s_eff);
       SG_CUDA(cudaEventRecord(h->ev[2], st));
       SG_CUDA(cudaStreamSynchronize(st));
-      if (sizeof(T) == 4) { tc_check_error(st); tc_update_check_error(st); }
+      if (sizeof(T) == 4) { tc_check_error(st); tc_update_check_error(st); oz_check_error(st); }
       else oz_check_error(st);
       {
         float a = 0, b = 0;
@@ -562,7 +562,7 @@ void solve_impl(sg_handle* h, const DevCsr& M, const SolveOpts& o,
         fetch(Gd, static_cast<int64_t>(p1) * p1, hb + static_cast<int64_t>(i) * p1);
         SG_CUDA(cudaEventRecord(h->ev[2], st));
         SG_CUDA(cudaStreamSynchronize(st));
-        if (sizeof(T) == 4) { tc_check_error(st); tc_update_check_error(st); }
+        if (sizeof(T) == 4) { tc_check_error(st); tc_update_check_error(st); oz_check_error(st); }
         else oz_check_error(st);
         {
           float b = 0;

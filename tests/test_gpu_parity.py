@@ -327,12 +327,14 @@ def test_block_dot_f32_tensor_cores(solver, n, i, s):
 
 @pytest.mark.parametrize("n,s", [(1, 5), (70001, 1), (4133, 6), (70001, 33), (70001, 120),
                                  (4133, 130)])
-def test_gram_f32_is_nearly_exact(solver, n, s):
-    """The FP32 Gram uses exact products and two-sum accumulation: its
-    error is at the eps_32^2 level relative to sum |x_k y_k|.  Up to 128
-    columns the triangle kernel computes it (one row, one column and a
-    partial last 4 x 4 block included); 130 columns take the square-tile
-    kernel."""
+def test_gram_f32_is_nearly_exact(solver, tc_path, n, s):
+    """The FP32 Gram uses exact products: on the FP32 pipe with two-sum
+    accumulation, on the tensor cores from exact digit slices.  Either way
+    its error is at the eps_32^2 level relative to sum |x_k y_k| for data
+    without extreme dynamic range.  Up to 128 columns the triangle kernel
+    (or the tensor-core Gram, from 256 rows) computes it (one row, one
+    column and a partial last 4 x 4 block included); 130 columns take the
+    square-tile kernel."""
     rng = np.random.default_rng(400 + s)
     X = rng.standard_normal((s, n)).astype(np.float32)
     Xd = dev(X, torch.float32)
@@ -342,6 +344,82 @@ def test_gram_f32_is_nearly_exact(solver, n, s):
     ref = X64 @ X64.T
     scale = np.abs(X64) @ np.abs(X64).T
     assert np.all(np.abs(G - ref) <= 1e-12 * scale)
+
+
+def _gram32(solver, X, n):
+    """G = X^T X of the FP32 columns X (s, ld) through the C ABI."""
+    Xd = dev(X, torch.float32)
+    solver.n = n
+    return host(solver.block_dot32(Xd, Xd, sym=True)).T
+
+
+GRAM32_SHAPES = [(256, 1), (257, 7), (4133, 32), (4133, 33), (70001, 64), (70001, 100),
+                 (70001, 106), (70001, 128), ((1 << 20) + 3, 106)]
+
+
+@pytest.mark.parametrize("n,s", GRAM32_SHAPES)
+def test_gram_f32_tensor_cores_exact_on_integers(solver, tc_always, n, s):
+    """Integers of at most 11 bits are exact in six digit slices (every
+    value within 2^23 of its column's largest), their products and level
+    sums are exact, and the Gram entries (< 2^53) round exactly: the
+    tensor-core Gram must equal X^T X bit for bit.  The shapes cover one
+    to four quarters of 32 output columns, a ragged last stage and splits
+    of many 128-row groups."""
+    rng = np.random.default_rng(n + 31 * s)
+    ld = (n + 3) // 4 * 4                      # 16-byte column stride for TMA
+    X = np.zeros((s, ld), dtype=np.float32)
+    X[:, :n] = rng.integers(-1000, 1001, size=(s, n))
+    X[:, n:] = 7.0                             # padding rows must not count
+    G = _gram32(solver, X, n)
+    X64 = X[:, :n].astype(np.float64)
+    assert np.array_equal(G, X64 @ X64.T)
+
+
+@pytest.mark.parametrize("n,s", [(4133, 33), (70001, 106), (70001, 128)])
+def test_gram_f32_tensor_cores_error_bound(solver, tc_always, n, s):
+    """Columns scaled over 2^-40 .. 2^40, some with single large outliers,
+    one all zero: each value is kept to 2^-47 of its column's largest
+    (six base-256 digits) and the digit pairs of levels above 7 are left
+    out, so entry (a, b) is within
+    2^-46 (max|x_a| sum|x_b| + max|x_b| sum|x_a|) + n 2^-58 max|x_a| max|x_b|
+    of X^T X, plus the final rounding."""
+    rng = np.random.default_rng(7 * n + s)
+    ld = (n + 3) // 4 * 4
+    X = np.zeros((s, ld), dtype=np.float32)
+    scales = 2.0 ** rng.uniform(-40, 40, size=s)
+    X[:, :n] = rng.standard_normal((s, n)) * scales[:, None]
+    for c in range(0, s, 5):                   # outliers 2^10 .. 2^20 above the rest
+        X[c, rng.integers(0, n)] *= 2.0 ** rng.uniform(10, 20)
+    X[s // 2, :] = 0.0
+    G = _gram32(solver, X, n)
+    X64 = X[:, :n].astype(np.float64)
+    ref = X64 @ X64.T
+    A = np.abs(X64)
+    mx = A.max(axis=1)
+    sm = A.sum(axis=1)
+    bound = (2.0 ** -46 * (np.outer(mx, sm) + np.outer(sm, mx)) + n * 2.0 ** -58 * np.outer(mx, mx)
+             + 2.0 ** -52 * np.abs(ref))
+    # the FP64 reference itself carries n u sum|x_a x_b|
+    bound += 2 * n * 2.0 ** -53 * (A @ A.T)
+    assert np.all(np.abs(G - ref) <= bound)
+    assert np.all(G[s // 2, :] == 0.0) and np.all(G[:, s // 2] == 0.0)
+    assert np.array_equal(G, G.T)
+
+
+def test_gram_f32_tensor_cores_non_finite_column(solver, tc_always):
+    """An Inf or NaN in a column makes that column's row and column of the
+    Gram NaN (so the Cholesky of CholQR stops), and leaves the rest exact."""
+    n, s = 4133, 40
+    rng = np.random.default_rng(11)
+    X = rng.integers(-100, 101, size=(s, 4136)).astype(np.float32)
+    X[3, 1000] = np.inf
+    X[17, 5] = np.nan
+    G = _gram32(solver, X, n)
+    bad = np.zeros(s, dtype=bool)
+    bad[[3, 17]] = True
+    assert np.all(np.isnan(G[bad, :])) and np.all(np.isnan(G[:, bad]))
+    X64 = X[~bad, :n].astype(np.float64)
+    assert np.array_equal(G[np.ix_(~bad, ~bad)], X64 @ X64.T)
 
 
 @pytest.mark.parametrize("n", [65, 70001])
