@@ -1111,6 +1111,27 @@ __device__ __forceinline__ void mma_f16_ss(uint32_t dtmem, uint64_t a, uint64_t 
       : "memory");
 }
 
+// This thread's lane, 8 consecutive 32-bit columns from taddr, without
+// waiting for the load (tmem_wait_ld16 waits and orders the uses).
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7])
+      : "r"(taddr));
+}
+
+// Waits for this thread's tensor-memory loads; the 16 registers are operands
+// so that no use of them is scheduled before the wait.
+__device__ __forceinline__ void tmem_wait_ld16(uint32_t* v) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]),
+                 "+r"(v[6]), "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]),
+                 "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15])
+               :
+               : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major operand, 64-byte swizzle (lines
 // of 64 bytes, the 16-byte chunk c of line r stored at c ^ ((r >> 1) & 3)),
 // 8-line groups 512 bytes apart (slice bases aligned to 1024 bytes).
@@ -1146,16 +1167,19 @@ oz_gram32_kernel(const __grid_constant__ CUtensorMap mapX, int64_t n, int s,
   auto failed = [&]() { return *reinterpret_cast<volatile int*>(&sh.fail) != 0; };
   auto group_end = [&](int k) { return (k % kGChunk) == kGChunk - 1 || k == nk - 1; };
 
+  // the warps whose lanes hold columns 0 .. 32q + 31 cut and read out; the
+  // others have no part in the stages (they wait at the end)
+  const uint32_t nwork = static_cast<uint32_t>(32 * 4 * (q + 1));
   if (tid == 0) {
     for (int r = 0; r < kGRing; ++r) {
       mbar_init(&sh.full[r], 1);
-      mbar_init(&sh.sfree[r], kDSplit);
+      mbar_init(&sh.sfree[r], nwork);
     }
     for (int b = 0; b < 2; ++b) {
-      mbar_init(&sh.afull[b], kDSplit);
+      mbar_init(&sh.afull[b], nwork);
       mbar_init(&sh.afree[b], 1);
       mbar_init(&sh.accfull[b], 1);
-      mbar_init(&sh.accfree[b], kDSplit);
+      mbar_init(&sh.accfree[b], nwork);
     }
     mbar_init(&sh.done, 1);
     sh.fail = 0;
@@ -1206,19 +1230,24 @@ oz_gram32_kernel(const __grid_constant__ CUtensorMap mapX, int64_t n, int s,
     if (!mbar_wait(&sh.accfull[a], static_cast<uint32_t>((g >> 1) & 1))) sh.fail = 1;
     if (__any_sync(0xffffffffu, failed())) return false;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (mine) {
+    {
       const uint32_t tl = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) +
                           static_cast<uint32_t>(a) * kGSetCol + static_cast<uint32_t>(cg * 8);
 #pragma unroll
-      for (int L = 0; L < kGLev; ++L) {
-        uint32_t v[8];
-        tmem_ld8(tl + static_cast<uint32_t>(kGN * L), v);
+      for (int L = 0; L < kGLev; L += 2) {
+        // two levels per wait for the loads
+        uint32_t v[16];
+        tmem_ld8_nowait(tl + static_cast<uint32_t>(kGN * L), v);
+        tmem_ld8_nowait(tl + static_cast<uint32_t>(kGN * (L + 1)), v + 8);
+        tmem_wait_ld16(v);
 #pragma unroll
-        for (int cc = 0; cc < 8; ++cc) {
-          const int64_t sv = level_int(v[cc]);
-          if (L < 4) ahi[cc] += sv * (int64_t(1) << (8 * (3 - L)));
-          else alo[cc] += sv * (int64_t(1) << (8 * (7 - L)));
-        }
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int cc = 0; cc < 8; ++cc) {
+            const int64_t sv = level_int(v[8 * h + cc]);
+            if (L + h < 4) ahi[cc] += sv * (int64_t(1) << (8 * (3 - L - h)));
+            else alo[cc] += sv * (int64_t(1) << (8 * (7 - L - h)));
+          }
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1291,9 +1320,9 @@ oz_gram32_kernel(const __grid_constant__ CUtensorMap mapX, int64_t n, int s,
       }
       mma_commit(&sh.done);
     }
-  } else {
+  } else if (mine) {
     // ------------------------------------------------ split, readout
-    const int em = (mine && m < s) ? ex[m] : -4000;
+    const int em = m < s ? ex[m] : -4000;
     // u = x 2^(6 - e) as two exact power-of-two scalings, both factors
     // normal; columns that are all zero, beyond s or hold an Inf or a NaN
     // are cut as zeros
@@ -1320,7 +1349,7 @@ oz_gram32_kernel(const __grid_constant__ CUtensorMap mapX, int64_t n, int s,
         stop = true;
         break;
       }
-      if (mine) {
+      {
         // column m's rows 8 cg .. + 7: chunks 2 cg, 2 cg + 1 of its 128-byte
         // swizzled line in the staged boxes
         const unsigned char* line = stage(r) + m * 128;
