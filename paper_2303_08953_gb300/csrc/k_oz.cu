@@ -1061,13 +1061,13 @@ int64_t oz_splits(int64_t n, int i, int s, int64_t* rows) {
 //     32 rows x 32 columns, 128-byte swizzled) into a six-deep ring (a stage
 //     is 4 to 16 KB, so the ring keeps enough bytes in flight to cover the
 //     latency of HBM);
-//   * warps 0-15 cut stage k into one of two sets of digit slices (one 16-byte store per
-//     digit: eight consecutive rows of one column, packed two digits per
-//     conversion) while warp 17 (one lane)
-//     issues stage k-1's MMAs;
+//   * warps 0-7 cut stage k into one of two sets of digit slices (one
+//     16-byte store per digit: eight consecutive rows of one column, packed
+//     two digits per conversion) while warp 17 (one lane) issues stage
+//     k-1's MMAs;
 //   * the level sums alternate between two sets of tensor-memory columns
-//     (8 levels x 32 columns each), so the readout of one 128-row group
-//     overlaps the next group's MMAs.
+//     (8 levels x 32 columns each); warps 8-15 read one set out while the
+//     MMAs fill the other, so neither the cut nor the MMAs wait for them.
 // Every wait is bounded, as in the kernels above.
 constexpr int kGK = 32;                         // rows per stage
 constexpr int kGN = 32;                         // output columns per CTA (MMA N)
@@ -1167,9 +1167,10 @@ oz_gram32_kernel(const __grid_constant__ CUtensorMap mapX, int64_t n, int s,
   auto failed = [&]() { return *reinterpret_cast<volatile int*>(&sh.fail) != 0; };
   auto group_end = [&](int k) { return (k % kGChunk) == kGChunk - 1 || k == nk - 1; };
 
-  // the warps whose lanes hold columns 0 .. 32q + 31 cut and read out; the
-  // others have no part in the stages (they wait at the end)
-  const uint32_t nwork = static_cast<uint32_t>(32 * 4 * (q + 1));
+  // warps 0-7 cut, warps 8-15 read out; of each, the two warps per group of
+  // 32 tensor-memory lanes whose lanes hold columns 0 .. 32q + 31 take part
+  // (the others wait at the end)
+  const uint32_t nwork = static_cast<uint32_t>(64 * (q + 1));
   if (tid == 0) {
     for (int r = 0; r < kGRing; ++r) {
       mbar_init(&sh.full[r], 1);
@@ -1212,42 +1213,40 @@ oz_gram32_kernel(const __grid_constant__ CUtensorMap mapX, int64_t n, int s,
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = sh.tmem_base;
 
-  // warp w's lanes are the columns m = 32 (w % 4) + lane (tensor-memory
-  // lanes); it cuts rows 8 (w / 4) .. + 7 of each stage and owns the
-  // outputs (m, 32q + 8 (w / 4) + c), c < 8, each as two int64 halves:
-  // ahi = sum of S_l 256^(3-l) over l = 0..3, alo = sum of S_l 256^(7-l)
-  // over l = 4..7 (|S_l| < 2^24: each half grows by < 2^48.1 per readout and
-  // stays exact for 2^14 readouts); V = ahi 2^32 + alo
+  // Warp w (w < 16) covers the tensor-memory lanes, i.e. columns,
+  // m = 32 (w % 4) + lane; half = (w / 4) % 2.  A cutting warp (w < 8) cuts
+  // rows 16 half .. + 15 of each stage of column m; a reading warp (w >= 8)
+  // owns the outputs (m, 32q + 16 half + c), c < 16, each as two int64
+  // halves: ahi = sum of S_l 256^(3-l) over l = 0..3, alo = sum of
+  // S_l 256^(7-l) over l = 4..7 (|S_l| < 2^24: each half grows by < 2^48.1
+  // per readout and stays exact for 2^14 readouts); V = ahi 2^32 + alo
   const int m = (warp & 3) * 32 + lane;
-  const int cg = warp >> 2;
+  const int half = (warp >> 2) & 1;
   const bool mine = (warp & 3) <= q;   // columns 32 (w % 4) .. + 31 are within 0 .. 32q + 31
-  int64_t alo[8];
-  int64_t ahi[8];
+  const bool cutter = warp < kDWarps / 2;
+  int64_t alo[16];
+  int64_t ahi[16];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) { alo[c] = 0; ahi[c] = 0; }
+  for (int c = 0; c < 16; ++c) { alo[c] = 0; ahi[c] = 0; }
   auto readout = [&](int g) -> bool {
     const int a = g & 1;
     if (!mbar_wait(&sh.accfull[a], static_cast<uint32_t>((g >> 1) & 1))) sh.fail = 1;
     if (__any_sync(0xffffffffu, failed())) return false;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    {
-      const uint32_t tl = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) +
-                          static_cast<uint32_t>(a) * kGSetCol + static_cast<uint32_t>(cg * 8);
+    const uint32_t tl = tmem + (static_cast<uint32_t>((warp & 3) * 32) << 16) +
+                        static_cast<uint32_t>(a) * kGSetCol + static_cast<uint32_t>(half * 16);
 #pragma unroll
-      for (int L = 0; L < kGLev; L += 2) {
-        // two levels per wait for the loads
-        uint32_t v[16];
-        tmem_ld8_nowait(tl + static_cast<uint32_t>(kGN * L), v);
-        tmem_ld8_nowait(tl + static_cast<uint32_t>(kGN * (L + 1)), v + 8);
-        tmem_wait_ld16(v);
+    for (int L = 0; L < kGLev; ++L) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+      for (int hh = 0; hh < 2; ++hh) {
+        uint32_t v[8];
+        tmem_ld8(tl + static_cast<uint32_t>(kGN * L + 8 * hh), v);
 #pragma unroll
-          for (int cc = 0; cc < 8; ++cc) {
-            const int64_t sv = level_int(v[8 * h + cc]);
-            if (L + h < 4) ahi[cc] += sv * (int64_t(1) << (8 * (3 - L - h)));
-            else alo[cc] += sv * (int64_t(1) << (8 * (7 - L - h)));
-          }
+        for (int c = 0; c < 8; ++c) {
+          const int64_t sv = level_int(v[c]);
+          if (L < 4) ahi[8 * hh + c] += sv * (int64_t(1) << (8 * (3 - L)));
+          else alo[8 * hh + c] += sv * (int64_t(1) << (8 * (7 - L)));
+        }
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1320,8 +1319,8 @@ oz_gram32_kernel(const __grid_constant__ CUtensorMap mapX, int64_t n, int s,
       }
       mma_commit(&sh.done);
     }
-  } else if (mine) {
-    // ------------------------------------------------ split, readout
+  } else if (mine && cutter) {
+    // ------------------------------------------------ cut
     const int em = m < s ? ex[m] : -4000;
     // u = x 2^(6 - e) as two exact power-of-two scalings, both factors
     // normal; columns that are all zero, beyond s or hold an Inf or a NaN
@@ -1331,8 +1330,6 @@ oz_gram32_kernel(const __grid_constant__ CUtensorMap mapX, int64_t n, int s,
     const float f1 = __int_as_float((127 + eb) << 23);
     const float f2 = live ? __int_as_float((127 + 6 - em - eb) << 23) : 0.0f;
     constexpr float kRound = 12582912.0f;   // 1.5 2^23: adding it rounds |v| < 2^22 to an integer
-    int pend = -1;
-    bool stop = false;
     for (int k = 0; k < nk; ++k) {
       const int b = k & 1;
       const int r = k % kGRing;
@@ -1345,13 +1342,12 @@ oz_gram32_kernel(const __grid_constant__ CUtensorMap mapX, int64_t n, int s,
           bad = true;
         }
       }
-      if (__any_sync(0xffffffffu, bad)) {
-        stop = true;
-        break;
-      }
-      {
-        // column m's rows 8 cg .. + 7: chunks 2 cg, 2 cg + 1 of its 128-byte
-        // swizzled line in the staged boxes
+      if (__any_sync(0xffffffffu, bad)) break;
+#pragma unroll
+      for (int gg = 0; gg < 2; ++gg) {
+        // column m's rows 8 cg .. + 7 (cg = 2 half + gg): chunks 2 cg,
+        // 2 cg + 1 of its 128-byte swizzled line in the staged boxes
+        const int cg = 2 * half + gg;
         const unsigned char* line = stage(r) + m * 128;
         const uint4 r0 = *reinterpret_cast<const uint4*>(line + (((2 * cg) ^ (m & 7)) << 4));
         const uint4 r1 = *reinterpret_cast<const uint4*>(line + (((2 * cg + 1) ^ (m & 7)) << 4));
@@ -1390,20 +1386,16 @@ oz_gram32_kernel(const __grid_constant__ CUtensorMap mapX, int64_t n, int s,
             *reinterpret_cast<uint4*>(dstb + t * kGSliceB) =
                 make_uint4(words[t][0], words[t][1], words[t][2], words[t][3]);
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(&sh.sfree[r]);
       mbar_arrive(&sh.afull[b]);
-      if (pend >= 0) {
-        if (!readout(pend)) {
-          stop = true;
-          break;
-        }
-        pend = -1;
-      }
-      if (group_end(k)) pend = k / kGChunk;
     }
-    if (!stop && pend >= 0) readout(pend);
+  } else if (mine) {
+    // ------------------------------------------------ readout
+    const int ngroups = (nk + kGChunk - 1) / kGChunk;
+    for (int g = 0; g < ngroups; ++g)
+      if (!readout(g)) break;
   }
   // (twice the limit: after a failure the MMA warp may first spend one
   // limit on a step that never came)
@@ -1413,12 +1405,12 @@ oz_gram32_kernel(const __grid_constant__ CUtensorMap mapX, int64_t n, int s,
   const bool good = !sh.fail;
   if (!good) {
     if (tid == 0) atomicExch(err, 1);
-  } else if (warp < kDWarps && mine && m < s) {
+  } else if (warp < kDWarps && !cutter && mine && m < s) {
     double* P = part + static_cast<int64_t>(blockIdx.y) * s * s;
     const int em = ex[m];
 #pragma unroll
-    for (int cc = 0; cc < 8; ++cc) {
-      const int nn = kGN * q + 8 * cg + cc;
+    for (int cc = 0; cc < 16; ++cc) {
+      const int nn = kGN * q + 16 * half + cc;
       if (m <= nn && nn < s) {
         const int en = ex[nn];
         double val;
@@ -1683,11 +1675,14 @@ bool oz_gram32_supported(int64_t n, const float* X, int64_t ldx, int s) {
 
 // Expected time of the tensor-core Gram: one CTA per SM takes a quarter of
 // 32 output columns through stages of 32 rows at about kStageUs each
-// (measured 1.8 us at n = 2^19 .. 2^21, s = 16 .. 128: the cut and the
-// exact readout on the CUDA cores, not the MMAs, set it), plus kFixedUs of
-// setup (the exponent and reduction launches, tensor memory).
+// (measured 1.6 us at n = 2^19 .. 2^21, s = 16 .. 128, whatever the
+// quarter: a warp reaches the tensor-memory lanes of its own scheduler
+// only, so each group of 32 columns is read out, and its columns cut, by
+// one scheduler's warps, and their instruction issue, not the MMAs, sets
+// the pace), plus kFixedUs of setup (the exponent and reduction launches,
+// tensor memory).
 double oz_gram32_seconds(int64_t n, int s) {
-  constexpr double kStageUs = 1.8, kFixedUs = 15.0;
+  constexpr double kStageUs = 1.6, kFixedUs = 15.0;
   const double nq = static_cast<double>((s + kGN - 1) / kGN);
   return (static_cast<double>((n + kGK - 1) / kGK) * nq * kStageUs /
               static_cast<double>(device_sm_count()) +
