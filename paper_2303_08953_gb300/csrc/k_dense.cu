@@ -250,15 +250,19 @@ void launch_reduce(int M, int N, int S, const double* part, double* W, int ldw,
 // upper triangle (entry (m, n), m <= n, at m + n s).
 constexpr int kGramMaxS = 128;
 constexpr int kGramBK = 32;
-constexpr int kGramLd = kGramMaxS + 4;
 constexpr int kGramThreads = 128;
 
 __host__ __device__ constexpr int gram_blocks(int s) { return ((s + 3) / 4) * ((s + 3) / 4 + 1) / 2; }
 
+template <int LDS>
 __global__ void __launch_bounds__(kGramThreads)
 gram_exact_kernel(int64_t K, int s, const float* __restrict__ X, int64_t ldx,
                   double* __restrict__ part, int64_t rows_per_split) {
-  __shared__ __align__(16) float Ss[kGramBK][kGramLd];
+  // the slab: kGramBK rows of LDS floats (at least the columns, padded to a
+  // multiple of 4, plus 4; a compile-time stride keeps the addressing in the
+  // instructions' offsets)
+  constexpr int lds = LDS;
+  extern __shared__ __align__(16) float Ss[];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;  // block of the triangle
   const int nb = gram_blocks(s);
   // block t -> (bi, bj), bi <= bj
@@ -276,6 +280,8 @@ gram_exact_kernel(int64_t K, int s, const float* __restrict__ X, int64_t ldx,
   const int ncol = 4 * (bjl + 1);
   const int64_t k0 = blockIdx.y * rows_per_split;
   const int64_t k1 = (k0 + rows_per_split < K) ? k0 + rows_per_split : K;
+  const float* pa = Ss + 4 * bi;
+  const float* pb = Ss + 4 * bj;
   float acc[4][4], comp[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -286,14 +292,14 @@ gram_exact_kernel(int64_t K, int s, const float* __restrict__ X, int64_t ldx,
     for (int e = threadIdx.x; e < kGramBK * ncol; e += blockDim.x) {
       const int kk = e % kGramBK, c = e / kGramBK;
       const int64_t k = kb + kk;
-      Ss[kk][c] = (k < k1 && c < s) ? X[k + c * ldx] : 0.0f;
+      Ss[kk * lds + c] = (k < k1 && c < s) ? X[k + c * ldx] : 0.0f;
     }
     __syncthreads();
     if (active) {
 #pragma unroll 2
       for (int kk = 0; kk < kGramBK; ++kk) {
-        const float4 a4 = *reinterpret_cast<const float4*>(&Ss[kk][4 * bi]);
-        const float4 b4 = *reinterpret_cast<const float4*>(&Ss[kk][4 * bj]);
+        const float4 a4 = *reinterpret_cast<const float4*>(pa + kk * lds);
+        const float4 b4 = *reinterpret_cast<const float4*>(pb + kk * lds);
         const float av[4] = {a4.x, a4.y, a4.z, a4.w};
         const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
@@ -339,13 +345,20 @@ double gram_exact_seconds(int64_t n, int s) {
   return static_cast<double>(n) * parts * T * 16.0 / 2.66e12;
 }
 
+// floats per slab row of the Gram kernel: the columns padded to a multiple
+// of 4, plus 4 (rows stay 16-byte aligned), one of three compiled strides
+int gram_lds(int s) { return s <= 32 ? 36 : (s <= 64 ? 68 : kGramMaxS + 4); }
+
 // splits of the Gram kernel: as many CTAs as fit on the SMs at 80
-// registers a thread (up to 8 per SM), >= 4 slabs per split
+// registers a thread and one slab of shared memory each (at most 32 per
+// SM), >= 4 slabs per split
 int64_t gram_splits(int64_t n, int s, int64_t* rows) {
   const int T = gram_cta_threads(s);
   const int parts = (gram_blocks(s) + T - 1) / T;
   int per_sm = 65536 / (80 * T);
-  if (per_sm > 8) per_sm = 8;
+  const int by_smem = (227 * 1024) / (kGramBK * gram_lds(s) * 4 + 1024);
+  if (per_sm > by_smem) per_sm = by_smem;
+  if (per_sm > 32) per_sm = 32;   // resident CTAs per SM
   if (per_sm < 1) per_sm = 1;
   int64_t S = (per_sm * static_cast<int64_t>(device_sm_count()) + parts - 1) / parts;
   const int64_t maxS = (n + 4 * kGramBK - 1) / (4 * kGramBK);
@@ -525,8 +538,16 @@ void block_dot_impl(int64_t n, const T* Q, int64_t ldq, int i, const T* X,
     SG_REQUIRE(S * s * s <= part_cap, SG_EINVAL, "block_dot: workspace too small");
     const int nt = gram_cta_threads(s);
     const int parts = (gram_blocks(s) + nt - 1) / nt;
-    gram_exact_kernel<<<dim3(parts, static_cast<unsigned>(S)), nt, 0, st>>>(
-        n, s, reinterpret_cast<const float*>(X), ldx, part, rows);
+    const int lds = gram_lds(s);
+    const dim3 grid(parts, static_cast<unsigned>(S));
+    const size_t smem = sizeof(float) * kGramBK * lds;
+    const float* Xf = reinterpret_cast<const float*>(X);
+    if (lds == 36)
+      gram_exact_kernel<36><<<grid, nt, smem, st>>>(n, s, Xf, ldx, part, rows);
+    else if (lds == 68)
+      gram_exact_kernel<68><<<grid, nt, smem, st>>>(n, s, Xf, ldx, part, rows);
+    else
+      gram_exact_kernel<kGramMaxS + 4><<<grid, nt, smem, st>>>(n, s, Xf, ldx, part, rows);
     SG_LAUNCH_CHECK();
     launch_reduce(s, s, static_cast<int>(S), part, W, ldw, true, st);
     return;
