@@ -277,9 +277,18 @@ sg_status sg_block_update(sg_handle* h, int64_t n, const double* Q,
 
 /* FP32 forms of the two block kernels, as used by the FP32 basis of
  * SG_PREC_FP32_IR: Q and X are FP32 (column-major), W is FP64.  With sym,
- * sg_block_dot_f32 forms the Gram matrix X^T X from exact FP32 products
- * accumulated with compensated sums (accurate to ~eps_32^2 relative to
- * sum |x_k y_k|).  Otherwise, when the leading dimensions are multiples of
+ * sg_block_dot_f32 forms the Gram matrix X^T X (the CholQR Gram of Alg. 4)
+ * without rounding its products in FP32: for s <= 128, n >= 256, X 16-byte
+ * aligned and ldx a multiple of 4, on the tensor cores when a cost model
+ * says so, from six 8-bit digit slices of each value relative to its
+ * column's largest magnitude (every value within 2^23 of it exact; entry
+ * (a, b) within 2^-46 (max|x_a| sum|x_b| + max|x_b| sum|x_a|)
+ * + n 2^-58 max|x_a| max|x_b| of the exact Gram, plus one rounding); else
+ * from exact FP32 products accumulated with compensated sums (accurate to
+ * ~eps_32^2 relative to sum |x_k y_k|).  An Inf or a NaN in a column makes
+ * that column's row and column of the Gram non-finite (NaN on the tensor
+ * cores).  Otherwise, when the
+ * leading dimensions are multiples of
  * 4, the pointers 16-byte aligned, n >= 512 and s <= 128, it runs on the
  * tensor cores (TMA + tcgen05, TF32 hi/lo split: hi*hi + lo*hi + hi*lo,
  * FP32 accumulation, Q's split parts in tensor memory), else in FP32 FFMA.
