@@ -341,7 +341,8 @@ void sg_destroy(sg_handle* h) {
   free_equil(h);
   free_csr(h->A);
   free_csr(h->AT);
-  double* d[] = {h->Q, h->V, h->Y, h->bvec, h->xvec, h->rvec, h->part, h->red, h->small, h->dvec};
+  double* d[] = {h->Q, h->V, h->Y, h->bvec, h->xvec, h->rvec, h->part, h->red, h->small, h->dvec,
+                 h->x0vec};
   for (double* p : d) if (p) cudaFree(p);
   if (h->sync) cudaFree(h->sync);
   float* f[] = {h->Q32, h->V32, h->Y32, h->r32};

@@ -40,6 +40,8 @@ struct sg_handle {
   int64_t ws32_n = 0;
   int ws32_m = 0, ws32_k = 0;
   double* dvec = nullptr;   // n, FP64 correction accumulator
+  double* x0vec = nullptr;  // n, the initial guess kept by the FP32-basis solve
+  int64_t x0_n = 0;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   // captured Ritz pre-pass graphs, keyed by everything their kernels read
   struct PrepassGraph {
