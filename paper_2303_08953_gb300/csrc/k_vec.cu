@@ -1,6 +1,7 @@
 // Vector kernels: deterministic dot products and norms (warp shuffles,
 // then a fixed-order sum of per-block partials), the solution update
 // x += Q y (Alg. 4, last line) and precision conversions.
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -238,6 +239,60 @@ void axpy_f32_to_f64(int64_t n, double alpha, const float* d, double* x,
                      cudaStream_t st) {
   axpy_f32_kernel<<<stream_grid(n), kThreads, 0, st>>>(n, alpha, d, x);
   SG_LAUNCH_CHECK();
+}
+
+// Checks of a square CSR matrix's structure, one thread per row: rowptr
+// starts at 0 and ends at nnz (bit 1), rows have 0 <= rowptr[r] <=
+// rowptr[r+1] <= nnz (bit 2; a row that fails it is not read further, so
+// no index leaves the arrays), columns lie in [0, ncols) (bit 4) and
+// increase strictly within a row (bit 8).  Bits are OR-ed into flags[0],
+// the longest row is merged into flags[1].
+__global__ void check_csr_kernel(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                 int64_t n, int64_t nnz, int64_t ncols, int* __restrict__ flags) {
+  int bad = 0, longest = 0;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t r = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; r < n; r += stride) {
+    const int64_t a = rp[r], b = rp[r + 1];
+    if (r == 0 && a != 0) bad |= 1;
+    if (r == n - 1 && b != nnz) bad |= 1;
+    if (a < 0 || b < a || b > nnz) {
+      bad |= 2;
+      continue;
+    }
+    longest = max(longest, static_cast<int>(b - a));
+    int64_t prev = -1;
+    for (int64_t k = a; k < b; ++k) {
+      const int64_t c = ci[k];
+      if (c < 0 || c >= ncols) bad |= 4;
+      if (c <= prev) bad |= 8;
+      prev = c;
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    bad |= __shfl_xor_sync(0xffffffffu, bad, off);
+    longest = max(longest, __shfl_xor_sync(0xffffffffu, longest, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (bad) atomicOr(flags, bad);
+    atomicMax(flags + 1, longest);
+  }
+}
+
+int check_csr(const int32_t* rowptr, const int32_t* colind, int64_t n, int64_t nnz,
+              int64_t ncols, int* flags, int* longest, cudaStream_t st) {
+  int* d = nullptr;
+  SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&d), 2 * sizeof(int)));
+  SG_CUDA(cudaMemsetAsync(d, 0, 2 * sizeof(int), st));
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 8 * static_cast<int64_t>(device_sm_count()));
+  check_csr_kernel<<<static_cast<unsigned>(blocks), 256, 0, st>>>(rowptr, colind, n, nnz, ncols, d);
+  SG_LAUNCH_CHECK();
+  int h[2] = {0, 0};
+  SG_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
+  SG_CUDA(cudaStreamSynchronize(st));
+  SG_CUDA(cudaFree(d));
+  *flags = h[0];
+  *longest = h[1];
+  return h[0];
 }
 
 void fill_zero(int64_t n, double* x, cudaStream_t st) {

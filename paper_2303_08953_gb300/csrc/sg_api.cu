@@ -368,46 +368,63 @@ static sg_status analyze_impl(sg_handle* h, const sg_csr* A, int64_t ncols, bool
     SG_CUDA(cudaSetDevice(h->device));
     cudaStream_t st = h->own;
     const int64_t n = A->n, nnz = A->nnz;
-    // validation on the host (from a host copy when A is on the device)
-    std::vector<int32_t> rp(n + 1), ci(nnz);
-    const cudaMemcpyKind kind = A->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
-    SG_CUDA(cudaMemcpy(rp.data(), A->rowptr, sizeof(int32_t) * (n + 1), kind));
-    if (nnz) SG_CUDA(cudaMemcpy(ci.data(), A->colind, sizeof(int32_t) * nnz, kind));
-    SG_REQUIRE(rp[0] == 0 && rp[n] == nnz, SG_EINVAL, "rowptr must start at 0 and end at nnz");
+    const bool dev = A->on_device != 0;
     int32_t maxrow = 0;
-    std::vector<int32_t> row;
-    for (int64_t r = 0; r < n; ++r) {
-      SG_REQUIRE(rp[r + 1] >= rp[r], SG_EINVAL, "rowptr not non-decreasing");
-      maxrow = std::max(maxrow, rp[r + 1] - rp[r]);
-      for (int32_t k = rp[r]; k < rp[r + 1]; ++k) {
-        SG_REQUIRE(ci[k] >= 0 && ci[k] < ncols, SG_EINVAL, "column index out of range");
-        SG_REQUIRE(block || k == rp[r] || ci[k] > ci[k - 1], SG_EINVAL,
-                   "columns not sorted/unique in a row");
-      }
-      if (block) {
+    if (block) {
+      // a row block: columns distinct but unsorted (local numbering), checked
+      // on the host (from a host copy when A is on the device)
+      std::vector<int32_t> rp(n + 1), ci(nnz);
+      const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+      SG_CUDA(cudaMemcpy(rp.data(), A->rowptr, sizeof(int32_t) * (n + 1), kind));
+      if (nnz) SG_CUDA(cudaMemcpy(ci.data(), A->colind, sizeof(int32_t) * nnz, kind));
+      SG_REQUIRE(rp[0] == 0 && rp[n] == nnz, SG_EINVAL, "rowptr must start at 0 and end at nnz");
+      std::vector<int32_t> row;
+      for (int64_t r = 0; r < n; ++r) {
+        SG_REQUIRE(rp[r + 1] >= rp[r], SG_EINVAL, "rowptr not non-decreasing");
+        maxrow = std::max(maxrow, rp[r + 1] - rp[r]);
+        for (int32_t k = rp[r]; k < rp[r + 1]; ++k)
+          SG_REQUIRE(ci[k] >= 0 && ci[k] < ncols, SG_EINVAL, "column index out of range");
         row.assign(ci.begin() + rp[r], ci.begin() + rp[r + 1]);
         std::sort(row.begin(), row.end());
         SG_REQUIRE(std::adjacent_find(row.begin(), row.end()) == row.end(), SG_EINVAL,
                    "repeated column in a row");
       }
     }
+    // the device copy, installed only once it has passed its checks (a
+    // rejected matrix leaves the handle's previous one in place)
+    sg::DevCsr T;
+    T.n = A->n;
+    T.nnz = nnz;
+    try {
+      SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&T.rowptr), sizeof(int32_t) * (n + 1)));
+      SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&T.colind), sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+      SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&T.val), sizeof(double) * std::max<int64_t>(nnz, 1)));
+      copy_in(T.rowptr, A->rowptr, n + 1, dev, st);
+      if (nnz) {
+        copy_in(T.colind, A->colind, nnz, dev, st);
+        copy_in(T.val, A->val, nnz, dev, st);
+      }
+      if (!block) {
+        // a square matrix: sorted, in-range columns, checked on the device
+        int flags = 0, longest = 0;
+        sg::check_csr(T.rowptr, T.colind, n, nnz, ncols, &flags, &longest, st);
+        SG_REQUIRE(!(flags & 1), SG_EINVAL, "rowptr must start at 0 and end at nnz");
+        SG_REQUIRE(!(flags & 2), SG_EINVAL, "rowptr not non-decreasing");
+        SG_REQUIRE(!(flags & 4), SG_EINVAL, "column index out of range");
+        SG_REQUIRE(!(flags & 8), SG_EINVAL, "columns not sorted/unique in a row");
+        maxrow = longest;
+      }
+    } catch (...) {
+      free_csr(T);
+      throw;
+    }
     h->drop_graphs();
     free_equil(h);
     free_csr(h->A);
     free_csr(h->AT);
     h->have_A = h->have_AT = false;
+    h->A = T;
     sg::DevCsr& D = h->A;
-    D.n = A->n;
-    D.nnz = nnz;
-    SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&D.rowptr), sizeof(int32_t) * (n + 1)));
-    SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&D.colind), sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
-    SG_CUDA(cudaMalloc(reinterpret_cast<void**>(&D.val), sizeof(double) * std::max<int64_t>(nnz, 1)));
-    const bool dev = A->on_device != 0;
-    copy_in(D.rowptr, A->rowptr, n + 1, dev, st);
-    if (nnz) {
-      copy_in(D.colind, A->colind, nnz, dev, st);
-      copy_in(D.val, A->val, nnz, dev, st);
-    }
     D.mean_row = static_cast<double>(nnz) / static_cast<double>(n);
     D.max_row = maxrow;
     sg::build_sell(D, st);

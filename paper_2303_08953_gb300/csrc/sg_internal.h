@@ -227,6 +227,13 @@ void tc_update(int64_t n, const float* Q, int64_t ldq, int i, const double* W,
 void tc_update_check_error(cudaStream_t st);
 
 // dst[k] = src[idx[k]], k < count (device arrays).
+// Structure checks of a square CSR matrix on the device (synchronises):
+// returns the OR of 1 (rowptr does not run from 0 to nnz), 2 (a row's
+// bounds are decreasing or outside [0, nnz]), 4 (a column outside
+// [0, ncols)), 8 (columns not increasing within a row); *longest = the
+// longest row.
+int check_csr(const int32_t* rowptr, const int32_t* colind, int64_t n, int64_t nnz,
+              int64_t ncols, int* flags, int* longest, cudaStream_t st);
 void gather(const int32_t* idx, int64_t count, const double* src, double* dst,
             cudaStream_t st);
 

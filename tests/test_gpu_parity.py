@@ -778,6 +778,31 @@ def test_analyze_rejects_bad_csr(solver):
                        np.array([1.0, 2.0, 3.0]))
 
 
+@pytest.mark.parametrize("rowptr,colind,what", [
+    ([1, 2, 3, 3], [0, 1, 2], "rowptr must start at 0"),
+    ([0, 2, 3, 4], [0, 1, 2], "end at nnz"),
+    ([0, 2, 1, 3], [0, 1, 2], "non-decreasing"),
+    ([0, 2, 9, 3], [0, 1, 2], "non-decreasing"),
+    ([0, 2, 2, 3], [0, 3, 2], "out of range"),
+    ([0, 2, 2, 3], [0, -1, 2], "out of range"),
+    ([0, 2, 2, 3], [1, 0, 2], "sorted"),
+    ([0, 2, 2, 3], [1, 1, 2], "sorted"),
+])
+def test_analyze_device_checks_keep_the_previous_matrix(solver, rowptr, colind, what):
+    """The structure of a square CSR matrix is checked on the device after
+    its copy (one thread per row; a row whose bounds fail is not read
+    further); a rejected matrix names the failed check and leaves the
+    previously analysed matrix in place."""
+    c = W.config_c1(12)
+    op = _analyze(solver, c["A"])
+    with pytest.raises(sg.SgError, match=what):
+        solver.analyze(np.array(rowptr, np.int32), np.array(colind, np.int32),
+                       np.arange(1.0, len(colind) + 1.0))
+    x, info = solver.solve(c["b"], m=30, s=4, tol=1e-10)
+    assert info.converged
+    assert np.linalg.norm(c["b"] - op @ np.asarray(x)) <= 1e-10 * np.linalg.norm(c["b"])
+
+
 # ------------------------------------------------------------ adjoint path
 def test_adjoint_solve_and_grad_values(solver):
     c = W.config_c1(30)
